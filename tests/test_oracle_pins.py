@@ -1,0 +1,381 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test states the passage it pins.  None of them compares the oracle with itself: the
+references are dense numpy linear algebra, scipy's sparse product, closed forms from the paper,
+hand-computed interpolation weights and invariants of the published AMG components.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import ncpgen
+import oracle
+
+TINY = [
+    ncpgen.GridConfig(6, 6, 1, sigma=1.0, absent_frac=0.3, absent_mode=0, seed=5),
+    ncpgen.GridConfig(4, 4, 4, sigma=2.0, absent_frac=0.5, absent_mode=1, seed=6),
+    ncpgen.GridConfig(5, 4, 3, sigma=1.0, layer_contrast=1e-4, absent_frac=0.4, absent_mode=1, seed=7),
+]
+
+
+def _level_sets(marker):
+    """Level-l dof lists (ascending original index) and the F/C splits of section 5."""
+    L = int(marker.max())
+    dofs = [np.nonzero(marker >= l)[0] for l in range(L + 1)]
+    return L, dofs
+
+
+def _schur(A, F, C):
+    Aff, Afc, Acf, Acc = A[np.ix_(F, F)], A[np.ix_(F, C)], A[np.ix_(C, F)], A[np.ix_(C, C)]
+    return Acc - Acf @ np.linalg.solve(Aff, Afc) if len(F) else Acc
+
+
+def _split(marker_l, l):
+    return np.nonzero(marker_l == l)[0], np.nonzero(marker_l > l)[0]
+
+
+@pytest.mark.parametrize("cfg", TINY)
+@pytest.mark.parametrize("rtype", [0, 1])
+def test_ideal_RAP_is_schur_complement(cfg, rtype):
+    """Section 4: with ideal P = [-A_ff^-1 A_fc; I], R A P equals S = A_cc - A_cf A_ff^-1 A_fc for
+    injective and non-injective R (RAQ = 0 in the MGR identities)."""
+    p = ncpgen.make_problem(cfg)
+    m = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker, ideal=1, restrict_type=[rtype] * 3)
+    L, dofs = _level_sets(p.cf_marker)
+    A = p.to_scipy().toarray()
+    for l in range(L):
+        mk = p.cf_marker[dofs[l]]
+        F, C = _split(mk, l)
+        A = _schur(A, F, C)
+        got = m.scipy(oracle.MAT_LEVEL, l + 1).toarray()
+        assert np.abs(got - A).max() <= 1e-11 * np.abs(A).max()
+
+
+@pytest.mark.parametrize("cfg", TINY)
+def test_ideal_preconditioner_is_exact_inverse(cfg):
+    """MGR identities (section 4): exact F-solves, ideal P and an exact coarse solve make the
+    two-level error propagator zero, so M^-1 A = I and FGMRES converges in one iteration."""
+    p = ncpgen.make_problem(cfg)
+    m = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker, ideal=1)
+    A = p.to_scipy()
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        x = rng.standard_normal(p.n)
+        z = m.apply(A @ x)
+        assert np.linalg.norm(z - x) <= 1e-10 * np.linalg.norm(x)
+    b = ncpgen.normals(p.n, 2)
+    x, info = m.fgmres(b, rtol=1e-9)
+    assert info["converged"] and info["iterations"] == 1
+
+
+@pytest.mark.parametrize("cfg", TINY)
+def test_level1_is_exact_and_matches_closed_form(cfg):
+    """Section 5: the first reduction is exact because C33 is diagonal, so with
+    W_p = -D_ff^-1 A_fc the coarse operator equals the closed form
+    [[A11 - A13 C33^-1 C31, A12 - A13 C33^-1 C32, A14], [...], [C41, C42, 0]] (the Schur complement)."""
+    p = ncpgen.make_problem(cfg)
+    m = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker)
+    A = p.to_scipy().toarray()
+    F, C = _split(p.cf_marker, 0)
+    Aff = A[np.ix_(F, F)]
+    assert np.count_nonzero(Aff - np.diag(np.diag(Aff))) == 0
+    S1 = A[np.ix_(C, C)] - A[np.ix_(C, F)] @ np.diag(1.0 / np.diag(Aff)) @ A[np.ix_(F, C)]
+    got = m.scipy(oracle.MAT_LEVEL, 1).toarray()
+    assert np.abs(got - S1).max() <= 1e-13 * np.abs(S1).max()
+    # gas-absent constraint rows keep their 0 diagonal: the paper's C41 C42 0 block
+    mk1 = p.cf_marker[C]
+    absent_rows = np.nonzero(mk1 == 2)[0]
+    assert np.all(np.diag(got)[absent_rows] == 0.0)
+
+
+@pytest.mark.parametrize("cfg", TINY)
+def test_levels_2_and_3_match_paper_formulas(cfg):
+    """Section 5: with injective R and S~_22 = diag(S_22),
+    S^2 = S^1_cc - S^1_cf diag(S^1_ff)^-1 S^1_fc (the displayed 2x2 block formula) and
+    S^3 = S^2_11 - S^2_12 diag(S^2_22)^-1 S^2_21; after level 2 the diagonal has no zeros."""
+    p = ncpgen.make_problem(cfg)
+    m = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker)
+    L, dofs = _level_sets(p.cf_marker)
+    for l in (1, 2):
+        Sl = m.scipy(oracle.MAT_LEVEL, l).toarray()
+        F, C = _split(p.cf_marker[dofs[l]], l)
+        D = np.diag(Sl[np.ix_(F, F)])
+        ref = Sl[np.ix_(C, C)] - Sl[np.ix_(C, F)] @ (Sl[np.ix_(F, C)] / D[:, None])
+        got = m.scipy(oracle.MAT_LEVEL, l + 1).toarray()
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        if l == 2:
+            assert np.all(np.diag(Sl) != 0.0)
+
+
+@pytest.mark.parametrize("cfg", TINY + [ncpgen.GridConfig(12, 10, 1, absent_frac=0.25, seed=9)])
+def test_level_sizes(cfg):
+    """Sections 3.2 and 5: level sizes 3N - M, 2N - M and N (M gas-present cells)."""
+    p = ncpgen.make_problem(cfg)
+    m = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker)
+    N, M = p.nb, int(p.gas_present.sum())
+    sizes = [m.mat(oracle.MAT_LEVEL, l)[3][0] for l in range(4)]
+    assert sizes == [3 * N, 3 * N - M, 2 * N - M, N]
+
+
+@pytest.mark.parametrize("cfg", [
+    ncpgen.GridConfig(4, 4, 1, sigma=0.5, absent_frac=0.3, seed=21),
+    ncpgen.GridConfig(8, 8, 1, sigma=1.0, absent_frac=0.3, seed=22),
+    ncpgen.GridConfig(4, 4, 4, sigma=1.0, absent_frac=0.5, absent_mode=1, seed=23),
+])
+def test_fgmres_mgr_matches_dense_solve(cfg):
+    """x = A^-1 b by dense LU (numpy) versus MGR-FGMRES run to 1e-12."""
+    p = ncpgen.make_problem(cfg)
+    A = p.to_scipy().toarray()
+    b = ncpgen.normals(p.n, 2)
+    xd = np.linalg.solve(A, b)
+    m = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker, amg_max_coarse=8)
+    x, info = m.fgmres(b, rtol=1e-12, restart=30, maxit=500)
+    assert info["converged"]
+    assert np.linalg.norm(b - A @ x) <= 1e-12 * np.linalg.norm(b) * 1.0001
+    err = np.linalg.norm(x - xd) / np.linalg.norm(xd)
+    assert err <= 1e-12 * np.linalg.cond(A)
+    assert err <= 1e-9
+
+
+def test_gmres_exact_in_n_steps_and_arnoldi_relation():
+    """GMRES(m >= n) on n = 48 unknowns terminates within n steps; A Z_j = V_{j+1} Hbar_j holds;
+    the implicit residual estimate agrees with the explicit one."""
+    p = ncpgen.make_problem(ncpgen.GridConfig(4, 4, 1, sigma=0.5, absent_frac=0.3, seed=31))
+    A = p.to_scipy().toarray()
+    b = ncpgen.normals(p.n, 2)
+    x, info = oracle.fgmres(p.rowptr, p.colind, p.values, b, rtol=1e-10, restart=p.n, maxit=p.n, capture=True)
+    assert info["converged"] and info["iterations"] <= p.n
+    k = info["iterations"]
+    V, Z, H = info["V"], info["Z"], info["H"]
+    lhs = A @ Z[:k].T
+    rhs = V[: k + 1].T @ H[: k + 1, :k]
+    assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(lhs).max()
+    # the leading basis vectors are orthonormal (MGS loses orthogonality only as the basis grows)
+    G = V[:8] @ V[:8].T
+    assert np.abs(G - np.eye(8)).max() < 1e-12
+    assert abs(info["relres_est"] - info["relres_true"]) <= 1e-9
+
+
+def test_flexible_arnoldi_relation_with_mgr():
+    """With the MGR preconditioner (Z != V) the flexible relation A Z_j = V_{j+1} Hbar_j holds."""
+    p = ncpgen.make_problem(ncpgen.GridConfig(6, 6, 1, sigma=1.0, absent_frac=0.3, seed=32))
+    A = p.to_scipy().toarray()
+    b = ncpgen.normals(p.n, 2)
+    m = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker, amg_max_coarse=8)
+    x, info = m.fgmres(b, rtol=1e-10, restart=20, capture=True)
+    k = min(info["iterations"], 20)
+    V, Z, H = info["V"], info["Z"], info["H"]
+    lhs = A @ Z[:k].T
+    rhs = V[: k + 1].T @ H[: k + 1, :k]
+    assert np.abs(lhs - rhs).max() <= 1e-11 * np.abs(lhs).max()
+
+
+def test_spgemm_matches_scipy():
+    rng = np.random.default_rng(3)
+    for m_, k_, n_, d in [(50, 40, 60, 0.1), (200, 150, 120, 0.03), (7, 9, 5, 0.5)]:
+        A = sp.random(m_, k_, density=d, random_state=rng, format="csr")
+        B = sp.random(k_, n_, density=d, random_state=rng, format="csr")
+        C = oracle.spgemm(A, B)
+        ref = (A @ B).toarray()
+        assert np.allclose(C.toarray(), ref, rtol=1e-14, atol=1e-15)
+        # structural pattern: every position of every product is present
+        patt = ((abs(A) > 0).astype(int) @ (abs(B) > 0).astype(int)).toarray() > 0
+        assert np.array_equal(C.toarray() != 0, (C.toarray() != 0) & patt)
+        assert C.nnz == patt.sum()
+
+
+def test_extpi_linear_interpolation_1d():
+    """Extended+i on the 1-D Laplacian with the split C F F C F F C: the distance-two formula gives
+    linear interpolation, weights (2/3, 1/3) and (1/3, 2/3); C points inject."""
+    n = 10
+    A = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1], format="csr")
+    A.sort_indices()
+    cf = np.array([1 if i % 3 == 0 else -1 for i in range(n)], np.int8)
+    P = oracle.extpi(A.indptr, A.indices, A.data, cf).toarray()
+    expect = np.zeros((n, 4))
+    for i in range(n):
+        c, r = divmod(i, 3)
+        if r == 0:
+            expect[i, c] = 1.0
+        else:
+            expect[i, c] = (3 - r) / 3.0
+            if c + 1 < 4:
+                expect[i, c + 1] = r / 3.0
+    # the last F pair (i = 10 would be C) does not occur: n = 10 ends on a C point
+    assert np.abs(P - expect).max() <= 1e-15
+
+
+def test_extpi_reproduces_constants_on_zero_row_sum_rows():
+    """Extended+i interpolation preserves constants on rows of a zero-row-sum M-matrix."""
+    rp, ci, v = ncpgen.poisson(12, 12, 1, neumann=True)
+    A = sp.csr_matrix((v, ci, rp))
+    amg = oracle.OracleAMG(rp, ci, v, amg_max_coarse=4)
+    cf = amg.vec(oracle.VEC_AMG_CF, 0).astype(np.int8)
+    P = oracle.extpi(rp, ci, v, cf)
+    s = np.asarray(P.sum(axis=1)).ravel()
+    nonempty = np.diff(P.indptr) > 0
+    assert nonempty.sum() > 0.9 * A.shape[0]
+    assert np.abs(s[nonempty] - 1.0).max() < 1e-13
+
+
+def test_strength_anisotropic():
+    """Classical strength with theta = 0.25 on the Laplacian with couplings -1 (x) and -0.1 (y):
+    only x-neighbours are strong."""
+    nx, ny = 10, 8
+    n = nx * ny
+    rows, cols, vals = [], [], []
+    for j in range(ny):
+        for i in range(nx):
+            r = j * nx + i
+            diag = 0.0
+            for di, dj, w in ((-1, 0, 1.0), (1, 0, 1.0), (0, -1, 0.1), (0, 1, 0.1)):
+                a, b = i + di, j + dj
+                if 0 <= a < nx and 0 <= b < ny:
+                    rows.append(r); cols.append(b * nx + a); vals.append(-w)
+                diag += w
+            rows.append(r); cols.append(r); vals.append(diag)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A.sort_indices()
+    amg = oracle.OracleAMG(A.indptr, A.indices, A.data, amg_max_coarse=4, amg_theta=0.25)
+    S = amg.scipy(oracle.MAT_AMG_S, 0).tocoo()
+    assert S.nnz > 0
+    assert np.all(np.abs(S.row - S.col) == 1)
+    assert S.nnz == 2 * (nx - 1) * ny
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 1), (8, 8, 8)])
+def test_pmis_is_maximal_independent_set_on_symmetric_graph(shape):
+    """PMIS (De Sterck, Yang & Heys 2006) on a symmetric strength graph yields C points that are
+    pairwise non-adjacent, and every F point with a strong connection has a strong C neighbour."""
+    rp, ci, v = ncpgen.poisson(*shape)
+    amg = oracle.OracleAMG(rp, ci, v, amg_max_coarse=4)
+    cf = amg.vec(oracle.VEC_AMG_CF, 0)
+    S = amg.scipy(oracle.MAT_AMG_S, 0)
+    assert (S != S.T).nnz == 0
+    C = cf == 1
+    S = S.tocsr()
+    for i in range(S.shape[0]):
+        nb = S.indices[S.indptr[i]:S.indptr[i + 1]]
+        if C[i]:
+            assert not C[nb].any()
+        elif len(nb):
+            assert C[nb].any()
+
+
+@pytest.mark.parametrize("shape,bound", [((64, 64, 1), 0.5), ((20, 20, 20), 0.5)])
+def test_amg_vcycle_converges_on_poisson(shape, bound):
+    """Textbook multigrid behaviour: the V(1,1) cycle as a stationary iteration on the Dirichlet
+    Poisson problem contracts the error by a mesh-independent factor well below one."""
+    rp, ci, v = ncpgen.poisson(*shape)
+    A = sp.csr_matrix((v, ci, rp))
+    amg = oracle.OracleAMG(rp, ci, v, amg_max_coarse=50)
+    rng = np.random.default_rng(1)
+    xs = rng.standard_normal(A.shape[0])
+    b = A @ xs
+    x = np.zeros_like(b)
+    errs = []
+    for _ in range(12):
+        x = x + amg.vcycle(b - A @ x)
+        errs.append(np.sqrt((x - xs) @ (A @ (x - xs))))
+    rho = (errs[-1] / errs[1]) ** (1.0 / 10)
+    assert rho < bound, rho
+
+
+def test_edge_cases_all_present_and_all_absent():
+    """M = N (no gas-absent cell: the third reduction has no F point) and M = 0 (no gas-present
+    cell: the first reduction has no F point) still give a convergent preconditioner."""
+    for frac in (0.0, 1.0):
+        p = ncpgen.make_problem(ncpgen.GridConfig(8, 8, 1, absent_frac=frac, seed=41))
+        m = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker)
+        b = ncpgen.normals(p.n, 2)
+        x, info = m.fgmres(b, rtol=1e-8)
+        assert info["converged"]
+        A = p.to_scipy()
+        assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b) * 1.0001
+
+
+def test_singular_diagonal_block_is_reported():
+    p = ncpgen.make_problem(ncpgen.GridConfig(4, 4, 1, seed=2))
+    vals = p.values.copy()
+    rows = np.repeat(np.arange(p.nb), np.diff(p.rowptr))
+    k = np.nonzero((rows == 3) & (p.colind == 3))[0][0]
+    vals[k] = 0.0
+    with pytest.raises(oracle.OracleError) as e:
+        oracle.OracleMGR(p.rowptr, p.colind, vals, p.cf_marker)
+    assert e.value.code == 2
+
+
+def test_dense_adjoint_matches_finite_differences():
+    """dL/db = lambda and dL/dA_ij = -lambda_i x_j for L = w . A^-1 b, by central differences."""
+    p = ncpgen.make_problem(ncpgen.GridConfig(3, 3, 1, seed=4))
+    b = ncpgen.normals(p.n, 2)
+    w = ncpgen.normals(p.n, 4, stream=4)
+    x, lam, g = oracle.dense_adjoint(p.rowptr, p.colind, p.values, b, w)
+
+    def loss(vals, bb):
+        A = sp.bsr_matrix((vals, p.colind, p.rowptr), shape=(p.n, p.n)).toarray()
+        return w @ np.linalg.solve(A, bb)
+
+    rng = np.random.default_rng(0)
+    for _ in range(8):
+        k, a, c = rng.integers(p.nnzb), rng.integers(3), rng.integers(3)
+        if p.values[k, a, c] == 0.0:
+            continue
+        h = 1e-6 * abs(p.values[k, a, c])
+        vp, vm = p.values.copy(), p.values.copy()
+        vp[k, a, c] += h
+        vm[k, a, c] -= h
+        fd = (loss(vp, b) - loss(vm, b)) / (2 * h)
+        assert abs(fd - g[k, a, c]) <= 1e-6 * max(abs(g[k, a, c]), 1e-3 * np.abs(g).max())
+    for i in rng.integers(p.n, size=5):
+        e = np.zeros(p.n); e[i] = 1e-6
+        fd = (loss(p.values, b + e) - loss(p.values, b - e)) / 2e-6
+        assert abs(fd - lam[i]) <= 1e-7 * max(1.0, abs(lam[i]))
+
+
+def test_global_relaxation_is_blockdiag_inverse():
+    """Algorithm step (1): e_1 = blockdiag(A)^-1 r.  On a block-diagonal matrix this is already
+    A^-1 r, the later steps add nothing, and M^-1 = A^-1."""
+    p = ncpgen.make_problem(ncpgen.GridConfig(5, 4, 1, absent_frac=0.4, seed=51))
+    rows = np.repeat(np.arange(p.nb), np.diff(p.rowptr))
+    vals = p.values.copy()
+    vals[rows != p.colind] = 0.0
+    m = oracle.OracleMGR(p.rowptr, p.colind, vals, p.cf_marker, amg_max_coarse=4)
+    A = sp.bsr_matrix((vals, p.colind, p.rowptr), shape=(p.n, p.n)).toarray()
+    r = ncpgen.normals(p.n, 2)
+    z = m.apply(r)
+    assert np.linalg.norm(z - np.linalg.solve(A, r)) <= 1e-12 * np.linalg.norm(z)
+    full = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker)
+    e1 = full.global_relax(r).reshape(-1, 3)
+    diag_blocks = p.values[rows == p.colind]
+    ref = np.linalg.solve(diag_blocks, r.reshape(-1, 3)[:, :, None])[:, :, 0]
+    assert np.abs(e1 - ref).max() <= 1e-12 * np.abs(ref).max()
+    binv = m.vec(oracle.VEC_BINV, 0).reshape(-1, 3, 3)
+    blocks = vals[rows == p.colind]
+    assert np.abs(np.einsum("kij,kjl->kil", binv, blocks) - np.eye(3)).max() < 1e-12
+
+
+@pytest.mark.parametrize("wy,strong", [(0.3, True), (0.2, False), (0.25, True), (0.26, True), (0.24, False)])
+def test_strength_threshold(wy, strong):
+    """Classical strength: j is strong for i iff -a_ij >= theta max_k(-a_ik); theta = 0.25 and the
+    x-couplings are -1, so a y-coupling -wy is strong exactly when wy >= 0.25."""
+    nx, ny = 6, 5
+    n = nx * ny
+    rows, cols, vals = [], [], []
+    for j in range(ny):
+        for i in range(nx):
+            r = j * nx + i
+            diag = 0.0
+            for di, dj, w in ((-1, 0, 1.0), (1, 0, 1.0), (0, -1, wy), (0, 1, wy)):
+                a, b = i + di, j + dj
+                if 0 <= a < nx and 0 <= b < ny:
+                    rows.append(r); cols.append(b * nx + a); vals.append(-w)
+                diag += w
+            rows.append(r); cols.append(r); vals.append(diag)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A.sort_indices()
+    amg = oracle.OracleAMG(A.indptr, A.indices, A.data, amg_max_coarse=4, amg_theta=0.25)
+    S = amg.scipy(oracle.MAT_AMG_S, 0).tocoo()
+    ny_links = int((np.abs(S.row - S.col) == nx).sum())
+    assert ny_links == (2 * nx * (ny - 1) if strong else 0)
+    assert int((np.abs(S.row - S.col) == 1).sum()) == 2 * (nx - 1) * ny
