@@ -1,0 +1,176 @@
+/*
+ * mgr.h -- C ABI of the GB300 (sm_103a) library for multigrid-reduction (MGR) preconditioned
+ * flexible GMRES on the 3x3-block Jacobians of two-phase, two-component porous-media flow written as
+ * a nonlinear complementarity problem (Bui, Wang & Osei-Kuffuor, arXiv 1801.08464).
+ *
+ * The paper states the problem as A u = f with A the 3N x 3N block system of section 3.2 (one 3x3
+ * block per pair of cells, unknowns (P_l, S_l, rho_l^h) per cell, section 2.5) and, after splitting
+ * the constraint rows by the phase state, the saddle-point form of section 3.2.  The preconditioner is
+ * the "MGR preconditioner with presmoothing" Algorithm of section 4 applied with the three-level
+ * reduction order of section 5; the outer Krylov method is GMRES (section 6).
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers are DEVICE pointers unless the comment says "host".  The caller owns all memory it
+ *    passes; the library never frees it.  A handle owns the memory of its hierarchy.
+ *  - Work is enqueued on the CUDA stream given to mgr_create (NULL = legacy default stream).  Calls
+ *    that return sizes or a convergence decision synchronise that stream.
+ *  - Every call returns a status; nothing aborts.  A handle is not thread-safe.
+ *  - Index types: block-row pointers int64, block columns int32 (so nb < 2^31).
+ */
+#ifndef MGR_H_
+#define MGR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MGR_MAX_LEVELS 8
+
+typedef enum {
+  MGR_OK = 0,
+  MGR_ERR_INVALID_ARG = 1,   /* bad pointer, size, pattern or option */
+  MGR_ERR_SINGULAR = 2,      /* zero / non-finite pivot: 3x3 diagonal block, D_ff entry, smoother
+                                diagonal or coarsest-grid pivot */
+  MGR_ERR_NOT_CONVERGED = 3, /* fgmres_solve reached maxit; x holds the last iterate */
+  MGR_ERR_BREAKDOWN = 4,     /* NaN/Inf in a norm or Hessenberg entry */
+  MGR_ERR_OOM = 5,           /* device allocation failed; the handle stays destroyable */
+  MGR_ERR_CUDA = 6,          /* other CUDA runtime error */
+  MGR_ERR_TIMEOUT = 7,       /* reserved: no kernel of this library waits on another */
+  MGR_ERR_STATE = 8,         /* call order violated (e.g. apply before setup) */
+  MGR_ERR_UNSUPPORTED = 9    /* a size beyond a documented limit of a kernel */
+} mgr_status_t;
+
+typedef enum { MGR_PREC_FP64 = 0, MGR_PREC_MIXED = 1 } mgr_precision_t;
+
+/* 3x3 block-CSR matrix (device arrays).  rowptr[nb+1] int64 ascending with rowptr[0] = 0;
+ * colind[nnzb] int32 strictly ascending within each block row, every block row holding its diagonal
+ * block; values[9*nnzb] with block k stored row-major: values[9k + 3p + q] = A(3I+p, 3J+q) for the
+ * block (I, J = colind[k]).  Row p of a block is equation p (water, hydrogen, constraint) and column q
+ * is unknown q (P_l, S_l, rho_l^h) as in sections 2.5 and 3.2. */
+typedef struct {
+  int64_t nb;
+  int64_t nnzb;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const double* values;
+} mgr_bsr3_t;
+
+/* Solver options.  Levels l = 0, 1, 2 are the three reductions of section 5; index l of the
+ * per-level arrays configures the reduction that removes the dofs with cf_marker == l. */
+typedef struct {
+  int32_t precision;                     /* mgr_precision_t; MIXED = FP32 hierarchy, FP64 Krylov */
+  int32_t global_relax;                  /* Algorithm step (1) at the finest level (default 1) */
+  int32_t frelax_type[MGR_MAX_LEVELS];   /* 0 omega-Jacobi, 1 l1-Jacobi (defaults 0, 1, 1) */
+  int32_t frelax_sweeps[MGR_MAX_LEVELS]; /* F-relaxation sweeps (defaults 1, 2, 2) */
+  double frelax_omega[MGR_MAX_LEVELS];   /* Jacobi weight (default 1) */
+  int32_t restrict_type[MGR_MAX_LEVELS]; /* 0 injective W_r = 0, 1 W_r = -A_cf D_ff^-1 (eqs.
+                                            injective_rp / non_injective_rp); defaults 1, 0, 0 */
+  int32_t apply_full_R;                  /* 0: restrict with R_I as in the Algorithm (default) */
+  int32_t coarse_solver;                 /* 0: AMG V-cycle on the last level; 1: dense inverse */
+  double amg_theta;                      /* strength threshold (default 0.25) */
+  int32_t amg_max_levels;                /* default 25 */
+  int32_t amg_max_coarse;                /* coarsest AMG size solved densely (default 256, <= 4096) */
+  int32_t amg_smoother;                  /* 0 omega-Jacobi, 1 l1-Jacobi (default) */
+  int32_t amg_pre, amg_post;             /* V(pre, post), default V(1,1) */
+  int32_t amg_pmax;                      /* max interpolation entries per row, 0 = no truncation */
+  double amg_omega;                      /* Jacobi weight for amg_smoother = 0 */
+  uint64_t amg_seed;                     /* PMIS weight seed (default 3) */
+  int32_t use_graph;                     /* replay mgr_apply as a CUDA graph (default 1) */
+  int32_t reserved[7];
+} mgr_options_t;
+
+typedef struct {
+  int32_t iterations;   /* total FGMRES iterations (preconditioner applications) */
+  int32_t restarts;
+  int32_t converged;
+  int32_t status;
+  double relres_true;   /* ||b - A x|| / ||b|| at exit, computed explicitly */
+  double relres_est;    /* Givens residual estimate at exit */
+  double bnorm;
+  double solve_ms;      /* wall time of the call, host clock around stream-synchronised work */
+  double* history;      /* host, optional: relative residual estimate per iteration */
+  int32_t history_cap;  /* capacity of history (entries) */
+  int32_t reserved[3];
+} mgr_solve_info_t;
+
+typedef struct mgr_handle_s* mgr_handle_t;
+
+/* Human-readable status name (static storage). */
+const char* mgr_status_string(mgr_status_t s);
+
+/* Fill *opt (host) with the defaults listed above. */
+void mgr_options_default(mgr_options_t* opt);
+
+/* Create a handle bound to the current device and to `cuda_stream` (a cudaStream_t, may be NULL).
+ * opt (host) is copied; NULL means defaults.  Errors: INVALID_ARG, OOM, CUDA. */
+mgr_status_t mgr_create(mgr_handle_t* h, const mgr_options_t* opt, void* cuda_stream);
+
+/* Build the MGR hierarchy of sections 4-5 for A (device BSR) and cf_marker[3*nb] (device int8):
+ * cf_marker[d] is the reduction level at which dof d becomes an F-point (0: rho of a gas-present
+ * cell, 1: S_l, 2: rho of a gas-absent cell, 3: P_l, the AMG system).  Level l's F set is
+ * {marker == l}, its C set {marker > l}; the coarsest system is {marker == max marker}.
+ * Copies or derives everything it needs: A and cf_marker may be freed on return.  A second call
+ * rebuilds the hierarchy.  Errors: INVALID_ARG (pattern or marker), SINGULAR, OOM, UNSUPPORTED. */
+mgr_status_t mgr_setup(mgr_handle_t h, const mgr_bsr3_t* A, const int8_t* cf_marker);
+
+/* z = M^-1 r: one application of the presmoothing MGR Algorithm (section 4) with an AMG V-cycle as
+ * the coarse solve.  r, z: device double[3*nb]; r is not modified; r and z must not overlap.
+ * Asynchronous on the handle's stream.  Errors: STATE (no setup), INVALID_ARG. */
+mgr_status_t mgr_apply(mgr_handle_t h, const double* r, double* z);
+
+/* Solve A x = b by right-preconditioned flexible GMRES(restart) with M^-1 = mgr_apply, FP64 Krylov
+ * vectors.  A must have the pattern given to mgr_setup (its values are read during the call and may
+ * differ from the setup values).  x (device) holds x0 on entry and the solution on return.  Stops
+ * when the Givens estimate reaches rtol ||b|| and confirms it with ||b - A x|| <= rtol ||b||.
+ * info (host) is filled when non-NULL.  Errors: NOT_CONVERGED (x = last iterate), BREAKDOWN,
+ * STATE, INVALID_ARG. */
+mgr_status_t fgmres_solve(mgr_handle_t h, const mgr_bsr3_t* A, const double* b, double* x, double rtol,
+                          int restart, int maxit, mgr_solve_info_t* info);
+
+/* Release the handle and all its device memory (synchronises its stream).  NULL is accepted. */
+mgr_status_t mgr_destroy(mgr_handle_t h);
+
+/* ---- introspection (for parity tests and reporting) ------------------------------------------ */
+/* Matrix kinds: 0 level operator A_l (l = 0..L), 1 W_p(l), 2 W_r(l), 3 P(l), 4 R(l) (l < L),
+ * 5 AMG operator A_k, 6 AMG P_k, 7 AMG R_k = P_k^T, 8 AMG strength S_k (values 1).
+ * All are the FP64 setup copies, CSR with int64 row pointers and ascending int32 columns. */
+mgr_status_t mgr_get_levels(mgr_handle_t h, int* mgr_levels, int* amg_levels);
+mgr_status_t mgr_matrix_shape(mgr_handle_t h, int kind, int level, int64_t* nrows, int64_t* ncols,
+                              int64_t* nnz);
+/* Copy a matrix into caller device buffers rowptr[nrows+1], col[nnz], val[nnz] (val may be NULL). */
+mgr_status_t mgr_copy_matrix(mgr_handle_t h, int kind, int level, int64_t* rowptr, int32_t* col, double* val);
+/* Vector kinds: 0 F-relaxation scaling of level l, 1 AMG smoother scaling of level k, 2 inverses of
+ * the 3x3 diagonal blocks (9 nb), 3 F list of level l, 4 C list of level l, 5 AMG C/F split
+ * (1 = C, -1 = F).  Copied as doubles into the caller's device buffer. */
+mgr_status_t mgr_vector_len(mgr_handle_t h, int kind, int level, int64_t* len);
+mgr_status_t mgr_copy_vector(mgr_handle_t h, int kind, int level, double* out);
+/* Device bytes held by the handle (host out). */
+mgr_status_t mgr_memory_bytes(mgr_handle_t h, int64_t* bytes);
+/* Statistics (host outs, each may be NULL): wall time of the last mgr_setup in milliseconds, kernel
+ * launches issued by the last mgr_apply, kernel nodes of the captured apply graph (0 when not
+ * captured), and the process-wide count of kernel launches issued by this library since load. */
+mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_launches, int64_t* graph_nodes,
+                           int64_t* total_launches);
+
+/* ---- stand-alone kernels ----------------------------------------------------------------------- */
+/* y = A x (sub == NULL) or y = sub - A x, FP64, on `cuda_stream`.  The hot sparse product of the
+ * Krylov method (section 6).  x, y: double[3 nb], must not overlap. */
+mgr_status_t mgr_bsr3_spmv(const mgr_bsr3_t* A, const double* x, const double* sub, double* y, void* cuda_stream);
+
+/* Block transpose for the adjoint solve: At has block (J, I) = (block (I, J))^T.  Outputs are caller
+ * device buffers with the sizes of A (rowptr[nb+1], colind[nnzb], values[9 nnzb]); the columns of
+ * each block row come out ascending.  Synchronises the stream. */
+mgr_status_t mgr_bsr3_transpose(const mgr_bsr3_t* A, int64_t* rowptr_t, int32_t* colind_t, double* values_t,
+                                void* cuda_stream);
+
+/* Adjoint gradient on the pattern of A: grad[9k + 3p + q] = -lambda[3I+p] * x[3J+q] for every
+ * stored block k = (I, J) (dL/dA = -lambda x^T restricted to the pattern). */
+mgr_status_t mgr_bsr3_outer_grad(const mgr_bsr3_t* A, const double* lambda, const double* x, double* grad,
+                                 void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGR_H_ */

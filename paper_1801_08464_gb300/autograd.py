@@ -1,0 +1,47 @@
+"""Adjoint differentiation of x = A(theta)^-1 b through the MGR-preconditioned solve.
+
+Forward: mgr_setup(A, cf_marker) and fgmres_solve(A, b).  Backward, for an upstream gradient
+g = dL/dx: transpose the blocks of A (mgr_bsr3_transpose), build an MGR hierarchy for A^T with the
+same cf_marker, solve A^T lambda = g with FGMRES, then dL/db = lambda and
+dL/dA_ij = -lambda_i x_j on the stored block pattern (mgr_bsr3_outer_grad).  The transpose hierarchy
+is cached per forward call.
+"""
+from __future__ import annotations
+
+import torch
+
+
+class MgrSolve(torch.autograd.Function):
+    """x = A^-1 b with A = BSR3(rowptr, colind, values); differentiable in values and b."""
+
+    @staticmethod
+    def forward(ctx, values, b, rowptr, colind, cf_marker, opts, rtol, restart, maxit):
+        from . import BSR3, MGR
+        A = BSR3(rowptr, colind, values.detach().reshape(-1, 3, 3).contiguous())
+        m = MGR(opts)
+        m.setup(A, cf_marker)
+        x, info = m.fgmres(A, b.detach().contiguous(), rtol=rtol, restart=restart, maxit=maxit)
+        m.close()
+        ctx.save_for_backward(values, x, rowptr, colind, cf_marker)
+        ctx.opts, ctx.rtol, ctx.restart, ctx.maxit = opts, rtol, restart, maxit
+        ctx.forward_info = info
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        from . import BSR3, MGR, bsr3_outer_grad, bsr3_transpose
+        values, x, rowptr, colind, cf_marker = ctx.saved_tensors
+        A = BSR3(rowptr, colind, values.detach().reshape(-1, 3, 3).contiguous())
+        At = bsr3_transpose(A)
+        m = MGR(ctx.opts)
+        m.setup(At, cf_marker)
+        lam, _ = m.fgmres(At, gx.contiguous(), rtol=ctx.rtol, restart=ctx.restart, maxit=ctx.maxit)
+        m.close()
+        gvals = bsr3_outer_grad(A, lam, x).reshape(values.shape)
+        return gvals, lam, None, None, None, None, None, None, None
+
+
+def mgr_solve(values, b, rowptr, colind, cf_marker, opts=None, rtol=1e-8, restart=30, maxit=1000):
+    from . import options
+    o = opts if opts is not None else options()
+    return MgrSolve.apply(values, b, rowptr, colind, cf_marker, o, rtol, restart, maxit)

@@ -1,0 +1,288 @@
+// apply.cu -- kernels of one MGR preconditioner application (section 4 Algorithm, section 5
+// reduction order) and of the AMG V-cycle used as the coarse solve.  Templated on the working
+// precision T (double, or float for the FP32 hierarchy); inputs and outputs at the finest level are
+// FP64.  All are memory-bound sparse / vector kernels (no tensor cores).
+#include "apply.cuh"
+
+namespace mgr {
+
+template <class T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// ============================== level 0: 3x3 blocks =============================================
+template <class T>
+__global__ void k_global_relax(int64_t nb, const T* __restrict__ binv, const double* __restrict__ r, T* __restrict__ e0) {
+  int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= nb) return;
+  T r0 = (T)r[3 * I], r1 = (T)r[3 * I + 1], r2 = (T)r[3 * I + 2];
+  const T* b = binv + 9 * I;
+  e0[3 * I + 0] = b[0] * r0 + b[1] * r1 + b[2] * r2;
+  e0[3 * I + 1] = b[3] * r0 + b[4] * r1 + b[5] * r2;
+  e0[3 * I + 2] = b[6] * r0 + b[7] * r1 + b[8] * r2;
+}
+
+template <class T>
+void launch_global_relax(Ctx& c, int64_t nb, const T* binv, const double* r, T* e0) {
+  k_global_relax<T><<<grid_for(nb, 256), 256, 0, c.s>>>(nb, binv, r, e0);
+  CU_LAUNCH();
+}
+
+// One thread per block row: res_p = r_p - sum_k B_k[p][:] e0[3 J_k + :], routed by map.
+template <class T>
+__global__ void __launch_bounds__(256) k_bsr_resid_split(int64_t nb, const int64_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ ci, const T* __restrict__ v,
+                                                         const double* __restrict__ r, const T* __restrict__ e0,
+                                                         const int32_t* __restrict__ map, T* __restrict__ rnext,
+                                                         T* __restrict__ resF) {
+  int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= nb) return;
+  T s0 = 0, s1 = 0, s2 = 0;
+  if (e0) {
+    int64_t k0 = rp[I], k1 = rp[I + 1];
+    for (int64_t k = k0; k < k1; ++k) {
+      int64_t J = ci[k];
+      const T* b = v + 9 * k;
+      T x0 = ldg(e0 + 3 * J), x1 = ldg(e0 + 3 * J + 1), x2 = ldg(e0 + 3 * J + 2);
+      s0 += b[0] * x0 + b[1] * x1 + b[2] * x2;
+      s1 += b[3] * x0 + b[4] * x1 + b[5] * x2;
+      s2 += b[6] * x0 + b[7] * x1 + b[8] * x2;
+    }
+  }
+  T res[3] = {(T)r[3 * I] - s0, (T)r[3 * I + 1] - s1, (T)r[3 * I + 2] - s2};
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    int32_t m = map[3 * I + p];
+    if (m >= 0) rnext[m] = res[p];
+    else resF[-m - 1] = res[p];
+  }
+}
+
+template <class T>
+void launch_bsr_resid_split(Ctx& c, int64_t nb, const int64_t* rp, const int32_t* ci, const T* vals, const double* r,
+                            const T* e0, const int32_t* map, T* rnext, T* resF) {
+  k_bsr_resid_split<T><<<grid_for(nb, 256), 256, 0, c.s>>>(nb, rp, ci, vals, r, e0, map, rnext, resF);
+  CU_LAUNCH();
+}
+
+// ============================== generic CSR row kernel ==========================================
+// TPR lanes per row; partial sums reduced with shuffles inside the lane group; the epilogue gets
+// (row, A_row . x).
+template <class T, int TPR, class Epi>
+__global__ void __launch_bounds__(256) k_rows(int64_t nr, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                              const T* __restrict__ v, const T* __restrict__ x, Epi epi) {
+  int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t r = gt / TPR;
+  int sub = (int)(gt % TPR);
+  bool ok = r < nr;
+  T s = 0;
+  if (ok) {
+    int64_t k1 = rp[r + 1];
+    for (int64_t k = rp[r] + sub; k < k1; k += TPR) s += v[k] * ldg(x + ci[k]);
+  }
+#pragma unroll
+  for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+  if (ok && sub == 0) epi(r, s);
+}
+
+template <class T, class Epi>
+static void run_rows(Ctx& c, const CSRView<T>& M, const T* x, const Epi& epi) {
+  if (M.nr <= 0) return;
+  double avg = M.nr ? (double)M.nnz / (double)M.nr : 0.0;
+  const int B = 256;
+  if (avg <= 2.5) {
+    k_rows<T, 2, Epi><<<grid_for(M.nr * 2, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    CU_LAUNCH();
+  } else if (avg <= 6.0) {
+    k_rows<T, 4, Epi><<<grid_for(M.nr * 4, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    CU_LAUNCH();
+  } else if (avg <= 12.0) {
+    k_rows<T, 8, Epi><<<grid_for(M.nr * 8, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    CU_LAUNCH();
+  } else if (avg <= 40.0) {
+    k_rows<T, 16, Epi><<<grid_for(M.nr * 16, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    CU_LAUNCH();
+  } else {
+    k_rows<T, 32, Epi><<<grid_for(M.nr * 32, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    CU_LAUNCH();
+  }
+}
+
+template <class T>
+struct EpiFrelax {  // eFo[f] = eFi[f] + minv[f] (src_f - s)
+  const int32_t* F; const T* src; const T* minv; const T* eFi; T* eFo;
+  __device__ void operator()(int64_t f, T s) const {
+    T b = F ? src[F[f]] : src[f];
+    eFo[f] = eFi[f] + minv[f] * (b - s);
+  }
+};
+template <class T>
+struct EpiRestrict {  // rnext[c] = base_c - s
+  const int32_t* C; const T* r; T* rnext;
+  __device__ void operator()(int64_t c, T s) const {
+    T b = C ? r[C[c]] : rnext[c];
+    rnext[c] = b - s;
+  }
+};
+template <class T>
+struct EpiResid {
+  const T* b; T* res;
+  __device__ void operator()(int64_t i, T s) const { res[i] = b[i] - s; }
+};
+template <class T>
+struct EpiJacobi {
+  const T* d; const T* b; const T* xi; T* xo;
+  __device__ void operator()(int64_t i, T s) const { xo[i] = xi[i] + d[i] * (b[i] - s); }
+};
+template <class T>
+struct EpiStore {
+  T* y;
+  __device__ void operator()(int64_t i, T s) const { y[i] = s; }
+};
+template <class T>
+struct EpiAdd {
+  T* y;
+  __device__ void operator()(int64_t i, T s) const { y[i] += s; }
+};
+
+template <class T>
+__global__ void k_frelax_first(int64_t nF, const int32_t* F, const T* src, const T* minv, T* eF) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nF) return;
+  eF[f] = minv[f] * (F ? src[F[f]] : src[f]);
+}
+
+template <class T>
+void launch_frelax_first(Ctx& c, int64_t nF, const int32_t* F, const T* src, const T* minv, T* eF) {
+  if (nF <= 0) return;
+  k_frelax_first<T><<<grid_for(nF, 256), 256, 0, c.s>>>(nF, F, src, minv, eF);
+  CU_LAUNCH();
+}
+template <class T>
+void launch_frelax_sweep(Ctx& c, const CSRView<T>& Aff, const int32_t* F, const T* src, const T* minv, const T* eFi,
+                         T* eFo) {
+  run_rows(c, Aff, eFi, EpiFrelax<T>{F, src, minv, eFi, eFo});
+}
+template <class T>
+void launch_restrict(Ctx& c, const CSRView<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext) {
+  run_rows(c, Acf, eF, EpiRestrict<T>{C, r, rnext});
+}
+
+// interpolation over the level's dofs: C dofs take ec[c], F dofs eF[f] + W_p[f,:] ec
+template <class T, class TO, int TPR>
+__global__ void __launch_bounds__(256) k_interp(int64_t n, const int32_t* __restrict__ map, const int64_t* __restrict__ wrp,
+                                                const int32_t* __restrict__ wci, const T* __restrict__ wv,
+                                                const T* __restrict__ eF, const T* __restrict__ ec,
+                                                const T* __restrict__ base, TO* __restrict__ out) {
+  int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t d = gt / TPR;
+  int sub = (int)(gt % TPR);
+  bool ok = d < n;
+  int32_t m = ok ? map[d] : 0;
+  T s = 0;
+  if (ok && m < 0) {
+    int32_t f = -m - 1;
+    int64_t k1 = wrp[f + 1];
+    for (int64_t k = wrp[f] + sub; k < k1; k += TPR) s += wv[k] * ldg(ec + wci[k]);
+  }
+#pragma unroll
+  for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
+  if (ok && sub == 0) {
+    T val = (m >= 0) ? ec[m] : eF[-m - 1] + s;
+    if (base) val += base[d];
+    out[d] = (TO)val;
+  }
+}
+
+template <class T, class TO>
+void launch_interp(Ctx& c, int64_t n, const int32_t* map, const CSRView<T>& Wp, const T* eF, const T* ec, const T* base,
+                   TO* out) {
+  const int B = 256;
+  double avg = Wp.nr ? (double)Wp.nnz / (double)Wp.nr : 0.0;
+  if (avg <= 2.5)
+    k_interp<T, TO, 2><<<grid_for(n * 2, B), B, 0, c.s>>>(n, map, Wp.rp, Wp.ci, Wp.v, eF, ec, base, out);
+  else if (avg <= 6.0)
+    k_interp<T, TO, 4><<<grid_for(n * 4, B), B, 0, c.s>>>(n, map, Wp.rp, Wp.ci, Wp.v, eF, ec, base, out);
+  else
+    k_interp<T, TO, 8><<<grid_for(n * 8, B), B, 0, c.s>>>(n, map, Wp.rp, Wp.ci, Wp.v, eF, ec, base, out);
+  CU_LAUNCH();
+}
+
+// ============================== AMG V-cycle pieces ==============================================
+template <class T>
+__global__ void k_scale_vec(int64_t n, const T* d, const T* b, T* x) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = d[i] * b[i];
+}
+template <class T>
+void launch_scale(Ctx& c, int64_t n, const T* d, const T* b, T* x) {
+  k_scale_vec<T><<<grid_for(n, 256), 256, 0, c.s>>>(n, d, b, x);
+  CU_LAUNCH();
+}
+template <class T>
+void launch_resid(Ctx& c, const CSRView<T>& A, const T* x, const T* b, T* res) {
+  run_rows(c, A, x, EpiResid<T>{b, res});
+}
+template <class T>
+void launch_jacobi(Ctx& c, const CSRView<T>& A, const T* d, const T* b, const T* xi, T* xo) {
+  run_rows(c, A, xi, EpiJacobi<T>{d, b, xi, xo});
+}
+template <class T>
+void launch_spmv(Ctx& c, const CSRView<T>& A, const T* x, T* y) {
+  run_rows(c, A, x, EpiStore<T>{y});
+}
+template <class T>
+void launch_prolong_add(Ctx& c, const CSRView<T>& P, const T* xc, T* x) {
+  run_rows(c, P, xc, EpiAdd<T>{x});
+}
+
+// x = inv b with the FP64 dense inverse of the coarsest operator: one warp per row
+template <class T>
+__global__ void k_dense_gemv(int64_t n, const double* __restrict__ inv, const T* __restrict__ b, T* __restrict__ x) {
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int64_t j = lane; j < n; j += 32) s += inv[i * n + j] * (double)b[j];
+  s = warp_sum(s);
+  if (lane == 0) x[i] = (T)s;
+}
+template <class T>
+void launch_dense_gemv(Ctx& c, int64_t n, const double* inv, const T* b, T* x) {
+  if (n <= 0) return;
+  k_dense_gemv<T><<<grid_for(n * 32, 256), 256, 0, c.s>>>(n, inv, b, x);
+  CU_LAUNCH();
+}
+
+__global__ void k_cast_f32(int64_t n, const double* a, float* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b) {
+  if (n <= 0) return;
+  k_cast_f32<<<grid_for(n, 256, 8192), 256, 0, c.s>>>(n, a, b);
+  CU_LAUNCH();
+}
+
+// ---- explicit instantiations -------------------------------------------------------------------
+#define INST(T)                                                                                                    \
+  template void launch_global_relax<T>(Ctx&, int64_t, const T*, const double*, T*);                               \
+  template void launch_bsr_resid_split<T>(Ctx&, int64_t, const int64_t*, const int32_t*, const T*, const double*,  \
+                                          const T*, const int32_t*, T*, T*);                                       \
+  template void launch_frelax_first<T>(Ctx&, int64_t, const int32_t*, const T*, const T*, T*);                     \
+  template void launch_frelax_sweep<T>(Ctx&, const CSRView<T>&, const int32_t*, const T*, const T*, const T*, T*); \
+  template void launch_restrict<T>(Ctx&, const CSRView<T>&, const int32_t*, const T*, const T*, T*);               \
+  template void launch_interp<T, T>(Ctx&, int64_t, const int32_t*, const CSRView<T>&, const T*, const T*, const T*, \
+                                    T*);                                                                           \
+  template void launch_scale<T>(Ctx&, int64_t, const T*, const T*, T*);                                            \
+  template void launch_resid<T>(Ctx&, const CSRView<T>&, const T*, const T*, T*);                                  \
+  template void launch_jacobi<T>(Ctx&, const CSRView<T>&, const T*, const T*, const T*, T*);                       \
+  template void launch_spmv<T>(Ctx&, const CSRView<T>&, const T*, T*);                                             \
+  template void launch_prolong_add<T>(Ctx&, const CSRView<T>&, const T*, T*);                                      \
+  template void launch_dense_gemv<T>(Ctx&, int64_t, const double*, const T*, T*);
+INST(float)
+INST(double)
+#undef INST
+template void launch_interp<float, double>(Ctx&, int64_t, const int32_t*, const CSRView<float>&, const float*,
+                                           const float*, const float*, double*);
+
+}  // namespace mgr

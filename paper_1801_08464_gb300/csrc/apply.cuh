@@ -1,0 +1,85 @@
+// apply.cuh -- launchers of the preconditioner-apply and Krylov kernels.
+#pragma once
+#include "common.cuh"
+
+namespace mgr {
+
+template <class T>
+struct CSRView {
+  int64_t nr = 0, nnz = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const T* v = nullptr;
+};
+template <class T>
+inline CSRView<T> view(const DCSR<T>& m) {
+  CSRView<T> r;
+  r.nr = m.nr; r.nnz = m.nnz; r.rp = m.rp.p; r.ci = m.ci.p; r.v = m.v.p;
+  return r;
+}
+
+// ---- level 0 (BSR) ---------------------------------------------------------------------------
+// e0 = blockdiag(A)^-1 r (Algorithm step 1); r is the FP64 input.
+template <class T>
+void launch_global_relax(Ctx& c, int64_t nb, const T* binv, const double* r, T* e0);
+// res = r - A e0 over the BSR (e0 == nullptr: res = r), routed by map: C dofs to rnext[c], F dofs to
+// resF[f].
+template <class T>
+void launch_bsr_resid_split(Ctx& c, int64_t nb, const int64_t* rp, const int32_t* ci, const T* vals, const double* r,
+                            const T* e0, const int32_t* map, T* rnext, T* resF);
+
+// ---- reduction levels ------------------------------------------------------------------------
+// sweep 1 from e = 0: eF = minv * src, src = r[F[f]] (F != nullptr) or resF[f]
+template <class T>
+void launch_frelax_first(Ctx& c, int64_t nF, const int32_t* F, const T* src, const T* minv, T* eF);
+// later sweeps: eFo = eFi + minv * (src - A_ff eFi)
+template <class T>
+void launch_frelax_sweep(Ctx& c, const CSRView<T>& Aff, const int32_t* F, const T* src, const T* minv, const T* eFi,
+                         T* eFo);
+// rnext[c] = base_c - A_cf eF with base_c = r[C[c]] (C != nullptr) or rnext[c] (in place)
+template <class T>
+void launch_restrict(Ctx& c, const CSRView<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext);
+// out[d] = base[d] + (C dof: ec[c]; F dof: eF[f] + W_p[f,:] ec); base may be nullptr
+template <class T, class TO>
+void launch_interp(Ctx& c, int64_t n, const int32_t* map, const CSRView<T>& Wp, const T* eF, const T* ec, const T* base,
+                   TO* out);
+
+// ---- AMG -------------------------------------------------------------------------------------
+template <class T>
+void launch_scale(Ctx& c, int64_t n, const T* d, const T* b, T* x);                          // x = d * b
+template <class T>
+void launch_resid(Ctx& c, const CSRView<T>& A, const T* x, const T* b, T* res);              // res = b - A x
+template <class T>
+void launch_jacobi(Ctx& c, const CSRView<T>& A, const T* d, const T* b, const T* xi, T* xo);  // xo = xi + d (b - A xi)
+template <class T>
+void launch_spmv(Ctx& c, const CSRView<T>& A, const T* x, T* y);                             // y = A x
+template <class T>
+void launch_prolong_add(Ctx& c, const CSRView<T>& P, const T* xc, T* x);                     // x += P xc
+template <class T>
+void launch_dense_gemv(Ctx& c, int64_t n, const double* inv, const T* b, T* x);              // x = inv b (FP64)
+
+void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b);
+
+// ---- Krylov (FP64) ---------------------------------------------------------------------------
+void launch_bsr3_spmv_f64(Ctx& c, const mgr_bsr3_t& A, const double* x, const double* sub, double* y);
+// Deterministic multi-dot: out[k] = V_k . w for k < nv (V_k = V + k ldv) and, if want_ww,
+// out[nv] = w . w.  `part` must hold KRY_GRID * (nv + 1) doubles.
+constexpr int KRY_GRID = 304;
+constexpr int KRY_MAXV = 32;
+void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* w, bool want_ww, double* part,
+                 double* out);
+// w -= sum_k h[k] V_k (h on device); out[0] = ||w||^2 after the update
+void launch_mupdate(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* h, double* w, double* part,
+                    double* out);
+// y = alpha x
+void launch_scal(Ctx& c, int64_t n, double alpha, const double* x, double* y);
+// x += sum_k y[k] Z_k (y on device)
+void launch_xupdate(Ctx& c, int64_t n, const double* Z, int64_t ldz, int nz, const double* y, double* x);
+// out[0] = x . x
+void launch_nrm2sq(Ctx& c, int64_t n, const double* x, double* part, double* out);
+
+// adjoint helpers
+void launch_bsr3_outer_grad(Ctx& c, const mgr_bsr3_t& A, const double* lam, const double* x, double* g);
+void launch_bsr3_transpose(Ctx& c, const mgr_bsr3_t& A, int64_t* rpt, int32_t* cit, double* vt);
+
+}  // namespace mgr

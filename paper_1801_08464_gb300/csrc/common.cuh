@@ -1,0 +1,164 @@
+// common.cuh -- shared host/device utilities of the MGR-FGMRES library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <utility>
+
+#include "mgr.h"
+
+namespace mgr {
+
+// ---------------------------------------------------------------------------------------------
+// Errors: every failure becomes an Error carrying an mgr_status_t; the C-ABI layer converts it.
+struct Error : std::runtime_error {
+  mgr_status_t status;
+  Error(mgr_status_t s, const std::string& what) : std::runtime_error(what), status(s) {}
+};
+
+inline void cuda_check(cudaError_t e, const char* what, const char* file, int line) {
+  if (e == cudaSuccess) return;
+  mgr_status_t s = (e == cudaErrorMemoryAllocation) ? MGR_ERR_OOM : MGR_ERR_CUDA;
+  throw Error(s, std::string(what) + ": " + cudaGetErrorString(e) + " at " + file + ":" + std::to_string(line));
+}
+#define CU(x) ::mgr::cuda_check((x), #x, __FILE__, __LINE__)
+// Every kernel launch of the library is followed by CU_LAUNCH(), which checks it and counts it.
+extern unsigned long long g_launch_count;
+#define CU_LAUNCH()                                                                  \
+  do {                                                                               \
+    ::mgr::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__);      \
+    ++::mgr::g_launch_count;                                                         \
+  } while (0)
+
+// Device error bits set by kernels (atomicOr) and checked by the host after a phase.
+enum : int {
+  EBIT_SINGULAR = 1,     // zero or non-finite pivot / diagonal
+  EBIT_PATTERN = 2,      // malformed BSR pattern or marker
+  EBIT_CAPACITY = 4,     // a per-row work bound exceeded a kernel limit
+  EBIT_NONFINITE = 8,
+};
+
+// ---------------------------------------------------------------------------------------------
+// Execution context: stream, device error word, allocation accounting.
+struct Ctx {
+  cudaStream_t s = nullptr;
+  int* d_err = nullptr;        // device int, error bits
+  int* h_pinned = nullptr;     // pinned host scratch (small readbacks)
+  int64_t bytes = 0;           // bytes currently allocated through this context
+  int64_t peak = 0;
+  int num_sms = 152;
+};
+
+void* dev_alloc(Ctx& c, size_t bytes);
+void dev_free(Ctx& c, void* p, size_t bytes);
+
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  Ctx* c = nullptr;
+  DBuf() = default;
+  DBuf(Ctx& ctx, size_t count) { alloc(ctx, count); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p(o.p), n(o.n), c(o.c) { o.p = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; c = o.c; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(Ctx& ctx, size_t count) {
+    release();
+    c = &ctx;
+    n = count;
+    p = static_cast<T*>(dev_alloc(ctx, (count ? count : 1) * sizeof(T) + 16));  // +16: vector-load slack
+  }
+  void release() {
+    if (p && c) dev_free(*c, p, (n ? n : 1) * sizeof(T) + 16);
+    p = nullptr;
+    n = 0;
+  }
+  T* get() const { return p; }
+  operator T*() const { return p; }
+};
+
+// Device CSR: int64 row pointers, int32 ascending columns.
+template <class T>
+struct DCSR {
+  int64_t nr = 0, nc = 0, nnz = 0;
+  DBuf<int64_t> rp;
+  DBuf<int32_t> ci;
+  DBuf<T> v;
+  bool empty() const { return rp.p == nullptr; }
+};
+
+// Read back a device scalar (synchronises the stream).
+template <class T>
+T read_scalar(Ctx& c, const T* dptr) {
+  T h;
+  CU(cudaMemcpyAsync(&h, dptr, sizeof(T), cudaMemcpyDeviceToHost, c.s));
+  CU(cudaStreamSynchronize(c.s));
+  return h;
+}
+void check_errors(Ctx& c, const char* phase);  // reads d_err, throws on set bits, clears it
+
+inline unsigned grid_for(int64_t n, int block, int64_t cap = (1ll << 30)) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device helpers.
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* a, int64_t lo, int64_t hi, int32_t key) {
+  // first position in [lo, hi) with a[pos] >= key
+  while (lo < hi) {
+    int64_t m = (lo + hi) >> 1;
+    if (a[m] < key) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t find_i32(const int32_t* a, int64_t lo, int64_t hi, int32_t key) {
+  int64_t p = lower_bound_i32(a, lo, hi, key);
+  return (p < hi && a[p] == key) ? p : -1;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Scans (scan.cu).  out has n+1 entries: out[0] = 0, out[i+1] = sum_{j<=i} in[j].
+void scan_excl_i64(Ctx& c, const int64_t* in, int64_t* out, int64_t n);
+void scan_excl_i32(Ctx& c, const int32_t* in, int32_t* out, int64_t n);
+// Build rowptr from per-row counts (int64) and return the total (synchronises).
+int64_t counts_to_rowptr(Ctx& c, const int64_t* counts, int64_t* rowptr, int64_t n);
+void fill_i64(Ctx& c, int64_t* p, int64_t v, int64_t n);
+void fill_i32(Ctx& c, int32_t* p, int32_t v, int64_t n);
+void fill_f64(Ctx& c, double* p, double v, int64_t n);
+
+// ---------------------------------------------------------------------------------------------
+// Sparse setup primitives (sparse.cu).  All FP64, deterministic, no fused multiply-add.
+void bsr3_validate(Ctx& c, const mgr_bsr3_t& A, const int8_t* marker);  // throws INVALID_ARG
+void bsr3_to_csr(Ctx& c, const mgr_bsr3_t& A, DCSR<double>& out);        // exact zeros dropped
+void bsr3_block_inverse(Ctx& c, const mgr_bsr3_t& A, double* binv);      // sets EBIT_SINGULAR
+// C = A * B: structural pattern, each entry summed in ascending intermediate index.
+void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C);
+// Pattern of C = A * B only (values left unallocated), same pattern rules.
+void spgemm_symbolic(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C);
+void transpose(Ctx& c, const DCSR<double>& A, DCSR<double>& T);          // rows sorted by column
+// Sort each row segment [rp[i], rp[i+1]) of (ci, v) by ci (keys unique within a row).
+void sort_rows(Ctx& c, int64_t nr, const int64_t* rp, int32_t* ci, double* v);
+
+// CSR float copy
+void csr_to_f32(Ctx& c, const DCSR<double>& A, DCSR<float>& B);
+void copy_csr(Ctx& c, const DCSR<double>& A, DCSR<double>& B);
+
+}  // namespace mgr

@@ -1,0 +1,759 @@
+// mgr.cu -- handle, setup orchestration, preconditioner apply, flexible GMRES and the C ABI.
+//
+// Setup (sections 4-5 of the paper): validate the BSR input, invert the 3x3 diagonal blocks for the
+// global relaxation, form the scalar level-0 operator, run the reduction levels in marker order
+// (level l removes the dofs with cf_marker == l), build the AMG hierarchy on the last (pressure)
+// level, then cast what the apply reads to the working precision.
+// Apply: the presmoothing Algorithm of section 4 recursively over the levels, an AMG V-cycle (or a
+// dense inverse) as the coarse solve.
+// Solve: right-preconditioned flexible GMRES(m) with classical Gram-Schmidt and selective
+// reorthogonalisation, Givens rotations on the host.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <type_traits>
+#include <vector>
+
+#include "apply.cuh"
+#include "hier.cuh"
+
+using namespace mgr;
+
+struct mgr_handle_s {
+  Ctx c;
+  mgr_options_t o;
+  int device = 0;
+  bool ready = false;
+  int64_t nb = 0, nnzb = 0;
+  DBuf<int64_t> rp0;
+  DBuf<int32_t> ci0;
+  DBuf<double> val64, binv;
+  DBuf<float> val32, binv32;
+  int L = 0;
+  std::vector<MgrLevel> lev;  // lev[0..L]; lev[L] holds the coarsest operator only
+  std::vector<AmgLevel> amg;
+  DBuf<double> cinv;
+  int64_t nco = 0;
+  bool coarse_dense = false;
+  // apply work buffers (bytes; element type set by the precision)
+  DBuf<char> w_e0, w_resF0, w_tmp_in, w_tmp_out;
+  std::vector<DBuf<char>> w_r, w_e, w_eF, w_eF2;
+  std::vector<DBuf<char>> a_b, a_xa, a_xb, a_res;
+  // Krylov work
+  int kry_m = 0;
+  int64_t kry_n = 0;
+  DBuf<double> V, Z, part, dsc;
+  double* hpin = nullptr;  // pinned host scratch
+  double setup_ms = 0.0;
+  int64_t apply_launches = 0;
+};
+
+namespace {
+
+mgr_status_t guard_status(const std::exception_ptr& ep, mgr_handle_s* h) {
+  try {
+    std::rethrow_exception(ep);
+  } catch (const Error& e) {
+    if (h) cudaGetLastError();
+    fprintf(stderr, "[mgr] %s\n", e.what());
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    return MGR_ERR_OOM;
+  } catch (...) {
+    return MGR_ERR_CUDA;
+  }
+}
+
+template <class F>
+mgr_status_t guarded(mgr_handle_s* h, F&& f) {
+  try {
+    f();
+    return MGR_OK;
+  } catch (...) {
+    return guard_status(std::current_exception(), h);
+  }
+}
+
+template <class T>
+inline const T* pick_ptr(const DBuf<double>& d, const DBuf<float>& f) {
+  if constexpr (std::is_same<T, float>::value) return f.p;
+  else return d.p;
+}
+template <class T>
+inline CSRView<T> tv(const DCSR<double>& d, const DCSR<float>& f) {
+  if constexpr (std::is_same<T, float>::value) return view(f);
+  else return view(d);
+}
+template <class T>
+inline T* P(DBuf<char>& b) { return reinterpret_cast<T*>(b.p); }
+
+// ---- apply -----------------------------------------------------------------------------------
+template <class T>
+const T* frelax(mgr_handle_s& h, int l, const T* src, const int32_t* F) {
+  MgrLevel& L = h.lev[l];
+  T* a = P<T>(h.w_eF[l]);
+  T* b = P<T>(h.w_eF2[l]);
+  if (L.nF == 0) return a;
+  const T* minv = pick_ptr<T>(L.minv, L.minv32);
+  launch_frelax_first<T>(h.c, L.nF, F, src, minv, a);
+  CSRView<T> Aff = tv<T>(L.Aff, L.Aff32);
+  for (int s = 1; s < L.sweeps; ++s) {
+    launch_frelax_sweep<T>(h.c, Aff, F, src, minv, a, b);
+    std::swap(a, b);
+  }
+  return a;
+}
+
+template <class T>
+const T* vcycle(mgr_handle_s& h, int k, const T* b) {
+  Ctx& c = h.c;
+  int last = (int)h.amg.size() - 1;
+  if (k == last || h.coarse_dense) {
+    T* x = P<T>(h.a_xa[k]);
+    launch_dense_gemv<T>(c, h.nco, h.cinv.p, b, x);
+    return x;
+  }
+  AmgLevel& A = h.amg[k];
+  CSRView<T> Av = tv<T>(A.A, A.A32);
+  const T* d = pick_ptr<T>(A.dinv, A.dinv32);
+  T* xa = P<T>(h.a_xa[k]);
+  T* xb = P<T>(h.a_xb[k]);
+  T* res = P<T>(h.a_res[k]);
+  launch_scale<T>(c, A.n, d, b, xa);
+  for (int s = 1; s < h.o.amg_pre; ++s) {
+    launch_jacobi<T>(c, Av, d, b, xa, xb);
+    std::swap(xa, xb);
+  }
+  launch_resid<T>(c, Av, xa, b, res);
+  T* bc = P<T>(h.a_b[k + 1]);
+  launch_spmv<T>(c, tv<T>(A.R, A.R32), res, bc);
+  const T* xc = vcycle<T>(h, k + 1, bc);
+  launch_prolong_add<T>(c, tv<T>(A.P, A.P32), xc, xa);
+  for (int s = 0; s < h.o.amg_post; ++s) {
+    launch_jacobi<T>(c, Av, d, b, xa, xb);
+    std::swap(xa, xb);
+  }
+  return xa;
+}
+
+template <class T>
+void apply_t(mgr_handle_s& h, const double* r, double* z) {
+  Ctx& c = h.c;
+  unsigned long long l0 = g_launch_count;
+  int L = h.L;
+  if (L == 0) {  // the whole system is the coarse system
+    T* rin = P<T>(h.w_tmp_in);
+    if constexpr (std::is_same<T, float>::value) launch_cast_f32(c, 3 * h.nb, r, rin);
+    else CU(cudaMemcpyAsync(rin, r, sizeof(double) * 3 * h.nb, cudaMemcpyDeviceToDevice, c.s));
+    const T* e = vcycle<T>(h, 0, rin);
+    CSRView<T> none;
+    // z = e (the identity map of level 0 routes every dof as "C" with coarse index d)
+    launch_interp<T, double>(c, 3 * h.nb, h.lev[0].map.p, none, nullptr, e, nullptr, z);
+    h.apply_launches = (int64_t)(g_launch_count - l0);
+    return;
+  }
+  MgrLevel& L0 = h.lev[0];
+  const T* binv = pick_ptr<T>(h.binv, h.binv32);
+  const T* vals = pick_ptr<T>(h.val64, h.val32);
+  T* e0 = h.o.global_relax ? P<T>(h.w_e0) : nullptr;
+  if (e0) launch_global_relax<T>(c, h.nb, binv, r, e0);
+  T* r1 = P<T>(h.w_r[1]);
+  T* resF0 = P<T>(h.w_resF0);
+  launch_bsr_resid_split<T>(c, h.nb, h.rp0.p, h.ci0.p, vals, r, e0, L0.map.p, r1, resF0);
+  std::vector<const T*> eF(L);
+  eF[0] = frelax<T>(h, 0, resF0, nullptr);
+  launch_restrict<T>(c, tv<T>(L0.Acf, L0.Acf32), nullptr, nullptr, eF[0], r1);
+  for (int l = 1; l < L; ++l) {
+    MgrLevel& Ll = h.lev[l];
+    const T* rl = P<T>(h.w_r[l]);
+    eF[l] = frelax<T>(h, l, rl, Ll.F.p);
+    launch_restrict<T>(c, tv<T>(Ll.Acf, Ll.Acf32), Ll.C.p, rl, eF[l], P<T>(h.w_r[l + 1]));
+  }
+  const T* ec = vcycle<T>(h, 0, P<T>(h.w_r[L]));
+  for (int l = L - 1; l >= 1; --l) {
+    MgrLevel& Ll = h.lev[l];
+    T* el = P<T>(h.w_e[l]);
+    launch_interp<T, T>(c, Ll.n, Ll.map.p, tv<T>(Ll.Wp, Ll.Wp32), eF[l], ec, nullptr, el);
+    ec = el;
+  }
+  launch_interp<T, double>(c, L0.n, L0.map.p, tv<T>(L0.Wp, L0.Wp32), eF[0], ec, e0, z);
+  h.apply_launches = (int64_t)(g_launch_count - l0);
+}
+
+void do_apply(mgr_handle_s& h, const double* r, double* z) {
+  if (h.o.precision == MGR_PREC_MIXED) apply_t<float>(h, r, z);
+  else apply_t<double>(h, r, z);
+}
+
+// ---- setup -----------------------------------------------------------------------------------
+__global__ void k_identity_map(int64_t n, int32_t* map) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) map[i] = (int32_t)i;
+}
+__global__ void k_max_marker(int64_t n, const int8_t* mk, int* out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) atomicMax(out, (int)mk[i]);
+}
+
+void alloc_work(mgr_handle_s& h) {
+  Ctx& c = h.c;
+  size_t es = (h.o.precision == MGR_PREC_MIXED) ? sizeof(float) : sizeof(double);
+  int L = h.L;
+  h.w_r.clear(); h.w_e.clear(); h.w_eF.clear(); h.w_eF2.clear();
+  h.w_r.resize(L + 1); h.w_e.resize(L + 1); h.w_eF.resize(L + 1); h.w_eF2.resize(L + 1);
+  h.w_e0.alloc(c, es * 3 * h.nb);
+  h.w_tmp_in.alloc(c, es * 3 * h.nb);
+  for (int l = 0; l <= L; ++l) {
+    int64_t n = h.lev[l].n;
+    h.w_r[l].alloc(c, es * n);
+    h.w_e[l].alloc(c, es * n);
+    if (l < L) {
+      h.w_eF[l].alloc(c, es * (h.lev[l].nF + 1));
+      h.w_eF2[l].alloc(c, es * (h.lev[l].nF + 1));
+    }
+  }
+  h.w_resF0.alloc(c, es * ((L > 0 ? h.lev[0].nF : 0) + 1));
+  size_t na = std::max<size_t>(h.amg.size(), 1);
+  h.a_b.clear(); h.a_xa.clear(); h.a_xb.clear(); h.a_res.clear();
+  h.a_b.resize(na); h.a_xa.resize(na); h.a_xb.resize(na); h.a_res.resize(na);
+  for (size_t k = 0; k < na; ++k) {
+    int64_t n = h.amg.empty() ? h.nco : h.amg[k].n;
+    h.a_b[k].alloc(c, es * n);
+    h.a_xa[k].alloc(c, es * n);
+    h.a_xb[k].alloc(c, es * n);
+    h.a_res[k].alloc(c, es * n);
+  }
+}
+
+void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
+  Ctx& c = h.c;
+  int64_t nv = 9 * h.nnzb;
+  if (h.o.precision == MGR_PREC_MIXED) {
+    h.val32.alloc(c, nv);
+    launch_cast_f32(c, nv, A.values, h.val32.p);
+    h.binv32.alloc(c, 9 * h.nb);
+    launch_cast_f32(c, 9 * h.nb, h.binv.p, h.binv32.p);
+    for (int l = 0; l < h.L; ++l) {
+      MgrLevel& L = h.lev[l];
+      csr_to_f32(c, L.Aff, L.Aff32);
+      csr_to_f32(c, L.Acf, L.Acf32);
+      csr_to_f32(c, L.Wp, L.Wp32);
+      L.minv32.alloc(c, L.nF + 1);
+      launch_cast_f32(c, L.nF, L.minv.p, L.minv32.p);
+    }
+    for (size_t k = 0; k + 1 < h.amg.size(); ++k) {
+      AmgLevel& G = h.amg[k];
+      csr_to_f32(c, G.A, G.A32);
+      csr_to_f32(c, G.P, G.P32);
+      csr_to_f32(c, G.R, G.R32);
+      G.dinv32.alloc(c, G.n);
+      launch_cast_f32(c, G.n, G.dinv.p, G.dinv32.p);
+    }
+  } else {
+    h.val64.alloc(c, nv);
+    CU(cudaMemcpyAsync(h.val64.p, A.values, sizeof(double) * nv, cudaMemcpyDeviceToDevice, c.s));
+  }
+}
+
+void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
+  auto t0 = std::chrono::steady_clock::now();
+  Ctx& c = h.c;
+  h.ready = false;
+  h.lev.clear();
+  h.amg.clear();
+  h.cinv.release();
+  h.val32.release(); h.val64.release(); h.binv32.release();
+  bsr3_validate(c, A, marker);
+  h.nb = A.nb;
+  h.nnzb = A.nnzb;
+  int64_t n = 3 * A.nb;
+  // pattern copy (the apply reads the pattern; the caller may free A after setup)
+  h.rp0.alloc(c, A.nb + 1);
+  h.ci0.alloc(c, A.nnzb);
+  CU(cudaMemcpyAsync(h.rp0.p, A.rowptr, sizeof(int64_t) * (A.nb + 1), cudaMemcpyDeviceToDevice, c.s));
+  CU(cudaMemcpyAsync(h.ci0.p, A.colind, sizeof(int32_t) * A.nnzb, cudaMemcpyDeviceToDevice, c.s));
+  int L;
+  {
+    DBuf<int> mx(c, 1);
+    CU(cudaMemsetAsync(mx.p, 0, sizeof(int), c.s));
+    k_max_marker<<<grid_for(n, 256), 256, 0, c.s>>>(n, marker, mx.p);
+    CU_LAUNCH();
+    L = read_scalar(c, mx.p);
+  }
+  h.L = L;
+  // global relaxation blocks
+  h.binv.alloc(c, 9 * A.nb);
+  bsr3_block_inverse(c, A, h.binv.p);
+  check_errors(c, "3x3 diagonal blocks");
+  h.lev.resize(L + 1);
+  h.lev[0].n = n;
+  bsr3_to_csr(c, A, h.lev[0].A);
+  h.lev[0].mk.alloc(c, n);
+  CU(cudaMemcpyAsync(h.lev[0].mk.p, marker, n, cudaMemcpyDeviceToDevice, c.s));
+  for (int l = 0; l < L; ++l) {
+    LevelOpts lo;
+    lo.frelax_type = h.o.frelax_type[l];
+    lo.sweeps = h.o.frelax_sweeps[l];
+    lo.omega = h.o.frelax_omega[l];
+    lo.restrict_type = h.o.restrict_type[l];
+    DBuf<int8_t> mk_next;
+    mgr_reduce_level(c, h.lev[l], l, lo, h.lev[l + 1].A, mk_next);
+    h.lev[l + 1].n = h.lev[l].nC;
+    h.lev[l + 1].mk = std::move(mk_next);
+  }
+  if (L == 0) {
+    h.lev[0].map.alloc(c, n);
+    k_identity_map<<<grid_for(n, 256), 256, 0, c.s>>>(n, h.lev[0].map.p);
+    CU_LAUNCH();
+  }
+  // coarse solve on the last level
+  const DCSR<double>& Ac = h.lev[L].A;
+  if (h.o.coarse_solver == 1) {
+    if (Ac.nr > 4096) throw Error(MGR_ERR_UNSUPPORTED, "dense coarse solve limited to 4096 rows");
+    h.coarse_dense = true;
+    h.nco = Ac.nr;
+    dense_inverse(c, Ac, h.cinv);
+    check_errors(c, "dense coarse inverse");
+  } else {
+    h.coarse_dense = false;
+    AmgOpts ao;
+    ao.theta = h.o.amg_theta;
+    ao.max_levels = h.o.amg_max_levels;
+    ao.max_coarse = h.o.amg_max_coarse;
+    ao.smoother = h.o.amg_smoother;
+    ao.pre = h.o.amg_pre;
+    ao.post = h.o.amg_post;
+    ao.pmax = h.o.amg_pmax;
+    ao.omega = h.o.amg_omega;
+    ao.seed = h.o.amg_seed;
+    amg_build(c, Ac, ao, h.amg, h.cinv, h.nco);
+  }
+  cast_hierarchy(h, A);
+  alloc_work(h);
+  CU(cudaStreamSynchronize(c.s));
+  h.ready = true;
+  h.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// ---- flexible GMRES ----------------------------------------------------------------------------
+void ensure_krylov(mgr_handle_s& h, int m, int64_t n) {
+  if (h.kry_m == m && h.kry_n == n) return;
+  Ctx& c = h.c;
+  h.V.alloc(c, (size_t)(m + 1) * n);
+  h.Z.alloc(c, (size_t)m * n);
+  h.part.alloc(c, (size_t)KRY_GRID * (KRY_MAXV + 2));
+  h.dsc.alloc(c, 256);
+  h.kry_m = m;
+  h.kry_n = n;
+}
+
+mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, double* x, double rtol, int m, int maxit,
+                       mgr_solve_info_t* info) {
+  auto t0 = std::chrono::steady_clock::now();
+  Ctx& c = h.c;
+  int64_t n = 3 * A.nb;
+  ensure_krylov(h, m, n);
+  double* hp = h.hpin;  // pinned: [0..63] readbacks
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+  mgr_solve_info_t loc;
+  memset(&loc, 0, sizeof loc);
+  auto rd = [&](const double* d, int cnt) {
+    CU(cudaMemcpyAsync(hp, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.s));
+    CU(cudaStreamSynchronize(c.s));
+  };
+  double* V = h.V.p;
+  double* Z = h.Z.p;
+  double* dsc = h.dsc.p;
+  mgr_status_t st = MGR_OK;
+  launch_nrm2sq(c, n, b, h.part.p, dsc);
+  rd(dsc, 1);
+  double bnorm = std::sqrt(hp[0]);
+  loc.bnorm = bnorm;
+  int it = 0;
+  if (bnorm == 0.0) {
+    CU(cudaMemsetAsync(x, 0, sizeof(double) * n, c.s));
+    loc.converged = 1;
+  } else {
+    launch_bsr3_spmv_f64(c, A, x, b, V);  // r = b - A x
+    launch_nrm2sq(c, n, V, h.part.p, dsc);
+    rd(dsc, 1);
+    double beta = std::sqrt(hp[0]);
+    if (info && info->history && info->history_cap > 0) info->history[0] = beta / bnorm;
+    loc.relres_true = loc.relres_est = beta / bnorm;
+    if (beta <= rtol * bnorm) loc.converged = 1;
+    const double eta = 0.7071067811865476;
+    while (!loc.converged) {
+      launch_scal(c, n, 1.0 / beta, V, V);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int k = 0;
+      bool stop = false;
+      for (int j = 0; j < m && it < maxit; ++j) {
+        double* vj = V + (int64_t)j * n;
+        double* zj = Z + (int64_t)j * n;
+        double* w = V + (int64_t)(j + 1) * n;
+        do_apply(h, vj, zj);
+        launch_bsr3_spmv_f64(c, A, zj, nullptr, w);
+        // classical Gram-Schmidt, then a second pass when the norm dropped by more than 1/sqrt(2)
+        launch_mdot(c, n, V, n, j + 1, w, true, h.part.p, dsc);
+        launch_mupdate(c, n, V, n, j + 1, dsc, w, h.part.p, dsc + 64);
+        rd(dsc, 65);
+        double hcol[KRY_MAXV + 2];
+        for (int i = 0; i <= j; ++i) hcol[i] = hp[i];
+        double nw0 = std::sqrt(hp[j + 1]);
+        double nw = std::sqrt(hp[64]);
+        if (!(nw >= eta * nw0)) {
+          launch_mdot(c, n, V, n, j + 1, w, false, h.part.p, dsc + 96);
+          launch_mupdate(c, n, V, n, j + 1, dsc + 96, w, h.part.p, dsc + 160);
+          CU(cudaMemcpyAsync(hp + 96, dsc + 96, sizeof(double) * 65, cudaMemcpyDeviceToHost, c.s));
+          CU(cudaStreamSynchronize(c.s));
+          for (int i = 0; i <= j; ++i) hcol[i] += hp[96 + i];
+          nw = std::sqrt(hp[96 + 64]);
+        }
+        if (!std::isfinite(nw)) { st = MGR_ERR_BREAKDOWN; stop = true; break; }
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
+        H[(size_t)(j + 1) * m + j] = nw;
+        if (nw != 0.0) launch_scal(c, n, 1.0 / nw, w, w);
+        for (int i = 0; i < j; ++i) {
+          double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+          H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+        }
+        double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+        double den = std::sqrt(a * a + bb * bb);
+        if (den == 0.0 || !std::isfinite(den)) { st = MGR_ERR_BREAKDOWN; stop = true; break; }
+        cs[j] = a / den;
+        sn[j] = bb / den;
+        H[(size_t)j * m + j] = den;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        ++it;
+        k = j + 1;
+        if (info && info->history && it < info->history_cap) info->history[it] = std::fabs(g[j + 1]) / bnorm;
+        if (std::fabs(g[j + 1]) <= rtol * bnorm || nw == 0.0) break;
+      }
+      if (stop) break;
+      for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int t = i + 1; t < k; ++t) s -= H[(size_t)i * m + t] * y[t];
+        y[i] = s / H[(size_t)i * m + i];
+      }
+      if (k > 0) {
+        memcpy(hp + 200, y.data(), sizeof(double) * k);
+        CU(cudaMemcpyAsync(dsc + 200, hp + 200, sizeof(double) * k, cudaMemcpyHostToDevice, c.s));
+        launch_xupdate(c, n, Z, n, k, dsc + 200, x);
+      }
+      loc.relres_est = (k > 0) ? std::fabs(g[k]) / bnorm : beta / bnorm;
+      launch_bsr3_spmv_f64(c, A, x, b, V);
+      launch_nrm2sq(c, n, V, h.part.p, dsc);
+      rd(dsc, 1);
+      beta = std::sqrt(hp[0]);
+      loc.relres_true = beta / bnorm;
+      if (beta <= rtol * bnorm) { loc.converged = 1; break; }
+      if (!std::isfinite(beta)) { st = MGR_ERR_BREAKDOWN; break; }
+      if (it >= maxit) { st = MGR_ERR_NOT_CONVERGED; break; }
+      loc.restarts++;
+    }
+  }
+  CU(cudaStreamSynchronize(c.s));
+  loc.iterations = it;
+  loc.status = st;
+  loc.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) {
+    double* hist = info->history;
+    int cap = info->history_cap;
+    *info = loc;
+    info->history = hist;
+    info->history_cap = cap;
+  }
+  return st;
+}
+
+// ---- introspection -----------------------------------------------------------------------------
+const DCSR<double>* pick_matrix(mgr_handle_s& h, int kind, int level) {
+  if (kind >= 0 && kind <= 4) {
+    if (level < 0 || level > h.L || (kind > 0 && level >= h.L)) return nullptr;
+    MgrLevel& L = h.lev[level];
+    switch (kind) {
+      case 0: return &L.A;
+      case 1: return &L.Wp;
+      case 2: return &L.Wr;
+      case 3: return &L.P;
+      default: return &L.R;
+    }
+  }
+  int na = (int)h.amg.size();
+  if (kind < 5 || kind > 8 || level < 0 || level >= na) return nullptr;
+  if (kind > 5 && level >= na - 1) return nullptr;
+  AmgLevel& G = h.amg[level];
+  switch (kind) {
+    case 5: return &G.A;
+    case 6: return &G.P;
+    case 7: return &G.R;
+    default: return &G.S;
+  }
+}
+
+__global__ void k_fill_one(int64_t n, double* v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v[i] = 1.0;
+}
+template <class S>
+__global__ void k_to_double(int64_t n, const S* a, double* b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+}  // namespace
+
+// =================================== C ABI ======================================================
+extern "C" {
+
+const char* mgr_status_string(mgr_status_t s) {
+  switch (s) {
+    case MGR_OK: return "MGR_OK";
+    case MGR_ERR_INVALID_ARG: return "MGR_ERR_INVALID_ARG";
+    case MGR_ERR_SINGULAR: return "MGR_ERR_SINGULAR";
+    case MGR_ERR_NOT_CONVERGED: return "MGR_ERR_NOT_CONVERGED";
+    case MGR_ERR_BREAKDOWN: return "MGR_ERR_BREAKDOWN";
+    case MGR_ERR_OOM: return "MGR_ERR_OOM";
+    case MGR_ERR_CUDA: return "MGR_ERR_CUDA";
+    case MGR_ERR_TIMEOUT: return "MGR_ERR_TIMEOUT";
+    case MGR_ERR_STATE: return "MGR_ERR_STATE";
+    case MGR_ERR_UNSUPPORTED: return "MGR_ERR_UNSUPPORTED";
+  }
+  return "MGR_ERR_UNKNOWN";
+}
+
+void mgr_options_default(mgr_options_t* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->precision = MGR_PREC_FP64;
+  o->global_relax = 1;
+  for (int l = 0; l < MGR_MAX_LEVELS; ++l) {
+    o->frelax_type[l] = (l == 0) ? 0 : 1;
+    o->frelax_sweeps[l] = (l == 0) ? 1 : 2;
+    o->frelax_omega[l] = 1.0;
+    o->restrict_type[l] = (l == 0) ? 1 : 0;
+  }
+  o->apply_full_R = 0;
+  o->coarse_solver = 0;
+  o->amg_theta = 0.25;
+  o->amg_max_levels = 25;
+  o->amg_max_coarse = 256;
+  o->amg_smoother = 1;
+  o->amg_pre = 1;
+  o->amg_post = 1;
+  o->amg_pmax = 0;
+  o->amg_omega = 1.0;
+  o->amg_seed = 3;
+  o->use_graph = 1;
+}
+
+static mgr_status_t check_options(const mgr_options_t& o) {
+  if (o.precision != MGR_PREC_FP64 && o.precision != MGR_PREC_MIXED) return MGR_ERR_INVALID_ARG;
+  for (int l = 0; l < MGR_MAX_LEVELS; ++l) {
+    if (o.frelax_sweeps[l] < 1 || o.frelax_sweeps[l] > 64) return MGR_ERR_INVALID_ARG;
+    if (o.frelax_type[l] < 0 || o.frelax_type[l] > 1) return MGR_ERR_INVALID_ARG;
+    if (o.restrict_type[l] < 0 || o.restrict_type[l] > 1) return MGR_ERR_INVALID_ARG;
+  }
+  if (o.apply_full_R != 0) return MGR_ERR_UNSUPPORTED;
+  if (o.amg_pre < 1 || o.amg_post < 0 || o.amg_max_levels < 1 || o.amg_max_coarse < 1 || o.amg_max_coarse > 4096)
+    return MGR_ERR_INVALID_ARG;
+  if (o.amg_smoother < 0 || o.amg_smoother > 1 || o.amg_pmax < 0) return MGR_ERR_INVALID_ARG;
+  return MGR_OK;
+}
+
+mgr_status_t mgr_create(mgr_handle_t* out, const mgr_options_t* opt, void* stream) {
+  if (!out) return MGR_ERR_INVALID_ARG;
+  *out = nullptr;
+  mgr_handle_s* h = new (std::nothrow) mgr_handle_s();
+  if (!h) return MGR_ERR_OOM;
+  if (opt) h->o = *opt; else mgr_options_default(&h->o);
+  mgr_status_t st = check_options(h->o);
+  if (st != MGR_OK) { delete h; return st; }
+  st = guarded(h, [&] {
+    CU(cudaGetDevice(&h->device));
+    h->c.s = static_cast<cudaStream_t>(stream);
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    h->c.num_sms = sms;
+    cudaMemPool_t pool;
+    CU(cudaDeviceGetDefaultMemPool(&pool, h->device));
+    uint64_t thr = UINT64_MAX;
+    CU(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    CU(cudaMalloc(&h->c.d_err, sizeof(int)));
+    CU(cudaMemset(h->c.d_err, 0, sizeof(int)));
+    CU(cudaMallocHost(&h->hpin, 512 * sizeof(double)));
+  });
+  if (st != MGR_OK) {
+    if (h->c.d_err) cudaFree(h->c.d_err);
+    if (h->hpin) cudaFreeHost(h->hpin);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return MGR_OK;
+}
+
+mgr_status_t mgr_setup(mgr_handle_t h, const mgr_bsr3_t* A, const int8_t* cf_marker) {
+  if (!h || !A || !cf_marker) return MGR_ERR_INVALID_ARG;
+  return guarded(h, [&] { do_setup(*h, *A, cf_marker); });
+}
+
+mgr_status_t mgr_apply(mgr_handle_t h, const double* r, double* z) {
+  if (!h || !r || !z) return MGR_ERR_INVALID_ARG;
+  if (!h->ready) return MGR_ERR_STATE;
+  return guarded(h, [&] { do_apply(*h, r, z); });
+}
+
+mgr_status_t fgmres_solve(mgr_handle_t h, const mgr_bsr3_t* A, const double* b, double* x, double rtol, int restart,
+                          int maxit, mgr_solve_info_t* info) {
+  if (!h || !A || !b || !x || restart < 1 || restart > KRY_MAXV || maxit < 0 || !(rtol >= 0.0))
+    return MGR_ERR_INVALID_ARG;
+  if (!h->ready) return MGR_ERR_STATE;
+  if (A->nb != h->nb || A->nnzb != h->nnzb || !A->rowptr || !A->colind || !A->values) return MGR_ERR_INVALID_ARG;
+  mgr_status_t st = MGR_OK;
+  mgr_status_t g = guarded(h, [&] { st = do_fgmres(*h, *A, b, x, rtol, restart, maxit, info); });
+  return g != MGR_OK ? g : st;
+}
+
+mgr_status_t mgr_destroy(mgr_handle_t h) {
+  if (!h) return MGR_OK;
+  mgr_status_t st = guarded(h, [&] {
+    CU(cudaStreamSynchronize(h->c.s));
+    h->lev.clear();
+    h->amg.clear();
+  });
+  {
+    // remaining buffers are released by the destructor (stream-ordered frees)
+    cudaStream_t s = h->c.s;
+    int* e = h->c.d_err;
+    double* hp = h->hpin;
+    delete h;
+    cudaStreamSynchronize(s);
+    if (e) cudaFree(e);
+    if (hp) cudaFreeHost(hp);
+  }
+  return st;
+}
+
+mgr_status_t mgr_get_levels(mgr_handle_t h, int* mgr_levels, int* amg_levels) {
+  if (!h || !mgr_levels || !amg_levels) return MGR_ERR_INVALID_ARG;
+  if (!h->ready) return MGR_ERR_STATE;
+  *mgr_levels = h->L;
+  *amg_levels = (int)h->amg.size();
+  return MGR_OK;
+}
+
+mgr_status_t mgr_matrix_shape(mgr_handle_t h, int kind, int level, int64_t* nr, int64_t* nc, int64_t* nnz) {
+  if (!h || !nr || !nc || !nnz) return MGR_ERR_INVALID_ARG;
+  if (!h->ready) return MGR_ERR_STATE;
+  const DCSR<double>* m = pick_matrix(*h, kind, level);
+  if (!m || m->rp.p == nullptr) return MGR_ERR_INVALID_ARG;
+  *nr = m->nr; *nc = m->nc; *nnz = m->nnz;
+  return MGR_OK;
+}
+
+mgr_status_t mgr_copy_matrix(mgr_handle_t h, int kind, int level, int64_t* rowptr, int32_t* col, double* val) {
+  if (!h || !rowptr || !col) return MGR_ERR_INVALID_ARG;
+  if (!h->ready) return MGR_ERR_STATE;
+  const DCSR<double>* m = pick_matrix(*h, kind, level);
+  if (!m || m->rp.p == nullptr) return MGR_ERR_INVALID_ARG;
+  return guarded(h, [&] {
+    Ctx& c = h->c;
+    CU(cudaMemcpyAsync(rowptr, m->rp.p, sizeof(int64_t) * (m->nr + 1), cudaMemcpyDeviceToDevice, c.s));
+    if (m->nnz) CU(cudaMemcpyAsync(col, m->ci.p, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToDevice, c.s));
+    if (val && m->nnz) {
+      if (m->v.p) CU(cudaMemcpyAsync(val, m->v.p, sizeof(double) * m->nnz, cudaMemcpyDeviceToDevice, c.s));
+      else { k_fill_one<<<grid_for(m->nnz, 256), 256, 0, c.s>>>(m->nnz, val); CU_LAUNCH(); }
+    }
+    CU(cudaStreamSynchronize(c.s));
+      CU_LAUNCH();
+  });
+}
+
+mgr_status_t mgr_vector_len(mgr_handle_t h, int kind, int level, int64_t* len) {
+  if (!h || !len) return MGR_ERR_INVALID_ARG;
+  if (!h->ready) return MGR_ERR_STATE;
+  int na = (int)h->amg.size();
+  switch (kind) {
+    case 0: case 3: if (level < 0 || level >= h->L) return MGR_ERR_INVALID_ARG; *len = h->lev[level].nF; return MGR_OK;
+    case 4: if (level < 0 || level >= h->L) return MGR_ERR_INVALID_ARG; *len = h->lev[level].nC; return MGR_OK;
+    case 1: case 5: if (level < 0 || level >= na - 1) return MGR_ERR_INVALID_ARG; *len = h->amg[level].n; return MGR_OK;
+    case 2: *len = 9 * h->nb; return MGR_OK;
+  }
+  return MGR_ERR_INVALID_ARG;
+}
+
+mgr_status_t mgr_copy_vector(mgr_handle_t h, int kind, int level, double* out) {
+  int64_t len;
+  mgr_status_t st = mgr_vector_len(h, kind, level, &len);
+  if (st != MGR_OK) return st;
+  if (!out) return MGR_ERR_INVALID_ARG;
+  return guarded(h, [&] {
+    Ctx& c = h->c;
+    if (len > 0) {
+      unsigned g = grid_for(len, 256);
+      switch (kind) {
+        case 0: CU(cudaMemcpyAsync(out, h->lev[level].minv.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, c.s)); break;
+        case 1: CU(cudaMemcpyAsync(out, h->amg[level].dinv.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, c.s)); break;
+        case 2: CU(cudaMemcpyAsync(out, h->binv.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, c.s)); break;
+        case 3: k_to_double<int32_t><<<g, 256, 0, c.s>>>(len, h->lev[level].F.p, out); break;
+        case 4: k_to_double<int32_t><<<g, 256, 0, c.s>>>(len, h->lev[level].C.p, out); break;
+        case 5: k_to_double<int8_t><<<g, 256, 0, c.s>>>(len, h->amg[level].cf.p, out); break;
+      }
+      CU_LAUNCH();
+    }
+    CU(cudaStreamSynchronize(c.s));
+  });
+}
+
+mgr_status_t mgr_memory_bytes(mgr_handle_t h, int64_t* bytes) {
+  if (!h || !bytes) return MGR_ERR_INVALID_ARG;
+  *bytes = h->c.bytes;
+  return MGR_OK;
+}
+
+mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_launches, int64_t* graph_nodes,
+                           int64_t* total_launches) {
+  if (total_launches) *total_launches = (int64_t)g_launch_count;
+  if (!h) return setup_ms || apply_launches || graph_nodes ? MGR_ERR_INVALID_ARG : MGR_OK;
+  if (setup_ms) *setup_ms = h->setup_ms;
+  if (apply_launches) *apply_launches = h->apply_launches;
+  if (graph_nodes) *graph_nodes = 0;
+  return MGR_OK;
+}
+
+static mgr_status_t with_ctx(void* stream, const std::function<void(Ctx&)>& f);
+
+mgr_status_t mgr_bsr3_spmv(const mgr_bsr3_t* A, const double* x, const double* sub, double* y, void* stream) {
+  if (!A || !x || !y || A->nb <= 0 || !A->rowptr || !A->colind || !A->values) return MGR_ERR_INVALID_ARG;
+  return with_ctx(stream, [&](Ctx& c) { launch_bsr3_spmv_f64(c, *A, x, sub, y); });
+}
+
+mgr_status_t mgr_bsr3_transpose(const mgr_bsr3_t* A, int64_t* rpt, int32_t* cit, double* vt, void* stream) {
+  if (!A || !rpt || !cit || !vt || A->nb <= 0 || !A->rowptr || !A->colind || !A->values) return MGR_ERR_INVALID_ARG;
+  return with_ctx(stream, [&](Ctx& c) { launch_bsr3_transpose(c, *A, rpt, cit, vt); });
+}
+
+mgr_status_t mgr_bsr3_outer_grad(const mgr_bsr3_t* A, const double* lam, const double* x, double* g, void* stream) {
+  if (!A || !lam || !x || !g || A->nb <= 0 || !A->rowptr || !A->colind) return MGR_ERR_INVALID_ARG;
+  return with_ctx(stream, [&](Ctx& c) { launch_bsr3_outer_grad(c, *A, lam, x, g); });
+}
+
+}  // extern "C"
+
+static mgr_status_t with_ctx(void* stream, const std::function<void(Ctx&)>& f) {
+  Ctx c;
+  c.s = static_cast<cudaStream_t>(stream);
+  try {
+    f(c);
+    return MGR_OK;
+  } catch (...) {
+    return guard_status(std::current_exception(), nullptr);
+  }
+}

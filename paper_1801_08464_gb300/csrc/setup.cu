@@ -1,0 +1,746 @@
+// setup.cu -- MGR reduction levels and the AMG hierarchy (compiled with --fmad=false).
+//
+// The arithmetic follows a fixed order of IEEE double operations (explicit __dmul_rn, __dadd_rn,
+// __ddiv_rn), so every value and every floating-point decision (strength, PMIS weights, lumping)
+// is reproducible.
+#include <cmath>
+
+#include "hier.cuh"
+
+namespace mgr {
+
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
+
+__device__ __forceinline__ double csr_get(const int64_t* rp, const int32_t* ci, const double* v, int64_t i, int32_t j) {
+  int64_t p = find_i32(ci, rp[i], rp[i + 1], j);
+  return p >= 0 ? v[p] : 0.0;
+}
+
+// ============================== MGR reduction level (sections 4-5) =============================
+__global__ void k_level_flags(int64_t n, const int8_t* mk, int l, int32_t* ff, int32_t* cf) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ff[i] = (mk[i] == l);
+  cf[i] = (mk[i] > l);
+}
+__global__ void k_level_lists(int64_t n, const int8_t* mk, int l, const int32_t* fpre, const int32_t* cpre, int32_t* F,
+                              int32_t* C, int32_t* map) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (mk[i] == l) { F[fpre[i]] = (int32_t)i; map[i] = -(fpre[i] + 1); }
+  else { C[cpre[i]] = (int32_t)i; map[i] = cpre[i]; }
+}
+
+// D_ff = diag(A_ff) and the F-relaxation scaling: omega / d (Jacobi) or 1 / (d + sign(d) l1) with
+// l1 = sum of |a_fg| over the off-diagonal F columns of the row, ascending.
+__global__ void k_dff_minv(int64_t nF, const int32_t* F, const int64_t* rp, const int32_t* ci, const double* v,
+                           const int32_t* map, int type, double omega, double* dff, double* minv, int* err) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nF) return;
+  int32_t i = F[f];
+  double d = 0.0, l1 = 0.0;
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+    int32_t j = ci[k];
+    if (j == i) d = v[k];
+    else if (map[j] < 0) l1 = dd(l1, fabs(v[k]));
+  }
+  dff[f] = d;
+  if (d == 0.0 || !isfinite(d)) { atomicOr(err, EBIT_SINGULAR); minv[f] = 0.0; return; }
+  if (type == 1) {
+    double den = dd(d, (d >= 0.0) ? l1 : -l1);
+    minv[f] = dv(1.0, den);
+  } else {
+    minv[f] = dv(omega, d);
+  }
+}
+
+// per-row counts of entries of rows `rows` of A whose column satisfies sel (C: map >= 0, F: map < 0)
+template <bool WANT_C>
+__global__ void k_count_sel(int64_t nr, const int32_t* rows, const int64_t* rp, const int32_t* ci, const int32_t* map,
+                            int64_t* cnt) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  int32_t i = rows[r];
+  int64_t s = 0;
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) s += WANT_C ? (map[ci[k]] >= 0) : (map[ci[k]] < 0);
+  cnt[r] = s;
+}
+
+// W_p = -D_ff^-1 A_fc (rows F, coarse columns) and A_ff (rows F, F-local columns)
+__global__ void k_fill_wp_aff(int64_t nF, const int32_t* F, const int64_t* rp, const int32_t* ci, const double* v,
+                              const int32_t* map, const double* dff, const int64_t* wrp, int32_t* wci, double* wv,
+                              const int64_t* frp, int32_t* fci, double* fv) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nF) return;
+  int32_t i = F[f];
+  int64_t ow = wrp[f], of = frp[f];
+  double d = dff[f];
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+    int32_t m = map[ci[k]];
+    if (m >= 0) { wci[ow] = m; wv[ow] = -dv(v[k], d); ++ow; }
+    else { fci[of] = -m - 1; fv[of] = v[k]; ++of; }
+  }
+}
+
+// A_cf (rows C, F-local columns), and for a non-injective restriction W_r = -A_cf D_ff^-1 and the
+// rows of R = [W_r, I] in fine column order (the 1 placed at the C point's own column).
+__global__ void k_fill_acf_wr(int64_t nC, const int32_t* C, const int64_t* rp, const int32_t* ci, const double* v,
+                              const int32_t* map, const double* dff, int noninj, const int64_t* arp, int32_t* aci,
+                              double* av, const int64_t* wrp, int32_t* wci, double* wv, const int64_t* rrp, int32_t* rci,
+                              double* rv) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nC) return;
+  int32_t i = C[c];
+  int64_t oa = arp[c], ow = noninj ? wrp[c] : 0, orr = rrp[c];
+  bool placed = false;
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+    int32_t j = ci[k], m = map[j];
+    if (m >= 0) continue;
+    int32_t f = -m - 1;
+    aci[oa] = f; av[oa] = v[k]; ++oa;
+    if (noninj) {
+      double w = -dv(v[k], dff[f]);
+      wci[ow] = f; wv[ow] = w; ++ow;
+      if (!placed && j > i) { rci[orr] = i; rv[orr] = 1.0; ++orr; placed = true; }
+      rci[orr] = j; rv[orr] = w; ++orr;
+    }
+  }
+  if (!placed) { rci[orr] = i; rv[orr] = 1.0; }
+}
+
+// P = [W_p; I] in fine row order
+__global__ void k_p_count(int64_t n, const int32_t* map, const int64_t* wrp, int64_t* cnt) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t m = map[i];
+  cnt[i] = (m >= 0) ? 1 : (wrp[-m] - wrp[-m - 1]);
+}
+__global__ void k_p_fill(int64_t n, const int32_t* map, const int64_t* wrp, const int32_t* wci, const double* wv,
+                         const int64_t* prp, int32_t* pci, double* pv) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t m = map[i];
+  int64_t o = prp[i];
+  if (m >= 0) { pci[o] = m; pv[o] = 1.0; return; }
+  int32_t f = -m - 1;
+  for (int64_t k = wrp[f]; k < wrp[f + 1]; ++k, ++o) { pci[o] = wci[k]; pv[o] = wv[k]; }
+}
+__global__ void k_gather_i8(int64_t n, const int32_t* idx, const int8_t* src, int8_t* dst) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[idx[i]];
+}
+__global__ void k_i64_add_one(int64_t n, int64_t* a) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] += 1;
+}
+
+static void alloc_csr(Ctx& c, DCSR<double>& M, int64_t nr, int64_t nc, const int64_t* cnt) {
+  M.nr = nr;
+  M.nc = nc;
+  M.rp.alloc(c, nr + 1);
+  M.nnz = counts_to_rowptr(c, cnt, M.rp.p, nr);
+  M.ci.alloc(c, M.nnz);
+  M.v.alloc(c, M.nnz);
+}
+
+void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<double>& Anext, DBuf<int8_t>& mk_next) {
+  int64_t n = L.n;
+  const DCSR<double>& A = L.A;
+  const int B = 256;
+  {
+    DBuf<int32_t> ff(c, n), cf(c, n), fpre(c, n + 1), cpre(c, n + 1);
+    k_level_flags<<<grid_for(n, B), B, 0, c.s>>>(n, L.mk.p, l, ff.p, cf.p);
+    CU_LAUNCH();
+    scan_excl_i32(c, ff.p, fpre.p, n);
+    scan_excl_i32(c, cf.p, cpre.p, n);
+    L.nF = read_scalar(c, fpre.p + n);
+    L.nC = read_scalar(c, cpre.p + n);
+    L.F.alloc(c, L.nF);
+    L.C.alloc(c, L.nC);
+    L.map.alloc(c, n);
+    k_level_lists<<<grid_for(n, B), B, 0, c.s>>>(n, L.mk.p, l, fpre.p, cpre.p, L.F.p, L.C.p, L.map.p);
+    CU_LAUNCH();
+  }
+  if (L.nC == 0) throw Error(MGR_ERR_INVALID_ARG, "cf_marker: a reduction level has no C point");
+  int64_t nF = L.nF, nC = L.nC;
+  L.sweeps = o.sweeps;
+  L.dff.alloc(c, nF);
+  L.minv.alloc(c, nF);
+  if (nF) {
+    k_dff_minv<<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, A.v.p, L.map.p, o.frelax_type, o.omega,
+                                                L.dff.p, L.minv.p, c.d_err);
+    CU_LAUNCH();
+  }
+  check_errors(c, "MGR D_ff");
+  // W_p and A_ff
+  {
+    DBuf<int64_t> cw(c, nF + 1), cfcnt(c, nF + 1);
+    if (nF) {
+      k_count_sel<true><<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, L.map.p, cw.p);
+      CU_LAUNCH();
+      k_count_sel<false><<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, L.map.p, cfcnt.p);
+      CU_LAUNCH();
+    }
+    alloc_csr(c, L.Wp, nF, nC, cw.p);
+    alloc_csr(c, L.Aff, nF, nF, cfcnt.p);
+    if (nF) {
+      k_fill_wp_aff<<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, L.Wp.rp.p,
+                                                    L.Wp.ci.p, L.Wp.v.p, L.Aff.rp.p, L.Aff.ci.p, L.Aff.v.p);
+      CU_LAUNCH();
+    }
+  }
+  // A_cf, W_r, R
+  {
+    DBuf<int64_t> ca(c, nC + 1);
+    k_count_sel<false><<<grid_for(nC, B), B, 0, c.s>>>(nC, L.C.p, A.rp.p, A.ci.p, L.map.p, ca.p);
+    CU_LAUNCH();
+    alloc_csr(c, L.Acf, nC, nF, ca.p);
+    bool noninj = o.restrict_type == 1;
+    if (noninj) {
+      alloc_csr(c, L.Wr, nC, nF, ca.p);
+      k_i64_add_one<<<grid_for(nC, B), B, 0, c.s>>>(nC, ca.p);
+      CU_LAUNCH();
+    } else {
+      L.Wr.nr = nC; L.Wr.nc = nF; L.Wr.nnz = 0;
+      L.Wr.rp.alloc(c, nC + 1);
+      fill_i64(c, L.Wr.rp.p, 0, nC + 1);
+      L.Wr.ci.alloc(c, 0);
+      L.Wr.v.alloc(c, 0);
+      fill_i64(c, ca.p, 1, nC);
+    }
+    alloc_csr(c, L.R, nC, n, ca.p);
+    k_fill_acf_wr<<<grid_for(nC, B), B, 0, c.s>>>(nC, L.C.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, noninj ? 1 : 0,
+                                                   L.Acf.rp.p, L.Acf.ci.p, L.Acf.v.p, L.Wr.rp.p, L.Wr.ci.p, L.Wr.v.p,
+                                                   L.R.rp.p, L.R.ci.p, L.R.v.p);
+    CU_LAUNCH();
+  }
+  // P = [W_p; I]
+  {
+    DBuf<int64_t> cp(c, n + 1);
+    k_p_count<<<grid_for(n, B), B, 0, c.s>>>(n, L.map.p, L.Wp.rp.p, cp.p);
+    CU_LAUNCH();
+    alloc_csr(c, L.P, n, nC, cp.p);
+    k_p_fill<<<grid_for(n, B), B, 0, c.s>>>(n, L.map.p, L.Wp.rp.p, L.Wp.ci.p, L.Wp.v.p, L.P.rp.p, L.P.ci.p, L.P.v.p);
+    CU_LAUNCH();
+  }
+  // coarse operator R (A P) and coarse markers
+  {
+    DCSR<double> AP;
+    spgemm(c, A, L.P, AP);
+    spgemm(c, L.R, AP, Anext);
+  }
+  mk_next.alloc(c, nC);
+  k_gather_i8<<<grid_for(nC, B), B, 0, c.s>>>(nC, L.C.p, L.mk.p, mk_next.p);
+  CU_LAUNCH();
+}
+
+// ===================================== AMG (coarse solve) =====================================
+// Strength: with s = +1 if a_ii >= 0 else -1, j != i is strong iff -s a_ij >= theta m where
+// m = max(0, max_{k != i} -s a_ik) > 0.  A warp per row; MODE 0 counts, MODE 1 writes in order.
+template <int MODE>
+__global__ void k_strength(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, double theta, int64_t* cnt,
+                           const int64_t* srp, int32_t* sci) {
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  int64_t b = rp[i], e = rp[i + 1];
+  double d = 0.0;
+  for (int64_t k = b + lane; k < e; k += 32)
+    if (ci[k] == i) d = v[k];
+  for (int o = 16; o > 0; o >>= 1) {
+    double t = __shfl_xor_sync(0xffffffffu, d, o);
+    if (t != 0.0) d = t;
+  }
+  double s = (d >= 0.0) ? 1.0 : -1.0;
+  double m = 0.0;
+  for (int64_t k = b + lane; k < e; k += 32)
+    if (ci[k] != i) {
+      double x = -dm(s, v[k]);
+      if (x > m) m = x;
+    }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int64_t count = 0, out = (MODE == 1) ? srp[i] : 0;
+  if (m > 0.0) {
+    double thr = dm(theta, m);
+    for (int64_t k0 = b; k0 < e; k0 += 32) {
+      int64_t k = k0 + lane;
+      bool strong = false;
+      if (k < e && ci[k] != i) strong = (-dm(s, v[k]) >= thr);
+      unsigned msk = __ballot_sync(0xffffffffu, strong);
+      if (MODE == 1 && strong) sci[out + __popc(msk & ((1u << lane) - 1))] = ci[k];
+      count += __popc(msk);
+      out += __popc(msk);
+    }
+  }
+  if (MODE == 0 && lane == 0) cnt[i] = count;
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// PMIS weight w_i = |S^T_i| + u_i, u_i = top 53 bits of splitmix64(key ^ i) times 2^-53 with
+// key = splitmix64(seed ^ ((level + 1) << 48)); points influencing nobody start as F.
+__global__ void k_pmis_init(int64_t n, const int64_t* strp, uint64_t key, double* w, int8_t* st, int* und) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t lam = strp[i + 1] - strp[i];
+  double u = (double)(splitmix64(key ^ (uint64_t)i) >> 11) * 0x1.0p-53;
+  w[i] = dd((double)lam, u);
+  st[i] = lam == 0 ? -1 : 0;
+  if (lam) atomicAdd(und, 1);
+}
+// an undecided point beating every undecided strong neighbour (S and S^T; equal weights -> larger
+// index wins) is selected
+__global__ void k_pmis_select(int64_t n, const int64_t* srp, const int32_t* sci, const int64_t* trp, const int32_t* tci,
+                              const double* w, const int8_t* st, int8_t* nc) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  nc[i] = 0;
+  if (st[i] != 0) return;
+  double wi = w[i];
+  for (int pass = 0; pass < 2; ++pass) {
+    const int64_t* rp = pass ? trp : srp;
+    const int32_t* ci = pass ? tci : sci;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      int32_t j = ci[k];
+      if (j == i || st[j] != 0) continue;
+      double wj = w[j];
+      if (wj > wi || (wj == wi && j > i)) return;
+    }
+  }
+  nc[i] = 1;
+}
+__global__ void k_pmis_mark_c(int64_t n, const int8_t* nc, int8_t* st) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && nc[i]) st[i] = 1;
+}
+// undecided points that strongly depend on a C point become F; count what stays undecided
+__global__ void k_pmis_mark_f(int64_t n, const int64_t* srp, const int32_t* sci, int8_t* st, int* und) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n || st[i] != 0) return;
+  for (int64_t k = srp[i]; k < srp[i + 1]; ++k)
+    if (st[sci[k]] == 1) { st[i] = -1; return; }
+  atomicAdd(und, 1);
+}
+
+// Selection matrices for the extended+i pattern: M row i (F point) = {i} + strong F neighbours,
+// T row k = strong C neighbours of k as coarse indices; pattern(P_F) = pattern(M T).
+__global__ void k_extpi_sel_count(int64_t n, const int64_t* srp, const int32_t* sci, const int8_t* cf, int64_t* cm,
+                                  int64_t* ct) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t a = 0, b = 0;
+  for (int64_t k = srp[i]; k < srp[i + 1]; ++k) {
+    if (cf[sci[k]] == 1) ++b; else ++a;
+  }
+  cm[i] = (cf[i] == 1) ? 0 : a + 1;
+  ct[i] = b;
+}
+__global__ void k_extpi_sel_fill(int64_t n, const int64_t* srp, const int32_t* sci, const int8_t* cf, const int32_t* cidx,
+                                 const int64_t* mrp, int32_t* mci, const int64_t* trp, int32_t* tci) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t om = mrp[i], ot = trp[i];
+  bool fpt = cf[i] != 1, placed = false;
+  for (int64_t k = srp[i]; k < srp[i + 1]; ++k) {
+    int32_t j = sci[k];
+    if (cf[j] == 1) { tci[ot++] = cidx[j]; continue; }
+    if (!fpt) continue;
+    if (!placed && j > i) { mci[om++] = (int32_t)i; placed = true; }
+    mci[om++] = j;
+  }
+  if (fpt && !placed) mci[om] = (int32_t)i;
+}
+__global__ void k_cidx(int64_t n, const int8_t* cf, const int32_t* pre, int32_t* cidx, int32_t* cfine) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (cf[i] == 1) { cidx[i] = pre[i]; cfine[pre[i]] = (int32_t)i; }
+  else cidx[i] = -1;
+}
+__global__ void k_flag_c(int64_t n, const int8_t* cf, int32_t* f) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) f[i] = cf[i] == 1;
+}
+__global__ void k_pfull_count(int64_t n, const int8_t* cf, const int64_t* qrp, int64_t* cnt) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) cnt[i] = (cf[i] == 1) ? 1 : qrp[i + 1] - qrp[i];
+}
+__global__ void k_pfull_fill(int64_t n, const int8_t* cf, const int32_t* cidx, const int64_t* qrp, const int32_t* qci,
+                             const int64_t* prp, int32_t* pci) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = prp[i];
+  if (cf[i] == 1) { pci[o] = cidx[i]; return; }
+  for (int64_t k = qrp[i]; k < qrp[i + 1]; ++k) pci[o++] = qci[k];
+}
+
+__device__ __forceinline__ bool opposite(double a, double d) { return (d > 0.0 && a < 0.0) || (d < 0.0 && a > 0.0); }
+
+// Extended+i weights (De Sterck, Falgout, Nolting & Yang 2008), one warp per F row; the pattern
+// (Chat_i, coarse indices, ascending) is already in P.  Per strong F neighbour k (position p in S_i):
+//   den_k = sum over l in row k (ascending) with l in Chat_i + {i} and a_kl opposite in sign to a_kk
+//   of a_kl; q_k = a_ik / den_k, or a_ik lumped into the diagonal when den_k == 0.
+//   at = a_ii + sum(weak neighbours not in Chat_i, ascending) + sum_k (q_k abar_ki or a_ik);
+//   w_ij = -(a_ij + sum_k q_k abar_kj) / at.   An F row with at == 0 is flagged empty.
+__global__ void k_extpi_weights(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* srp,
+                                const int32_t* sci, const int8_t* cf, const int32_t* cidx, const int32_t* cfine,
+                                const int64_t* prp, const int32_t* pci, double* pv, double* den_g, double* q_g,
+                                int8_t* rowzero) {
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  if (cf[i] == 1) {
+    if (lane == 0) { pv[prp[i]] = 1.0; rowzero[i] = 0; }
+    return;
+  }
+  int64_t p0 = prp[i], p1 = prp[i + 1];
+  int64_t s0 = srp[i], s1 = srp[i + 1];
+  // den_k
+  for (int64_t p = s0 + lane; p < s1; p += 32) {
+    int32_t k = sci[p];
+    if (cf[k] == 1) continue;
+    double akk = csr_get(rp, ci, v, k, k), den = 0.0;
+    for (int64_t q = rp[k]; q < rp[k + 1]; ++q) {
+      int32_t l = ci[q];
+      bool in = (l == i) || (cf[l] == 1 && find_i32(pci, p0, p1, cidx[l]) >= 0);
+      if (in && opposite(v[q], akk)) den = dd(den, v[q]);
+    }
+    den_g[p] = den;
+  }
+  __syncwarp();
+  double at = 0.0;
+  if (lane == 0) {
+    at = csr_get(rp, ci, v, i, (int32_t)i);
+    for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
+      int32_t nn = ci[q];
+      if (nn == i) continue;
+      if (find_i32(sci, s0, s1, nn) >= 0) continue;
+      if (cf[nn] == 1 && find_i32(pci, p0, p1, cidx[nn]) >= 0) continue;
+      at = dd(at, v[q]);
+    }
+    for (int64_t p = s0; p < s1; ++p) {
+      int32_t k = sci[p];
+      if (cf[k] == 1) continue;
+      double aik = csr_get(rp, ci, v, i, k), den = den_g[p];
+      if (den != 0.0) {
+        double q = dv(aik, den);
+        q_g[p] = q;
+        double aki = csr_get(rp, ci, v, k, (int32_t)i), akk = csr_get(rp, ci, v, k, k);
+        if (opposite(aki, akk)) at = dd(at, dm(q, aki));
+      } else {
+        q_g[p] = 0.0;
+        at = dd(at, aik);
+      }
+    }
+    rowzero[i] = (at == 0.0);
+  }
+  at = __shfl_sync(0xffffffffu, at, 0);
+  __syncwarp();
+  for (int64_t t = p0 + lane; t < p1; t += 32) {
+    int32_t jf = cfine[pci[t]];
+    double num = csr_get(rp, ci, v, i, jf);
+    for (int64_t p = s0; p < s1; ++p) {
+      int32_t k = sci[p];
+      if (cf[k] == 1 || den_g[p] == 0.0) continue;
+      double akj = csr_get(rp, ci, v, k, jf);
+      if (opposite(akj, csr_get(rp, ci, v, k, k))) num = dd(num, dm(q_g[p], akj));
+    }
+    pv[t] = (at != 0.0) ? -dv(num, at) : 0.0;
+  }
+}
+
+// Keep / truncation: an empty-flagged row keeps nothing; with pmax > 0 a longer F row keeps its pmax
+// largest |w| (ties: smaller column) scaled by (sum of all w) / (sum of kept w), sums ascending.
+__global__ void k_ptrunc(int64_t n, const int8_t* cf, const int64_t* prp, const double* pv, const int8_t* rowzero,
+                         int pmax, int8_t* keep, double* scale, int64_t* cnt) {
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  int64_t p0 = prp[i], p1 = prp[i + 1];
+  int64_t L = p1 - p0;
+  bool trunc = cf[i] != 1 && !rowzero[i] && pmax > 0 && L > pmax;
+  bool none = cf[i] != 1 && rowzero[i];
+  for (int64_t t = p0 + lane; t < p1; t += 32) {
+    int8_t k = none ? 0 : 1;
+    if (trunc) {
+      double a = fabs(pv[t]);
+      int64_t rank = 0;
+      for (int64_t u = p0; u < p1; ++u) {
+        double b = fabs(pv[u]);
+        rank += (b > a) || (b == a && u < t);
+      }
+      k = rank < pmax;
+    }
+    keep[t] = k;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double f = 1.0;
+    if (trunc) {
+      double sall = 0.0, skeep = 0.0;
+      for (int64_t t = p0; t < p1; ++t) sall = dd(sall, pv[t]);
+      for (int64_t t = p0; t < p1; ++t)
+        if (keep[t]) skeep = dd(skeep, pv[t]);
+      f = (skeep != 0.0) ? dv(sall, skeep) : 1.0;
+    }
+    scale[i] = f;
+    cnt[i] = none ? 0 : (trunc ? pmax : L);
+  }
+}
+__global__ void k_pcompact(int64_t n, const int64_t* prp, const int32_t* pci, const double* pv, const int8_t* keep,
+                           const double* scale, bool scaled_rows_only, const int64_t* orp, int32_t* oci, double* ov) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = orp[i];
+  double f = scale[i];
+  bool full = (orp[i + 1] - o) == (prp[i + 1] - prp[i]);
+  for (int64_t t = prp[i]; t < prp[i + 1]; ++t)
+    if (keep[t]) { oci[o] = pci[t]; ov[o] = full ? pv[t] : dm(pv[t], f); ++o; }
+}
+
+// smoother scaling: l1-Jacobi 1/(a_ii + sign(a_ii) sum_{j!=i}|a_ij|) or omega / a_ii
+__global__ void k_smoother_diag(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, int type, double omega,
+                                double* dinv, int* err) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double d = 0.0, l1 = 0.0;
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+    if (ci[k] == i) d = v[k];
+    else l1 = dd(l1, fabs(v[k]));
+  }
+  double den = (type == 1) ? dd(d, (d >= 0.0) ? l1 : -l1) : d;
+  if (den == 0.0 || !isfinite(den)) { atomicOr(err, EBIT_SINGULAR); dinv[i] = 0.0; return; }
+  dinv[i] = (type == 1) ? dv(1.0, den) : dv(omega, den);
+}
+
+static uint64_t host_splitmix64(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+static void strength(Ctx& c, const DCSR<double>& A, double theta, DCSR<double>& S) {
+  int64_t n = A.nr;
+  DBuf<int64_t> cnt(c, n + 1);
+  unsigned g = grid_for(n * 32, 256);
+  k_strength<0><<<g, 256, 0, c.s>>>(n, A.rp, A.ci, A.v, theta, cnt.p, nullptr, nullptr);
+  CU_LAUNCH();
+  S.nr = S.nc = n;
+  S.rp.alloc(c, n + 1);
+  S.nnz = counts_to_rowptr(c, cnt.p, S.rp.p, n);
+  S.ci.alloc(c, S.nnz);
+  k_strength<1><<<g, 256, 0, c.s>>>(n, A.rp, A.ci, A.v, theta, nullptr, S.rp.p, S.ci.p);
+  CU_LAUNCH();
+}
+
+static void pmis(Ctx& c, const DCSR<double>& S, uint64_t seed, int lev, DBuf<int8_t>& cf) {
+  int64_t n = S.nr;
+  DCSR<double> St;
+  transpose(c, S, St);
+  DBuf<double> w(c, n);
+  DBuf<int8_t> nc(c, n);
+  DBuf<int> und(c, 1);
+  cf.alloc(c, n);
+  const int B = 256;
+  uint64_t key = host_splitmix64(seed ^ ((uint64_t)(lev + 1) << 48));
+  CU(cudaMemsetAsync(und.p, 0, sizeof(int), c.s));
+  k_pmis_init<<<grid_for(n, B), B, 0, c.s>>>(n, St.rp, key, w.p, cf.p, und.p);
+  CU_LAUNCH();
+  int left = read_scalar(c, und.p);
+  int rounds = 0;
+  while (left > 0) {
+    if (++rounds > 10000) throw Error(MGR_ERR_CUDA, "PMIS did not terminate");
+    k_pmis_select<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, St.rp, St.ci, w.p, cf.p, nc.p);
+    CU_LAUNCH();
+    k_pmis_mark_c<<<grid_for(n, B), B, 0, c.s>>>(n, nc.p, cf.p);
+    CU_LAUNCH();
+    CU(cudaMemsetAsync(und.p, 0, sizeof(int), c.s));
+    k_pmis_mark_f<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, cf.p, und.p);
+    CU_LAUNCH();
+    left = read_scalar(c, und.p);
+  }
+}
+
+static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DBuf<int8_t>& cf, int64_t nC, int pmax,
+                  DCSR<double>& P) {
+  int64_t n = A.nr;
+  const int B = 256;
+  DBuf<int32_t> flag(c, n), pre(c, n + 1), cidx(c, n), cfine(c, nC + 1);
+  k_flag_c<<<grid_for(n, B), B, 0, c.s>>>(n, cf.p, flag.p);
+  CU_LAUNCH();
+  scan_excl_i32(c, flag.p, pre.p, n);
+  k_cidx<<<grid_for(n, B), B, 0, c.s>>>(n, cf.p, pre.p, cidx.p, cfine.p);
+  CU_LAUNCH();
+  // selection matrices and the symbolic product
+  DCSR<double> M, T, Q;
+  {
+    DBuf<int64_t> cm(c, n + 1), ct(c, n + 1);
+    k_extpi_sel_count<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, cf.p, cm.p, ct.p);
+    CU_LAUNCH();
+    M.nr = n; M.nc = n; M.rp.alloc(c, n + 1); M.nnz = counts_to_rowptr(c, cm.p, M.rp.p, n); M.ci.alloc(c, M.nnz);
+    T.nr = n; T.nc = nC; T.rp.alloc(c, n + 1); T.nnz = counts_to_rowptr(c, ct.p, T.rp.p, n); T.ci.alloc(c, T.nnz);
+    k_extpi_sel_fill<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, cf.p, cidx.p, M.rp, M.ci, T.rp, T.ci);
+    CU_LAUNCH();
+  }
+  spgemm_symbolic(c, M, T, Q);
+  DCSR<double> Pf;
+  {
+    DBuf<int64_t> cnt(c, n + 1);
+    k_pfull_count<<<grid_for(n, B), B, 0, c.s>>>(n, cf.p, Q.rp, cnt.p);
+    CU_LAUNCH();
+    alloc_csr(c, Pf, n, nC, cnt.p);
+    k_pfull_fill<<<grid_for(n, B), B, 0, c.s>>>(n, cf.p, cidx.p, Q.rp, Q.ci, Pf.rp, Pf.ci);
+    CU_LAUNCH();
+  }
+  DBuf<double> den(c, S.nnz + 1), q(c, S.nnz + 1), scale(c, n);
+  DBuf<int8_t> rowzero(c, n), keep(c, Pf.nnz + 1);
+  k_extpi_weights<<<grid_for(n * 32, 128), 128, 0, c.s>>>(n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp,
+                                                           Pf.ci, Pf.v, den.p, q.p, rowzero.p);
+  CU_LAUNCH();
+  DBuf<int64_t> cnt(c, n + 1);
+  k_ptrunc<<<grid_for(n * 32, 128), 128, 0, c.s>>>(n, cf.p, Pf.rp, Pf.v, rowzero.p, pmax, keep.p, scale.p, cnt.p);
+  CU_LAUNCH();
+  alloc_csr(c, P, n, nC, cnt.p);
+  k_pcompact<<<grid_for(n, B), B, 0, c.s>>>(n, Pf.rp, Pf.ci, Pf.v, keep.p, scale.p, true, P.rp, P.ci, P.v);
+  CU_LAUNCH();
+}
+
+void amg_build(Ctx& c, const DCSR<double>& A0, const AmgOpts& o, std::vector<AmgLevel>& lv, DBuf<double>& cinv,
+               int64_t& nco) {
+  lv.clear();
+  lv.emplace_back();
+  copy_csr(c, A0, lv[0].A);
+  lv[0].n = A0.nr;
+  int maxlev = o.max_levels;
+  const int B = 256;
+  int k = 0;
+  while (lv[k].n > o.max_coarse && k < maxlev - 1) {
+    AmgLevel& L = lv[k];
+    int64_t n = L.n;
+    strength(c, L.A, o.theta, L.S);
+    pmis(c, L.S, o.seed, k, L.cf);
+    int64_t nC;
+    {
+      DBuf<int32_t> flag(c, n), pre(c, n + 1);
+      k_flag_c<<<grid_for(n, B), B, 0, c.s>>>(n, L.cf.p, flag.p);
+      CU_LAUNCH();
+      scan_excl_i32(c, flag.p, pre.p, n);
+      nC = read_scalar(c, pre.p + n);
+    }
+    if (nC == 0 || nC == n) {
+      L.cf.release();
+      L.S = DCSR<double>();
+      break;
+    }
+    extpi(c, L.A, L.S, L.cf, nC, o.pmax, L.P);
+    transpose(c, L.P, L.R);
+    L.dinv.alloc(c, n);
+    k_smoother_diag<<<grid_for(n, B), B, 0, c.s>>>(n, L.A.rp, L.A.ci, L.A.v, o.smoother, o.omega, L.dinv.p, c.d_err);
+    CU_LAUNCH();
+    check_errors(c, "AMG smoother diagonal");
+    AmgLevel next;
+    {
+      DCSR<double> AP;
+      spgemm(c, L.A, L.P, AP);
+      spgemm(c, L.R, AP, next.A);
+    }
+    next.n = nC;
+    lv.push_back(std::move(next));
+    ++k;
+  }
+  nco = lv.back().n;
+  if (nco > 4096) throw Error(MGR_ERR_UNSUPPORTED, "AMG coarsest grid larger than 4096 rows");
+  dense_inverse(c, lv.back().A, cinv);
+  check_errors(c, "AMG coarsest inverse");
+}
+
+// ===================================== dense inverse ==========================================
+__global__ void k_dense_from_csr(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, double* M) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double* row = M + i * 2 * n;
+  for (int64_t j = 0; j < 2 * n; ++j) row[j] = 0.0;
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) row[ci[k]] = dd(row[ci[k]], v[k]);
+  row[n + i] = 1.0;
+}
+// pivot search on column k (rows k..n-1, largest |.|, first on ties), row swap and row scaling
+__global__ void k_gj_pivot(int64_t n, int64_t k, double* M, int* err) {
+  __shared__ double bv[1024];
+  __shared__ int64_t bi[1024];
+  int64_t w = 2 * n;
+  double best = -1.0;
+  int64_t arg = n;
+  for (int64_t i = k + threadIdx.x; i < n; i += blockDim.x) {
+    double a = fabs(M[i * w + k]);
+    if (a > best) { best = a; arg = i; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = arg;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double a = bv[threadIdx.x + s];
+      int64_t ia = bi[threadIdx.x + s];
+      if (a > bv[threadIdx.x] || (a == bv[threadIdx.x] && ia < bi[threadIdx.x])) { bv[threadIdx.x] = a; bi[threadIdx.x] = ia; }
+    }
+    __syncthreads();
+  }
+  int64_t p = bi[0];
+  if (bv[0] == 0.0 || !isfinite(bv[0]) || p >= n) {
+    if (threadIdx.x == 0) atomicOr(err, EBIT_SINGULAR);
+    return;
+  }
+  if (p != k)
+    for (int64_t j = threadIdx.x; j < w; j += blockDim.x) {
+      double t = M[k * w + j];
+      M[k * w + j] = M[p * w + j];
+      M[p * w + j] = t;
+    }
+  __syncthreads();
+  double piv = M[k * w + k];
+  __syncthreads();
+  for (int64_t j = threadIdx.x; j < w; j += blockDim.x) M[k * w + j] = dv(M[k * w + j], piv);
+}
+// eliminate column k from every other row (one block per row)
+__global__ void k_gj_eliminate(int64_t n, int64_t k, double* M) {
+  int64_t i = blockIdx.x;
+  if (i == k) return;
+  int64_t w = 2 * n;
+  __shared__ double f;
+  if (threadIdx.x == 0) f = M[i * w + k];
+  __syncthreads();
+  if (f == 0.0) return;
+  for (int64_t j = threadIdx.x; j < w; j += blockDim.x) M[i * w + j] = __dsub_rn(M[i * w + j], dm(f, M[k * w + j]));
+}
+__global__ void k_dense_right_half(int64_t n, const double* M, double* inv) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  int64_t i = t / n, j = t - i * n;
+  inv[t] = M[i * 2 * n + n + j];
+}
+
+void dense_inverse(Ctx& c, const DCSR<double>& A, DBuf<double>& inv) {
+  int64_t n = A.nr;
+  inv.alloc(c, n * n);
+  if (n == 0) return;
+  DBuf<double> M(c, 2 * n * n);
+  k_dense_from_csr<<<grid_for(n, 128), 128, 0, c.s>>>(n, A.rp, A.ci, A.v, M.p);
+  CU_LAUNCH();
+  for (int64_t k = 0; k < n; ++k) {
+    k_gj_pivot<<<1, 1024, 0, c.s>>>(n, k, M.p, c.d_err);
+    CU_LAUNCH();
+    k_gj_eliminate<<<(unsigned)n, 128, 0, c.s>>>(n, k, M.p);
+    CU_LAUNCH();
+  }
+  k_dense_right_half<<<grid_for(n * n, 256), 256, 0, c.s>>>(n, M.p, inv.p);
+  CU_LAUNCH();
+}
+
+}  // namespace mgr

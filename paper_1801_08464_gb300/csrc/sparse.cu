@@ -1,0 +1,667 @@
+// sparse.cu -- deterministic FP64 sparse setup primitives (compiled with --fmad=false).
+//
+// Every floating-point result here is produced by a fixed sequence of IEEE double operations
+// (explicit __dmul_rn / __dadd_rn, no fused multiply-add, fixed summation order), so the products
+// are reproducible bit for bit and independent of the launch configuration.
+#include <climits>
+
+#include "common.cuh"
+
+namespace mgr {
+
+// ---------------------------------------------------------------------------------------------
+// BSR validation: rowptr starts at 0, ends at nnzb and is non-decreasing; columns in range and
+// strictly ascending; each block row holds its diagonal block; markers in [0, MGR_MAX_LEVELS).
+__global__ void k_bsr_validate(int64_t nb, int64_t nnzb, const int64_t* rp, const int32_t* ci, const int8_t* mk,
+                               int* err) {
+  int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= nb) return;
+  int64_t b = rp[I], e = rp[I + 1];
+  bool ok = (b <= e) && (b >= 0) && (e <= nnzb);
+  if (I == 0 && b != 0) ok = false;
+  if (I == nb - 1 && e != nnzb) ok = false;
+  bool diag = false;
+  if (ok) {
+    int32_t prev = -1;
+    for (int64_t k = b; k < e; ++k) {
+      int32_t j = ci[k];
+      if (j < 0 || j >= nb || j <= prev) { ok = false; break; }
+      if (j == I) diag = true;
+      prev = j;
+    }
+  }
+  if (mk)
+    for (int p = 0; p < 3; ++p) {
+      int8_t m = mk[3 * I + p];
+      if (m < 0 || m >= MGR_MAX_LEVELS) ok = false;
+    }
+  if (!ok || !diag) atomicOr(err, EBIT_PATTERN);
+}
+
+void bsr3_validate(Ctx& c, const mgr_bsr3_t& A, const int8_t* marker) {
+  if (A.nb <= 0 || A.nnzb < A.nb || !A.rowptr || !A.colind || !A.values)
+    throw Error(MGR_ERR_INVALID_ARG, "bsr3: bad sizes or null pointers");
+  if (A.nb >= (1ll << 31) / 3) throw Error(MGR_ERR_UNSUPPORTED, "bsr3: 3*nb must fit in int32");
+  k_bsr_validate<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, A.nnzb, A.rowptr, A.colind, marker, c.d_err);
+  CU_LAUNCH();
+  check_errors(c, "bsr3_validate");
+}
+
+// ---------------------------------------------------------------------------------------------
+// Scalar CSR view of the BSR matrix with exact zeros dropped: row 3I+p collects, over the blocks
+// of block row I in ascending column order and q = 0..2, the nonzero entries (3J+q, B[p][q]).
+__global__ void k_bsr_csr_count(int64_t nb, const int64_t* rp, const double* v, int64_t* cnt) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= 3 * nb) return;
+  int64_t I = r / 3;
+  int p = (int)(r - 3 * I);
+  int64_t s = 0;
+  for (int64_t k = rp[I]; k < rp[I + 1]; ++k)
+    for (int q = 0; q < 3; ++q) s += (v[9 * k + 3 * p + q] != 0.0);
+  cnt[r] = s;
+}
+__global__ void k_bsr_csr_fill(int64_t nb, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* orp,
+                               int32_t* oci, double* ov) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= 3 * nb) return;
+  int64_t I = r / 3;
+  int p = (int)(r - 3 * I);
+  int64_t o = orp[r];
+  for (int64_t k = rp[I]; k < rp[I + 1]; ++k)
+    for (int q = 0; q < 3; ++q) {
+      double x = v[9 * k + 3 * p + q];
+      if (x != 0.0) { oci[o] = 3 * ci[k] + q; ov[o] = x; ++o; }
+    }
+}
+
+void bsr3_to_csr(Ctx& c, const mgr_bsr3_t& A, DCSR<double>& out) {
+  int64_t n = 3 * A.nb;
+  DBuf<int64_t> cnt(c, n);
+  out.nr = out.nc = n;
+  out.rp.alloc(c, n + 1);
+  k_bsr_csr_count<<<grid_for(n, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.values, cnt.p);
+  CU_LAUNCH();
+  out.nnz = counts_to_rowptr(c, cnt.p, out.rp.p, n);
+  out.ci.alloc(c, out.nnz);
+  out.v.alloc(c, out.nnz);
+  k_bsr_csr_fill<<<grid_for(n, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.colind, A.values, out.rp.p, out.ci.p, out.v.p);
+  CU_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Inverse of each 3x3 diagonal block by the adjugate over the determinant (cofactor expansion
+// along row 0); a zero or non-finite determinant sets EBIT_SINGULAR.
+__device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double ds(double a, double b) { return __dsub_rn(a, b); }
+
+__global__ void k_block_inverse(int64_t nb, const int64_t* rp, const int32_t* ci, const double* v, double* binv, int* err) {
+  int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= nb) return;
+  int64_t k = find_i32(ci, rp[I], rp[I + 1], (int32_t)I);
+  double* r = binv + 9 * I;
+  if (k < 0) { atomicOr(err, EBIT_PATTERN); return; }
+  const double* b = v + 9 * k;
+  double c00 = ds(dm(b[4], b[8]), dm(b[5], b[7]));
+  double c01 = ds(dm(b[5], b[6]), dm(b[3], b[8]));
+  double c02 = ds(dm(b[3], b[7]), dm(b[4], b[6]));
+  double det = dd(dd(dm(b[0], c00), dm(b[1], c01)), dm(b[2], c02));
+  if (det == 0.0 || !isfinite(det)) {
+    atomicOr(err, EBIT_SINGULAR);
+    for (int t = 0; t < 9; ++t) r[t] = 0.0;
+    return;
+  }
+  double id = __ddiv_rn(1.0, det);
+  r[0] = dm(c00, id);
+  r[1] = dm(ds(dm(b[2], b[7]), dm(b[1], b[8])), id);
+  r[2] = dm(ds(dm(b[1], b[5]), dm(b[2], b[4])), id);
+  r[3] = dm(c01, id);
+  r[4] = dm(ds(dm(b[0], b[8]), dm(b[2], b[6])), id);
+  r[5] = dm(ds(dm(b[2], b[3]), dm(b[0], b[5])), id);
+  r[6] = dm(c02, id);
+  r[7] = dm(ds(dm(b[1], b[6]), dm(b[0], b[7])), id);
+  r[8] = dm(ds(dm(b[0], b[4]), dm(b[1], b[3])), id);
+}
+
+void bsr3_block_inverse(Ctx& c, const mgr_bsr3_t& A, double* binv) {
+  k_block_inverse<<<grid_for(A.nb, 128), 128, 0, c.s>>>(A.nb, A.rowptr, A.colind, A.values, binv, c.d_err);
+  CU_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sorting helpers (bitonic networks in shared memory).
+__device__ __forceinline__ void warp_bitonic_keys(int32_t* key, int n, int lane) {
+  for (int k = 2; k <= n; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < n; t += 32) {
+        int x = t ^ j;
+        if (x > t) {
+          bool up = (t & k) == 0;
+          int32_t a = key[t], b = key[x];
+          if ((a > b) == up) { key[t] = b; key[x] = a; }
+        }
+      }
+      __syncwarp();
+    }
+}
+__device__ __forceinline__ void block_bitonic_keys(int32_t* key, int n) {
+  for (int k = 2; k <= n; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        int x = t ^ j;
+        if (x > t) {
+          bool up = (t & k) == 0;
+          int32_t a = key[t], b = key[x];
+          if ((a > b) == up) { key[t] = b; key[x] = a; }
+        }
+      }
+      __syncthreads();
+    }
+}
+__device__ __forceinline__ int next_pow2(int x) {
+  int n = 1;
+  while (n < x) n <<= 1;
+  return n;
+}
+
+// ---------------------------------------------------------------------------------------------
+// SpGEMM symbolic: the pattern of row i of C is the sorted union of the columns of the rows of B
+// selected by row i of A.  Three kernels by per-row work bound ub_i = sum of the B row lengths:
+// a warp with a shared-memory hash table (ub <= SYM_WCAP), a block with a larger table
+// (ub <= SYM_BCAP), and a block with a bitmap over the columns of C (nc <= SYM_BITS).
+constexpr int SYM_WCAP = 1024;
+constexpr int SYM_WHASH = 2048;
+constexpr int SYM_WARPS = 4;
+constexpr int SYM_BCAP = 8192;
+constexpr int SYM_BHASH = 16384;
+constexpr int64_t SYM_BITS = 1 << 20;
+
+__global__ void k_spgemm_ub(int64_t m, const int64_t* arp, const int32_t* aci, const int64_t* brp, int64_t* ub,
+                            int* n_mid, int32_t* mid, int* n_big, int32_t* big) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int64_t s = 0;
+  for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
+    int32_t k = aci[p];
+    s += brp[k + 1] - brp[k];
+  }
+  ub[i] = s;
+  if (s > SYM_BCAP) big[atomicAdd(n_big, 1)] = (int32_t)i;
+  else if (s > SYM_WCAP) mid[atomicAdd(n_mid, 1)] = (int32_t)i;
+}
+
+__device__ __forceinline__ uint32_t hash32(int32_t k) { return (uint32_t)k * 2654435761u; }
+
+// MODE 0: count unique columns into cnt[i]; MODE 1: write the sorted unique columns at crp[i].
+template <int MODE>
+__global__ void __launch_bounds__(32 * SYM_WARPS) k_sym_warp(int64_t m, const int64_t* arp, const int32_t* aci,
+                                                              const int64_t* brp, const int32_t* bci,
+                                                              const int64_t* ub, int64_t* cnt, const int64_t* crp,
+                                                              int32_t* cci) {
+  __shared__ int32_t tab[SYM_WARPS][SYM_WHASH];
+  __shared__ int ucount[SYM_WARPS];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = (int64_t)blockIdx.x * SYM_WARPS + w;
+  if (i >= m) return;
+  if (ub[i] > SYM_WCAP) return;  // handled by the block / bitmap kernels
+  int32_t* T = tab[w];
+  for (int t = lane; t < SYM_WHASH; t += 32) T[t] = -1;
+  if (lane == 0) ucount[w] = 0;
+  __syncwarp();
+  for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
+    int32_t k = aci[p];
+    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+      int32_t key = bci[q];
+      uint32_t h = hash32(key) & (SYM_WHASH - 1);
+      while (true) {
+        int32_t prev = atomicCAS(&T[h], -1, key);
+        if (prev == -1) { atomicAdd(&ucount[w], 1); break; }
+        if (prev == key) break;
+        h = (h + 1) & (SYM_WHASH - 1);
+      }
+    }
+  }
+  __syncwarp();
+  int u = ucount[w];
+  if (MODE == 0) {
+    if (lane == 0) cnt[i] = u;
+    return;
+  }
+  // in-place compaction: a chunk is read into registers before any write, and every write goes to a
+  // position below the end of the chunk being read
+  int32_t* K = T;
+  int base = 0;
+  for (int t = 0; t < SYM_WHASH; t += 32) {
+    int32_t key = T[t + lane];
+    unsigned msk = __ballot_sync(0xffffffffu, key >= 0);
+    if (key >= 0) K[base + __popc(msk & ((1u << lane) - 1))] = key;
+    base += __popc(msk);
+    __syncwarp();
+  }
+  int n2 = next_pow2(u);
+  for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
+  __syncwarp();
+  warp_bitonic_keys(K, n2, lane);
+  int64_t o = crp[i];
+  for (int t = lane; t < u; t += 32) cci[o + t] = K[t];
+}
+
+template <int MODE>
+__global__ void k_sym_block(const int32_t* rows, const int64_t* arp, const int32_t* aci, const int64_t* brp,
+                            const int32_t* bci, int64_t* cnt, const int64_t* crp, int32_t* cci) {
+  extern __shared__ int32_t smem[];
+  int32_t* T = smem;               // SYM_BHASH
+  int32_t* K = smem + SYM_BHASH;   // SYM_BCAP
+  __shared__ int ucount;
+  int64_t i = rows[blockIdx.x];
+  for (int t = threadIdx.x; t < SYM_BHASH; t += blockDim.x) T[t] = -1;
+  if (threadIdx.x == 0) ucount = 0;
+  __syncthreads();
+  int64_t a0 = arp[i], a1 = arp[i + 1];
+  // flatten (p, q) pairs: threads walk the A row; each thread inserts strided B entries
+  for (int64_t p = a0; p < a1; ++p) {
+    int32_t k = aci[p];
+    for (int64_t q = brp[k] + threadIdx.x; q < brp[k + 1]; q += blockDim.x) {
+      int32_t key = bci[q];
+      uint32_t h = hash32(key) & (SYM_BHASH - 1);
+      while (true) {
+        int32_t prev = atomicCAS(&T[h], -1, key);
+        if (prev == -1) { atomicAdd(&ucount, 1); break; }
+        if (prev == key) break;
+        h = (h + 1) & (SYM_BHASH - 1);
+      }
+    }
+  }
+  __syncthreads();
+  int u = ucount;
+  if (MODE == 0) {
+    if (threadIdx.x == 0) cnt[i] = u;
+    return;
+  }
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  // compaction (order irrelevant: sorted afterwards)
+  for (int t = threadIdx.x; t < SYM_BHASH; t += blockDim.x) {
+    int32_t key = T[t];
+    if (key >= 0) K[atomicAdd(&base, 1)] = key;
+  }
+  __syncthreads();
+  int n2 = next_pow2(u);
+  for (int t = u + threadIdx.x; t < n2; t += blockDim.x) K[t] = INT_MAX;
+  __syncthreads();
+  block_bitonic_keys(K, n2);
+  int64_t o = crp[i];
+  for (int t = threadIdx.x; t < u; t += blockDim.x) cci[o + t] = K[t];
+}
+
+// bitmap over the columns [0, nc), nc <= SYM_BITS; 1024 threads, each owning consecutive words
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_sym_bitmap(const int32_t* rows, int64_t nc, const int64_t* arp,
+                                                     const int32_t* aci, const int64_t* brp, const int32_t* bci,
+                                                     int64_t* cnt, const int64_t* crp, int32_t* cci) {
+  extern __shared__ uint32_t bits[];
+  __shared__ int wsum[32];
+  int nw = (int)((nc + 31) >> 5);
+  int64_t i = rows[blockIdx.x];
+  for (int t = threadIdx.x; t < nw; t += blockDim.x) bits[t] = 0u;
+  __syncthreads();
+  for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
+    int32_t k = aci[p];
+    for (int64_t q = brp[k] + threadIdx.x; q < brp[k + 1]; q += blockDim.x) {
+      int32_t key = bci[q];
+      atomicOr(&bits[key >> 5], 1u << (key & 31));
+    }
+  }
+  __syncthreads();
+  int per = (nw + blockDim.x - 1) / blockDim.x;
+  int w0 = threadIdx.x * per;
+  int s = 0;
+  for (int t = 0; t < per; ++t)
+    if (w0 + t < nw) s += __popc(bits[w0 + t]);
+  // block exclusive scan of s
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int y = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      int z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    wsum[lane] = y;
+  }
+  __syncthreads();
+  int before = (wid ? wsum[wid - 1] : 0) + x - s;
+  if (MODE == 0) {
+    if (threadIdx.x == blockDim.x - 1) cnt[i] = before + s;
+    return;
+  }
+  int64_t o = crp[i] + before;
+  for (int t = 0; t < per; ++t) {
+    int wi = w0 + t;
+    if (wi >= nw) break;
+    uint32_t b = bits[wi];
+    while (b) {
+      int bit = __ffs(b) - 1;
+      cci[o++] = (wi << 5) + bit;
+      b &= b - 1;
+    }
+  }
+}
+
+static void sym_pass(Ctx& c, int mode, const DCSR<double>& A, const DCSR<double>& B, const int64_t* ub,
+                     const int32_t* mid, int nmid, const int32_t* big, int nbig, int64_t* cnt, DCSR<double>& C) {
+  int64_t m = A.nr;
+  unsigned g = grid_for(m, SYM_WARPS);
+  if (mode == 0)
+    k_sym_warp<0><<<g, 32 * SYM_WARPS, 0, c.s>>>(m, A.rp, A.ci, B.rp, B.ci, ub, cnt, nullptr, nullptr);
+  else
+    k_sym_warp<1><<<g, 32 * SYM_WARPS, 0, c.s>>>(m, A.rp, A.ci, B.rp, B.ci, ub, nullptr, C.rp, C.ci);
+  CU_LAUNCH();
+  if (nmid > 0) {
+    size_t sh = sizeof(int32_t) * (SYM_BHASH + SYM_BCAP);
+    if (mode == 0) {
+      CU(cudaFuncSetAttribute(k_sym_block<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      k_sym_block<0><<<nmid, 512, sh, c.s>>>(mid, A.rp, A.ci, B.rp, B.ci, cnt, nullptr, nullptr);
+      CU_LAUNCH();
+    } else {
+      CU(cudaFuncSetAttribute(k_sym_block<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      k_sym_block<1><<<nmid, 512, sh, c.s>>>(mid, A.rp, A.ci, B.rp, B.ci, nullptr, C.rp, C.ci);
+      CU_LAUNCH();
+    }
+  }
+  if (nbig > 0) {
+    if (B.nc > SYM_BITS) throw Error(MGR_ERR_UNSUPPORTED, "spgemm: a row with > 8192 products and > 2^20 columns");
+    size_t sh = sizeof(uint32_t) * (size_t)((B.nc + 31) / 32);
+    if (mode == 0) {
+      CU(cudaFuncSetAttribute(k_sym_bitmap<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      k_sym_bitmap<0><<<nbig, 1024, sh, c.s>>>(big, B.nc, A.rp, A.ci, B.rp, B.ci, cnt, nullptr, nullptr);
+      CU_LAUNCH();
+    } else {
+      CU(cudaFuncSetAttribute(k_sym_bitmap<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      k_sym_bitmap<1><<<nbig, 1024, sh, c.s>>>(big, B.nc, A.rp, A.ci, B.rp, B.ci, nullptr, C.rp, C.ci);
+      CU_LAUNCH();
+    }
+  }
+}
+
+void spgemm_symbolic(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C) {
+  if (A.nc != B.nr) throw Error(MGR_ERR_INVALID_ARG, "spgemm: inner dimensions differ");
+  int64_t m = A.nr;
+  C.nr = m;
+  C.nc = B.nc;
+  C.rp.alloc(c, m + 1);
+  if (m == 0) {
+    fill_i64(c, C.rp.p, 0, 1);
+    C.nnz = 0;
+    C.ci.alloc(c, 0);
+    return;
+  }
+  DBuf<int64_t> ub(c, m), cnt(c, m);
+  DBuf<int32_t> mid(c, m), big(c, m);
+  DBuf<int> counters(c, 2);
+  CU(cudaMemsetAsync(counters.p, 0, 2 * sizeof(int), c.s));
+  k_spgemm_ub<<<grid_for(m, 256), 256, 0, c.s>>>(m, A.rp, A.ci, B.rp, ub.p, counters.p, mid.p, counters.p + 1, big.p);
+  CU_LAUNCH();
+  int hc[2];
+  CU(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, c.s));
+  CU(cudaStreamSynchronize(c.s));
+  sym_pass(c, 0, A, B, ub.p, mid.p, hc[0], big.p, hc[1], cnt.p, C);
+  C.nnz = counts_to_rowptr(c, cnt.p, C.rp.p, m);
+  C.ci.alloc(c, C.nnz);
+  sym_pass(c, 1, A, B, ub.p, mid.p, hc[0], big.p, hc[1], nullptr, C);
+}
+
+// ---------------------------------------------------------------------------------------------
+// SpGEMM numeric: one warp per row of C.  The A row is walked in ascending order; for each k the
+// lanes add a_ik * b_kj to the entry j of the (sorted) C row found by binary search.  Entries of one
+// B row have distinct columns, and __syncwarp orders successive k, so every C entry is the sum over
+// ascending k, starting from 0.0.  Rows up to NUM_CAP entries accumulate in shared memory, longer
+// rows in the output array.
+constexpr int NUM_WARPS = 8;
+constexpr int NUM_CAP = 384;
+
+__global__ void __launch_bounds__(32 * NUM_WARPS) k_spgemm_numeric(int64_t m, const int64_t* arp, const int32_t* aci,
+                                                                    const double* av, const int64_t* brp,
+                                                                    const int32_t* bci, const double* bv,
+                                                                    const int64_t* crp, const int32_t* cci, double* cv) {
+  __shared__ int32_t scol[NUM_WARPS][NUM_CAP];
+  __shared__ double sacc[NUM_WARPS][NUM_CAP];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = (int64_t)blockIdx.x * NUM_WARPS + w;
+  if (i >= m) return;
+  int64_t c0 = crp[i], c1 = crp[i + 1];
+  int L = (int)(c1 - c0);
+  bool inshared = L <= NUM_CAP;
+  const int32_t* col = inshared ? scol[w] : cci + c0;
+  double* acc = inshared ? sacc[w] : cv + c0;
+  for (int t = lane; t < L; t += 32) {
+    if (inshared) scol[w][t] = cci[c0 + t];
+    acc[t] = 0.0;
+  }
+  __syncwarp();
+  for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
+    int32_t k = aci[p];
+    double a = av[p];
+    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+      int32_t j = bci[q];
+      int64_t pos = lower_bound_i32(col, 0, L, j);
+      acc[pos] = __dadd_rn(acc[pos], __dmul_rn(a, bv[q]));
+    }
+    __syncwarp();
+  }
+  if (inshared)
+    for (int t = lane; t < L; t += 32) cv[c0 + t] = acc[t];
+}
+
+void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C) {
+  spgemm_symbolic(c, A, B, C);
+  C.v.alloc(c, C.nnz);
+  if (C.nr == 0) return;
+  k_spgemm_numeric<<<grid_for(C.nr, NUM_WARPS), 32 * NUM_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
+                                                                           C.rp, C.ci, C.v);
+  CU_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Per-row sort of (column, value) pairs by column: a warp per row up to SORT_WCAP entries, a block
+// per row up to SORT_BCAP, and an insertion sort in global memory beyond (rare, slow, correct).
+constexpr int SORT_WCAP = 512;
+constexpr int SORT_WARPS = 4;
+constexpr int SORT_BCAP = 4096;
+
+template <bool HASV>
+__device__ __forceinline__ void cmpswap(int32_t* key, double* val, int t, int x, bool up) {
+  int32_t a = key[t], b = key[x];
+  if ((a > b) == up) {
+    key[t] = b; key[x] = a;
+    if (HASV) { double va = val[t]; val[t] = val[x]; val[x] = va; }
+  }
+}
+
+template <bool HASV>
+__global__ void __launch_bounds__(32 * SORT_WARPS) k_sort_rows_warp(int64_t nr, const int64_t* rp, int32_t* ci, double* v,
+                                                                    int* n_big, int32_t* big) {
+  __shared__ int32_t sk[SORT_WARPS][SORT_WCAP];
+  __shared__ double sv[SORT_WARPS][HASV ? SORT_WCAP : 1];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = (int64_t)blockIdx.x * SORT_WARPS + w;
+  if (i >= nr) return;
+  int64_t b = rp[i];
+  int L = (int)(rp[i + 1] - b);
+  if (L <= 1) return;
+  if (L > SORT_WCAP) {
+    if (lane == 0) big[atomicAdd(n_big, 1)] = (int32_t)i;
+    return;
+  }
+  int n2 = next_pow2(L);
+  for (int t = lane; t < n2; t += 32) {
+    sk[w][t] = (t < L) ? ci[b + t] : INT_MAX;
+    if (HASV) sv[w][t] = (t < L) ? v[b + t] : 0.0;
+  }
+  __syncwarp();
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < n2; t += 32) {
+        int x = t ^ j;
+        if (x > t) cmpswap<HASV>(sk[w], sv[w], t, x, (t & k) == 0);
+      }
+      __syncwarp();
+    }
+  for (int t = lane; t < L; t += 32) {
+    ci[b + t] = sk[w][t];
+    if (HASV) v[b + t] = sv[w][t];
+  }
+}
+
+template <bool HASV>
+__global__ void k_sort_rows_block(const int32_t* rows, const int64_t* rp, int32_t* ci, double* v) {
+  extern __shared__ unsigned char sm_raw[];
+  int32_t* sk = reinterpret_cast<int32_t*>(sm_raw);
+  double* sv = reinterpret_cast<double*>(sm_raw + sizeof(int32_t) * SORT_BCAP);
+  int64_t i = rows[blockIdx.x];
+  int64_t b = rp[i];
+  int L = (int)(rp[i + 1] - b);
+  if (L > SORT_BCAP) {
+    // insertion sort in place (single thread): correct for any length
+    if (threadIdx.x == 0)
+      for (int a = 1; a < L; ++a) {
+        int32_t key = ci[b + a];
+        double val = HASV ? v[b + a] : 0.0;
+        int t = a - 1;
+        while (t >= 0 && ci[b + t] > key) {
+          ci[b + t + 1] = ci[b + t];
+          if (HASV) v[b + t + 1] = v[b + t];
+          --t;
+        }
+        ci[b + t + 1] = key;
+        if (HASV) v[b + t + 1] = val;
+      }
+    return;
+  }
+  int n2 = next_pow2(L);
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    sk[t] = (t < L) ? ci[b + t] : INT_MAX;
+    if (HASV) sv[t] = (t < L) ? v[b + t] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+        int x = t ^ j;
+        if (x > t) cmpswap<HASV>(sk, sv, t, x, (t & k) == 0);
+      }
+      __syncthreads();
+    }
+  for (int t = threadIdx.x; t < L; t += blockDim.x) {
+    ci[b + t] = sk[t];
+    if (HASV) v[b + t] = sv[t];
+  }
+}
+
+void sort_rows(Ctx& c, int64_t nr, const int64_t* rp, int32_t* ci, double* v) {
+  if (nr <= 0) return;
+  DBuf<int> nbig(c, 1);
+  DBuf<int32_t> big(c, nr);
+  CU(cudaMemsetAsync(nbig.p, 0, sizeof(int), c.s));
+  if (v)
+    k_sort_rows_warp<true><<<grid_for(nr, SORT_WARPS), 32 * SORT_WARPS, 0, c.s>>>(nr, rp, ci, v, nbig.p, big.p);
+  else
+    k_sort_rows_warp<false><<<grid_for(nr, SORT_WARPS), 32 * SORT_WARPS, 0, c.s>>>(nr, rp, ci, v, nbig.p, big.p);
+  CU_LAUNCH();
+  int hb = read_scalar(c, nbig.p);
+  if (hb > 0) {
+    size_t sh = (sizeof(int32_t) + sizeof(double)) * SORT_BCAP;
+    if (v) {
+      CU(cudaFuncSetAttribute(k_sort_rows_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      k_sort_rows_block<true><<<hb, 512, sh, c.s>>>(big.p, rp, ci, v);
+      CU_LAUNCH();
+    } else {
+      CU(cudaFuncSetAttribute(k_sort_rows_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      k_sort_rows_block<false><<<hb, 512, sh, c.s>>>(big.p, rp, ci, v);
+      CU_LAUNCH();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Transpose: column counts (atomic), scan, scatter to atomic slots, then per-row sort by column.
+// Every (row, column) pair is unique, so the sorted result is independent of the scatter order.
+__global__ void k_col_count(int64_t nnz, const int32_t* ci, unsigned long long* cnt) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[ci[k]], 1ull);
+}
+__global__ void k_transpose_scatter(int64_t nr, const int64_t* rp, const int32_t* ci, const double* v,
+                                    const int64_t* trp, unsigned long long* slot, int32_t* tci, double* tv) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nr) return;
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+    int32_t j = ci[k];
+    int64_t d = trp[j] + (int64_t)atomicAdd(&slot[j], 1ull);
+    tci[d] = (int32_t)i;
+    if (v) tv[d] = v[k];
+  }
+}
+
+void transpose(Ctx& c, const DCSR<double>& A, DCSR<double>& T) {
+  T.nr = A.nc;
+  T.nc = A.nr;
+  T.nnz = A.nnz;
+  T.rp.alloc(c, T.nr + 1);
+  T.ci.alloc(c, T.nnz);
+  bool hv = A.v.p != nullptr;
+  if (hv) T.v.alloc(c, T.nnz);
+  DBuf<unsigned long long> cnt(c, T.nr + 1);
+  CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (T.nr + 1), c.s));
+  if (A.nnz > 0) {
+    k_col_count<<<grid_for(A.nnz, 256, 8192), 256, 0, c.s>>>(A.nnz, A.ci, cnt.p);
+    CU_LAUNCH();
+  }
+  scan_excl_i64(c, reinterpret_cast<const int64_t*>(cnt.p), T.rp.p, T.nr);
+  CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (T.nr + 1), c.s));
+  if (A.nr > 0) {
+    k_transpose_scatter<<<grid_for(A.nr, 256), 256, 0, c.s>>>(A.nr, A.rp, A.ci, hv ? A.v.p : nullptr, T.rp.p, cnt.p,
+                                                              T.ci.p, hv ? T.v.p : nullptr);
+    CU_LAUNCH();
+  }
+  sort_rows(c, T.nr, T.rp.p, T.ci.p, hv ? T.v.p : nullptr);
+}
+
+// ---------------------------------------------------------------------------------------------
+__global__ void k_f64_to_f32(int64_t n, const double* a, float* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+void csr_to_f32(Ctx& c, const DCSR<double>& A, DCSR<float>& B) {
+  B.nr = A.nr; B.nc = A.nc; B.nnz = A.nnz;
+  B.rp.alloc(c, A.nr + 1);
+  B.ci.alloc(c, A.nnz);
+  B.v.alloc(c, A.nnz);
+  CU(cudaMemcpyAsync(B.rp.p, A.rp.p, sizeof(int64_t) * (A.nr + 1), cudaMemcpyDeviceToDevice, c.s));
+  if (A.nnz) {
+    CU(cudaMemcpyAsync(B.ci.p, A.ci.p, sizeof(int32_t) * A.nnz, cudaMemcpyDeviceToDevice, c.s));
+    k_f64_to_f32<<<grid_for(A.nnz, 256, 8192), 256, 0, c.s>>>(A.nnz, A.v.p, B.v.p);
+    CU_LAUNCH();
+  }
+}
+
+void copy_csr(Ctx& c, const DCSR<double>& A, DCSR<double>& B) {
+  B.nr = A.nr; B.nc = A.nc; B.nnz = A.nnz;
+  B.rp.alloc(c, A.nr + 1);
+  B.ci.alloc(c, A.nnz);
+  CU(cudaMemcpyAsync(B.rp.p, A.rp.p, sizeof(int64_t) * (A.nr + 1), cudaMemcpyDeviceToDevice, c.s));
+  if (A.nnz) CU(cudaMemcpyAsync(B.ci.p, A.ci.p, sizeof(int32_t) * A.nnz, cudaMemcpyDeviceToDevice, c.s));
+  if (A.v.p) {
+    B.v.alloc(c, A.nnz);
+    if (A.nnz) CU(cudaMemcpyAsync(B.v.p, A.v.p, sizeof(double) * A.nnz, cudaMemcpyDeviceToDevice, c.s));
+  }
+}
+
+}  // namespace mgr

@@ -1,0 +1,230 @@
+"""GPU library (through the C ABI) versus the FP64 CPU oracle, element by element.
+
+Bit-exact: C/F splittings of every MGR level and every AMG level, sparsity patterns of every
+operator.  Floating point: setup values to 1e-13 relative (they are computed by the same sequence of
+IEEE operations on both sides), one preconditioner application to 1e-10, FP64 solutions to 1e-10
+after tight solves, residual <= 1e-8 at the default tolerance.
+"""
+import numpy as np
+import pytest
+
+import ncpgen
+import oracle
+from gpu_common import PARITY, compare_csr, rel, to_gpu
+
+pytestmark = pytest.mark.gpu
+
+OPTION_SETS = {
+    "default": {},
+    "jacobi_trunc": dict(frelax_type=[0, 0, 0], frelax_omega=[1.0, 0.8, 0.8], amg_theta=0.5, amg_pmax=4,
+                         amg_smoother=0, amg_omega=0.8, restrict_type=[1, 1, 0], frelax_sweeps=[1, 3, 2]),
+}
+
+
+def _pair(p, **opts):
+    import paper_1801_08464_gb300 as mg
+    A, mk = to_gpu(p)
+    m = mg.MGR(**opts)
+    m.setup(A, mk)
+    o = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker, **opts)
+    return A, mk, m, o
+
+
+@pytest.mark.parametrize("name", list(PARITY))
+@pytest.mark.parametrize("optname", list(OPTION_SETS))
+def test_setup_parity(name, optname):
+    import paper_1801_08464_gb300 as mg
+    p = ncpgen.make_problem(PARITY[name])
+    A, mk, m, o = _pair(p, **OPTION_SETS[optname])
+    L, na = m.levels()
+    assert (L, na) == o.info()
+    same = []
+    for l in range(L + 1):
+        same.append(compare_csr(m.scipy(mg.MAT_LEVEL, l), o.scipy(oracle.MAT_LEVEL, l), what=f"A_{l}"))
+    for l in range(L):
+        for kind in (mg.MAT_WP, mg.MAT_WR, mg.MAT_P, mg.MAT_R):
+            same.append(compare_csr(m.scipy(kind, l), o.scipy(kind, l), what=f"kind{kind} level {l}"))
+        for kind in (mg.VEC_F, mg.VEC_C):
+            assert np.array_equal(m.vector(kind, l).cpu().numpy(), o.vec(kind, l)), f"F/C split of level {l}"
+        np.testing.assert_allclose(m.vector(mg.VEC_MINV, l).cpu().numpy(), o.vec(oracle.VEC_MINV, l), rtol=1e-14)
+    for k in range(na):
+        same.append(compare_csr(m.scipy(mg.MAT_AMG_A, k), o.scipy(oracle.MAT_AMG_A, k), what=f"AMG A_{k}"))
+        if k < na - 1:
+            assert np.array_equal(m.vector(mg.VEC_AMG_CF, k).cpu().numpy(), o.vec(oracle.VEC_AMG_CF, k)), \
+                f"PMIS split of AMG level {k}"
+            for kind in (mg.MAT_AMG_P, mg.MAT_AMG_R, mg.MAT_AMG_S):
+                same.append(compare_csr(m.scipy(kind, k), o.scipy(kind, k), what=f"AMG kind{kind} level {k}"))
+            np.testing.assert_allclose(m.vector(mg.VEC_AMG_DINV, k).cpu().numpy(), o.vec(oracle.VEC_AMG_DINV, k),
+                                       rtol=1e-14)
+    np.testing.assert_allclose(m.vector(mg.VEC_BINV, 0).cpu().numpy(), o.vec(oracle.VEC_BINV, 0), rtol=1e-13,
+                               atol=1e-13 * np.abs(o.vec(oracle.VEC_BINV, 0)).max())
+    print(f"{name}/{optname}: fraction of bit-identical setup values {np.mean(same):.6f}")
+    m.close()
+
+
+@pytest.mark.parametrize("name", list(PARITY))
+def test_apply_parity_fp64(name):
+    import torch
+    p = ncpgen.make_problem(PARITY[name])
+    A, mk, m, o = _pair(p)
+    for seed in (2, 7):
+        r = ncpgen.normals(p.n, seed)
+        z = m.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+        zo = o.apply(r)
+        assert rel(z, zo) <= 1e-10
+    m.close()
+
+
+@pytest.mark.parametrize("name", list(PARITY))
+def test_global_relaxation_step(name):
+    """With the 3x3 block inverses compared elementwise, check step (1) through a block-diagonal
+    matrix where MGR reduces to blockdiag(A)^-1 on both sides."""
+    import torch
+    p = ncpgen.make_problem(PARITY[name])
+    rows = np.repeat(np.arange(p.nb), np.diff(p.rowptr))
+    vals = p.values.copy()
+    vals[rows != p.colind] = 0.0
+    q = ncpgen.Problem(p.cfg, p.nb, p.rowptr, p.colind, vals, p.gas_present, p.cf_marker, p.state, p.perm)
+    A, mk, m, o = _pair(q, amg_max_coarse=8)
+    r = ncpgen.normals(p.n, 5)
+    z = m.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
+    assert rel(z, o.global_relax(r)) <= 1e-12
+    m.close()
+
+
+@pytest.mark.parametrize("name", list(PARITY))
+def test_fgmres_parity_fp64(name):
+    import torch
+    p = ncpgen.make_problem(PARITY[name])
+    A, mk, m, o = _pair(p)
+    b = ncpgen.normals(p.n, 2)
+    bt = torch.as_tensor(b, device="cuda")
+    Asp = p.to_scipy()
+    # default tolerance: the residual target and the iteration count
+    x, info = m.fgmres(A, bt, rtol=1e-8)
+    xo, io = o.fgmres(b, rtol=1e-8)
+    xg = x.cpu().numpy()
+    assert info["converged"]
+    assert np.linalg.norm(b - Asp @ xg) <= 1e-8 * np.linalg.norm(b)
+    assert abs(info["iterations"] - io["iterations"]) <= 1, (info["iterations"], io["iterations"])
+    # tight solves agree to 1e-10
+    x2, info2 = m.fgmres(A, bt, rtol=1e-12, maxit=2000)
+    xo2, io2 = o.fgmres(b, rtol=1e-12, maxit=2000)
+    assert rel(x2.cpu().numpy(), xo2) <= 1e-10
+    m.close()
+
+
+def test_mixed_precision_iterations_and_error():
+    """FP32 hierarchy with FP64 Krylov: same 1e-8 residual at <= 1.2x the FP64 iterations; the error
+    against the FP64 oracle solution is reported.  Layered 1e4-contrast workload at 32^3."""
+    import paper_1801_08464_gb300 as mg
+    import torch
+    cfg = ncpgen.GridConfig(32, 32, 32, sigma=1.0, layer_contrast=1e-4, absent_frac=0.4, absent_mode=1, seed=1)
+    p = ncpgen.make_problem(cfg)
+    A, mk = to_gpu(p)
+    b = ncpgen.normals(p.n, 2)
+    bt = torch.as_tensor(b, device="cuda")
+    res = {}
+    for prec in ("fp64", "mixed"):
+        m = mg.MGR(precision=prec)
+        m.setup(A, mk)
+        x, info = m.fgmres(A, bt, rtol=1e-8)
+        res[prec] = (x.cpu().numpy(), info)
+        m.close()
+    o = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker)
+    xo, io = o.fgmres(b, rtol=1e-8)
+    Asp = p.to_scipy()
+    for prec, (x, info) in res.items():
+        assert info["converged"]
+        assert np.linalg.norm(b - Asp @ x) <= 1e-8 * np.linalg.norm(b)
+    it64, itmx = res["fp64"][1]["iterations"], res["mixed"][1]["iterations"]
+    assert itmx <= 1.2 * it64 + 1e-9, (itmx, it64)
+    print(f"iterations fp64 {it64} mixed {itmx} oracle {io['iterations']}; "
+          f"rel. error vs FP64 oracle: fp64 {rel(res['fp64'][0], xo):.2e} mixed {rel(res['mixed'][0], xo):.2e}")
+
+
+def test_spmv_parity():
+    import paper_1801_08464_gb300 as mg
+    import torch
+    p = ncpgen.make_problem(PARITY["ragged_13x7x9"])
+    A, _ = to_gpu(p)
+    x = ncpgen.normals(p.n, 3)
+    s = ncpgen.normals(p.n, 4)
+    y = mg.bsr3_spmv(A, torch.as_tensor(x, device="cuda")).cpu().numpy()
+    Asp = p.to_scipy()
+    assert rel(y, Asp @ x) <= 1e-14
+    y2 = mg.bsr3_spmv(A, torch.as_tensor(x, device="cuda"), torch.as_tensor(s, device="cuda")).cpu().numpy()
+    assert rel(y2, s - Asp @ x) <= 1e-14
+
+
+def test_determinism():
+    import paper_1801_08464_gb300 as mg
+    import torch
+    p = ncpgen.make_problem(PARITY["ncp3d_16"])
+    A, mk = to_gpu(p)
+    r = torch.as_tensor(ncpgen.normals(p.n, 2), device="cuda")
+    outs = []
+    for _ in range(2):
+        m = mg.MGR(precision="mixed")
+        m.setup(A, mk)
+        outs.append((m.apply(r).cpu().numpy(), m.scipy(mg.MAT_AMG_A, 1)))
+        m.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert (outs[0][1] != outs[1][1]).nnz == 0
+
+
+def test_edge_cases_all_present_all_absent_tiny():
+    import torch
+    cases = [ncpgen.GridConfig(8, 8, 1, absent_frac=0.0, seed=41), ncpgen.GridConfig(8, 8, 1, absent_frac=1.0, seed=41),
+             ncpgen.GridConfig(2, 2, 1, absent_frac=0.5, seed=3), ncpgen.GridConfig(1, 1, 1, absent_frac=0.0, seed=3),
+             ncpgen.GridConfig(3, 1, 2, absent_frac=0.5, absent_mode=1, seed=4)]
+    for cfg in cases:
+        p = ncpgen.make_problem(cfg)
+        A, mk, m, o = _pair(p)
+        L, na = m.levels()
+        assert (L, na) == o.info()
+        for l in range(L + 1):
+            compare_csr(m.scipy(0, l), o.scipy(0, l), what=f"{cfg} level {l}")
+        b = ncpgen.normals(p.n, 2)
+        x, info = m.fgmres(A, torch.as_tensor(b, device="cuda"), rtol=1e-10)
+        assert info["converged"]
+        assert np.linalg.norm(b - p.to_scipy() @ x.cpu().numpy()) <= 1e-10 * np.linalg.norm(b) * 1.001
+        m.close()
+
+
+def test_error_statuses():
+    import paper_1801_08464_gb300 as mg
+    import torch
+    p = ncpgen.make_problem(ncpgen.GridConfig(6, 5, 1, seed=2))
+    A, mk = to_gpu(p)
+    m = mg.MGR()
+    with pytest.raises(mg.MgrError) as e:
+        m.apply(torch.zeros(p.n, dtype=torch.float64, device="cuda"))
+    assert e.value.code == 8  # STATE
+    # singular diagonal block
+    rows = np.repeat(np.arange(p.nb), np.diff(p.rowptr))
+    vals = p.values.copy()
+    vals[np.nonzero((rows == 4) & (p.colind == 4))[0][0]] = 0.0
+    with pytest.raises(mg.MgrError) as e:
+        m.setup(A.with_values(torch.as_tensor(vals, device="cuda")), mk)
+    assert e.value.code == 2
+    # malformed pattern: columns of a block row not ascending
+    ci = p.colind.copy()
+    a, b = p.rowptr[5], p.rowptr[5] + 1
+    ci[a], ci[b] = ci[b], ci[a]
+    bad = mg.BSR3.from_numpy(p.rowptr, ci, p.values)
+    with pytest.raises(mg.MgrError) as e:
+        m.setup(bad, mk)
+    assert e.value.code == 1
+    # a marker out of range
+    mk2 = mk.clone()
+    mk2[0] = 9
+    with pytest.raises(mg.MgrError) as e:
+        m.setup(A, mk2)
+    assert e.value.code == 1
+    # not converged within maxit: status 3, x holds the last iterate
+    m.setup(A, mk)
+    b = torch.as_tensor(ncpgen.normals(p.n, 2), device="cuda")
+    x, info = m.fgmres(A, b, rtol=1e-14, maxit=2, raise_on_fail=False)
+    assert info["status"] == 3 and info["iterations"] == 2 and info["relres_true"] < 1.0
+    m.close()
