@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark: MGR-preconditioned FGMRES(30) time to a 1e-8 relative residual on the 128^3 x 3
+two-phase two-component NCP workload (FP32 hierarchy / FP64 Krylov, FP64 beside it), with the HBM
+roofline fraction of the dominant kernel.
+
+A step is one pass of the hot path over one synthetic Jacobian resident in HBM: mgr_setup (global
+relaxation blocks, the three reductions with their R(AP) products, AMG setup on the pressure system,
+FP32 cast) followed by fgmres_solve from x0 = 0 to ||b - A x|| <= 1e-8 ||b||.  value = milliseconds
+per step (lower is better).  One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MGR-FGMRES time-to-1e-8 residual & HBM GB/s fraction, 128^3x3; FP32-mix vs FP64"
+WORKLOAD = "ncp3d_128_layered"
+RTOL, RESTART, MAXIT = 1e-8, 30, 1000
+# Solver settings used for the 3-D workloads: strength threshold 0.5 and interpolation truncation to 4
+# entries keep the AMG operator complexity low on the 25-63 point pressure stencils; omega-Jacobi
+# (0.8) smoothing converges in fewer iterations than l1-Jacobi on these operators.
+SOLVER = dict(amg_theta=0.5, amg_pmax=4, amg_smoother=0, amg_omega=0.8)
+
+
+KERNEL_NAMES = ("bsr3_spmv_f64", "bsr_resid_split", "global_relax", "csr_rows", "interp", "mdot", "mupdate",
+                "spgemm_numeric", "spgemm_symbolic", "setup_total", "setup_mgr_level", "setup_mgr_rap", "setup_amg",
+                "setup_amg_strength", "setup_amg_pmis", "setup_amg_extpi", "setup_amg_transpose", "setup_amg_rap",
+                "setup_dense_inverse", "setup_cast_alloc")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--solver", default="", help="JSON dict of solver options overriding the defaults")
+    args = ap.parse_args()
+    if args.solver:
+        SOLVER.update(json.loads(args.solver))
+    return args
+
+
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """Largest value over the ranks (the job's time is its slowest replica)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_config(cfg, rank: int):
+    """Replicas only: every rank solves the same workload recipe independently (no data exchange)."""
+    return cfg
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _cpu_sample_cfg(cfg, n):
+    import dataclasses
+    return dataclasses.replace(cfg, nx=n, ny=n, nz=n if cfg.nz > 1 else 1)
+
+
+def run_oracle_sample(cfg, n_sample):
+    """Oracle (FP64, one thread) setup + solve on an n_sample^3 instance of the workload recipe."""
+    import ncpgen
+    import oracle
+    sc = _cpu_sample_cfg(cfg, n_sample)
+    p = ncpgen.make_problem(sc)
+    b = ncpgen.normals(p.n, 2)
+    t0 = time.perf_counter()
+    o = oracle.OracleMGR(p.rowptr, p.colind, p.values, p.cf_marker, **SOLVER)
+    t1 = time.perf_counter()
+    x, info = o.fgmres(b, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+    t2 = time.perf_counter()
+    return dict(cells=p.nb, setup_s=t1 - t0, solve_s=t2 - t1, iterations=info["iterations"],
+                converged=info["converged"])
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _shape(m, kind, lev):
+    import ctypes
+    import paper_1801_08464_gb300 as mg
+    nr, nc, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    mg.lib().mgr_matrix_shape(m._h, kind, lev, ctypes.byref(nr), ctypes.byref(nc), ctypes.byref(nnz))
+    return nr.value, nnz.value
+
+
+def spmv_bytes(nb, nnzb, residual):
+    """Algorithmic bytes of one FP64 BSR SpMV launch: the 3x3 values, block columns and row pointers
+    once, x once, y written (and the subtrahend read in residual mode)."""
+    return 72 * nnzb + 4 * nnzb + 8 * (nb + 1) + 24 * nb + 24 * nb + (24 * nb if residual else 0)
+
+
+def main():
+    a = _args()
+    if a.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    import ncpgen
+    cfg = ncpgen.WORKLOADS[a.workload]
+    grid = [cfg.nx, cfg.ny, cfg.nz]
+    config = {"workload": a.workload, "grid": grid, "unknowns": 3 * cfg.nx * cfg.ny * cfg.nz,
+              "precision": "fp32 hierarchy, fp64 krylov", "rtol": RTOL, "restart": RESTART,
+              "solver": SOLVER, "l2": "inputs larger than L2 (FP64 BSR values > 1 GB)",
+              "parallelism": f"replicas x{a.gpus}"}
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        n_s = 32
+        cells_full = cfg.nx * cfg.ny * cfg.nz
+        for _ in range(a.warmup):
+            run_oracle_sample(cfg, n_s)
+        times = []
+        for _ in range(a.steps):
+            r = run_oracle_sample(cfg, n_s)
+            times.append((r["setup_s"] + r["solve_s"]) * 1e3)
+        scale = cells_full / r["cells"]
+        v = statistics.mean(times) * scale
+        sample = (f"{n_s}^3 instance of the {a.workload} recipe, FP64 oracle setup+solve to 1e-8, "
+                  f"time scaled by cell count x{scale:.1f}")
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": a.gpus,
+                          "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(times),
+                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": config,
+                          "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+                          "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                          "iterations": r["iterations"]}))
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1801_08464_gb300 as mg
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    p = ncpgen.make_problem(replica_config(cfg, rank))
+    b_h = ncpgen.normals(p.n, 2)
+    A = mg.BSR3.from_numpy(p.rowptr, p.colind, p.values)
+    mk = torch.as_tensor(p.cf_marker, device="cuda")
+    b = torch.as_tensor(b_h, device="cuda")
+    x = torch.zeros_like(b)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def _max(v):
+        return max_over_ranks(v, dist, "cuda")
+
+    def timed(prec, steps, profile=False):
+        m = mg.MGR(precision=prec, **SOLVER)
+        infos = []
+        for _ in range(a.warmup):
+            m.setup(A, mk)
+            x.zero_()
+            m.fgmres(A, b, x, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+        if profile:
+            m.profile(True)
+        barrier()
+        sampler = ClockSampler(local) if (profile and rank == 0) else None
+        l0 = mg.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        setup_ms = []
+        for _ in range(steps):
+            m.setup(A, mk)
+            setup_ms.append(m.stats()["setup_ms"])
+            x.zero_()
+            _, info = m.fgmres(A, b, x, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+            infos.append(info)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = mg.launch_count() - l0
+        clocks = sampler.stop() if sampler else None
+        ms = _max(e0.elapsed_time(e1)) / steps
+        kt = {k: m.kernel_time(k) for k in KERNEL_NAMES} if profile else {}
+        mem = m.memory_bytes()
+        L, na = m.levels()
+        hier = {"mgr": [list(_shape(m, mg.MAT_LEVEL, l)) for l in range(L + 1)],
+                "amg": [list(_shape(m, mg.MAT_AMG_A, k)) for k in range(na)]}
+        m.close()
+        return ms, infos, setup_ms, launches, clocks, kt, mem, hier
+
+    ms, infos, setup_ms, launches, clocks, kt, mem, hier = timed("mixed", a.steps, profile=True)
+    xr = x.cpu().numpy()
+    relres = float(np.linalg.norm(b_h - p.to_scipy() @ xr) / np.linalg.norm(b_h))
+    out = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic", "config": config,
+           "iterations": infos[-1]["iterations"], "setup_ms": statistics.mean(setup_ms),
+           "solve_ms": statistics.mean(i["solve_ms"] for i in infos), "relres_true": relres,
+           "solves_per_s_all_gpus": a.gpus * 1000.0 / ms, "gpu_launches": int(launches),
+           "device_memory_gb": mem / 1e9, "hierarchy_rows_nnz": hier}
+    # dominant kernel roofline: the FP64 BSR SpMV of the Krylov iteration (timed live above)
+    peak, peak_kind = _peaks()
+    n_sp, t_sp = kt.get("bsr3_spmv_f64", (0, 0.0))
+    if n_sp:
+        per_launch_bytes = spmv_bytes(p.nb, p.nnzb, residual=False)
+        achieved = per_launch_bytes / (t_sp / n_sp * 1e-3) / 1e9
+        out["roofline"] = {"kernel": "bsr3_spmv_f64", "bound": "hbm", "achieved": achieved, "peak": peak,
+                           "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                           "traffic": None, "bytes_per_launch": per_launch_bytes,
+                           "avg_launch_us": t_sp / n_sp * 1e3, "launches": n_sp}
+    out["kernel_ms_per_step"] = {k: v[1] / a.steps for k, v in kt.items() if v[0]}
+    if clocks:
+        out["clocks"] = clocks
+    if not a.no_fp64:
+        ms64, infos64, setup64, _, _, _, _, _ = timed("fp64", max(1, a.steps))
+        out["fp64"] = {"ms_per_step": ms64, "iterations": infos64[-1]["iterations"],
+                       "setup_ms": statistics.mean(setup64), "solve_ms": statistics.mean(i["solve_ms"] for i in infos64),
+                       "speedup_mixed_vs_fp64": ms64 / ms}
+    if not a.no_e2e:
+        # end to end through the public API with host buffers: pinned host -> device copies of the
+        # matrix, marker and rhs, setup, solve, and the solution back to the host, every step
+        hp = {k: torch.as_tensor(v).pin_memory() for k, v in
+              dict(rp=p.rowptr, ci=p.colind, v=p.values, mk=p.cf_marker, b=b_h).items()}
+        xh = torch.empty(p.n, dtype=torch.float64).pin_memory()
+        m = mg.MGR(precision="mixed", **SOLVER)
+        h2d = sum(t.numel() * t.element_size() for t in hp.values())
+        d2h = xh.numel() * xh.element_size()
+
+        def e2e_step():
+            Ad = mg.BSR3(hp["rp"].cuda(non_blocking=True), hp["ci"].cuda(non_blocking=True),
+                         hp["v"].cuda(non_blocking=True))
+            mkd = hp["mk"].cuda(non_blocking=True)
+            bd = hp["b"].cuda(non_blocking=True)
+            m.setup(Ad, mkd)
+            xd, _ = m.fgmres(Ad, bd, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+            xh.copy_(xd, non_blocking=True)
+
+        for _ in range(a.warmup):
+            e2e_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        m.close()
+        out["e2e"] = {"value": _max(e0.elapsed_time(e1)) / a.steps, "unit": "ms",
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        n_s = 40
+        r = run_oracle_sample(cfg, n_s)
+        scale = (cfg.nx * cfg.ny * cfg.nz) / r["cells"]
+        out["cpu_baseline"] = {"value": (r["setup_s"] + r["solve_s"]) * 1e3 * scale, "unit": "ms", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"{n_s}^3 instance of the {a.workload} recipe, FP64 oracle setup "
+                                         f"{r['setup_s']:.2f} s + solve {r['solve_s']:.2f} s "
+                                         f"({r['iterations']} it), scaled by cell count x{scale:.1f}"}
+    if rank == 0:
+        print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -154,6 +154,14 @@ mgr_status_t mgr_memory_bytes(mgr_handle_t h, int64_t* bytes);
 mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_launches, int64_t* graph_nodes,
                            int64_t* total_launches);
 
+/* Per-kernel timing on the handle's stream: enable = 1 starts recording CUDA events around every
+ * launch of the named kernels and clears earlier totals, enable = 0 stops.  mgr_kernel_time returns
+ * the launches and the summed device milliseconds recorded for `name` (synchronises).  Names:
+ * "bsr3_spmv_f64", "mdot", "mupdate", "global_relax", "bsr_resid_split", "csr_rows", "interp",
+ * "spgemm_numeric". */
+mgr_status_t mgr_profile(mgr_handle_t h, int enable);
+mgr_status_t mgr_kernel_time(mgr_handle_t h, const char* name, int64_t* launches, double* total_ms);
+
 /* ---- stand-alone kernels ----------------------------------------------------------------------- */
 /* y = A x (sub == NULL) or y = sub - A x, FP64, on `cuda_stream`.  The hot sparse product of the
  * Krylov method (section 6).  x, y: double[3 nb], must not overlap. */

@@ -62,7 +62,7 @@ class SolveInfo(ctypes.Structure):
 EXPORTS = ["mgr_status_string", "mgr_options_default", "mgr_create", "mgr_setup", "mgr_apply", "fgmres_solve",
            "mgr_destroy", "mgr_get_levels", "mgr_matrix_shape", "mgr_copy_matrix", "mgr_vector_len",
            "mgr_copy_vector", "mgr_memory_bytes", "mgr_get_stats", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
-           "mgr_bsr3_outer_grad"]
+           "mgr_bsr3_outer_grad", "mgr_profile", "mgr_kernel_time"]
 
 
 def lib():
@@ -93,6 +93,8 @@ def lib():
         L.mgr_bsr3_spmv.argtypes = [P(Bsr3), vp, vp, vp, vp]
         L.mgr_bsr3_transpose.argtypes = [P(Bsr3), vp, vp, vp, vp]
         L.mgr_bsr3_outer_grad.argtypes = [P(Bsr3), vp, vp, vp, vp]
+        L.mgr_profile.argtypes = [vp, i32]
+        L.mgr_kernel_time.argtypes = [vp, ctypes.c_char_p, P(i64), P(ctypes.c_double)]
         for name in EXPORTS:
             getattr(L, name).restype = ctypes.c_int if name not in ("mgr_status_string", "mgr_options_default") \
                 else getattr(L, name).restype
@@ -260,6 +262,16 @@ class MGR:
         out = torch.empty(max(n.value, 1), dtype=torch.float64, device="cuda")
         _check(lib().mgr_copy_vector(self._h, kind, level, _ptr(out)), "mgr_copy_vector")
         return out[: n.value]
+
+    def profile(self, enable: bool = True):
+        """Start (clearing totals) or stop CUDA-event timing of the library's named kernels."""
+        _check(lib().mgr_profile(self._h, 1 if enable else 0), "mgr_profile")
+
+    def kernel_time(self, name: str):
+        """(launches, total device ms) recorded for a named kernel since profile(True)."""
+        n, ms = ctypes.c_int64(), ctypes.c_double()
+        _check(lib().mgr_kernel_time(self._h, name.encode(), ctypes.byref(n), ctypes.byref(ms)), "mgr_kernel_time")
+        return n.value, ms.value
 
     def memory_bytes(self) -> int:
         b = ctypes.c_int64()

@@ -3,6 +3,7 @@
 // precision T (double, or float for the FP32 hierarchy); inputs and outputs at the finest level are
 // FP64.  All are memory-bound sparse / vector kernels (no tensor cores).
 #include "apply.cuh"
+#include "bsr_sell.cuh"
 
 namespace mgr {
 
@@ -23,6 +24,7 @@ __global__ void k_global_relax(int64_t nb, const T* __restrict__ binv, const dou
 
 template <class T>
 void launch_global_relax(Ctx& c, int64_t nb, const T* binv, const double* r, T* e0) {
+  ProfScope ps(c, "global_relax");
   k_global_relax<T><<<grid_for(nb, 256), 256, 0, c.s>>>(nb, binv, r, e0);
   CU_LAUNCH();
 }
@@ -58,10 +60,29 @@ __global__ void __launch_bounds__(256) k_bsr_resid_split(int64_t nb, const int64
 }
 
 template <class T>
-void launch_bsr_resid_split(Ctx& c, int64_t nb, const int64_t* rp, const int32_t* ci, const T* vals, const double* r,
-                            const T* e0, const int32_t* map, T* rnext, T* resF) {
-  k_bsr_resid_split<T><<<grid_for(nb, 256), 256, 0, c.s>>>(nb, rp, ci, vals, r, e0, map, rnext, resF);
-  CU_LAUNCH();
+struct EpiSplit {  // res = r - A e0 routed by map
+  const double* r; const int32_t* map; T* rnext; T* resF;
+  __device__ void operator()(int64_t I, T s0, T s1, T s2) const {
+    T res[3] = {(T)r[3 * I] - s0, (T)r[3 * I + 1] - s1, (T)r[3 * I + 2] - s2};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      int32_t m = map[3 * I + p];
+      if (m >= 0) rnext[m] = res[p];
+      else resF[-m - 1] = res[p];
+    }
+  }
+};
+
+template <class T>
+void launch_bsr_resid_split(Ctx& c, const SellPattern& S, const T* vals, const double* r, const T* e0,
+                            const int32_t* map, T* rnext, T* resF) {
+  ProfScope ps(c, "bsr_resid_split");
+  if (e0) {
+    launch_bsr_sell<T, T>(c, S, vals, e0, EpiSplit<T>{r, map, rnext, resF});
+  } else {
+    k_bsr_resid_split<T><<<grid_for(S.nb, 256), 256, 0, c.s>>>(S.nb, nullptr, nullptr, vals, r, e0, map, rnext, resF);
+    CU_LAUNCH();
+  }
 }
 
 // ============================== generic CSR row kernel ==========================================
@@ -87,6 +108,7 @@ __global__ void __launch_bounds__(256) k_rows(int64_t nr, const int64_t* __restr
 template <class T, class Epi>
 static void run_rows(Ctx& c, const CSRView<T>& M, const T* x, const Epi& epi) {
   if (M.nr <= 0) return;
+  ProfScope ps(c, "csr_rows");
   double avg = M.nr ? (double)M.nnz / (double)M.nr : 0.0;
   const int B = 256;
   if (avg <= 2.5) {
@@ -197,6 +219,7 @@ template <class T, class TO>
 void launch_interp(Ctx& c, int64_t n, const int32_t* map, const CSRView<T>& Wp, const T* eF, const T* ec, const T* base,
                    TO* out) {
   const int B = 256;
+  ProfScope ps(c, "interp");
   double avg = Wp.nr ? (double)Wp.nnz / (double)Wp.nr : 0.0;
   if (avg <= 2.5)
     k_interp<T, TO, 2><<<grid_for(n * 2, B), B, 0, c.s>>>(n, map, Wp.rp, Wp.ci, Wp.v, eF, ec, base, out);
@@ -266,8 +289,8 @@ void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b) {
 // ---- explicit instantiations -------------------------------------------------------------------
 #define INST(T)                                                                                                    \
   template void launch_global_relax<T>(Ctx&, int64_t, const T*, const double*, T*);                               \
-  template void launch_bsr_resid_split<T>(Ctx&, int64_t, const int64_t*, const int32_t*, const T*, const double*,  \
-                                          const T*, const int32_t*, T*, T*);                                       \
+  template void launch_bsr_resid_split<T>(Ctx&, const SellPattern&, const T*, const double*, const T*,            \
+                                          const int32_t*, T*, T*);                                                 \
   template void launch_frelax_first<T>(Ctx&, int64_t, const int32_t*, const T*, const T*, T*);                     \
   template void launch_frelax_sweep<T>(Ctx&, const CSRView<T>&, const int32_t*, const T*, const T*, const T*, T*); \
   template void launch_restrict<T>(Ctx&, const CSRView<T>&, const int32_t*, const T*, const T*, T*);               \

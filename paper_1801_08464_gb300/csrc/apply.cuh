@@ -1,5 +1,6 @@
 // apply.cuh -- launchers of the preconditioner-apply and Krylov kernels.
 #pragma once
+#include "bsr_sell.cuh"
 #include "common.cuh"
 
 namespace mgr {
@@ -22,11 +23,11 @@ inline CSRView<T> view(const DCSR<T>& m) {
 // e0 = blockdiag(A)^-1 r (Algorithm step 1); r is the FP64 input.
 template <class T>
 void launch_global_relax(Ctx& c, int64_t nb, const T* binv, const double* r, T* e0);
-// res = r - A e0 over the BSR (e0 == nullptr: res = r), routed by map: C dofs to rnext[c], F dofs to
-// resF[f].
+// res = r - A e0 over the sliced BSR layout (e0 == nullptr: res = r), routed by map: C dofs to
+// rnext[c], F dofs to resF[f].
 template <class T>
-void launch_bsr_resid_split(Ctx& c, int64_t nb, const int64_t* rp, const int32_t* ci, const T* vals, const double* r,
-                            const T* e0, const int32_t* map, T* rnext, T* resF);
+void launch_bsr_resid_split(Ctx& c, const SellPattern& S, const T* vals, const double* r, const T* e0,
+                            const int32_t* map, T* rnext, T* resF);
 
 // ---- reduction levels ------------------------------------------------------------------------
 // sweep 1 from e = 0: eF = minv * src, src = r[F[f]] (F != nullptr) or resF[f]
@@ -62,15 +63,22 @@ void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b);
 
 // ---- Krylov (FP64) ---------------------------------------------------------------------------
 void launch_bsr3_spmv_f64(Ctx& c, const mgr_bsr3_t& A, const double* x, const double* sub, double* y);
-// Deterministic multi-dot: out[k] = V_k . w for k < nv (V_k = V + k ldv) and, if want_ww,
-// out[nv] = w . w.  `part` must hold KRY_GRID * (nv + 1) doubles.
+// the same product over the sliced layout (values filled by sell_fill_values)
+void launch_sell_spmv_f64(Ctx& c, const SellPattern& S, const double* vals, const double* x, const double* sub,
+                          double* y);
+// Deterministic multi-dot: out[k] = V_k . w for k < nv (V_k = V + k ldv, ldv even) and, if
+// want_ww, out[nv] = w . w.  `part` must hold KRY_PART doubles.
 constexpr int KRY_GRID = 304;
 constexpr int KRY_MAXV = 32;
+constexpr int KRY_PART = 1216 * (KRY_MAXV + 1);
 void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* w, bool want_ww, double* part,
                  double* out);
-// w -= sum_k h[k] V_k (h on device); out[0] = ||w||^2 after the update
-void launch_mupdate(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* h, double* w, double* part,
-                    double* out);
+// vout = scale (w - sum_k h[k] V_k) with h and *scale on the device (scale == nullptr: 1); vout may
+// alias w; out[0] = ||vout||^2 when out != nullptr
+void launch_mupdate(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* h, const double* scale,
+                    const double* w, double* vout, double* part, double* out);
+// out[0] = ww - sum h_k^2 and out[1] = 1 / sqrt(out[0]) (0 if out[0] <= 0)
+void launch_pyth_scale(Ctx& c, int nv, const double* h, const double* ww, double* out);
 // y = alpha x
 void launch_scal(Ctx& c, int64_t n, double alpha, const double* x, double* y);
 // x += sum_k y[k] Z_k (y on device)

@@ -4,7 +4,9 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <stdexcept>
+#include <vector>
 #include <string>
 #include <utility>
 
@@ -42,14 +44,71 @@ enum : int {
 };
 
 // ---------------------------------------------------------------------------------------------
+// Optional per-kernel timing: CUDA events recorded on the launching stream around each launch of a
+// named kernel; elapsed times are summed when queried.
+struct Prof {
+  struct Rec {
+    std::vector<cudaEvent_t> a, b;
+    double ms = 0.0;
+    int64_t n = 0;
+  };
+  std::map<std::string, Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void settle() {  // fold recorded pairs into totals (synchronises on the events)
+    for (auto& kv : recs) {
+      Rec& r = kv.second;
+      for (size_t i = 0; i < r.a.size(); ++i) {
+        float t = 0.f;
+        cudaEventSynchronize(r.b[i]);
+        cudaEventElapsedTime(&t, r.a[i], r.b[i]);
+        r.ms += t;
+        r.n += 1;
+        pool.push_back(r.a[i]);
+        pool.push_back(r.b[i]);
+      }
+      r.a.clear();
+      r.b.clear();
+    }
+  }
+  ~Prof() {
+    settle();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
 // Execution context: stream, device error word, allocation accounting.
 struct Ctx {
+  Prof* prof = nullptr;
   cudaStream_t s = nullptr;
   int* d_err = nullptr;        // device int, error bits
   int* h_pinned = nullptr;     // pinned host scratch (small readbacks)
   int64_t bytes = 0;           // bytes currently allocated through this context
   int64_t peak = 0;
   int num_sms = 152;
+};
+
+struct ProfScope {
+  Ctx& c;
+  const char* name;
+  cudaEvent_t e1 = nullptr;
+  ProfScope(Ctx& ctx, const char* n) : c(ctx), name(n) {
+    if (!c.prof) return;
+    cudaEvent_t e0 = c.prof->get();
+    e1 = c.prof->get();
+    cudaEventRecord(e0, c.s);
+    c.prof->recs[name].a.push_back(e0);
+  }
+  ~ProfScope() {
+    if (!c.prof) return;
+    cudaEventRecord(e1, c.s);
+    c.prof->recs[name].b.push_back(e1);
+  }
 };
 
 void* dev_alloc(Ctx& c, size_t bytes);
@@ -126,6 +185,13 @@ __device__ __forceinline__ int64_t find_i32(const int32_t* a, int64_t lo, int64_
   int64_t p = lower_bound_i32(a, lo, hi, key);
   return (p < hi && a[p] == key) ? p : -1;
 }
+
+// 16-byte asynchronous global->shared copy (cp.async, L2 only) and its completion wait.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -4,6 +4,7 @@
 // gradient.  Reductions are two-stage with a fixed grid, so results do not depend on timing.
 #include "apply.cuh"
 
+
 namespace mgr {
 
 // y = A x or y = sub - A x, one thread per block row
@@ -29,13 +30,32 @@ __global__ void __launch_bounds__(256) k_bsr3_spmv_f64(int64_t nb, const int64_t
   y[3 * I + 2] = s2;
 }
 
+struct EpiSpmvF64 {  // y = A x, or y = sub - A x
+  const double* sub;
+  double* y;
+  __device__ void operator()(int64_t I, double s0, double s1, double s2) const {
+    if (sub) { s0 = sub[3 * I] - s0; s1 = sub[3 * I + 1] - s1; s2 = sub[3 * I + 2] - s2; }
+    y[3 * I] = s0;
+    y[3 * I + 1] = s1;
+    y[3 * I + 2] = s2;
+  }
+};
+
 void launch_bsr3_spmv_f64(Ctx& c, const mgr_bsr3_t& A, const double* x, const double* sub, double* y) {
   k_bsr3_spmv_f64<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.colind, A.values, x, sub, y);
   CU_LAUNCH();
 }
 
+void launch_sell_spmv_f64(Ctx& c, const SellPattern& S, const double* vals, const double* x, const double* sub,
+                          double* y) {
+  ProfScope ps(c, "bsr3_spmv_f64");
+  launch_bsr_sell<double, double>(c, S, vals, x, EpiSpmvF64{sub, y});
+}
+
 // ---- multi-dot ---------------------------------------------------------------------------------
 constexpr int KT = 256;
+constexpr int MD_VEC = 8;        // vectors per block column of the 2-D multi-dot grid
+constexpr int MD_BLOCKS = 1216;  // 8 resident blocks per SM on 152 SMs
 
 template <int NA>
 __device__ __forceinline__ void block_reduce_store(double (&acc)[NA], int na, double* part) {
@@ -56,81 +76,155 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NA], int na, do
   }
 }
 
+// 2-D multi-dot: block b handles vector group g = b % ng (vectors 8g .. 8g+7) on row chunk
+// x = b / ng, so the ng blocks sharing a chunk of w run together and re-read it from L2.  Group 0
+// also accumulates w . w.  Partial sums go to part[k * nx + x] (k = nv for w . w).
 __global__ void __launch_bounds__(KT) k_mdot(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
-                                             const double* __restrict__ w, int ww, double* __restrict__ part) {
-  // acc[0..nv) = V_k . w, acc[KRY_MAXV] = w . w; all indices compile-time after unrolling
-  double acc[KRY_MAXV + 1];
+                                             const double* __restrict__ w, int ww, int ng, int nx, int64_t chunk,
+                                             double* __restrict__ part) {
+  int g = blockIdx.x % ng;
+  int x = blockIdx.x / ng;
+  int k0 = g * MD_VEC;
+  int kn = nv - k0 < MD_VEC ? nv - k0 : MD_VEC;
+  bool dow = ww && g == 0;
+  int64_t i0 = (int64_t)x * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
+  double acc[MD_VEC + 1];
 #pragma unroll
-  for (int k = 0; k <= KRY_MAXV; ++k) acc[k] = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
-    double wi = w[i];
+  for (int k = 0; k <= MD_VEC; ++k) acc[k] = 0.0;
+  // pairs of doubles: chunk is even and ldv is even, so every pair is 16-byte aligned
+  for (int64_t i = i0 + 2 * threadIdx.x; i < i1; i += 2 * KT) {
+    if (i + 1 < i1) {
+      double2 wi = *reinterpret_cast<const double2*>(w + i);
 #pragma unroll
-    for (int k = 0; k < KRY_MAXV; ++k)
-      if (k < nv) acc[k] += V[k * ldv + i] * wi;
-    if (ww) acc[KRY_MAXV] += wi * wi;
-  }
-  __shared__ double sh[KT / 32][KRY_MAXV + 1];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      for (int k = 0; k < MD_VEC; ++k)
+        if (k < kn) {
+          double2 v = __ldg(reinterpret_cast<const double2*>(V + (k0 + k) * ldv + i));
+          acc[k] += v.x * wi.x + v.y * wi.y;
+        }
+      if (dow) acc[MD_VEC] += wi.x * wi.x + wi.y * wi.y;
+    } else {
+      double wi = w[i];
 #pragma unroll
-  for (int k = 0; k <= KRY_MAXV; ++k) {
-    if (k < nv || (k == KRY_MAXV && ww)) {
-      double v = warp_sum(acc[k]);
-      if (lane == 0) sh[wid][k] = v;
+      for (int k = 0; k < MD_VEC; ++k)
+        if (k < kn) acc[k] += V[(k0 + k) * ldv + i] * wi;
+      if (dow) acc[MD_VEC] += wi * wi;
     }
   }
+  __shared__ double sh[KT / 32][MD_VEC + 1];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k <= MD_VEC; ++k) {
+    double v = warp_sum(acc[k]);
+    if (lane == 0) sh[wid][k] = v;
+  }
   __syncthreads();
-  int na = nv + ww;
-  if (threadIdx.x < na) {
-    int k = (threadIdx.x < nv) ? threadIdx.x : KRY_MAXV;
-    double s = 0.0;
-    for (int w2 = 0; w2 < KT / 32; ++w2) s += sh[w2][k];
-    part[(int64_t)blockIdx.x * na + threadIdx.x] = s;
+  if (threadIdx.x <= MD_VEC) {
+    int k = threadIdx.x;
+    if (k < kn || (k == MD_VEC && dow)) {
+      double s = 0.0;
+      for (int w2 = 0; w2 < KT / 32; ++w2) s += sh[w2][k];
+      int out = (k == MD_VEC) ? nv : k0 + k;
+      part[(int64_t)out * nx + x] = s;
+    }
   }
 }
 
-__global__ void k_reduce_final(int nblk, int na, const double* __restrict__ part, double* __restrict__ out) {
-  int k = threadIdx.x;
+// out[k] = sum over the nx partials of k, in a fixed order (a warp per k, strided lanes, then a
+// fixed shuffle tree)
+__global__ void k_reduce_parts(int nx, int na, const double* __restrict__ part, double* __restrict__ out) {
+  int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
   if (k >= na) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * na + k];
-  out[k] = s;
+  for (int x = lane; x < nx; x += 32) s += part[(int64_t)k * nx + x];
+  s = warp_sum(s);
+  if (lane == 0) out[k] = s;
+}
+
+static int md_nx(int64_t n, int ng, int64_t* chunk) {
+  int nx = MD_BLOCKS / ng;
+  if (nx < 1) nx = 1;
+  int64_t c = (n + nx - 1) / nx;
+  c = (c + 1) & ~int64_t(1);
+  if (c < 2 * KT) c = 2 * KT;
+  *chunk = c;
+  return (int)((n + c - 1) / c);
 }
 
 void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* w, bool want_ww, double* part,
                  double* out) {
   if (nv > KRY_MAXV) throw Error(MGR_ERR_UNSUPPORTED, "multi-dot with more than 32 vectors");
   int ww = want_ww ? 1 : 0;
-  k_mdot<<<KRY_GRID, KT, 0, c.s>>>(n, V, ldv, nv, w, ww, part);
+  int ng = (nv + MD_VEC - 1) / MD_VEC;
+  if (ng < 1) ng = 1;
+  int64_t chunk;
+  int nx = md_nx(n, ng, &chunk);
+  ProfScope ps(c, "mdot");
+  k_mdot<<<ng * nx, KT, 0, c.s>>>(n, V, ldv, nv, w, ww, ng, nx, chunk, part);
   CU_LAUNCH();
-  k_reduce_final<<<1, 64, 0, c.s>>>(KRY_GRID, nv + ww, part, out);
+  int na = nv + ww;
+  k_reduce_parts<<<(na + 7) / 8, 256, 0, c.s>>>(nx, na, part, out);
   CU_LAUNCH();
 }
 
-// w -= sum_k h[k] V_k, then ||w||^2
+// v_out = s (w - sum_k h[k] V_k) (h and s read from device memory; s == nullptr means 1), and
+// ||v_out||^2 partials when part != nullptr.  v_out may alias w.
 __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
-                                                const double* __restrict__ h, double* __restrict__ w,
-                                                double* __restrict__ part) {
+                                                const double* __restrict__ h, const double* __restrict__ sp,
+                                                const double* w, double* vout, double* __restrict__ part) {
   __shared__ double sh_h[KRY_MAXV];
   if (threadIdx.x < nv) sh_h[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
+  double sc = sp ? *sp : 1.0;
   double acc[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) {
+  int64_t n2 = n >> 1;
+  for (int64_t q = blockIdx.x * (int64_t)KT + threadIdx.x; q < n2; q += (int64_t)gridDim.x * KT) {
+    int64_t i = 2 * q;
+    double2 s = *reinterpret_cast<const double2*>(w + i);
+#pragma unroll 8
+    for (int k = 0; k < nv; ++k) {
+      double2 v = __ldg(reinterpret_cast<const double2*>(V + k * ldv + i));
+      s.x -= sh_h[k] * v.x;
+      s.y -= sh_h[k] * v.y;
+    }
+    s.x *= sc;
+    s.y *= sc;
+    *reinterpret_cast<double2*>(vout + i) = s;
+    acc[0] += s.x * s.x + s.y * s.y;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    int64_t i = n - 1;
     double s = w[i];
-#pragma unroll
-    for (int k = 0; k < KRY_MAXV; ++k)
-      if (k < nv) s -= sh_h[k] * V[k * ldv + i];
-    w[i] = s;
+    for (int k = 0; k < nv; ++k) s -= sh_h[k] * V[k * ldv + i];
+    s *= sc;
+    vout[i] = s;
     acc[0] += s * s;
   }
-  block_reduce_store<1>(acc, 1, part);
+  if (part) block_reduce_store<1>(acc, 1, part);
 }
 
-void launch_mupdate(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* h, double* w, double* part,
-                    double* out) {
+void launch_mupdate(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* h, const double* scale,
+                    const double* w, double* vout, double* part, double* out) {
   if (nv > KRY_MAXV) throw Error(MGR_ERR_UNSUPPORTED, "update with more than 32 vectors");
-  k_mupdate<<<KRY_GRID, KT, 0, c.s>>>(n, V, ldv, nv, h, w, part);
+  ProfScope ps(c, "mupdate");
+  k_mupdate<<<KRY_GRID, KT, 0, c.s>>>(n, V, ldv, nv, h, scale, w, vout, out ? part : nullptr);
   CU_LAUNCH();
-  k_reduce_final<<<1, 64, 0, c.s>>>(KRY_GRID, 1, part, out);
+  if (out) {
+    k_reduce_parts<<<1, 32, 0, c.s>>>(KRY_GRID, 1, part, out);
+    CU_LAUNCH();
+  }
+}
+
+// s_out = 1 / sqrt(ww - sum_k h_k^2): the Pythagorean norm of w - V h for orthonormal V
+__global__ void k_pyth_scale(int nv, const double* __restrict__ h, const double* __restrict__ ww, double* out) {
+  if (threadIdx.x != 0) return;
+  double s = *ww;
+  for (int k = 0; k < nv; ++k) s -= h[k] * h[k];
+  out[0] = s;                          // squared norm (for the host)
+  out[1] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+}
+void launch_pyth_scale(Ctx& c, int nv, const double* h, const double* ww, double* out) {
+  k_pyth_scale<<<1, 32, 0, c.s>>>(nv, h, ww, out);
   CU_LAUNCH();
 }
 
@@ -142,7 +236,7 @@ __global__ void __launch_bounds__(KT) k_nrm2sq(int64_t n, const double* __restri
 void launch_nrm2sq(Ctx& c, int64_t n, const double* x, double* part, double* out) {
   k_nrm2sq<<<KRY_GRID, KT, 0, c.s>>>(n, x, part);
   CU_LAUNCH();
-  k_reduce_final<<<1, 64, 0, c.s>>>(KRY_GRID, 1, part, out);
+  k_reduce_parts<<<1, 32, 0, c.s>>>(KRY_GRID, 1, part, out);
   CU_LAUNCH();
 }
 

@@ -29,8 +29,10 @@ struct mgr_handle_s {
   int64_t nb = 0, nnzb = 0;
   DBuf<int64_t> rp0;
   DBuf<int32_t> ci0;
-  DBuf<double> val64, binv;
+  DBuf<double> val64, binv;       // val64 / val32: level-0 values in the sliced layout of `sell`
   DBuf<float> val32, binv32;
+  SellPattern sell;               // sliced layout of A's pattern (apply and Krylov products)
+  DBuf<double> kry_vals;          // A's values in the sliced layout, refreshed by each fgmres_solve
   int L = 0;
   std::vector<MgrLevel> lev;  // lev[0..L]; lev[L] holds the coarsest operator only
   std::vector<AmgLevel> amg;
@@ -43,11 +45,12 @@ struct mgr_handle_s {
   std::vector<DBuf<char>> a_b, a_xa, a_xb, a_res;
   // Krylov work
   int kry_m = 0;
-  int64_t kry_n = 0;
+  int64_t kry_n = 0, kry_ld = 0;
   DBuf<double> V, Z, part, dsc;
   double* hpin = nullptr;  // pinned host scratch
   double setup_ms = 0.0;
   int64_t apply_launches = 0;
+  Prof* prof = nullptr;
 };
 
 namespace {
@@ -161,7 +164,7 @@ void apply_t(mgr_handle_s& h, const double* r, double* z) {
   if (e0) launch_global_relax<T>(c, h.nb, binv, r, e0);
   T* r1 = P<T>(h.w_r[1]);
   T* resF0 = P<T>(h.w_resF0);
-  launch_bsr_resid_split<T>(c, h.nb, h.rp0.p, h.ci0.p, vals, r, e0, L0.map.p, r1, resF0);
+  launch_bsr_resid_split<T>(c, h.sell, vals, r, e0, L0.map.p, r1, resF0);
   std::vector<const T*> eF(L);
   eF[0] = frelax<T>(h, 0, resF0, nullptr);
   launch_restrict<T>(c, tv<T>(L0.Acf, L0.Acf32), nullptr, nullptr, eF[0], r1);
@@ -229,10 +232,10 @@ void alloc_work(mgr_handle_s& h) {
 
 void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
   Ctx& c = h.c;
-  int64_t nv = 9 * h.nnzb;
+  int64_t nv = 9 * SELL_C * h.sell.slots;
   if (h.o.precision == MGR_PREC_MIXED) {
     h.val32.alloc(c, nv);
-    launch_cast_f32(c, nv, A.values, h.val32.p);
+    sell_fill_values<double, float>(c, h.sell, A.values, h.val32.p);
     h.binv32.alloc(c, 9 * h.nb);
     launch_cast_f32(c, 9 * h.nb, h.binv.p, h.binv32.p);
     for (int l = 0; l < h.L; ++l) {
@@ -253,7 +256,7 @@ void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
     }
   } else {
     h.val64.alloc(c, nv);
-    CU(cudaMemcpyAsync(h.val64.p, A.values, sizeof(double) * nv, cudaMemcpyDeviceToDevice, c.s));
+    sell_fill_values<double, double>(c, h.sell, A.values, h.val64.p);
   }
 }
 
@@ -265,6 +268,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   h.amg.clear();
   h.cinv.release();
   h.val32.release(); h.val64.release(); h.binv32.release();
+  ProfScope ps_all(c, "setup_total");
   bsr3_validate(c, A, marker);
   h.nb = A.nb;
   h.nnzb = A.nnzb;
@@ -274,6 +278,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   h.ci0.alloc(c, A.nnzb);
   CU(cudaMemcpyAsync(h.rp0.p, A.rowptr, sizeof(int64_t) * (A.nb + 1), cudaMemcpyDeviceToDevice, c.s));
   CU(cudaMemcpyAsync(h.ci0.p, A.colind, sizeof(int32_t) * A.nnzb, cudaMemcpyDeviceToDevice, c.s));
+  sell_build_pattern(c, A.nb, A.rowptr, A.colind, h.sell);
   int L;
   {
     DBuf<int> mx(c, 1);
@@ -299,6 +304,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     lo.omega = h.o.frelax_omega[l];
     lo.restrict_type = h.o.restrict_type[l];
     DBuf<int8_t> mk_next;
+    ProfScope ps(c, "setup_mgr_level");
     mgr_reduce_level(c, h.lev[l], l, lo, h.lev[l + 1].A, mk_next);
     h.lev[l + 1].n = h.lev[l].nC;
     h.lev[l + 1].mk = std::move(mk_next);
@@ -328,25 +334,34 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     ao.pmax = h.o.amg_pmax;
     ao.omega = h.o.amg_omega;
     ao.seed = h.o.amg_seed;
+    ProfScope ps(c, "setup_amg");
     amg_build(c, Ac, ao, h.amg, h.cinv, h.nco);
   }
-  cast_hierarchy(h, A);
-  alloc_work(h);
+  {
+    ProfScope ps(c, "setup_cast_alloc");
+    cast_hierarchy(h, A);
+    alloc_work(h);
+  }
   CU(cudaStreamSynchronize(c.s));
   h.ready = true;
   h.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
 // ---- flexible GMRES ----------------------------------------------------------------------------
+// Krylov basis storage: vector k starts at k * ld with ld = n rounded up to 256 doubles plus 160, so
+// successive vectors are staggered by 1280 bytes across the HBM channels instead of aliasing at a
+// large power-of-two stride; ld is even, so every vector is 16-byte aligned for paired loads.
 void ensure_krylov(mgr_handle_s& h, int m, int64_t n) {
   if (h.kry_m == m && h.kry_n == n) return;
   Ctx& c = h.c;
-  h.V.alloc(c, (size_t)(m + 1) * n);
-  h.Z.alloc(c, (size_t)m * n);
-  h.part.alloc(c, (size_t)KRY_GRID * (KRY_MAXV + 2));
+  int64_t ld = ((n + 255) / 256) * 256 + 160;
+  h.V.alloc(c, (size_t)(m + 1) * ld);
+  h.Z.alloc(c, (size_t)m * ld);
+  h.part.alloc(c, (size_t)KRY_PART);
   h.dsc.alloc(c, 256);
   h.kry_m = m;
   h.kry_n = n;
+  h.kry_ld = ld;
 }
 
 mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, double* x, double rtol, int m, int maxit,
@@ -365,6 +380,13 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
   };
   double* V = h.V.p;
   double* Z = h.Z.p;
+  const int64_t ld = h.kry_ld;
+  // A's values in the sliced layout (the pattern is the one given to mgr_setup)
+  h.kry_vals.alloc(c, 9 * SELL_C * h.sell.slots);
+  sell_fill_values<double, double>(c, h.sell, A.values, h.kry_vals.p);
+  auto spmv = [&](const double* xx, const double* sub, double* yy) {
+    launch_sell_spmv_f64(c, h.sell, h.kry_vals.p, xx, sub, yy);
+  };
   double* dsc = h.dsc.p;
   mgr_status_t st = MGR_OK;
   launch_nrm2sq(c, n, b, h.part.p, dsc);
@@ -376,7 +398,7 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
     CU(cudaMemsetAsync(x, 0, sizeof(double) * n, c.s));
     loc.converged = 1;
   } else {
-    launch_bsr3_spmv_f64(c, A, x, b, V);  // r = b - A x
+    spmv(x, b, V);  // r = b - A x
     launch_nrm2sq(c, n, V, h.part.p, dsc);
     rd(dsc, 1);
     double beta = std::sqrt(hp[0]);
@@ -391,31 +413,37 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
       int k = 0;
       bool stop = false;
       for (int j = 0; j < m && it < maxit; ++j) {
-        double* vj = V + (int64_t)j * n;
-        double* zj = Z + (int64_t)j * n;
-        double* w = V + (int64_t)(j + 1) * n;
+        double* vj = V + (int64_t)j * ld;
+        double* zj = Z + (int64_t)j * ld;
+        double* w = V + (int64_t)(j + 1) * ld;
         do_apply(h, vj, zj);
-        launch_bsr3_spmv_f64(c, A, zj, nullptr, w);
-        // classical Gram-Schmidt, then a second pass when the norm dropped by more than 1/sqrt(2)
-        launch_mdot(c, n, V, n, j + 1, w, true, h.part.p, dsc);
-        launch_mupdate(c, n, V, n, j + 1, dsc, w, h.part.p, dsc + 64);
-        rd(dsc, 65);
+        spmv(zj, nullptr, w);
+        // classical Gram-Schmidt: h = V^T w and w.w in one pass; the norm of w - V h follows from
+        // Pythagoras; when it drops below 1/sqrt(2) of ||w|| a second pass re-orthogonalises
+        launch_mdot(c, n, V, ld, j + 1, w, true, h.part.p, dsc);
+        launch_pyth_scale(c, j + 1, dsc, dsc + j + 1, dsc + 64);
+        rd(dsc, 66);
         double hcol[KRY_MAXV + 2];
         for (int i = 0; i <= j; ++i) hcol[i] = hp[i];
-        double nw0 = std::sqrt(hp[j + 1]);
-        double nw = std::sqrt(hp[64]);
-        if (!(nw >= eta * nw0)) {
-          launch_mdot(c, n, V, n, j + 1, w, false, h.part.p, dsc + 96);
-          launch_mupdate(c, n, V, n, j + 1, dsc + 96, w, h.part.p, dsc + 160);
-          CU(cudaMemcpyAsync(hp + 96, dsc + 96, sizeof(double) * 65, cudaMemcpyDeviceToHost, c.s));
+        double ww = hp[j + 1], nrm2 = hp[64];
+        double nw;
+        if (nrm2 >= eta * eta * ww && std::isfinite(nrm2)) {
+          launch_mupdate(c, n, V, ld, j + 1, dsc, dsc + 65, w, w, h.part.p, nullptr);
+          nw = std::sqrt(nrm2);
+        } else {
+          launch_mupdate(c, n, V, ld, j + 1, dsc, nullptr, w, w, h.part.p, nullptr);
+          launch_mdot(c, n, V, ld, j + 1, w, true, h.part.p, dsc + 96);
+          launch_pyth_scale(c, j + 1, dsc + 96, dsc + 96 + j + 1, dsc + 160);
+          CU(cudaMemcpyAsync(hp + 96, dsc + 96, sizeof(double) * 66, cudaMemcpyDeviceToHost, c.s));
           CU(cudaStreamSynchronize(c.s));
           for (int i = 0; i <= j; ++i) hcol[i] += hp[96 + i];
-          nw = std::sqrt(hp[96 + 64]);
+          double n2 = hp[96 + 64];
+          nw = n2 > 0.0 ? std::sqrt(n2) : 0.0;
+          launch_mupdate(c, n, V, ld, j + 1, dsc + 96, dsc + 161, w, w, h.part.p, nullptr);
         }
         if (!std::isfinite(nw)) { st = MGR_ERR_BREAKDOWN; stop = true; break; }
         for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
         H[(size_t)(j + 1) * m + j] = nw;
-        if (nw != 0.0) launch_scal(c, n, 1.0 / nw, w, w);
         for (int i = 0; i < j; ++i) {
           double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
           H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
@@ -444,10 +472,10 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
       if (k > 0) {
         memcpy(hp + 200, y.data(), sizeof(double) * k);
         CU(cudaMemcpyAsync(dsc + 200, hp + 200, sizeof(double) * k, cudaMemcpyHostToDevice, c.s));
-        launch_xupdate(c, n, Z, n, k, dsc + 200, x);
+        launch_xupdate(c, n, Z, ld, k, dsc + 200, x);
       }
       loc.relres_est = (k > 0) ? std::fabs(g[k]) / bnorm : beta / bnorm;
-      launch_bsr3_spmv_f64(c, A, x, b, V);
+      spmv(x, b, V);
       launch_nrm2sq(c, n, V, h.part.p, dsc);
       rd(dsc, 1);
       beta = std::sqrt(hp[0]);
@@ -633,7 +661,10 @@ mgr_status_t mgr_destroy(mgr_handle_t h) {
     cudaStream_t s = h->c.s;
     int* e = h->c.d_err;
     double* hp = h->hpin;
+    Prof* pr = h->prof;
+    h->c.prof = nullptr;
     delete h;
+    delete pr;
     cudaStreamSynchronize(s);
     if (e) cudaFree(e);
     if (hp) cudaFreeHost(hp);
@@ -709,6 +740,33 @@ mgr_status_t mgr_copy_vector(mgr_handle_t h, int kind, int level, double* out) {
       CU_LAUNCH();
     }
     CU(cudaStreamSynchronize(c.s));
+  });
+}
+
+mgr_status_t mgr_profile(mgr_handle_t h, int enable) {
+  if (!h) return MGR_ERR_INVALID_ARG;
+  return guarded(h, [&] {
+    CU(cudaStreamSynchronize(h->c.s));
+    if (enable) {
+      if (!h->prof) h->prof = new Prof();
+      h->prof->settle();
+      h->prof->recs.clear();
+      h->c.prof = h->prof;
+    } else {
+      h->c.prof = nullptr;
+    }
+  });
+}
+
+mgr_status_t mgr_kernel_time(mgr_handle_t h, const char* name, int64_t* launches, double* total_ms) {
+  if (!h || !name || !launches || !total_ms) return MGR_ERR_INVALID_ARG;
+  *launches = 0;
+  *total_ms = 0.0;
+  if (!h->prof) return MGR_OK;
+  return guarded(h, [&] {
+    h->prof->settle();
+    auto it = h->prof->recs.find(name);
+    if (it != h->prof->recs.end()) { *launches = it->second.n; *total_ms = it->second.ms; }
   });
 }
 

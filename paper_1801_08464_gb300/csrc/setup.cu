@@ -227,6 +227,7 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
   }
   // coarse operator R (A P) and coarse markers
   {
+    ProfScope ps(c, "setup_mgr_rap");
     DCSR<double> AP;
     spgemm(c, A, L.P, AP);
     spgemm(c, L.R, AP, Anext);
@@ -624,8 +625,14 @@ void amg_build(Ctx& c, const DCSR<double>& A0, const AmgOpts& o, std::vector<Amg
   while (lv[k].n > o.max_coarse && k < maxlev - 1) {
     AmgLevel& L = lv[k];
     int64_t n = L.n;
-    strength(c, L.A, o.theta, L.S);
-    pmis(c, L.S, o.seed, k, L.cf);
+    {
+      ProfScope ps(c, "setup_amg_strength");
+      strength(c, L.A, o.theta, L.S);
+    }
+    {
+      ProfScope ps(c, "setup_amg_pmis");
+      pmis(c, L.S, o.seed, k, L.cf);
+    }
     int64_t nC;
     {
       DBuf<int32_t> flag(c, n), pre(c, n + 1);
@@ -639,14 +646,21 @@ void amg_build(Ctx& c, const DCSR<double>& A0, const AmgOpts& o, std::vector<Amg
       L.S = DCSR<double>();
       break;
     }
-    extpi(c, L.A, L.S, L.cf, nC, o.pmax, L.P);
-    transpose(c, L.P, L.R);
+    {
+      ProfScope ps(c, "setup_amg_extpi");
+      extpi(c, L.A, L.S, L.cf, nC, o.pmax, L.P);
+    }
+    {
+      ProfScope ps(c, "setup_amg_transpose");
+      transpose(c, L.P, L.R);
+    }
     L.dinv.alloc(c, n);
     k_smoother_diag<<<grid_for(n, B), B, 0, c.s>>>(n, L.A.rp, L.A.ci, L.A.v, o.smoother, o.omega, L.dinv.p, c.d_err);
     CU_LAUNCH();
     check_errors(c, "AMG smoother diagonal");
     AmgLevel next;
     {
+      ProfScope ps(c, "setup_amg_rap");
       DCSR<double> AP;
       spgemm(c, L.A, L.P, AP);
       spgemm(c, L.R, AP, next.A);
@@ -657,6 +671,7 @@ void amg_build(Ctx& c, const DCSR<double>& A0, const AmgOpts& o, std::vector<Amg
   }
   nco = lv.back().n;
   if (nco > 4096) throw Error(MGR_ERR_UNSUPPORTED, "AMG coarsest grid larger than 4096 rows");
+  ProfScope ps(c, "setup_dense_inverse");
   dense_inverse(c, lv.back().A, cinv);
   check_errors(c, "AMG coarsest inverse");
 }

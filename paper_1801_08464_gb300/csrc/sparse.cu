@@ -393,6 +393,7 @@ static void sym_pass(Ctx& c, int mode, const DCSR<double>& A, const DCSR<double>
 
 void spgemm_symbolic(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C) {
   if (A.nc != B.nr) throw Error(MGR_ERR_INVALID_ARG, "spgemm: inner dimensions differ");
+  ProfScope ps(c, "spgemm_symbolic");
   int64_t m = A.nr;
   C.nr = m;
   C.nc = B.nc;
@@ -419,51 +420,128 @@ void spgemm_symbolic(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<
 }
 
 // ---------------------------------------------------------------------------------------------
-// SpGEMM numeric: one warp per row of C.  The A row is walked in ascending order; for each k the
-// lanes add a_ik * b_kj to the entry j of the (sorted) C row found by binary search.  Entries of one
-// B row have distinct columns, and __syncwarp orders successive k, so every C entry is the sum over
-// ascending k, starting from 0.0.  Rows up to NUM_CAP entries accumulate in shared memory, longer
-// rows in the output array.
+// SpGEMM numeric.  Every entry of C is the sum over ascending intermediate index k of a_ik b_kj,
+// starting from 0.0 (Gustavson's order), computed with explicit round-to-nearest multiplies and adds.
+//
+// k_spgemm_numeric_expand (rows with at most NX_CAPA entries in A and NX_CAPC in C): a warp per row
+// enumerates the products of row i in (k, q) order, 32 at a time, one per lane.  Lanes whose products
+// land on the same output entry are grouped with __match_any_sync; the lowest lane of a group adds the
+// group's products in lane order, and groups of successive chunks are added in chunk order, so each
+// entry still receives its products in ascending k.  All lanes work even when the rows of B are short.
+// k_spgemm_numeric (the remaining rows): the A row is walked in ascending order; for each k the lanes
+// add a_ik b_kj to entry j of the sorted C row found by binary search (distinct j within one B row,
+// __syncwarp between successive k), accumulating in the output array.
 constexpr int NUM_WARPS = 8;
-constexpr int NUM_CAP = 384;
+constexpr int NX_WARPS = 4;
+constexpr int NX_CAPA = 256;
+constexpr int NX_CAPC = 512;
+
+__global__ void __launch_bounds__(32 * NX_WARPS) k_spgemm_numeric_expand(
+    int64_t m, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
+    const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
+    const int64_t* __restrict__ crp, const int32_t* __restrict__ cci, double* __restrict__ cv) {
+  __shared__ int32_t scol[NX_WARPS][NX_CAPC];
+  __shared__ double sacc[NX_WARPS][NX_CAPC];
+  __shared__ int32_t sstart[NX_WARPS][NX_CAPA + 1];
+  __shared__ int64_t sbeg[NX_WARPS][NX_CAPA];
+  __shared__ double sa[NX_WARPS][NX_CAPA];
+  __shared__ double sval[NX_WARPS][32];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = (int64_t)blockIdx.x * NX_WARPS + w;
+  if (i >= m) return;
+  int64_t a0 = arp[i], c0 = crp[i];
+  int na = (int)(arp[i + 1] - a0), L = (int)(crp[i + 1] - c0);
+  if (na > NX_CAPA || L > NX_CAPC) return;  // handled by k_spgemm_numeric
+  for (int t = lane; t < L; t += 32) { scol[w][t] = cci[c0 + t]; sacc[w][t] = 0.0; }
+  // exclusive scan of the B row lengths along the A row
+  int carry = 0;
+  for (int p0 = 0; p0 < na; p0 += 32) {
+    int p = p0 + lane;
+    int len = 0;
+    if (p < na) {
+      int32_t k = aci[a0 + p];
+      int64_t b0 = brp[k];
+      len = (int)(brp[k + 1] - b0);
+      sbeg[w][p] = b0;
+      sa[w][p] = av[a0 + p];
+    }
+    int x = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (p < na) sstart[w][p] = carry + x - len;
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) sstart[w][na] = carry;
+  __syncwarp();
+  int P = carry;
+  for (int t0 = 0; t0 < P; t0 += 32) {
+    int t = t0 + lane;
+    int pos = -1 - lane;  // distinct sentinel: idle lanes never group with each other
+    double val = 0.0;
+    if (t < P) {
+      // product t belongs to A entry p with sstart[p] <= t < sstart[p+1]
+      int lo = 0, hi = na;
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (sstart[w][mid] <= t) lo = mid; else hi = mid;
+      }
+      int64_t q = sbeg[w][lo] + (t - sstart[w][lo]);
+      val = __dmul_rn(sa[w][lo], bv[q]);
+      pos = (int)lower_bound_i32(scol[w], 0, L, bci[q]);
+    }
+    unsigned grp = __match_any_sync(0xffffffffu, pos);
+    sval[w][lane] = val;
+    __syncwarp();
+    if (t < P && lane == __ffs(grp) - 1) {
+      double acc = sacc[w][pos];
+      unsigned g = grp;
+      while (g) {
+        int l = __ffs(g) - 1;
+        acc = __dadd_rn(acc, sval[w][l]);
+        g &= g - 1;
+      }
+      sacc[w][pos] = acc;
+    }
+    __syncwarp();
+  }
+  for (int t = lane; t < L; t += 32) cv[c0 + t] = sacc[w][t];
+}
 
 __global__ void __launch_bounds__(32 * NUM_WARPS) k_spgemm_numeric(int64_t m, const int64_t* arp, const int32_t* aci,
                                                                     const double* av, const int64_t* brp,
                                                                     const int32_t* bci, const double* bv,
                                                                     const int64_t* crp, const int32_t* cci, double* cv) {
-  __shared__ int32_t scol[NUM_WARPS][NUM_CAP];
-  __shared__ double sacc[NUM_WARPS][NUM_CAP];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * NUM_WARPS + w;
   if (i >= m) return;
   int64_t c0 = crp[i], c1 = crp[i + 1];
-  int L = (int)(c1 - c0);
-  bool inshared = L <= NUM_CAP;
-  const int32_t* col = inshared ? scol[w] : cci + c0;
-  double* acc = inshared ? sacc[w] : cv + c0;
-  for (int t = lane; t < L; t += 32) {
-    if (inshared) scol[w][t] = cci[c0 + t];
-    acc[t] = 0.0;
-  }
+  int64_t L = c1 - c0;
+  if (arp[i + 1] - arp[i] <= NX_CAPA && L <= NX_CAPC) return;  // done by the expand kernel
+  const int32_t* col = cci + c0;
+  double* acc = cv + c0;
+  for (int64_t t = lane; t < L; t += 32) acc[t] = 0.0;
   __syncwarp();
   for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
     int32_t k = aci[p];
     double a = av[p];
     for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
-      int32_t j = bci[q];
-      int64_t pos = lower_bound_i32(col, 0, L, j);
+      int64_t pos = lower_bound_i32(col, 0, L, bci[q]);
       acc[pos] = __dadd_rn(acc[pos], __dmul_rn(a, bv[q]));
     }
     __syncwarp();
   }
-  if (inshared)
-    for (int t = lane; t < L; t += 32) cv[c0 + t] = acc[t];
 }
 
 void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C) {
   spgemm_symbolic(c, A, B, C);
   C.v.alloc(c, C.nnz);
   if (C.nr == 0) return;
+  ProfScope ps(c, "spgemm_numeric");
+  k_spgemm_numeric_expand<<<grid_for(C.nr, NX_WARPS), 32 * NX_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci,
+                                                                                B.v, C.rp, C.ci, C.v);
+  CU_LAUNCH();
   k_spgemm_numeric<<<grid_for(C.nr, NUM_WARPS), 32 * NUM_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
                                                                            C.rp, C.ci, C.v);
   CU_LAUNCH();
