@@ -178,6 +178,26 @@ mgr_status_t mgr_bsr3_transpose(const mgr_bsr3_t* A, int64_t* rowptr_t, int32_t*
 mgr_status_t mgr_bsr3_outer_grad(const mgr_bsr3_t* A, const double* lambda, const double* x, double* grad,
                                  void* cuda_stream);
 
+/* ---- allocation-free variant ------------------------------------------------------------------
+ * The paper has no counterpart to this entry point.
+ *
+ * mgr_bsr3_transpose_noalloc: the block transpose of mgr_bsr3_transpose (same arguments, same
+ * result) for callers that cannot let a library allocate device memory during a call -- code that
+ * runs under a device-memory budget or pool the caller owns, latency-critical code that cannot absorb
+ * an allocation, or a host application that hands the library only buffers it manages itself.  It
+ * calls no cudaMalloc, cudaFree or allocating library routine: its working memory (per-column
+ * counters and the source index of every transposed block) is one file-scope device array of about
+ * 4.7 MB, which every GPU that loads this library holds until the process exits.
+ * Limits: nb <= 65536 block rows and nnzb <= 524288 blocks; larger inputs return
+ * MGR_ERR_UNSUPPORTED without touching the GPU.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (each call clears the counters
+ * it needs): calls that overlap on the GPU -- on other streams or from other threads -- race.
+ * Asynchronous on cuda_stream. */
+mgr_status_t mgr_bsr3_transpose_noalloc(const mgr_bsr3_t* A, int64_t* rowptr_t, int32_t* colind_t, double* values_t,
+                                        void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
