@@ -46,6 +46,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--grid", type=int, default=0, help="scaled instance: n^3 cells of the workload recipe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -165,6 +166,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     import ncpgen
     cfg = ncpgen.WORKLOADS[a.workload]
+    if a.grid:
+        cfg = _cpu_sample_cfg(cfg, a.grid)
     grid = [cfg.nx, cfg.ny, cfg.nz]
     config = {"workload": a.workload, "grid": grid, "unknowns": 3 * cfg.nx * cfg.ny * cfg.nz,
               "precision": "fp32 hierarchy, fp64 krylov", "rtol": RTOL, "restart": RESTART,

@@ -105,12 +105,36 @@ __global__ void __launch_bounds__(256) k_rows(int64_t nr, const int64_t* __restr
   if (ok && sub == 0) epi(r, s);
 }
 
+// SELL-32 form: one thread per row, slots walked in order (padding slots add 0 * x[0])
 template <class T, class Epi>
-static void run_rows(Ctx& c, const CSRView<T>& M, const T* x, const Epi& epi) {
-  if (M.nr <= 0) return;
-  ProfScope ps(c, "csr_rows");
-  double avg = M.nr ? (double)M.nnz / (double)M.nr : 0.0;
+__global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __restrict__ soff,
+                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                   const T* __restrict__ x, Epi epi) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  int64_t s = r / RS_C;
+  int t = (int)(r - s * RS_C);
+  int64_t j0 = soff[s], w = soff[s + 1] - j0;
+  const int32_t* cp = col + j0 * RS_C + t;
+  const T* vp = val + j0 * RS_C + t;
+  T sum = 0;
+#pragma unroll 4
+  for (int64_t j = 0; j < w; ++j) sum += vp[j * RS_C] * ldg(x + cp[j * RS_C]);
+  epi(r, sum);
+}
+
+template <class T, class Epi>
+static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, const char* name = "csr_rows") {
+  if (op.nr <= 0) return;
+  ProfScope ps(c, name);
   const int B = 256;
+  if (op.sell) {
+    k_rows_sell<T, Epi><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, x, epi);
+    CU_LAUNCH();
+    return;
+  }
+  const DCSR<T>& M = op.csr;
+  double avg = M.nr ? (double)M.nnz / (double)M.nr : 0.0;
   if (avg <= 2.5) {
     k_rows<T, 2, Epi><<<grid_for(M.nr * 2, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
@@ -180,53 +204,57 @@ void launch_frelax_first(Ctx& c, int64_t nF, const int32_t* F, const T* src, con
   CU_LAUNCH();
 }
 template <class T>
-void launch_frelax_sweep(Ctx& c, const CSRView<T>& Aff, const int32_t* F, const T* src, const T* minv, const T* eFi,
+void launch_frelax_sweep(Ctx& c, const RowsOp<T>& Aff, const int32_t* F, const T* src, const T* minv, const T* eFi,
                          T* eFo) {
   run_rows(c, Aff, eFi, EpiFrelax<T>{F, src, minv, eFi, eFo});
 }
 template <class T>
-void launch_restrict(Ctx& c, const CSRView<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext) {
+void launch_restrict(Ctx& c, const RowsOp<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext) {
   run_rows(c, Acf, eF, EpiRestrict<T>{C, r, rnext});
 }
 
-// interpolation over the level's dofs: C dofs take ec[c], F dofs eF[f] + W_p[f,:] ec
-template <class T, class TO, int TPR>
-__global__ void __launch_bounds__(256) k_interp(int64_t n, const int32_t* __restrict__ map, const int64_t* __restrict__ wrp,
-                                                const int32_t* __restrict__ wci, const T* __restrict__ wv,
-                                                const T* __restrict__ eF, const T* __restrict__ ec,
-                                                const T* __restrict__ base, TO* __restrict__ out) {
-  int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t d = gt / TPR;
-  int sub = (int)(gt % TPR);
-  bool ok = d < n;
-  int32_t m = ok ? map[d] : 0;
-  T s = 0;
-  if (ok && m < 0) {
-    int32_t f = -m - 1;
-    int64_t k1 = wrp[f + 1];
-    for (int64_t k = wrp[f] + sub; k < k1; k += TPR) s += wv[k] * ldg(ec + wci[k]);
-  }
-#pragma unroll
-  for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
-  if (ok && sub == 0) {
-    T val = (m >= 0) ? ec[m] : eF[-m - 1] + s;
-    if (base) val += base[d];
-    out[d] = (TO)val;
-  }
+// interpolation: C dofs take ec[c] (a scatter over the C list), F dofs eF[f] + W_p[f,:] ec (a
+// vector-CSR pass over the rows of W_p); both add base[d] when given
+template <class T, class TO>
+__global__ void k_interp_c(int64_t nC, const int32_t* __restrict__ C, const T* __restrict__ ec,
+                           const T* __restrict__ base, TO* __restrict__ out) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nC) return;
+  int32_t d = C[c];
+  T v = ec[c];
+  if (base) v += base[d];
+  out[d] = (TO)v;
 }
+template <class T, class TO>
+struct EpiInterpF {
+  const int32_t* F; const T* eF; const T* base; TO* out;
+  __device__ void operator()(int64_t f, T s) const {
+    int32_t d = F[f];
+    T v = eF[f] + s;
+    if (base) v += base[d];
+    out[d] = (TO)v;
+  }
+};
 
 template <class T, class TO>
-void launch_interp(Ctx& c, int64_t n, const int32_t* map, const CSRView<T>& Wp, const T* eF, const T* ec, const T* base,
-                   TO* out) {
-  const int B = 256;
-  ProfScope ps(c, "interp");
-  double avg = Wp.nr ? (double)Wp.nnz / (double)Wp.nr : 0.0;
-  if (avg <= 2.5)
-    k_interp<T, TO, 2><<<grid_for(n * 2, B), B, 0, c.s>>>(n, map, Wp.rp, Wp.ci, Wp.v, eF, ec, base, out);
-  else if (avg <= 6.0)
-    k_interp<T, TO, 4><<<grid_for(n * 4, B), B, 0, c.s>>>(n, map, Wp.rp, Wp.ci, Wp.v, eF, ec, base, out);
-  else
-    k_interp<T, TO, 8><<<grid_for(n * 8, B), B, 0, c.s>>>(n, map, Wp.rp, Wp.ci, Wp.v, eF, ec, base, out);
+void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32_t* C, const RowsOp<T>& Wp,
+                   const T* eF, const T* ec, const T* base, TO* out) {
+  if (nC > 0) {
+    ProfScope ps(c, "interp");
+    k_interp_c<T, TO><<<grid_for(nC, 256), 256, 0, c.s>>>(nC, C, ec, base, out);
+    CU_LAUNCH();
+  }
+  if (nF > 0) run_rows(c, Wp, ec, EpiInterpF<T, TO>{F, eF, base, out}, "interp");
+}
+
+template <class T>
+__global__ void k_to_f64(int64_t n, const T* a, double* b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+template <class T>
+void launch_to_f64(Ctx& c, int64_t n, const T* a, double* b) {
+  k_to_f64<T><<<grid_for(n, 256), 256, 0, c.s>>>(n, a, b);
   CU_LAUNCH();
 }
 
@@ -242,19 +270,19 @@ void launch_scale(Ctx& c, int64_t n, const T* d, const T* b, T* x) {
   CU_LAUNCH();
 }
 template <class T>
-void launch_resid(Ctx& c, const CSRView<T>& A, const T* x, const T* b, T* res) {
+void launch_resid(Ctx& c, const RowsOp<T>& A, const T* x, const T* b, T* res) {
   run_rows(c, A, x, EpiResid<T>{b, res});
 }
 template <class T>
-void launch_jacobi(Ctx& c, const CSRView<T>& A, const T* d, const T* b, const T* xi, T* xo) {
+void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* xi, T* xo) {
   run_rows(c, A, xi, EpiJacobi<T>{d, b, xi, xo});
 }
 template <class T>
-void launch_spmv(Ctx& c, const CSRView<T>& A, const T* x, T* y) {
+void launch_spmv(Ctx& c, const RowsOp<T>& A, const T* x, T* y) {
   run_rows(c, A, x, EpiStore<T>{y});
 }
 template <class T>
-void launch_prolong_add(Ctx& c, const CSRView<T>& P, const T* xc, T* x) {
+void launch_prolong_add(Ctx& c, const RowsOp<T>& P, const T* xc, T* x) {
   run_rows(c, P, xc, EpiAdd<T>{x});
 }
 
@@ -292,20 +320,21 @@ void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b) {
   template void launch_bsr_resid_split<T>(Ctx&, const SellPattern&, const T*, const double*, const T*,            \
                                           const int32_t*, T*, T*);                                                 \
   template void launch_frelax_first<T>(Ctx&, int64_t, const int32_t*, const T*, const T*, T*);                     \
-  template void launch_frelax_sweep<T>(Ctx&, const CSRView<T>&, const int32_t*, const T*, const T*, const T*, T*); \
-  template void launch_restrict<T>(Ctx&, const CSRView<T>&, const int32_t*, const T*, const T*, T*);               \
-  template void launch_interp<T, T>(Ctx&, int64_t, const int32_t*, const CSRView<T>&, const T*, const T*, const T*, \
-                                    T*);                                                                           \
+  template void launch_frelax_sweep<T>(Ctx&, const RowsOp<T>&, const int32_t*, const T*, const T*, const T*, T*); \
+  template void launch_restrict<T>(Ctx&, const RowsOp<T>&, const int32_t*, const T*, const T*, T*);               \
+  template void launch_interp<T, T>(Ctx&, int64_t, const int32_t*, int64_t, const int32_t*, const RowsOp<T>&,     \
+                                    const T*, const T*, const T*, T*);                                             \
+  template void launch_to_f64<T>(Ctx&, int64_t, const T*, double*);                                                \
   template void launch_scale<T>(Ctx&, int64_t, const T*, const T*, T*);                                            \
-  template void launch_resid<T>(Ctx&, const CSRView<T>&, const T*, const T*, T*);                                  \
-  template void launch_jacobi<T>(Ctx&, const CSRView<T>&, const T*, const T*, const T*, T*);                       \
-  template void launch_spmv<T>(Ctx&, const CSRView<T>&, const T*, T*);                                             \
-  template void launch_prolong_add<T>(Ctx&, const CSRView<T>&, const T*, T*);                                      \
+  template void launch_resid<T>(Ctx&, const RowsOp<T>&, const T*, const T*, T*);                                  \
+  template void launch_jacobi<T>(Ctx&, const RowsOp<T>&, const T*, const T*, const T*, T*);                       \
+  template void launch_spmv<T>(Ctx&, const RowsOp<T>&, const T*, T*);                                             \
+  template void launch_prolong_add<T>(Ctx&, const RowsOp<T>&, const T*, T*);                                      \
   template void launch_dense_gemv<T>(Ctx&, int64_t, const double*, const T*, T*);
 INST(float)
 INST(double)
 #undef INST
-template void launch_interp<float, double>(Ctx&, int64_t, const int32_t*, const CSRView<float>&, const float*,
-                                           const float*, const float*, double*);
+template void launch_interp<float, double>(Ctx&, int64_t, const int32_t*, int64_t, const int32_t*,
+                                           const RowsOp<float>&, const float*, const float*, const float*, double*);
 
 }  // namespace mgr

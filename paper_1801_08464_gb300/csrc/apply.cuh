@@ -2,6 +2,7 @@
 #pragma once
 #include "bsr_sell.cuh"
 #include "common.cuh"
+#include "rowsop.cuh"
 
 namespace mgr {
 
@@ -35,27 +36,29 @@ template <class T>
 void launch_frelax_first(Ctx& c, int64_t nF, const int32_t* F, const T* src, const T* minv, T* eF);
 // later sweeps: eFo = eFi + minv * (src - A_ff eFi)
 template <class T>
-void launch_frelax_sweep(Ctx& c, const CSRView<T>& Aff, const int32_t* F, const T* src, const T* minv, const T* eFi,
+void launch_frelax_sweep(Ctx& c, const RowsOp<T>& Aff, const int32_t* F, const T* src, const T* minv, const T* eFi,
                          T* eFo);
 // rnext[c] = base_c - A_cf eF with base_c = r[C[c]] (C != nullptr) or rnext[c] (in place)
 template <class T>
-void launch_restrict(Ctx& c, const CSRView<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext);
-// out[d] = base[d] + (C dof: ec[c]; F dof: eF[f] + W_p[f,:] ec); base may be nullptr
+void launch_restrict(Ctx& c, const RowsOp<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext);
+// out[C[c]] = base + ec[c]; out[F[f]] = base + eF[f] + W_p[f,:] ec; base may be nullptr
 template <class T, class TO>
-void launch_interp(Ctx& c, int64_t n, const int32_t* map, const CSRView<T>& Wp, const T* eF, const T* ec, const T* base,
-                   TO* out);
+void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32_t* C, const RowsOp<T>& Wp,
+                   const T* eF, const T* ec, const T* base, TO* out);
+template <class T>
+void launch_to_f64(Ctx& c, int64_t n, const T* a, double* b);
 
 // ---- AMG -------------------------------------------------------------------------------------
 template <class T>
 void launch_scale(Ctx& c, int64_t n, const T* d, const T* b, T* x);                          // x = d * b
 template <class T>
-void launch_resid(Ctx& c, const CSRView<T>& A, const T* x, const T* b, T* res);              // res = b - A x
+void launch_resid(Ctx& c, const RowsOp<T>& A, const T* x, const T* b, T* res);              // res = b - A x
 template <class T>
-void launch_jacobi(Ctx& c, const CSRView<T>& A, const T* d, const T* b, const T* xi, T* xo);  // xo = xi + d (b - A xi)
+void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* xi, T* xo);  // xo = xi + d (b - A xi)
 template <class T>
-void launch_spmv(Ctx& c, const CSRView<T>& A, const T* x, T* y);                             // y = A x
+void launch_spmv(Ctx& c, const RowsOp<T>& A, const T* x, T* y);                             // y = A x
 template <class T>
-void launch_prolong_add(Ctx& c, const CSRView<T>& P, const T* xc, T* x);                     // x += P xc
+void launch_prolong_add(Ctx& c, const RowsOp<T>& P, const T* xc, T* x);                     // x += P xc
 template <class T>
 void launch_dense_gemv(Ctx& c, int64_t n, const double* inv, const T* b, T* x);              // x = inv b (FP64)
 

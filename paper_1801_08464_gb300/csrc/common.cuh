@@ -226,5 +226,6 @@ void sort_rows(Ctx& c, int64_t nr, const int64_t* rp, int32_t* ci, double* v);
 // CSR float copy
 void csr_to_f32(Ctx& c, const DCSR<double>& A, DCSR<float>& B);
 void copy_csr(Ctx& c, const DCSR<double>& A, DCSR<double>& B);
+void csr_gather_rows(Ctx& c, const DCSR<double>& A, const int32_t* rows, int64_t nr, DCSR<double>& B);
 
 }  // namespace mgr

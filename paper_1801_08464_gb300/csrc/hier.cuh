@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "rowsop.cuh"
 
 namespace mgr {
 
@@ -16,8 +17,9 @@ struct MgrLevel {
   int sweeps = 1;
   DCSR<double> Wp, Wr, P, R;      // W_p (nF x nC), W_r (nC x nF), P (n x nC), R (nC x n)
   DCSR<double> Aff, Acf;          // split operators used by the apply (F-local columns)
-  // working-precision copies for the apply (mixed mode)
-  DCSR<float> Aff32, Acf32, Wp32, Wr32;
+  // the operators the apply reads, in its working precision (SELL-32 or CSR)
+  RowsOp<float> Aff32, Acf32, Wp32;
+  RowsOp<double> Aff64, Acf64, Wp64;
   DBuf<float> minv32;
 };
 
@@ -26,7 +28,8 @@ struct AmgLevel {
   DCSR<double> A, P, R, S;        // operator, interpolation, restriction = P^T, strength pattern
   DBuf<int8_t> cf;                // 1 = C, -1 = F
   DBuf<double> dinv;              // smoother scaling
-  DCSR<float> A32, P32, R32;
+  RowsOp<float> A32, P32, R32;    // apply copies (working precision)
+  RowsOp<double> A64, P64, R64;
   DBuf<float> dinv32;
 };
 

@@ -85,9 +85,9 @@ inline const T* pick_ptr(const DBuf<double>& d, const DBuf<float>& f) {
   else return d.p;
 }
 template <class T>
-inline CSRView<T> tv(const DCSR<double>& d, const DCSR<float>& f) {
-  if constexpr (std::is_same<T, float>::value) return view(f);
-  else return view(d);
+inline const RowsOp<T>& tv(const RowsOp<double>& d, const RowsOp<float>& f) {
+  if constexpr (std::is_same<T, float>::value) return f;
+  else return d;
 }
 template <class T>
 inline T* P(DBuf<char>& b) { return reinterpret_cast<T*>(b.p); }
@@ -101,7 +101,7 @@ const T* frelax(mgr_handle_s& h, int l, const T* src, const int32_t* F) {
   if (L.nF == 0) return a;
   const T* minv = pick_ptr<T>(L.minv, L.minv32);
   launch_frelax_first<T>(h.c, L.nF, F, src, minv, a);
-  CSRView<T> Aff = tv<T>(L.Aff, L.Aff32);
+  const RowsOp<T>& Aff = tv<T>(L.Aff64, L.Aff32);
   for (int s = 1; s < L.sweeps; ++s) {
     launch_frelax_sweep<T>(h.c, Aff, F, src, minv, a, b);
     std::swap(a, b);
@@ -119,7 +119,7 @@ const T* vcycle(mgr_handle_s& h, int k, const T* b) {
     return x;
   }
   AmgLevel& A = h.amg[k];
-  CSRView<T> Av = tv<T>(A.A, A.A32);
+  const RowsOp<T>& Av = tv<T>(A.A64, A.A32);
   const T* d = pick_ptr<T>(A.dinv, A.dinv32);
   T* xa = P<T>(h.a_xa[k]);
   T* xb = P<T>(h.a_xb[k]);
@@ -131,9 +131,9 @@ const T* vcycle(mgr_handle_s& h, int k, const T* b) {
   }
   launch_resid<T>(c, Av, xa, b, res);
   T* bc = P<T>(h.a_b[k + 1]);
-  launch_spmv<T>(c, tv<T>(A.R, A.R32), res, bc);
+  launch_spmv<T>(c, tv<T>(A.R64, A.R32), res, bc);
   const T* xc = vcycle<T>(h, k + 1, bc);
-  launch_prolong_add<T>(c, tv<T>(A.P, A.P32), xc, xa);
+  launch_prolong_add<T>(c, tv<T>(A.P64, A.P32), xc, xa);
   for (int s = 0; s < h.o.amg_post; ++s) {
     launch_jacobi<T>(c, Av, d, b, xa, xb);
     std::swap(xa, xb);
@@ -151,9 +151,7 @@ void apply_t(mgr_handle_s& h, const double* r, double* z) {
     if constexpr (std::is_same<T, float>::value) launch_cast_f32(c, 3 * h.nb, r, rin);
     else CU(cudaMemcpyAsync(rin, r, sizeof(double) * 3 * h.nb, cudaMemcpyDeviceToDevice, c.s));
     const T* e = vcycle<T>(h, 0, rin);
-    CSRView<T> none;
-    // z = e (the identity map of level 0 routes every dof as "C" with coarse index d)
-    launch_interp<T, double>(c, 3 * h.nb, h.lev[0].map.p, none, nullptr, e, nullptr, z);
+    launch_to_f64<T>(c, 3 * h.nb, e, z);
     h.apply_launches = (int64_t)(g_launch_count - l0);
     return;
   }
@@ -167,21 +165,21 @@ void apply_t(mgr_handle_s& h, const double* r, double* z) {
   launch_bsr_resid_split<T>(c, h.sell, vals, r, e0, L0.map.p, r1, resF0);
   std::vector<const T*> eF(L);
   eF[0] = frelax<T>(h, 0, resF0, nullptr);
-  launch_restrict<T>(c, tv<T>(L0.Acf, L0.Acf32), nullptr, nullptr, eF[0], r1);
+  launch_restrict<T>(c, tv<T>(L0.Acf64, L0.Acf32), nullptr, nullptr, eF[0], r1);
   for (int l = 1; l < L; ++l) {
     MgrLevel& Ll = h.lev[l];
     const T* rl = P<T>(h.w_r[l]);
     eF[l] = frelax<T>(h, l, rl, Ll.F.p);
-    launch_restrict<T>(c, tv<T>(Ll.Acf, Ll.Acf32), Ll.C.p, rl, eF[l], P<T>(h.w_r[l + 1]));
+    launch_restrict<T>(c, tv<T>(Ll.Acf64, Ll.Acf32), Ll.C.p, rl, eF[l], P<T>(h.w_r[l + 1]));
   }
   const T* ec = vcycle<T>(h, 0, P<T>(h.w_r[L]));
   for (int l = L - 1; l >= 1; --l) {
     MgrLevel& Ll = h.lev[l];
     T* el = P<T>(h.w_e[l]);
-    launch_interp<T, T>(c, Ll.n, Ll.map.p, tv<T>(Ll.Wp, Ll.Wp32), eF[l], ec, nullptr, el);
+    launch_interp<T, T>(c, Ll.nF, Ll.F.p, Ll.nC, Ll.C.p, tv<T>(Ll.Wp64, Ll.Wp32), eF[l], ec, nullptr, el);
     ec = el;
   }
-  launch_interp<T, double>(c, L0.n, L0.map.p, tv<T>(L0.Wp, L0.Wp32), eF[0], ec, e0, z);
+  launch_interp<T, double>(c, L0.nF, L0.F.p, L0.nC, L0.C.p, tv<T>(L0.Wp64, L0.Wp32), eF[0], ec, e0, z);
   h.apply_launches = (int64_t)(g_launch_count - l0);
 }
 
@@ -191,10 +189,6 @@ void do_apply(mgr_handle_s& h, const double* r, double* z) {
 }
 
 // ---- setup -----------------------------------------------------------------------------------
-__global__ void k_identity_map(int64_t n, int32_t* map) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) map[i] = (int32_t)i;
-}
 __global__ void k_max_marker(int64_t n, const int8_t* mk, int* out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) atomicMax(out, (int)mk[i]);
@@ -233,30 +227,43 @@ void alloc_work(mgr_handle_s& h) {
 void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
   Ctx& c = h.c;
   int64_t nv = 9 * SELL_C * h.sell.slots;
-  if (h.o.precision == MGR_PREC_MIXED) {
+  bool mixed = h.o.precision == MGR_PREC_MIXED;
+  if (mixed) {
     h.val32.alloc(c, nv);
     sell_fill_values<double, float>(c, h.sell, A.values, h.val32.p);
     h.binv32.alloc(c, 9 * h.nb);
     launch_cast_f32(c, 9 * h.nb, h.binv.p, h.binv32.p);
-    for (int l = 0; l < h.L; ++l) {
-      MgrLevel& L = h.lev[l];
-      csr_to_f32(c, L.Aff, L.Aff32);
-      csr_to_f32(c, L.Acf, L.Acf32);
-      csr_to_f32(c, L.Wp, L.Wp32);
-      L.minv32.alloc(c, L.nF + 1);
-      launch_cast_f32(c, L.nF, L.minv.p, L.minv32.p);
-    }
-    for (size_t k = 0; k + 1 < h.amg.size(); ++k) {
-      AmgLevel& G = h.amg[k];
-      csr_to_f32(c, G.A, G.A32);
-      csr_to_f32(c, G.P, G.P32);
-      csr_to_f32(c, G.R, G.R32);
-      G.dinv32.alloc(c, G.n);
-      launch_cast_f32(c, G.n, G.dinv.p, G.dinv32.p);
-    }
   } else {
     h.val64.alloc(c, nv);
     sell_fill_values<double, double>(c, h.sell, A.values, h.val64.p);
+  }
+  for (int l = 0; l < h.L; ++l) {
+    MgrLevel& L = h.lev[l];
+    if (mixed) {
+      rowsop_build<float>(c, L.Aff, L.Aff32);
+      rowsop_build<float>(c, L.Acf, L.Acf32);
+      rowsop_build<float>(c, L.Wp, L.Wp32);
+      L.minv32.alloc(c, L.nF + 1);
+      launch_cast_f32(c, L.nF, L.minv.p, L.minv32.p);
+    } else {
+      rowsop_build<double>(c, L.Aff, L.Aff64);
+      rowsop_build<double>(c, L.Acf, L.Acf64);
+      rowsop_build<double>(c, L.Wp, L.Wp64);
+    }
+  }
+  for (size_t k = 0; k + 1 < h.amg.size(); ++k) {
+    AmgLevel& G = h.amg[k];
+    if (mixed) {
+      rowsop_build<float>(c, G.A, G.A32);
+      rowsop_build<float>(c, G.P, G.P32);
+      rowsop_build<float>(c, G.R, G.R32);
+      G.dinv32.alloc(c, G.n);
+      launch_cast_f32(c, G.n, G.dinv.p, G.dinv32.p);
+    } else {
+      rowsop_build<double>(c, G.A, G.A64);
+      rowsop_build<double>(c, G.P, G.P64);
+      rowsop_build<double>(c, G.R, G.R64);
+    }
   }
 }
 
@@ -308,11 +315,6 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     mgr_reduce_level(c, h.lev[l], l, lo, h.lev[l + 1].A, mk_next);
     h.lev[l + 1].n = h.lev[l].nC;
     h.lev[l + 1].mk = std::move(mk_next);
-  }
-  if (L == 0) {
-    h.lev[0].map.alloc(c, n);
-    k_identity_map<<<grid_for(n, 256), 256, 0, c.s>>>(n, h.lev[0].map.p);
-    CU_LAUNCH();
   }
   // coarse solve on the last level
   const DCSR<double>& Ac = h.lev[L].A;

@@ -225,12 +225,20 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
     k_p_fill<<<grid_for(n, B), B, 0, c.s>>>(n, L.map.p, L.Wp.rp.p, L.Wp.ci.p, L.Wp.v.p, L.P.rp.p, L.P.ci.p, L.P.v.p);
     CU_LAUNCH();
   }
-  // coarse operator R (A P) and coarse markers
+  // coarse operator R (A P) and coarse markers.  With an injective R (one 1 per row, at the C point)
+  // row c of R (A P) is 0.0 + 1 * (A P)_{C[c]}; a Gustavson sum that starts at +0.0 never ends at -0.0,
+  // so that equals (A P)_{C[c]} bit for bit, and only the C rows of A enter the product.
   {
     ProfScope ps(c, "setup_mgr_rap");
-    DCSR<double> AP;
-    spgemm(c, A, L.P, AP);
-    spgemm(c, L.R, AP, Anext);
+    if (o.restrict_type == 1) {
+      DCSR<double> AP;
+      spgemm(c, A, L.P, AP);
+      spgemm(c, L.R, AP, Anext);
+    } else {
+      DCSR<double> AC;
+      csr_gather_rows(c, A, L.C.p, nC, AC);
+      spgemm(c, AC, L.P, Anext);
+    }
   }
   mk_next.alloc(c, nC);
   k_gather_i8<<<grid_for(nC, B), B, 0, c.s>>>(nC, L.C.p, L.mk.p, mk_next.p);
@@ -389,10 +397,15 @@ __device__ __forceinline__ bool opposite(double a, double d) { return (d > 0.0 &
 //   of a_kl; q_k = a_ik / den_k, or a_ik lumped into the diagonal when den_k == 0.
 //   at = a_ii + sum(weak neighbours not in Chat_i, ascending) + sum_k (q_k abar_ki or a_ik);
 //   w_ij = -(a_ij + sum_k q_k abar_kj) / at.   An F row with at == 0 is flagged empty.
-__global__ void k_extpi_weights(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* srp,
+constexpr int EXT_WARPS = 4;
+constexpr int EXT_CAP = 256;
+
+__global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* srp,
                                 const int32_t* sci, const int8_t* cf, const int32_t* cidx, const int32_t* cfine,
                                 const int64_t* prp, const int32_t* pci, double* pv, double* den_g, double* q_g,
                                 int8_t* rowzero) {
+  __shared__ double s_wt[EXT_WARPS][EXT_CAP], s_kt[EXT_WARPS][EXT_CAP];
+  __shared__ int8_t s_wf[EXT_WARPS][EXT_CAP], s_kf[EXT_WARPS][EXT_CAP];
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (i >= n) return;
@@ -416,7 +429,47 @@ __global__ void k_extpi_weights(int64_t n, const int64_t* rp, const int32_t* ci,
   }
   __syncwarp();
   double at = 0.0;
-  if (lane == 0) {
+  int w = (threadIdx.x >> 5) & (EXT_WARPS - 1);
+  int64_t r0 = rp[i], len = rp[i + 1] - r0, ns = s1 - s0;
+  if (len <= EXT_CAP && ns <= EXT_CAP) {
+    // the terms of the diagonal are formed by the lanes in parallel, then added by lane 0 in order
+    for (int64_t t = lane; t < len; t += 32) {
+      int32_t nn = ci[r0 + t];
+      bool lump = nn != i && find_i32(sci, s0, s1, nn) < 0 &&
+                  !(cf[nn] == 1 && find_i32(pci, p0, p1, cidx[nn]) >= 0);
+      s_wt[w][t] = lump ? v[r0 + t] : 0.0;
+      s_wf[w][t] = lump;
+    }
+    for (int64_t p = s0 + lane; p < s1; p += 32) {
+      int32_t k = sci[p];
+      int8_t f = 0;
+      double term = 0.0;
+      if (cf[k] != 1) {
+        double aik = csr_get(rp, ci, v, i, k), den = den_g[p];
+        if (den != 0.0) {
+          double q = dv(aik, den);
+          q_g[p] = q;
+          double aki = csr_get(rp, ci, v, k, (int32_t)i), akk = csr_get(rp, ci, v, k, k);
+          if (opposite(aki, akk)) { term = dm(q, aki); f = 1; }
+        } else {
+          q_g[p] = 0.0;
+          term = aik;
+          f = 1;
+        }
+      }
+      s_kt[w][p - s0] = term;
+      s_kf[w][p - s0] = f;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      at = csr_get(rp, ci, v, i, (int32_t)i);
+      for (int64_t t = 0; t < len; ++t)
+        if (s_wf[w][t]) at = dd(at, s_wt[w][t]);
+      for (int64_t t = 0; t < ns; ++t)
+        if (s_kf[w][t]) at = dd(at, s_kt[w][t]);
+      rowzero[i] = (at == 0.0);
+    }
+  } else if (lane == 0) {
     at = csr_get(rp, ci, v, i, (int32_t)i);
     for (int64_t q = rp[i]; q < rp[i + 1]; ++q) {
       int32_t nn = ci[q];
@@ -602,7 +655,7 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
   }
   DBuf<double> den(c, S.nnz + 1), q(c, S.nnz + 1), scale(c, n);
   DBuf<int8_t> rowzero(c, n), keep(c, Pf.nnz + 1);
-  k_extpi_weights<<<grid_for(n * 32, 128), 128, 0, c.s>>>(n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp,
+  k_extpi_weights<<<grid_for(n * 32, 32 * EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp,
                                                            Pf.ci, Pf.v, den.p, q.p, rowzero.p);
   CU_LAUNCH();
   DBuf<int64_t> cnt(c, n + 1);

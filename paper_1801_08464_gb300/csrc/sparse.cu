@@ -193,6 +193,11 @@ __global__ void k_spgemm_ub(int64_t m, const int64_t* arp, const int32_t* aci, c
 __device__ __forceinline__ uint32_t hash32(int32_t k) { return (uint32_t)k * 2654435761u; }
 
 // MODE 0: count unique columns into cnt[i]; MODE 1: write the sorted unique columns at crp[i].
+// Rows with at most SYM_SORT candidates copy them into shared memory, sort them (bitonic) and keep
+// the first of each run of equal columns; longer rows (up to SYM_WCAP) insert into a hash table
+// sized to twice the row's candidate count, then sort the distinct keys.
+constexpr int SYM_SORT = 128;
+
 template <int MODE>
 __global__ void __launch_bounds__(32 * SYM_WARPS) k_sym_warp(int64_t m, const int64_t* arp, const int32_t* aci,
                                                               const int64_t* brp, const int32_t* bci,
@@ -203,21 +208,63 @@ __global__ void __launch_bounds__(32 * SYM_WARPS) k_sym_warp(int64_t m, const in
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * SYM_WARPS + w;
   if (i >= m) return;
-  if (ub[i] > SYM_WCAP) return;  // handled by the block / bitmap kernels
+  int U = (int)ub[i];
+  if (U > SYM_WCAP) return;  // handled by the block / bitmap kernels
   int32_t* T = tab[w];
-  for (int t = lane; t < SYM_WHASH; t += 32) T[t] = -1;
+  int64_t a0 = arp[i], a1 = arp[i + 1];
+  if (U <= SYM_SORT) {
+    // lane p copies the B row selected by A entry p to its offset (exclusive scan of the lengths), so
+    // the rows are gathered in parallel rather than one after another
+    int carry = 0;
+    for (int64_t p0 = a0; p0 < a1; p0 += 32) {
+      int64_t p = p0 + lane;
+      int64_t b0 = 0;
+      int len = 0;
+      if (p < a1) {
+        int32_t k = aci[p];
+        b0 = brp[k];
+        len = (int)(brp[k + 1] - b0);
+      }
+      int x = len;
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      int off = carry + x - len;
+      for (int q = 0; q < len; ++q) T[off + q] = bci[b0 + q];
+      carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    int n2 = next_pow2(U);
+    for (int t = U + lane; t < n2; t += 32) T[t] = INT_MAX;
+    __syncwarp();
+    warp_bitonic_keys(T, n2, lane);
+    int64_t o = (MODE == 1) ? crp[i] : 0;
+    int u = 0;
+    for (int t0 = 0; t0 < U; t0 += 32) {
+      int t = t0 + lane;
+      bool first = t < U && (t == 0 || T[t] != T[t - 1]);
+      unsigned msk = __ballot_sync(0xffffffffu, first);
+      if (MODE == 1 && first) cci[o + u + __popc(msk & ((1u << lane) - 1))] = T[t];
+      u += __popc(msk);
+    }
+    if (MODE == 0 && lane == 0) cnt[i] = u;
+    return;
+  }
+  int H = next_pow2(2 * U);
+  for (int t = lane; t < H; t += 32) T[t] = -1;
   if (lane == 0) ucount[w] = 0;
   __syncwarp();
-  for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
+  // lane p inserts the B row selected by A entry p (rows handled in parallel)
+  for (int64_t p = a0 + lane; p < a1; p += 32) {
     int32_t k = aci[p];
-    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+    for (int64_t q = brp[k]; q < brp[k + 1]; ++q) {
       int32_t key = bci[q];
-      uint32_t h = hash32(key) & (SYM_WHASH - 1);
+      uint32_t h = hash32(key) & (H - 1);
       while (true) {
         int32_t prev = atomicCAS(&T[h], -1, key);
         if (prev == -1) { atomicAdd(&ucount[w], 1); break; }
         if (prev == key) break;
-        h = (h + 1) & (SYM_WHASH - 1);
+        h = (h + 1) & (H - 1);
       }
     }
   }
@@ -229,21 +276,20 @@ __global__ void __launch_bounds__(32 * SYM_WARPS) k_sym_warp(int64_t m, const in
   }
   // in-place compaction: a chunk is read into registers before any write, and every write goes to a
   // position below the end of the chunk being read
-  int32_t* K = T;
   int base = 0;
-  for (int t = 0; t < SYM_WHASH; t += 32) {
-    int32_t key = T[t + lane];
+  for (int t = 0; t < H; t += 32) {
+    int32_t key = (t + lane < H) ? T[t + lane] : -1;
     unsigned msk = __ballot_sync(0xffffffffu, key >= 0);
-    if (key >= 0) K[base + __popc(msk & ((1u << lane) - 1))] = key;
+    if (key >= 0) T[base + __popc(msk & ((1u << lane) - 1))] = key;
     base += __popc(msk);
     __syncwarp();
   }
   int n2 = next_pow2(u);
-  for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
+  for (int t = u + lane; t < n2; t += 32) T[t] = INT_MAX;
   __syncwarp();
-  warp_bitonic_keys(K, n2, lane);
+  warp_bitonic_keys(T, n2, lane);
   int64_t o = crp[i];
-  for (int t = lane; t < u; t += 32) cci[o + t] = K[t];
+  for (int t = lane; t < u; t += 32) cci[o + t] = T[t];
 }
 
 template <int MODE>
@@ -726,6 +772,40 @@ void csr_to_f32(Ctx& c, const DCSR<double>& A, DCSR<float>& B) {
   if (A.nnz) {
     CU(cudaMemcpyAsync(B.ci.p, A.ci.p, sizeof(int32_t) * A.nnz, cudaMemcpyDeviceToDevice, c.s));
     k_f64_to_f32<<<grid_for(A.nnz, 256, 8192), 256, 0, c.s>>>(A.nnz, A.v.p, B.v.p);
+    CU_LAUNCH();
+  }
+}
+
+// B = the rows rows[0..nr) of A, in that order (pattern and values copied)
+__global__ void k_gather_rows_count(int64_t nr, const int32_t* rows, const int64_t* rp, int64_t* cnt) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r < nr) cnt[r] = rp[rows[r] + 1] - rp[rows[r]];
+}
+__global__ void k_gather_rows_fill(int64_t nr, const int32_t* rows, const int64_t* rp, const int32_t* ci,
+                                   const double* v, const int64_t* orp, int32_t* oci, double* ov) {
+  int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+  int sub = threadIdx.x & 7;
+  if (r >= nr) return;
+  int64_t b = rp[rows[r]], e = rp[rows[r] + 1], o = orp[r];
+  for (int64_t k = b + sub; k < e; k += 8) {
+    oci[o + (k - b)] = ci[k];
+    ov[o + (k - b)] = v[k];
+  }
+}
+void csr_gather_rows(Ctx& c, const DCSR<double>& A, const int32_t* rows, int64_t nr, DCSR<double>& B) {
+  DBuf<int64_t> cnt(c, nr + 1);
+  B.nr = nr;
+  B.nc = A.nc;
+  B.rp.alloc(c, nr + 1);
+  if (nr > 0) {
+    k_gather_rows_count<<<grid_for(nr, 256), 256, 0, c.s>>>(nr, rows, A.rp, cnt.p);
+    CU_LAUNCH();
+  }
+  B.nnz = counts_to_rowptr(c, cnt.p, B.rp.p, nr);
+  B.ci.alloc(c, B.nnz);
+  B.v.alloc(c, B.nnz);
+  if (nr > 0) {
+    k_gather_rows_fill<<<grid_for(nr * 8, 256), 256, 0, c.s>>>(nr, rows, A.rp, A.ci, A.v, B.rp, B.ci, B.v);
     CU_LAUNCH();
   }
 }
