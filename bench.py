@@ -36,7 +36,9 @@ SOLVER = dict(amg_theta=0.5, amg_pmax=4, amg_smoother=0, amg_omega=0.8)
 KERNEL_NAMES = ("bsr3_spmv_f64", "bsr_resid_split", "global_relax", "csr_rows", "interp", "mdot", "mupdate",
                 "spgemm_numeric", "spgemm_symbolic", "setup_total", "setup_mgr_level", "setup_mgr_rap", "setup_amg",
                 "setup_amg_strength", "setup_amg_pmis", "setup_amg_extpi", "setup_amg_transpose", "setup_amg_rap",
-                "setup_dense_inverse", "setup_cast_alloc")
+                "setup_dense_inverse", "setup_cast_alloc", "sym_ub", "sym_count_warp", "sym_fill_warp", "sym_block",
+                "sym_bitmap", "numeric_expand", "spgemm", "fused_small", "fused_copy",
+                "extpi_pattern", "extpi_weights", "amg0_rows")
 
 
 def _args():

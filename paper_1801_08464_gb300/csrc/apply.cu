@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_rows(int64_t nr, const int64_t* __restr
   if (ok && sub == 0) epi(r, s);
 }
 
-// SELL-32 form: one thread per row, slots walked in order (padding slots add 0 * x[0])
+// SELL form: one thread per row, slots walked in order (padding slots add 0 * x[0])
 template <class T, class Epi>
 __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __restrict__ soff,
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
@@ -270,12 +270,12 @@ void launch_scale(Ctx& c, int64_t n, const T* d, const T* b, T* x) {
   CU_LAUNCH();
 }
 template <class T>
-void launch_resid(Ctx& c, const RowsOp<T>& A, const T* x, const T* b, T* res) {
-  run_rows(c, A, x, EpiResid<T>{b, res});
+void launch_resid(Ctx& c, const RowsOp<T>& A, const T* x, const T* b, T* res, const char* name) {
+  run_rows(c, A, x, EpiResid<T>{b, res}, name);
 }
 template <class T>
-void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* xi, T* xo) {
-  run_rows(c, A, xi, EpiJacobi<T>{d, b, xi, xo});
+void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* xi, T* xo, const char* name) {
+  run_rows(c, A, xi, EpiJacobi<T>{d, b, xi, xo}, name);
 }
 template <class T>
 void launch_spmv(Ctx& c, const RowsOp<T>& A, const T* x, T* y) {
@@ -326,8 +326,8 @@ void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b) {
                                     const T*, const T*, const T*, T*);                                             \
   template void launch_to_f64<T>(Ctx&, int64_t, const T*, double*);                                                \
   template void launch_scale<T>(Ctx&, int64_t, const T*, const T*, T*);                                            \
-  template void launch_resid<T>(Ctx&, const RowsOp<T>&, const T*, const T*, T*);                                  \
-  template void launch_jacobi<T>(Ctx&, const RowsOp<T>&, const T*, const T*, const T*, T*);                       \
+  template void launch_resid<T>(Ctx&, const RowsOp<T>&, const T*, const T*, T*, const char*);                     \
+  template void launch_jacobi<T>(Ctx&, const RowsOp<T>&, const T*, const T*, const T*, T*, const char*);          \
   template void launch_spmv<T>(Ctx&, const RowsOp<T>&, const T*, T*);                                             \
   template void launch_prolong_add<T>(Ctx&, const RowsOp<T>&, const T*, T*);                                      \
   template void launch_dense_gemv<T>(Ctx&, int64_t, const double*, const T*, T*);

@@ -52,9 +52,11 @@ void launch_to_f64(Ctx& c, int64_t n, const T* a, double* b);
 template <class T>
 void launch_scale(Ctx& c, int64_t n, const T* d, const T* b, T* x);                          // x = d * b
 template <class T>
-void launch_resid(Ctx& c, const RowsOp<T>& A, const T* x, const T* b, T* res);              // res = b - A x
+void launch_resid(Ctx& c, const RowsOp<T>& A, const T* x, const T* b, T* res,
+                  const char* name = "csr_rows");                                           // res = b - A x
 template <class T>
-void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* xi, T* xo);  // xo = xi + d (b - A xi)
+void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* xi, T* xo,
+                   const char* name = "csr_rows");                                          // xo = xi + d (b - A xi)
 template <class T>
 void launch_spmv(Ctx& c, const RowsOp<T>& A, const T* x, T* y);                             // y = A x
 template <class T>

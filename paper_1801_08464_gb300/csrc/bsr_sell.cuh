@@ -42,9 +42,10 @@ __global__ void __launch_bounds__(256) k_bsr_sell(int64_t nb, const int64_t* __r
     int64_t J = col[j * SELL_C + t];
     const T* v = val + j * 9 * SELL_C + t;
     T x0 = (T)__ldg(x + 3 * J), x1 = (T)__ldg(x + 3 * J + 1), x2 = (T)__ldg(x + 3 * J + 2);
-    s0 += v[0 * SELL_C] * x0 + v[1 * SELL_C] * x1 + v[2 * SELL_C] * x2;
-    s1 += v[3 * SELL_C] * x0 + v[4 * SELL_C] * x1 + v[5 * SELL_C] * x2;
-    s2 += v[6 * SELL_C] * x0 + v[7 * SELL_C] * x1 + v[8 * SELL_C] * x2;
+    // one FMA per product (FP64 instructions bound the FP64 variant on this GPU)
+    s0 = fma(v[0 * SELL_C], x0, s0); s0 = fma(v[1 * SELL_C], x1, s0); s0 = fma(v[2 * SELL_C], x2, s0);
+    s1 = fma(v[3 * SELL_C], x0, s1); s1 = fma(v[4 * SELL_C], x1, s1); s1 = fma(v[5 * SELL_C], x2, s1);
+    s2 = fma(v[6 * SELL_C], x0, s2); s2 = fma(v[7 * SELL_C], x1, s2); s2 = fma(v[8 * SELL_C], x2, s2);
   }
   epi(I, s0, s1, s2);
 }

@@ -17,7 +17,7 @@ struct MgrLevel {
   int sweeps = 1;
   DCSR<double> Wp, Wr, P, R;      // W_p (nF x nC), W_r (nC x nF), P (n x nC), R (nC x n)
   DCSR<double> Aff, Acf;          // split operators used by the apply (F-local columns)
-  // the operators the apply reads, in its working precision (SELL-32 or CSR)
+  // the operators the apply reads, in its working precision (SELL-8 or CSR)
   RowsOp<float> Aff32, Acf32, Wp32;
   RowsOp<double> Aff64, Acf64, Wp64;
   DBuf<float> minv32;

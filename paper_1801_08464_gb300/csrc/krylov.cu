@@ -20,9 +20,9 @@ __global__ void __launch_bounds__(256) k_bsr3_spmv_f64(int64_t nb, const int64_t
     int64_t J = ci[k];
     const double* b = v + 9 * k;
     double x0 = __ldg(x + 3 * J), x1 = __ldg(x + 3 * J + 1), x2 = __ldg(x + 3 * J + 2);
-    s0 += b[0] * x0 + b[1] * x1 + b[2] * x2;
-    s1 += b[3] * x0 + b[4] * x1 + b[5] * x2;
-    s2 += b[6] * x0 + b[7] * x1 + b[8] * x2;
+    s0 = fma(b[0], x0, s0); s0 = fma(b[1], x1, s0); s0 = fma(b[2], x2, s0);
+    s1 = fma(b[3], x0, s1); s1 = fma(b[4], x1, s1); s1 = fma(b[5], x2, s1);
+    s2 = fma(b[6], x0, s2); s2 = fma(b[7], x1, s2); s2 = fma(b[8], x2, s2);
   }
   if (sub) { s0 = sub[3 * I] - s0; s1 = sub[3 * I + 1] - s1; s2 = sub[3 * I + 2] - s2; }
   y[3 * I] = s0;
@@ -95,19 +95,24 @@ __global__ void __launch_bounds__(KT) k_mdot(int64_t n, const double* __restrict
   for (int64_t i = i0 + 2 * threadIdx.x; i < i1; i += 2 * KT) {
     if (i + 1 < i1) {
       double2 wi = *reinterpret_cast<const double2*>(w + i);
+      // one FMA per product: FP64 instructions, not bytes, bound this kernel on this GPU
 #pragma unroll
       for (int k = 0; k < MD_VEC; ++k)
         if (k < kn) {
           double2 v = __ldg(reinterpret_cast<const double2*>(V + (k0 + k) * ldv + i));
-          acc[k] += v.x * wi.x + v.y * wi.y;
+          acc[k] = fma(v.x, wi.x, acc[k]);
+          acc[k] = fma(v.y, wi.y, acc[k]);
         }
-      if (dow) acc[MD_VEC] += wi.x * wi.x + wi.y * wi.y;
+      if (dow) {
+        acc[MD_VEC] = fma(wi.x, wi.x, acc[MD_VEC]);
+        acc[MD_VEC] = fma(wi.y, wi.y, acc[MD_VEC]);
+      }
     } else {
       double wi = w[i];
 #pragma unroll
       for (int k = 0; k < MD_VEC; ++k)
-        if (k < kn) acc[k] += V[(k0 + k) * ldv + i] * wi;
-      if (dow) acc[MD_VEC] += wi * wi;
+        if (k < kn) acc[k] = fma(V[(k0 + k) * ldv + i], wi, acc[k]);
+      if (dow) acc[MD_VEC] = fma(wi, wi, acc[MD_VEC]);
     }
   }
   __shared__ double sh[KT / 32][MD_VEC + 1];
@@ -190,7 +195,8 @@ __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restr
     s.x *= sc;
     s.y *= sc;
     *reinterpret_cast<double2*>(vout + i) = s;
-    acc[0] += s.x * s.x + s.y * s.y;
+    acc[0] = fma(s.x, s.x, acc[0]);
+    acc[0] = fma(s.y, s.y, acc[0]);
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     int64_t i = n - 1;

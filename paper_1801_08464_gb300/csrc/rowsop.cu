@@ -1,4 +1,4 @@
-// rowsop.cu -- construction of the apply operators in SELL-32 or CSR form (see rowsop.cuh).
+// rowsop.cu -- construction of the apply operators in SELL-8 or CSR form (see rowsop.cuh).
 #include "rowsop.cuh"
 
 namespace mgr {

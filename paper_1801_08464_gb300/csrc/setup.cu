@@ -643,7 +643,15 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
     k_extpi_sel_fill<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, cf.p, cidx.p, M.rp, M.ci, T.rp, T.ci);
     CU_LAUNCH();
   }
-  spgemm_symbolic(c, M, T, Q);
+  // pattern of M T through the fused product (unit values; only the pattern is used)
+  M.v.alloc(c, M.nnz);
+  T.v.alloc(c, T.nnz);
+  fill_f64(c, M.v.p, 1.0, M.nnz);
+  fill_f64(c, T.v.p, 1.0, T.nnz);
+  {
+    ProfScope ps(c, "extpi_pattern");
+    spgemm(c, M, T, Q);
+  }
   DCSR<double> Pf;
   {
     DBuf<int64_t> cnt(c, n + 1);
@@ -655,6 +663,7 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
   }
   DBuf<double> den(c, S.nnz + 1), q(c, S.nnz + 1), scale(c, n);
   DBuf<int8_t> rowzero(c, n), keep(c, Pf.nnz + 1);
+  ProfScope psw(c, "extpi_weights");
   k_extpi_weights<<<grid_for(n * 32, 32 * EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp,
                                                            Pf.ci, Pf.v, den.p, q.p, rowzero.p);
   CU_LAUNCH();

@@ -197,12 +197,13 @@ __device__ __forceinline__ uint32_t hash32(int32_t k) { return (uint32_t)k * 265
 // the first of each run of equal columns; longer rows (up to SYM_WCAP) insert into a hash table
 // sized to twice the row's candidate count, then sort the distinct keys.
 constexpr int SYM_SORT = 128;
+constexpr int FUSE_CAP = 1024;  // rows with up to FUSE_CAP products take the fused (one-pass) kernels
 
 template <int MODE>
 __global__ void __launch_bounds__(32 * SYM_WARPS) k_sym_warp(int64_t m, const int64_t* arp, const int32_t* aci,
                                                               const int64_t* brp, const int32_t* bci,
                                                               const int64_t* ub, int64_t* cnt, const int64_t* crp,
-                                                              int32_t* cci) {
+                                                              int32_t* cci, int skip_small) {
   __shared__ int32_t tab[SYM_WARPS][SYM_WHASH];
   __shared__ int ucount[SYM_WARPS];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -210,6 +211,7 @@ __global__ void __launch_bounds__(32 * SYM_WARPS) k_sym_warp(int64_t m, const in
   if (i >= m) return;
   int U = (int)ub[i];
   if (U > SYM_WCAP) return;  // handled by the block / bitmap kernels
+  if (skip_small && U <= FUSE_CAP) return;  // handled by the fused kernel
   int32_t* T = tab[w];
   int64_t a0 = arp[i], a1 = arp[i + 1];
   if (U <= SYM_SORT) {
@@ -402,15 +404,18 @@ __global__ void __launch_bounds__(1024) k_sym_bitmap(const int32_t* rows, int64_
 }
 
 static void sym_pass(Ctx& c, int mode, const DCSR<double>& A, const DCSR<double>& B, const int64_t* ub,
-                     const int32_t* mid, int nmid, const int32_t* big, int nbig, int64_t* cnt, DCSR<double>& C) {
+                     const int32_t* mid, int nmid, const int32_t* big, int nbig, int64_t* cnt, DCSR<double>& C,
+                     int skip_small = 0) {
   int64_t m = A.nr;
   unsigned g = grid_for(m, SYM_WARPS);
+  ProfScope ps(c, mode == 0 ? "sym_count_warp" : "sym_fill_warp");
   if (mode == 0)
-    k_sym_warp<0><<<g, 32 * SYM_WARPS, 0, c.s>>>(m, A.rp, A.ci, B.rp, B.ci, ub, cnt, nullptr, nullptr);
+    k_sym_warp<0><<<g, 32 * SYM_WARPS, 0, c.s>>>(m, A.rp, A.ci, B.rp, B.ci, ub, cnt, nullptr, nullptr, skip_small);
   else
-    k_sym_warp<1><<<g, 32 * SYM_WARPS, 0, c.s>>>(m, A.rp, A.ci, B.rp, B.ci, ub, nullptr, C.rp, C.ci);
+    k_sym_warp<1><<<g, 32 * SYM_WARPS, 0, c.s>>>(m, A.rp, A.ci, B.rp, B.ci, ub, nullptr, C.rp, C.ci, skip_small);
   CU_LAUNCH();
   if (nmid > 0) {
+    ProfScope ps2(c, "sym_block");
     size_t sh = sizeof(int32_t) * (SYM_BHASH + SYM_BCAP);
     if (mode == 0) {
       CU(cudaFuncSetAttribute(k_sym_block<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
@@ -423,6 +428,7 @@ static void sym_pass(Ctx& c, int mode, const DCSR<double>& A, const DCSR<double>
     }
   }
   if (nbig > 0) {
+    ProfScope ps3(c, "sym_bitmap");
     if (B.nc > SYM_BITS) throw Error(MGR_ERR_UNSUPPORTED, "spgemm: a row with > 8192 products and > 2^20 columns");
     size_t sh = sizeof(uint32_t) * (size_t)((B.nc + 31) / 32);
     if (mode == 0) {
@@ -454,7 +460,10 @@ void spgemm_symbolic(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<
   DBuf<int32_t> mid(c, m), big(c, m);
   DBuf<int> counters(c, 2);
   CU(cudaMemsetAsync(counters.p, 0, 2 * sizeof(int), c.s));
-  k_spgemm_ub<<<grid_for(m, 256), 256, 0, c.s>>>(m, A.rp, A.ci, B.rp, ub.p, counters.p, mid.p, counters.p + 1, big.p);
+  {
+    ProfScope ps(c, "sym_ub");
+    k_spgemm_ub<<<grid_for(m, 256), 256, 0, c.s>>>(m, A.rp, A.ci, B.rp, ub.p, counters.p, mid.p, counters.p + 1, big.p);
+  }
   CU_LAUNCH();
   int hc[2];
   CU(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, c.s));
@@ -485,7 +494,8 @@ constexpr int NX_CAPC = 512;
 __global__ void __launch_bounds__(32 * NX_WARPS) k_spgemm_numeric_expand(
     int64_t m, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
     const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
-    const int64_t* __restrict__ crp, const int32_t* __restrict__ cci, double* __restrict__ cv) {
+    const int64_t* __restrict__ crp, const int32_t* __restrict__ cci, double* __restrict__ cv,
+    const int64_t* __restrict__ ub) {
   __shared__ int32_t scol[NX_WARPS][NX_CAPC];
   __shared__ double sacc[NX_WARPS][NX_CAPC];
   __shared__ int32_t sstart[NX_WARPS][NX_CAPA + 1];
@@ -495,6 +505,7 @@ __global__ void __launch_bounds__(32 * NX_WARPS) k_spgemm_numeric_expand(
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * NX_WARPS + w;
   if (i >= m) return;
+  if (ub[i] <= FUSE_CAP) return;  // done by the fused kernel
   int64_t a0 = arp[i], c0 = crp[i];
   int na = (int)(arp[i + 1] - a0), L = (int)(crp[i + 1] - c0);
   if (na > NX_CAPA || L > NX_CAPC) return;  // handled by k_spgemm_numeric
@@ -558,10 +569,11 @@ __global__ void __launch_bounds__(32 * NX_WARPS) k_spgemm_numeric_expand(
 __global__ void __launch_bounds__(32 * NUM_WARPS) k_spgemm_numeric(int64_t m, const int64_t* arp, const int32_t* aci,
                                                                     const double* av, const int64_t* brp,
                                                                     const int32_t* bci, const double* bv,
-                                                                    const int64_t* crp, const int32_t* cci, double* cv) {
+                                                                    const int64_t* crp, const int32_t* cci, double* cv,
+                                                                    const int64_t* ub) {
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t i = (int64_t)blockIdx.x * NUM_WARPS + w;
-  if (i >= m) return;
+  if (i >= m || ub[i] <= FUSE_CAP) return;
   int64_t c0 = crp[i], c1 = crp[i + 1];
   int64_t L = c1 - c0;
   if (arp[i + 1] - arp[i] <= NX_CAPA && L <= NX_CAPC) return;  // done by the expand kernel
@@ -580,16 +592,308 @@ __global__ void __launch_bounds__(32 * NUM_WARPS) k_spgemm_numeric(int64_t m, co
   }
 }
 
+// Fused product for the rows with at most FUSE_CAP products that k_spgemm_fused_chunk left (long A
+// rows or more than FZ_SLOTS / 2 products): the A row is walked in ascending
+// order (ascending k); the products of one A entry have distinct columns, so the lanes add them to a
+// shared-memory hash table (column -> running sum) without conflicts, and __syncwarp orders successive
+// k.  Each sum therefore starts from 0.0 and adds its products in ascending k (Gustavson's order).
+// The distinct columns are then compacted, sorted (bitonic, values carried) and staged.
+constexpr int FH_WARPS = 2;
+constexpr int FH_SLOTS = 2 * FUSE_CAP;
+
+__global__ void __launch_bounds__(32 * FH_WARPS) k_spgemm_fused_hash(
+    int64_t m, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
+    const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
+    const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
+    double* __restrict__ sval, int64_t* __restrict__ cnt, const int* __restrict__ done) {
+  __shared__ int32_t hk[FH_WARPS][FH_SLOTS];
+  __shared__ double hv[FH_WARPS][FH_SLOTS];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = (int64_t)blockIdx.x * FH_WARPS + w;
+  if (i >= m) return;
+  int U = (int)ub[i];
+  if (U > FUSE_CAP || done[i]) return;
+  int32_t* K = hk[w];
+  double* Vv = hv[w];
+  int H = 1;
+  while (H < 2 * U) H <<= 1;
+  for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
+  __syncwarp();
+  for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
+    int32_t k = aci[p];
+    double a = av[p];
+    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+      int32_t key = bci[q];
+      double prod = __dmul_rn(a, bv[q]);
+      uint32_t h = hash32(key) & (H - 1);
+      while (true) {
+        int32_t prev = atomicCAS(&K[h], -1, key);
+        if (prev == -1 || prev == key) break;
+        h = (h + 1) & (H - 1);
+      }
+      Vv[h] = __dadd_rn(Vv[h], prod);
+    }
+    __syncwarp();
+  }
+  // compaction of the occupied slots to the front (order irrelevant: sorted next)
+  int base = 0;
+  for (int t0 = 0; t0 < H; t0 += 32) {
+    int t = t0 + lane;
+    int32_t key = t < H ? K[t] : -1;
+    double v = t < H ? Vv[t] : 0.0;
+    unsigned msk = __ballot_sync(0xffffffffu, key >= 0);
+    __syncwarp();
+    if (key >= 0) {
+      int pos = base + __popc(msk & ((1u << lane) - 1));
+      K[pos] = key;
+      Vv[pos] = v;
+    }
+    base += __popc(msk);
+    __syncwarp();
+  }
+  int u = base;
+  int n2 = 1;
+  while (n2 < u) n2 <<= 1;
+  for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
+  __syncwarp();
+  for (int k2 = 2; k2 <= n2; k2 <<= 1)
+    for (int j = k2 >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < n2; t += 32) {
+        int x = t ^ j;
+        if (x > t) {
+          bool up = (t & k2) == 0;
+          int32_t ka = K[t], kb = K[x];
+          if ((ka > kb) == up) {
+            K[t] = kb; K[x] = ka;
+            double va = Vv[t]; Vv[t] = Vv[x]; Vv[x] = va;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  int64_t o = soff[i];
+  for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
+  if (lane == 0) cnt[i] = u;
+}
+
+// Fused product for rows with at most FUSE_CAP products and FZ_CAPA entries in A (the common case):
+// products are taken 32 at a time in (k, q) order, i.e. ascending intermediate index k (lane t holds
+// product t0 + t; its A entry comes from a scan of the B row lengths kept in shared memory, and the
+// next chunk's loads are issued before the current chunk is added).  Lanes holding the same column
+// form a group (__match_any_sync); the group's lowest lane adds the group's products in lane order
+// to the column's running sum in a row-sized shared hash table.  Every sum therefore starts at 0.0
+// and adds its products in ascending k (Gustavson's order).  Only the distinct columns are then
+// sorted (bitonic, sums carried) and staged.
+constexpr int FZ_WARPS = 4;
+constexpr int FZ_CAPA = 128;
+constexpr int FZ_SLOTS = 512;
+
+__global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
+    int64_t m, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
+    const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
+    const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
+    double* __restrict__ sval, int64_t* __restrict__ cnt, int* __restrict__ done) {
+  __shared__ int32_t hk[FZ_WARPS][FZ_SLOTS];
+  __shared__ double hv[FZ_WARPS][FZ_SLOTS];
+  __shared__ int32_t sst[FZ_WARPS][FZ_CAPA + 1];
+  __shared__ int64_t sbg[FZ_WARPS][FZ_CAPA];
+  __shared__ double sa[FZ_WARPS][FZ_CAPA];
+  __shared__ double gv[FZ_WARPS][32];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = (int64_t)blockIdx.x * FZ_WARPS + w;
+  if (i >= m) return;
+  int U = (int)ub[i];
+  int64_t a0 = arp[i];
+  int na = (int)(arp[i + 1] - a0);
+  if (U > FZ_SLOTS / 2 || na > FZ_CAPA) return;  // the row goes to the larger kernels
+  int32_t* K = hk[w];
+  double* Vv = hv[w];
+  int H = 32;
+  while (H < 2 * U) H <<= 1;
+  for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
+  int carry = 0;
+  for (int p0 = 0; p0 < na; p0 += 32) {
+    int p = p0 + lane;
+    int len = 0;
+    if (p < na) {
+      int32_t k = aci[a0 + p];
+      int64_t b0 = brp[k];
+      len = (int)(brp[k + 1] - b0);
+      sbg[w][p] = b0;
+      sa[w][p] = av[a0 + p];
+    }
+    int x = len;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (p < na) sst[w][p] = carry + x - len;
+    carry += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) sst[w][na] = carry;
+  __syncwarp();
+  // product t -> (column, value); loads for the next chunk are issued before this chunk is added
+  auto fetch = [&](int t, int32_t& col, double& val) {
+    col = -1 - lane;
+    val = 0.0;
+    if (t < U) {
+      int lo = 0, hi = na;
+      while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (sst[w][mid] <= t) lo = mid; else hi = mid;
+      }
+      int64_t q = sbg[w][lo] + (t - sst[w][lo]);
+      col = bci[q];
+      val = __dmul_rn(sa[w][lo], bv[q]);
+    }
+  };
+  int32_t ncol;
+  double nval;
+  fetch(lane, ncol, nval);
+  for (int t0 = 0; t0 < U; t0 += 32) {
+    int32_t col = ncol;
+    double val = nval;
+    if (t0 + 32 < U) fetch(t0 + 32 + lane, ncol, nval);
+    unsigned grp = __match_any_sync(0xffffffffu, col);
+    gv[w][lane] = val;
+    __syncwarp();
+    if (col >= 0 && lane == __ffs(grp) - 1) {
+      uint32_t h = hash32(col) & (H - 1);
+      while (true) {
+        int32_t prev = atomicCAS(&K[h], -1, col);
+        if (prev == -1 || prev == col) break;
+        h = (h + 1) & (H - 1);
+      }
+      double acc = Vv[h];
+      unsigned g = grp;
+      while (g) {
+        int l = __ffs(g) - 1;
+        acc = __dadd_rn(acc, gv[w][l]);
+        g &= g - 1;
+      }
+      Vv[h] = acc;
+    }
+    __syncwarp();
+  }
+  // compact the occupied slots, sort them by column, stage
+  int base = 0;
+  for (int t0 = 0; t0 < H; t0 += 32) {
+    int t = t0 + lane;
+    int32_t key = t < H ? K[t] : -1;
+    double v = t < H ? Vv[t] : 0.0;
+    unsigned msk = __ballot_sync(0xffffffffu, key >= 0);
+    __syncwarp();
+    if (key >= 0) {
+      int pos = base + __popc(msk & ((1u << lane) - 1));
+      K[pos] = key;
+      Vv[pos] = v;
+    }
+    base += __popc(msk);
+    __syncwarp();
+  }
+  int u = base;
+  int n2 = 1;
+  while (n2 < u) n2 <<= 1;
+  for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
+  __syncwarp();
+  for (int k2 = 2; k2 <= n2; k2 <<= 1)
+    for (int j = k2 >> 1; j > 0; j >>= 1) {
+      for (int t = lane; t < n2; t += 32) {
+        int x = t ^ j;
+        if (x > t) {
+          bool up = (t & k2) == 0;
+          int32_t ka = K[t], kb = K[x];
+          if ((ka > kb) == up) {
+            K[t] = kb; K[x] = ka;
+            double va = Vv[t]; Vv[t] = Vv[x]; Vv[x] = va;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  int64_t o = soff[i];
+  for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
+  if (lane == 0) { cnt[i] = u; done[i] = 1; }
+}
+
+// copy the staged columns and values of the fused rows to their final place in C
+__global__ void k_spgemm_fused_copy(int64_t m, const int64_t* __restrict__ ub, const int64_t* __restrict__ soff,
+                                    const int32_t* __restrict__ scol, const double* __restrict__ sval,
+                                    const int64_t* __restrict__ crp, int32_t* __restrict__ cci,
+                                    double* __restrict__ cv) {
+  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+  int sub = threadIdx.x & 7;
+  if (i >= m || ub[i] > FUSE_CAP) return;
+  int64_t o = soff[i], c0 = crp[i], L = crp[i + 1] - c0;
+  for (int64_t t = sub; t < L; t += 8) {
+    cci[c0 + t] = scol[o + t];
+    cv[c0 + t] = sval[o + t];
+  }
+}
+__global__ void k_small_ub(int64_t m, const int64_t* ub, int64_t* us) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < m) us[i] = ub[i] <= FUSE_CAP ? ub[i] : 0;
+}
+
 void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C) {
-  spgemm_symbolic(c, A, B, C);
+  if (A.nc != B.nr) throw Error(MGR_ERR_INVALID_ARG, "spgemm: inner dimensions differ");
+  int64_t m = A.nr;
+  C.nr = m;
+  C.nc = B.nc;
+  C.rp.alloc(c, m + 1);
+  if (m == 0) {
+    fill_i64(c, C.rp.p, 0, 1);
+    C.nnz = 0;
+    C.ci.alloc(c, 0);
+    C.v.alloc(c, 0);
+    return;
+  }
+  ProfScope ps(c, "spgemm");
+  DBuf<int64_t> ub(c, m), cnt(c, m + 1), us(c, m + 1);
+  DBuf<int32_t> mid(c, m), big(c, m);
+  DBuf<int> counters(c, 2);
+  CU(cudaMemsetAsync(counters.p, 0, 2 * sizeof(int), c.s));
+  {
+    ProfScope ps1(c, "sym_ub");
+    k_spgemm_ub<<<grid_for(m, 256), 256, 0, c.s>>>(m, A.rp, A.ci, B.rp, ub.p, counters.p, mid.p, counters.p + 1, big.p);
+    CU_LAUNCH();
+    k_small_ub<<<grid_for(m, 256), 256, 0, c.s>>>(m, ub.p, us.p);
+    CU_LAUNCH();
+  }
+  DBuf<int64_t> soff(c, m + 1);
+  int64_t nstage = counts_to_rowptr(c, us.p, soff.p, m);
+  int hc[2];
+  CU(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, c.s));
+  CU(cudaStreamSynchronize(c.s));
+  DBuf<int32_t> scol(c, nstage + 1);
+  DBuf<double> sval(c, nstage + 1);
+  {
+    ProfScope ps2(c, "fused_small");
+    DBuf<int> done(c, m);
+    CU(cudaMemsetAsync(done.p, 0, sizeof(int) * m, c.s));
+    k_spgemm_fused_chunk<<<grid_for(m, FZ_WARPS), 32 * FZ_WARPS, 0, c.s>>>(m, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p,
+                                                                           soff.p, scol.p, sval.p, cnt.p, done.p);
+    CU_LAUNCH();
+    k_spgemm_fused_hash<<<grid_for(m, FH_WARPS), 32 * FH_WARPS, 0, c.s>>>(m, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p,
+                                                                         soff.p, scol.p, sval.p, cnt.p, done.p);
+    CU_LAUNCH();
+  }
+  sym_pass(c, 0, A, B, ub.p, mid.p, hc[0], big.p, hc[1], cnt.p, C, 1);
+  C.nnz = counts_to_rowptr(c, cnt.p, C.rp.p, m);
+  C.ci.alloc(c, C.nnz);
   C.v.alloc(c, C.nnz);
-  if (C.nr == 0) return;
-  ProfScope ps(c, "spgemm_numeric");
+  sym_pass(c, 1, A, B, ub.p, mid.p, hc[0], big.p, hc[1], nullptr, C, 1);
+  {
+    ProfScope ps3(c, "fused_copy");
+    k_spgemm_fused_copy<<<grid_for(m * 8, 256), 256, 0, c.s>>>(m, ub.p, soff.p, scol.p, sval.p, C.rp.p, C.ci.p, C.v.p);
+    CU_LAUNCH();
+  }
+  ProfScope ps4(c, "spgemm_numeric");
   k_spgemm_numeric_expand<<<grid_for(C.nr, NX_WARPS), 32 * NX_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci,
-                                                                                B.v, C.rp, C.ci, C.v);
+                                                                                B.v, C.rp, C.ci, C.v, ub.p);
   CU_LAUNCH();
   k_spgemm_numeric<<<grid_for(C.nr, NUM_WARPS), 32 * NUM_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
-                                                                           C.rp, C.ci, C.v);
+                                                                           C.rp, C.ci, C.v, ub.p);
   CU_LAUNCH();
 }
 
