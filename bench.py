@@ -33,12 +33,18 @@ RTOL, RESTART, MAXIT = 1e-8, 30, 1000
 SOLVER = dict(amg_theta=0.5, amg_pmax=4, amg_smoother=0, amg_omega=0.8)
 
 
-KERNEL_NAMES = ("bsr3_spmv_f64", "bsr_resid_split", "global_relax", "csr_rows", "interp", "mdot", "mupdate",
+KERNEL_NAMES = ("bsr3_spmv_f64", "bsr_resid_split", "global_relax", "amg0_rows", "amgc_rows", "amg_restrict",
+                "amg_prolong", "frelax", "restrict", "csr_rows", "interp", "mdot", "mupdate",
                 "spgemm_numeric", "spgemm_symbolic", "setup_total", "setup_mgr_level", "setup_mgr_rap", "setup_amg",
                 "setup_amg_strength", "setup_amg_pmis", "setup_amg_extpi", "setup_amg_transpose", "setup_amg_rap",
                 "setup_dense_inverse", "setup_cast_alloc", "sym_ub", "sym_count_warp", "sym_fill_warp", "sym_block",
                 "sym_bitmap", "numeric_expand", "spgemm", "fused_small", "fused_copy",
-                "extpi_pattern", "extpi_weights", "amg0_rows")
+                "extpi_pattern", "extpi_weights")
+SOLVE_KERNELS = ("bsr3_spmv_f64", "amg0_rows", "amgc_rows", "amg_restrict", "amg_prolong", "frelax", "restrict",
+                 "csr_rows", "mdot", "mupdate", "bsr_resid_split", "interp", "global_relax")
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture of the
+# kernel on an 80^3 instance of the workload, scaled to the launch by the stored entries it streams)
+TRAFFIC = {}
 
 
 def _args():
@@ -154,12 +160,6 @@ def _shape(m, kind, lev):
     return nr.value, nnz.value
 
 
-def spmv_bytes(nb, nnzb, residual):
-    """Algorithmic bytes of one FP64 BSR SpMV launch: the 3x3 values, block columns and row pointers
-    once, x once, y written (and the subtrahend read in residual mode)."""
-    return 72 * nnzb + 4 * nnzb + 8 * (nb + 1) + 24 * nb + 24 * nb + (24 * nb if residual else 0)
-
-
 def main():
     a = _args()
     if a.warmup < 3:
@@ -252,7 +252,7 @@ def main():
         launches = mg.launch_count() - l0
         clocks = sampler.stop() if sampler else None
         ms = _max(e0.elapsed_time(e1)) / steps
-        kt = {k: m.kernel_time(k) for k in KERNEL_NAMES} if profile else {}
+        kt = {k: m.kernel_time(k) + (m.kernel_bytes(k),) for k in KERNEL_NAMES} if profile else {}
         mem = m.memory_bytes()
         L, na = m.levels()
         hier = {"mgr": [list(_shape(m, mg.MAT_LEVEL, l)) for l in range(L + 1)],
@@ -270,16 +270,29 @@ def main():
            "solve_ms": statistics.mean(i["solve_ms"] for i in infos), "relres_true": relres,
            "solves_per_s_all_gpus": a.gpus * 1000.0 / ms, "gpu_launches": int(launches),
            "device_memory_gb": mem / 1e9, "hierarchy_rows_nnz": hier}
-    # dominant kernel roofline: the FP64 BSR SpMV of the Krylov iteration (timed live above)
+    # per-kernel achieved algorithmic bandwidth of the solve kernels (bytes declared by the library
+    # for each timed launch, divided by the CUDA-event time of those launches); the roofline entry is
+    # the one of these single-operator kernels with the most time per step
     peak, peak_kind = _peaks()
-    n_sp, t_sp = kt.get("bsr3_spmv_f64", (0, 0.0))
-    if n_sp:
-        per_launch_bytes = spmv_bytes(p.nb, p.nnzb, residual=False)
-        achieved = per_launch_bytes / (t_sp / n_sp * 1e-3) / 1e9
-        out["roofline"] = {"kernel": "bsr3_spmv_f64", "bound": "hbm", "achieved": achieved, "peak": peak,
-                           "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                           "traffic": None, "bytes_per_launch": per_launch_bytes,
-                           "avg_launch_us": t_sp / n_sp * 1e3, "launches": n_sp}
+    rk = {}
+    for k in SOLVE_KERNELS:
+        n_k, t_k, by_k = kt.get(k, (0, 0.0, 0.0))
+        if n_k and by_k and t_k > 0:
+            gbs = by_k / (t_k * 1e-3) / 1e9
+            rk[k] = {"launches_per_step": n_k / a.steps, "ms_per_step": t_k / a.steps, "achieved_gbs": gbs,
+                     "frac": gbs / peak, "bytes_per_step": by_k / a.steps}
+    out["kernel_bandwidth"] = rk
+    cands = [k for k in ("bsr3_spmv_f64", "amg0_rows") if k in rk]
+    if cands:
+        k = max(cands, key=lambda c: rk[c]["ms_per_step"])
+        n_k, t_k, by_k = kt[k]
+        per_launch = by_k / n_k
+        achieved = per_launch / (t_k / n_k * 1e-3) / 1e9
+        tr = TRAFFIC.get(k)
+        out["roofline"] = {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "peak_source": peak_kind,
+                           "traffic": tr(p) if tr else None, "bytes_per_launch": per_launch,
+                           "avg_launch_us": t_k / n_k * 1e3, "launches": n_k}
     out["kernel_ms_per_step"] = {k: v[1] / a.steps for k, v in kt.items() if v[0]}
     if clocks:
         out["clocks"] = clocks

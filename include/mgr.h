@@ -148,6 +148,9 @@ mgr_status_t mgr_vector_len(mgr_handle_t h, int kind, int level, int64_t* len);
 mgr_status_t mgr_copy_vector(mgr_handle_t h, int kind, int level, double* out);
 /* Device bytes held by the handle (host out). */
 mgr_status_t mgr_memory_bytes(mgr_handle_t h, int64_t* bytes);
+/* Largest number of device bytes the handle has held at once since mgr_create, setup and solve
+ * work buffers included (host out). */
+mgr_status_t mgr_memory_peak_bytes(mgr_handle_t h, int64_t* bytes);
 /* Statistics (host outs, each may be NULL): wall time of the last mgr_setup in milliseconds, kernel
  * launches issued by the last mgr_apply, kernel nodes of the captured apply graph (0 when not
  * captured), and the process-wide count of kernel launches issued by this library since load. */
@@ -157,10 +160,24 @@ mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_laun
 /* Per-kernel timing on the handle's stream: enable = 1 starts recording CUDA events around every
  * launch of the named kernels and clears earlier totals, enable = 0 stops.  mgr_kernel_time returns
  * the launches and the summed device milliseconds recorded for `name` (synchronises).  Names:
- * "bsr3_spmv_f64", "mdot", "mupdate", "global_relax", "bsr_resid_split", "csr_rows", "interp",
- * "spgemm_numeric". */
+ *   solve:  "bsr3_spmv_f64" (Krylov SpMV), "mdot", "mupdate" (Arnoldi), "global_relax",
+ *           "bsr_resid_split" (level-0 residual), "frelax" (F-relaxation sweeps), "restrict"
+ *           (coarse residual r_C - A_cf e_F), "interp" (e = P e_c), "amg0_rows" (smoothing and
+ *           residual on the AMG level-0 operator), "amgc_rows" (the same on coarser AMG levels),
+ *           "amg_restrict", "amg_prolong" (AMG transfers);
+ *   setup:  "setup_total", "setup_mgr_level", "setup_mgr_rap", "setup_amg", "setup_amg_strength",
+ *           "setup_amg_pmis", "setup_amg_extpi", "extpi_pattern", "extpi_weights",
+ *           "setup_amg_transpose", "setup_amg_rap", "setup_dense_inverse", "setup_cast_alloc",
+ *           "spgemm", "fused_small", "fused_copy", "spgemm_numeric", "sym_ub", "sym_count_warp",
+ *           "sym_fill_warp", "sym_block", "sym_bitmap".
+ * Unknown names report 0 launches. */
 mgr_status_t mgr_profile(mgr_handle_t h, int enable);
 mgr_status_t mgr_kernel_time(mgr_handle_t h, const char* name, int64_t* launches, double* total_ms);
+/* Algorithmic bytes of the launches recorded for `name` since profiling was enabled (host out): for
+ * the solve kernels, every input element read once and every output element written once (values,
+ * indices, row pointers, vectors), padding and cache re-reads not counted; 0 for the setup scopes.
+ * Divided by mgr_kernel_time's milliseconds it gives the achieved algorithmic bandwidth. */
+mgr_status_t mgr_kernel_bytes(mgr_handle_t h, const char* name, double* bytes);
 
 /* ---- stand-alone kernels ----------------------------------------------------------------------- */
 /* y = A x (sub == NULL) or y = sub - A x, FP64, on `cuda_stream`.  The hot sparse product of the

@@ -61,8 +61,8 @@ class SolveInfo(ctypes.Structure):
 
 EXPORTS = ["mgr_status_string", "mgr_options_default", "mgr_create", "mgr_setup", "mgr_apply", "fgmres_solve",
            "mgr_destroy", "mgr_get_levels", "mgr_matrix_shape", "mgr_copy_matrix", "mgr_vector_len",
-           "mgr_copy_vector", "mgr_memory_bytes", "mgr_get_stats", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
-           "mgr_bsr3_outer_grad", "mgr_profile", "mgr_kernel_time"]
+           "mgr_copy_vector", "mgr_memory_bytes", "mgr_memory_peak_bytes", "mgr_get_stats", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
+           "mgr_bsr3_outer_grad", "mgr_profile", "mgr_kernel_time", "mgr_kernel_bytes"]
 
 
 def lib():
@@ -89,12 +89,14 @@ def lib():
         L.mgr_vector_len.argtypes = [vp, i32, i32, P(i64)]
         L.mgr_copy_vector.argtypes = [vp, i32, i32, vp]
         L.mgr_memory_bytes.argtypes = [vp, P(i64)]
+        L.mgr_memory_peak_bytes.argtypes = [vp, P(i64)]
         L.mgr_get_stats.argtypes = [vp, P(ctypes.c_double), P(i64), P(i64), P(i64)]
         L.mgr_bsr3_spmv.argtypes = [P(Bsr3), vp, vp, vp, vp]
         L.mgr_bsr3_transpose.argtypes = [P(Bsr3), vp, vp, vp, vp]
         L.mgr_bsr3_outer_grad.argtypes = [P(Bsr3), vp, vp, vp, vp]
         L.mgr_profile.argtypes = [vp, i32]
         L.mgr_kernel_time.argtypes = [vp, ctypes.c_char_p, P(i64), P(ctypes.c_double)]
+        L.mgr_kernel_bytes.argtypes = [vp, ctypes.c_char_p, P(ctypes.c_double)]
         for name in EXPORTS:
             getattr(L, name).restype = ctypes.c_int if name not in ("mgr_status_string", "mgr_options_default") \
                 else getattr(L, name).restype
@@ -273,9 +275,21 @@ class MGR:
         _check(lib().mgr_kernel_time(self._h, name.encode(), ctypes.byref(n), ctypes.byref(ms)), "mgr_kernel_time")
         return n.value, ms.value
 
+    def kernel_bytes(self, name: str) -> float:
+        """Algorithmic bytes declared by the launches recorded for a named kernel since profile(True)."""
+        b = ctypes.c_double()
+        _check(lib().mgr_kernel_bytes(self._h, name.encode(), ctypes.byref(b)), "mgr_kernel_bytes")
+        return b.value
+
     def memory_bytes(self) -> int:
         b = ctypes.c_int64()
         _check(lib().mgr_memory_bytes(self._h, ctypes.byref(b)), "mgr_memory_bytes")
+        return b.value
+
+    def memory_peak_bytes(self) -> int:
+        """Most device bytes the handle has held at once since it was created."""
+        b = ctypes.c_int64()
+        _check(lib().mgr_memory_peak_bytes(self._h, ctypes.byref(b)), "mgr_memory_peak_bytes")
         return b.value
 
     def stats(self):

@@ -24,7 +24,7 @@ __global__ void k_global_relax(int64_t nb, const T* __restrict__ binv, const dou
 
 template <class T>
 void launch_global_relax(Ctx& c, int64_t nb, const T* binv, const double* r, T* e0) {
-  ProfScope ps(c, "global_relax");
+  ProfScope ps(c, "global_relax", (double)nb * (9 * sizeof(T) + 24 + 3 * sizeof(T)));
   k_global_relax<T><<<grid_for(nb, 256), 256, 0, c.s>>>(nb, binv, r, e0);
   CU_LAUNCH();
 }
@@ -76,7 +76,10 @@ struct EpiSplit {  // res = r - A e0 routed by map
 template <class T>
 void launch_bsr_resid_split(Ctx& c, const SellPattern& S, const T* vals, const double* r, const T* e0,
                             const int32_t* map, T* rnext, T* resF) {
-  ProfScope ps(c, "bsr_resid_split");
+  // values, block columns, row pointers, e0, r, map, one output per dof
+  ProfScope ps(c, "bsr_resid_split",
+               e0 ? (double)S.nnzb_real * (9 * sizeof(T) + 4) + 8.0 * (S.nb + 1) + (double)S.nb * (3 * sizeof(T) + 24 + 12 + 3 * sizeof(T))
+                  : (double)S.nb * (24 + 12 + 3 * sizeof(T)));
   if (e0) {
     launch_bsr_sell<T, T>(c, S, vals, e0, EpiSplit<T>{r, map, rnext, resF});
   } else {
@@ -105,7 +108,31 @@ __global__ void __launch_bounds__(256) k_rows(int64_t nr, const int64_t* __restr
   if (ok && sub == 0) epi(r, s);
 }
 
-// SELL form: one thread per row, slots walked in order (padding slots add 0 * x[0])
+// SELL form: one thread per row, slots walked four at a time (padding slots add 0 * x[0])
+template <class T>
+struct Quad;
+template <>
+struct Quad<float> {
+  __device__ static __forceinline__ float dot(const float* vp, int4 c, const float* x) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(vp));
+    float s = v.x * __ldg(x + c.x);
+    s = fmaf(v.y, __ldg(x + c.y), s);
+    s = fmaf(v.z, __ldg(x + c.z), s);
+    return fmaf(v.w, __ldg(x + c.w), s);
+  }
+};
+template <>
+struct Quad<double> {
+  __device__ static __forceinline__ double dot(const double* vp, int4 c, const double* x) {
+    double2 a = __ldg(reinterpret_cast<const double2*>(vp));
+    double2 b = __ldg(reinterpret_cast<const double2*>(vp) + 1);
+    double s = a.x * __ldg(x + c.x);
+    s = fma(a.y, __ldg(x + c.y), s);
+    s = fma(b.x, __ldg(x + c.z), s);
+    return fma(b.y, __ldg(x + c.w), s);
+  }
+};
+
 template <class T, class Epi>
 __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __restrict__ soff,
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
@@ -114,19 +141,24 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
   if (r >= nr) return;
   int64_t s = r / RS_C;
   int t = (int)(r - s * RS_C);
-  int64_t j0 = soff[s], w = soff[s + 1] - j0;
-  const int32_t* cp = col + j0 * RS_C + t;
-  const T* vp = val + j0 * RS_C + t;
+  int64_t j0 = soff[s], nq = (soff[s + 1] - j0) / RS_Q;
+  const int32_t* cp = col + j0 * RS_C + t * RS_Q;
+  const T* vp = val + j0 * RS_C + t * RS_Q;
   T sum = 0;
-#pragma unroll 4
-  for (int64_t j = 0; j < w; ++j) sum += vp[j * RS_C] * ldg(x + cp[j * RS_C]);
+#pragma unroll 2
+  for (int64_t q = 0; q < nq; ++q) {
+    int4 c = __ldg(reinterpret_cast<const int4*>(cp + q * (RS_Q * RS_C)));
+    sum += Quad<T>::dot(vp + q * (RS_Q * RS_C), c, x);
+  }
   epi(r, sum);
 }
 
 template <class T, class Epi>
 static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, const char* name = "csr_rows") {
   if (op.nr <= 0) return;
-  ProfScope ps(c, name);
+  // values and columns, row pointers, x once, the epilogue's row vectors
+  ProfScope ps(c, name, (double)op.nnz * (sizeof(T) + 4) + 8.0 * (op.nr + 1) + (double)op.nc * sizeof(T) +
+                            (double)op.nr * epi.row_bytes());
   const int B = 256;
   if (op.sell) {
     k_rows_sell<T, Epi><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, x, epi);
@@ -160,6 +192,7 @@ struct EpiFrelax {  // eFo[f] = eFi[f] + minv[f] (src_f - s)
     T b = F ? src[F[f]] : src[f];
     eFo[f] = eFi[f] + minv[f] * (b - s);
   }
+  double row_bytes() const { return (F ? 4 : 0) + 4.0 * sizeof(T); }
 };
 template <class T>
 struct EpiRestrict {  // rnext[c] = base_c - s
@@ -168,26 +201,31 @@ struct EpiRestrict {  // rnext[c] = base_c - s
     T b = C ? r[C[c]] : rnext[c];
     rnext[c] = b - s;
   }
+  double row_bytes() const { return (C ? 4 : 0) + 2.0 * sizeof(T); }
 };
 template <class T>
 struct EpiResid {
   const T* b; T* res;
   __device__ void operator()(int64_t i, T s) const { res[i] = b[i] - s; }
+  double row_bytes() const { return 2.0 * sizeof(T); }
 };
 template <class T>
 struct EpiJacobi {
   const T* d; const T* b; const T* xi; T* xo;
   __device__ void operator()(int64_t i, T s) const { xo[i] = xi[i] + d[i] * (b[i] - s); }
+  double row_bytes() const { return 4.0 * sizeof(T); }
 };
 template <class T>
 struct EpiStore {
   T* y;
   __device__ void operator()(int64_t i, T s) const { y[i] = s; }
+  double row_bytes() const { return 1.0 * sizeof(T); }
 };
 template <class T>
 struct EpiAdd {
   T* y;
   __device__ void operator()(int64_t i, T s) const { y[i] += s; }
+  double row_bytes() const { return 2.0 * sizeof(T); }
 };
 
 template <class T>
@@ -206,11 +244,11 @@ void launch_frelax_first(Ctx& c, int64_t nF, const int32_t* F, const T* src, con
 template <class T>
 void launch_frelax_sweep(Ctx& c, const RowsOp<T>& Aff, const int32_t* F, const T* src, const T* minv, const T* eFi,
                          T* eFo) {
-  run_rows(c, Aff, eFi, EpiFrelax<T>{F, src, minv, eFi, eFo});
+  run_rows(c, Aff, eFi, EpiFrelax<T>{F, src, minv, eFi, eFo}, "frelax");
 }
 template <class T>
 void launch_restrict(Ctx& c, const RowsOp<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext) {
-  run_rows(c, Acf, eF, EpiRestrict<T>{C, r, rnext});
+  run_rows(c, Acf, eF, EpiRestrict<T>{C, r, rnext}, "restrict");
 }
 
 // interpolation: C dofs take ec[c] (a scatter over the C list), F dofs eF[f] + W_p[f,:] ec (a
@@ -234,13 +272,14 @@ struct EpiInterpF {
     if (base) v += base[d];
     out[d] = (TO)v;
   }
+  double row_bytes() const { return 4.0 + sizeof(T) + (base ? sizeof(T) : 0) + sizeof(TO); }
 };
 
 template <class T, class TO>
 void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32_t* C, const RowsOp<T>& Wp,
                    const T* eF, const T* ec, const T* base, TO* out) {
   if (nC > 0) {
-    ProfScope ps(c, "interp");
+    ProfScope ps(c, "interp", (double)nC * (4.0 + sizeof(T) + (base ? sizeof(T) : 0) + sizeof(TO)));
     k_interp_c<T, TO><<<grid_for(nC, 256), 256, 0, c.s>>>(nC, C, ec, base, out);
     CU_LAUNCH();
   }
@@ -279,11 +318,11 @@ void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* 
 }
 template <class T>
 void launch_spmv(Ctx& c, const RowsOp<T>& A, const T* x, T* y) {
-  run_rows(c, A, x, EpiStore<T>{y});
+  run_rows(c, A, x, EpiStore<T>{y}, "amg_restrict");
 }
 template <class T>
 void launch_prolong_add(Ctx& c, const RowsOp<T>& P, const T* xc, T* x) {
-  run_rows(c, P, xc, EpiAdd<T>{x});
+  run_rows(c, P, xc, EpiAdd<T>{x}, "amg_prolong");
 }
 
 // x = inv b with the FP64 dense inverse of the coarsest operator: one warp per row

@@ -16,13 +16,15 @@ constexpr int SELL_C = 32;
 
 struct SellPattern {
   int64_t nb = 0, nslices = 0, slots = 0;
+  int64_t nnzb_real = 0;  // stored blocks of the source matrix (slots * 32 minus padding)
   DBuf<int64_t> soff;  // nslices + 1 slot offsets
   DBuf<int32_t> col;   // slots * 32
   DBuf<int64_t> src;   // slots * 32: source block index in the BSR arrays, -1 for padding
 };
 
 // Builds the pattern of the sliced layout from a BSR pattern (rowptr, colind on the device).
-void sell_build_pattern(Ctx& c, int64_t nb, const int64_t* rowptr, const int32_t* colind, SellPattern& S);
+void sell_build_pattern(Ctx& c, int64_t nb, int64_t nnzb, const int64_t* rowptr, const int32_t* colind,
+                        SellPattern& S);
 // Scatters BSR values (9 per block, row-major) into the sliced value layout (slots * 32 * 9).
 template <class TS, class TD>
 void sell_fill_values(Ctx& c, const SellPattern& S, const TS* values, TD* out);

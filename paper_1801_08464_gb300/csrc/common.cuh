@@ -51,6 +51,7 @@ struct Prof {
     std::vector<cudaEvent_t> a, b;
     double ms = 0.0;
     int64_t n = 0;
+    double bytes = 0.0;  // algorithmic bytes declared by the timed launches
   };
   std::map<std::string, Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -97,12 +98,16 @@ struct ProfScope {
   Ctx& c;
   const char* name;
   cudaEvent_t e1 = nullptr;
-  ProfScope(Ctx& ctx, const char* n) : c(ctx), name(n) {
+  // bytes: the algorithmic bytes of the work inside the scope (each input element read once, each
+  // output written once), summed per name for achieved-bandwidth figures
+  ProfScope(Ctx& ctx, const char* n, double bytes = 0.0) : c(ctx), name(n) {
     if (!c.prof) return;
     cudaEvent_t e0 = c.prof->get();
     e1 = c.prof->get();
     cudaEventRecord(e0, c.s);
-    c.prof->recs[name].a.push_back(e0);
+    Prof::Rec& r = c.prof->recs[name];
+    r.a.push_back(e0);
+    r.bytes += bytes;
   }
   ~ProfScope() {
     if (!c.prof) return;

@@ -2,8 +2,10 @@
 // MGR preconditioner) and of the adjoint helpers: BSR SpMV, deterministic multi-dot products with
 // warp-shuffle reductions, Gram-Schmidt updates, solution update, block transpose, outer-product
 // gradient.  Reductions are two-stage with a fixed grid, so results do not depend on timing.
-#include "apply.cuh"
+#include <map>
+#include <mutex>
 
+#include "apply.cuh"
 
 namespace mgr {
 
@@ -48,14 +50,15 @@ void launch_bsr3_spmv_f64(Ctx& c, const mgr_bsr3_t& A, const double* x, const do
 
 void launch_sell_spmv_f64(Ctx& c, const SellPattern& S, const double* vals, const double* x, const double* sub,
                           double* y) {
-  ProfScope ps(c, "bsr3_spmv_f64");
+  // values, block columns, row pointers, x, y (and the subtrahend)
+  ProfScope ps(c, "bsr3_spmv_f64", 76.0 * S.nnzb_real + 8.0 * (S.nb + 1) + 48.0 * S.nb + (sub ? 24.0 * S.nb : 0.0));
   launch_bsr_sell<double, double>(c, S, vals, x, EpiSpmvF64{sub, y});
 }
 
 // ---- multi-dot ---------------------------------------------------------------------------------
 constexpr int KT = 256;
 constexpr int MD_VEC = 8;        // vectors per block column of the 2-D multi-dot grid
-constexpr int MD_BLOCKS = 1216;  // 8 resident blocks per SM on 152 SMs
+constexpr int MD_BLOCKS = 1216;  // upper bound of the grids below (8 blocks per SM on 152 SMs)
 
 template <int NA>
 __device__ __forceinline__ void block_reduce_store(double (&acc)[NA], int na, double* part) {
@@ -146,8 +149,29 @@ __global__ void k_reduce_parts(int nx, int na, const double* __restrict__ part, 
   if (lane == 0) out[k] = s;
 }
 
+// Blocks of `fn` (KT threads, static shared memory only) resident on the whole device at once, at
+// most MD_BLOCKS: streaming kernels launch exactly one full wave, with no partial second wave.
+static int one_wave(const void* fn) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> cache;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(dev, fn);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0, sms = 0;
+  CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, KT, 0));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int nb = per_sm * sms;
+  if (nb < 1) nb = 1;
+  if (nb > MD_BLOCKS) nb = MD_BLOCKS;
+  cache[key] = nb;
+  return nb;
+}
+
 static int md_nx(int64_t n, int ng, int64_t* chunk) {
-  int nx = MD_BLOCKS / ng;
+  int nx = one_wave((const void*)k_mdot) / ng;
   if (nx < 1) nx = 1;
   int64_t c = (n + nx - 1) / nx;
   c = (c + 1) & ~int64_t(1);
@@ -164,7 +188,7 @@ void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const 
   if (ng < 1) ng = 1;
   int64_t chunk;
   int nx = md_nx(n, ng, &chunk);
-  ProfScope ps(c, "mdot");
+  ProfScope ps(c, "mdot", 8.0 * (nv + 1) * n);
   k_mdot<<<ng * nx, KT, 0, c.s>>>(n, V, ldv, nv, w, ww, ng, nx, chunk, part);
   CU_LAUNCH();
   int na = nv + ww;
@@ -212,11 +236,12 @@ __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restr
 void launch_mupdate(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* h, const double* scale,
                     const double* w, double* vout, double* part, double* out) {
   if (nv > KRY_MAXV) throw Error(MGR_ERR_UNSUPPORTED, "update with more than 32 vectors");
-  ProfScope ps(c, "mupdate");
-  k_mupdate<<<KRY_GRID, KT, 0, c.s>>>(n, V, ldv, nv, h, scale, w, vout, out ? part : nullptr);
+  ProfScope ps(c, "mupdate", 8.0 * (nv + 2) * n);
+  const int grid = one_wave((const void*)k_mupdate);
+  k_mupdate<<<grid, KT, 0, c.s>>>(n, V, ldv, nv, h, scale, w, vout, out ? part : nullptr);
   CU_LAUNCH();
   if (out) {
-    k_reduce_parts<<<1, 32, 0, c.s>>>(KRY_GRID, 1, part, out);
+    k_reduce_parts<<<1, 32, 0, c.s>>>(grid, 1, part, out);
     CU_LAUNCH();
   }
 }

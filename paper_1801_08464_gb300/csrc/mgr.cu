@@ -124,8 +124,8 @@ const T* vcycle(mgr_handle_s& h, int k, const T* b) {
   T* xa = P<T>(h.a_xa[k]);
   T* xb = P<T>(h.a_xb[k]);
   T* res = P<T>(h.a_res[k]);
-  // the level-0 operator (the pressure matrix) is timed under its own name
-  const char* nm = (k == 0) ? "amg0_rows" : "csr_rows";
+  // the level-0 operator (the pressure matrix) is timed apart from the coarser levels
+  const char* nm = (k == 0) ? "amg0_rows" : "amgc_rows";
   launch_scale<T>(c, A.n, d, b, xa);
   for (int s = 1; s < h.o.amg_pre; ++s) {
     launch_jacobi<T>(c, Av, d, b, xa, xb, nm);
@@ -287,7 +287,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   h.ci0.alloc(c, A.nnzb);
   CU(cudaMemcpyAsync(h.rp0.p, A.rowptr, sizeof(int64_t) * (A.nb + 1), cudaMemcpyDeviceToDevice, c.s));
   CU(cudaMemcpyAsync(h.ci0.p, A.colind, sizeof(int32_t) * A.nnzb, cudaMemcpyDeviceToDevice, c.s));
-  sell_build_pattern(c, A.nb, A.rowptr, A.colind, h.sell);
+  sell_build_pattern(c, A.nb, A.nnzb, A.rowptr, A.colind, h.sell);
   int L;
   {
     DBuf<int> mx(c, 1);
@@ -780,9 +780,26 @@ mgr_status_t mgr_kernel_time(mgr_handle_t h, const char* name, int64_t* launches
   });
 }
 
+mgr_status_t mgr_kernel_bytes(mgr_handle_t h, const char* name, double* bytes) {
+  if (!h || !name || !bytes) return MGR_ERR_INVALID_ARG;
+  *bytes = 0.0;
+  if (!h->prof) return MGR_OK;
+  return guarded(h, [&] {
+    h->prof->settle();
+    auto it = h->prof->recs.find(name);
+    if (it != h->prof->recs.end()) *bytes = it->second.bytes;
+  });
+}
+
 mgr_status_t mgr_memory_bytes(mgr_handle_t h, int64_t* bytes) {
   if (!h || !bytes) return MGR_ERR_INVALID_ARG;
   *bytes = h->c.bytes;
+  return MGR_OK;
+}
+
+mgr_status_t mgr_memory_peak_bytes(mgr_handle_t h, int64_t* bytes) {
+  if (!h || !bytes) return MGR_ERR_INVALID_ARG;
+  *bytes = h->c.peak;
   return MGR_OK;
 }
 

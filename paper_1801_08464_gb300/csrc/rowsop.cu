@@ -8,7 +8,7 @@ __global__ void k_rs_width(int64_t nr, const int64_t* rp, int64_t nslices, int64
   if (s >= nslices) return;
   int64_t w = 0, e = (s + 1) * RS_C < nr ? (s + 1) * RS_C : nr;
   for (int64_t r = s * RS_C; r < e; ++r) w = max(w, rp[r + 1] - rp[r]);
-  width[s] = w;
+  width[s] = (w + RS_Q - 1) / RS_Q * RS_Q;
 }
 
 template <class T>
@@ -21,7 +21,7 @@ __global__ void k_rs_fill(int64_t nr, int64_t npad, const int64_t* rp, const int
   int64_t b0 = soff[s], w = soff[s + 1] - b0;
   int64_t k0 = r < nr ? rp[r] : 0, len = r < nr ? rp[r + 1] - k0 : 0;
   for (int64_t j = 0; j < w; ++j) {
-    int64_t o = (b0 + j) * RS_C + t;
+    int64_t o = b0 * RS_C + (j / RS_Q) * (RS_Q * RS_C) + t * RS_Q + (j % RS_Q);
     if (j < len) { scol[o] = ci[k0 + j]; sval[o] = (T)v[k0 + j]; }
     else { scol[o] = 0; sval[o] = T(0); }  // column 0 exists in every operator with nonzeros
   }
@@ -36,6 +36,7 @@ __global__ void k_rs_cast(int64_t n, const double* a, T* b) {
 template <class T>
 void rowsop_build(Ctx& c, const DCSR<double>& A, RowsOp<T>& op) {
   op.nr = A.nr;
+  op.nc = A.nc;
   op.nnz = A.nnz;
   op.sell = false;
   op.slots = 0;

@@ -1,11 +1,15 @@
 // rowsop.cuh -- scalar sparse operators of the preconditioner apply, in one of two layouts.
 //
-// SELL-8 (sliced ELL): rows grouped in slices of 8 consecutive rows; slice s holds W_s slots (its
-// longest row) and, for slot j, the 8 rows' column and value at col[(B_s + j) * 8 + t],
-// val[(B_s + j) * 8 + t] (t = row within the slice; padding: column 0, value 0).  One thread per row
-// walks its slots; each slot of a slice is one full 32-byte sector per array and a slice's slots are
-// contiguous, so a warp streams 4 slices sector by sector.  Slices of 8 rather than 32 keep the
-// padding of the pressure-level operators (rows of 25 to 63 entries side by side) near 10 %.
+// SELL-8 (sliced ELL) with slots in groups of 4: rows are grouped in slices of 8 consecutive rows;
+// slice s holds W_s slots (its longest row, rounded up to a multiple of 4) starting at slot B_s (a
+// multiple of 4).  Slot j of row t (t = row within the slice) is stored at
+//   (B_s * 8) + (j / 4) * 32 + t * 4 + (j % 4)
+// in col[] and val[] (padding: column 0, value 0).  So one thread per row reads its slots four at a
+// time as one 16-byte load of columns and one 16-byte (FP32) or two 16-byte (FP64) loads of values,
+// and the 8 rows of a slice read one contiguous 128-byte line per group: few, wide, fully used loads,
+// which keep more bytes in flight per thread than one 4-byte load per slot.  Slices of 8 rather
+// than 32 keep the padding of the pressure-level operators (rows of 25 to 63 entries side by side)
+// near 10 %.
 // CSR: kept when the slices would pad more than 30 % above the nonzeros (rows of very different
 // lengths side by side); the vector-CSR kernel (TPR lanes per row) runs those.
 #pragma once
@@ -14,13 +18,14 @@
 namespace mgr {
 
 constexpr int RS_C = 8;
+constexpr int RS_Q = 4;  // slots per group
 constexpr double RS_MAX_PAD = 1.3;
 
 template <class T>
 struct RowsOp {
-  int64_t nr = 0, nnz = 0;
+  int64_t nr = 0, nc = 0, nnz = 0;
   bool sell = false;
-  // SELL-8
+  // SELL-8 with 4-slot groups
   int64_t slots = 0;
   DBuf<int64_t> soff;
   DBuf<int32_t> scol;

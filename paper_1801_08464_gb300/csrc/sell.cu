@@ -31,8 +31,10 @@ __global__ void k_sell_fill_pattern(int64_t nb, int64_t nrows_padded, const int6
   }
 }
 
-void sell_build_pattern(Ctx& c, int64_t nb, const int64_t* rowptr, const int32_t* colind, SellPattern& S) {
+void sell_build_pattern(Ctx& c, int64_t nb, int64_t nnzb, const int64_t* rowptr, const int32_t* colind,
+                        SellPattern& S) {
   S.nb = nb;
+  S.nnzb_real = nnzb;
   S.nslices = (nb + SELL_C - 1) / SELL_C;
   DBuf<int64_t> width(c, S.nslices + 1);
   k_sell_width<<<grid_for(S.nslices, 256), 256, 0, c.s>>>(nb, rowptr, S.nslices, width.p);

@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(32 * NUM_WARPS) k_spgemm_numeric(int64_t m, co
 }
 
 // Fused product for the rows with at most FUSE_CAP products that k_spgemm_fused_chunk left (long A
-// rows or more than FZ_SLOTS / 2 products): the A row is walked in ascending
+// rows or more than FZ_SLOTS / 2 products; it lists them): the A row is walked in ascending
 // order (ascending k); the products of one A entry have distinct columns, so the lanes add them to a
 // shared-memory hash table (column -> running sum) without conflicts, and __syncwarp orders successive
 // k.  Each sum therefore starts from 0.0 and adds its products in ascending k (Gustavson's order).
@@ -602,78 +602,82 @@ constexpr int FH_WARPS = 2;
 constexpr int FH_SLOTS = 2 * FUSE_CAP;
 
 __global__ void __launch_bounds__(32 * FH_WARPS) k_spgemm_fused_hash(
-    int64_t m, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
-    const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
-    const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
-    double* __restrict__ sval, int64_t* __restrict__ cnt, const int* __restrict__ done) {
+    const int32_t* __restrict__ rows, const int* __restrict__ nrows, const int64_t* __restrict__ arp,
+    const int32_t* __restrict__ aci, const double* __restrict__ av, const int64_t* __restrict__ brp,
+    const int32_t* __restrict__ bci, const double* __restrict__ bv, const int64_t* __restrict__ ub,
+    const int64_t* __restrict__ soff, int32_t* __restrict__ scol, double* __restrict__ sval,
+    int64_t* __restrict__ cnt) {
   __shared__ int32_t hk[FH_WARPS][FH_SLOTS];
   __shared__ double hv[FH_WARPS][FH_SLOTS];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t i = (int64_t)blockIdx.x * FH_WARPS + w;
-  if (i >= m) return;
-  int U = (int)ub[i];
-  if (U > FUSE_CAP || done[i]) return;
-  int32_t* K = hk[w];
-  double* Vv = hv[w];
-  int H = 1;
-  while (H < 2 * U) H <<= 1;
-  for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
-  __syncwarp();
-  for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
-    int32_t k = aci[p];
-    double a = av[p];
-    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
-      int32_t key = bci[q];
-      double prod = __dmul_rn(a, bv[q]);
-      uint32_t h = hash32(key) & (H - 1);
-      while (true) {
-        int32_t prev = atomicCAS(&K[h], -1, key);
-        if (prev == -1 || prev == key) break;
-        h = (h + 1) & (H - 1);
-      }
-      Vv[h] = __dadd_rn(Vv[h], prod);
-    }
+  const int64_t nr = *nrows;
+  // a fixed grid walks the list of rows left by k_spgemm_fused_chunk
+  for (int64_t r = (int64_t)blockIdx.x * FH_WARPS + w; r < nr; r += (int64_t)gridDim.x * FH_WARPS) {
+    const int64_t i = rows[r];
+    int U = (int)ub[i];
+    int32_t* K = hk[w];
+    double* Vv = hv[w];
+    int H = 1;
+    while (H < 2 * U) H <<= 1;
+    for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
     __syncwarp();
-  }
-  // compaction of the occupied slots to the front (order irrelevant: sorted next)
-  int base = 0;
-  for (int t0 = 0; t0 < H; t0 += 32) {
-    int t = t0 + lane;
-    int32_t key = t < H ? K[t] : -1;
-    double v = t < H ? Vv[t] : 0.0;
-    unsigned msk = __ballot_sync(0xffffffffu, key >= 0);
-    __syncwarp();
-    if (key >= 0) {
-      int pos = base + __popc(msk & ((1u << lane) - 1));
-      K[pos] = key;
-      Vv[pos] = v;
-    }
-    base += __popc(msk);
-    __syncwarp();
-  }
-  int u = base;
-  int n2 = 1;
-  while (n2 < u) n2 <<= 1;
-  for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
-  __syncwarp();
-  for (int k2 = 2; k2 <= n2; k2 <<= 1)
-    for (int j = k2 >> 1; j > 0; j >>= 1) {
-      for (int t = lane; t < n2; t += 32) {
-        int x = t ^ j;
-        if (x > t) {
-          bool up = (t & k2) == 0;
-          int32_t ka = K[t], kb = K[x];
-          if ((ka > kb) == up) {
-            K[t] = kb; K[x] = ka;
-            double va = Vv[t]; Vv[t] = Vv[x]; Vv[x] = va;
-          }
+    for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
+      int32_t k = aci[p];
+      double a = av[p];
+      for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+        int32_t key = bci[q];
+        double prod = __dmul_rn(a, bv[q]);
+        uint32_t h = hash32(key) & (H - 1);
+        while (true) {
+          int32_t prev = atomicCAS(&K[h], -1, key);
+          if (prev == -1 || prev == key) break;
+          h = (h + 1) & (H - 1);
         }
+        Vv[h] = __dadd_rn(Vv[h], prod);
       }
       __syncwarp();
     }
-  int64_t o = soff[i];
-  for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
-  if (lane == 0) cnt[i] = u;
+    // compaction of the occupied slots to the front (order irrelevant: sorted next)
+    int base = 0;
+    for (int t0 = 0; t0 < H; t0 += 32) {
+      int t = t0 + lane;
+      int32_t key = t < H ? K[t] : -1;
+      double v = t < H ? Vv[t] : 0.0;
+      unsigned msk = __ballot_sync(0xffffffffu, key >= 0);
+      __syncwarp();
+      if (key >= 0) {
+        int pos = base + __popc(msk & ((1u << lane) - 1));
+        K[pos] = key;
+        Vv[pos] = v;
+      }
+      base += __popc(msk);
+      __syncwarp();
+    }
+    int u = base;
+    int n2 = 1;
+    while (n2 < u) n2 <<= 1;
+    for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
+    __syncwarp();
+    for (int k2 = 2; k2 <= n2; k2 <<= 1)
+      for (int j = k2 >> 1; j > 0; j >>= 1) {
+        for (int t = lane; t < n2; t += 32) {
+          int x = t ^ j;
+          if (x > t) {
+            bool up = (t & k2) == 0;
+            int32_t ka = K[t], kb = K[x];
+            if ((ka > kb) == up) {
+              K[t] = kb; K[x] = ka;
+              double va = Vv[t]; Vv[t] = Vv[x]; Vv[x] = va;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    int64_t o = soff[i];
+    for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
+    if (lane == 0) cnt[i] = u;
+    __syncwarp();
+  }
 }
 
 // Fused product for rows with at most FUSE_CAP products and FZ_CAPA entries in A (the common case):
@@ -692,7 +696,7 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
     int64_t m, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
     const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
     const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
-    double* __restrict__ sval, int64_t* __restrict__ cnt, int* __restrict__ done) {
+    double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ rest, int* __restrict__ nrest) {
   __shared__ int32_t hk[FZ_WARPS][FZ_SLOTS];
   __shared__ double hv[FZ_WARPS][FZ_SLOTS];
   __shared__ int32_t sst[FZ_WARPS][FZ_CAPA + 1];
@@ -705,7 +709,10 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
   int U = (int)ub[i];
   int64_t a0 = arp[i];
   int na = (int)(arp[i + 1] - a0);
-  if (U > FZ_SLOTS / 2 || na > FZ_CAPA) return;  // the row goes to the larger kernels
+  if (U > FZ_SLOTS / 2 || na > FZ_CAPA) {  // the row goes to the larger kernels
+    if (U <= FUSE_CAP && lane == 0) rest[atomicAdd(nrest, 1)] = (int32_t)i;
+    return;
+  }
   int32_t* K = hk[w];
   double* Vv = hv[w];
   int H = 32;
@@ -813,7 +820,7 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
     }
   int64_t o = soff[i];
   for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
-  if (lane == 0) { cnt[i] = u; done[i] = 1; }
+  if (lane == 0) cnt[i] = u;
 }
 
 // copy the staged columns and values of the fused rows to their final place in C
@@ -869,13 +876,16 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
   DBuf<double> sval(c, nstage + 1);
   {
     ProfScope ps2(c, "fused_small");
-    DBuf<int> done(c, m);
-    CU(cudaMemsetAsync(done.p, 0, sizeof(int) * m, c.s));
+    DBuf<int32_t> rest(c, m);
+    DBuf<int> nrest(c, 1);
+    CU(cudaMemsetAsync(nrest.p, 0, sizeof(int), c.s));
     k_spgemm_fused_chunk<<<grid_for(m, FZ_WARPS), 32 * FZ_WARPS, 0, c.s>>>(m, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p,
-                                                                           soff.p, scol.p, sval.p, cnt.p, done.p);
+                                                                           soff.p, scol.p, sval.p, cnt.p, rest.p,
+                                                                           nrest.p);
     CU_LAUNCH();
-    k_spgemm_fused_hash<<<grid_for(m, FH_WARPS), 32 * FH_WARPS, 0, c.s>>>(m, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p,
-                                                                         soff.p, scol.p, sval.p, cnt.p, done.p);
+    // 4 blocks of 48 KB shared memory per SM on 152 SMs, 4 rounds
+    k_spgemm_fused_hash<<<grid_for(m, FH_WARPS, 152 * 16), 32 * FH_WARPS, 0, c.s>>>(
+        rest.p, nrest.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p);
     CU_LAUNCH();
   }
   sym_pass(c, 0, A, B, ub.p, mid.p, hc[0], big.p, hc[1], cnt.p, C, 1);
