@@ -77,8 +77,13 @@ typedef struct {
   int32_t amg_pmax;                      /* max interpolation entries per row, 0 = no truncation */
   double amg_omega;                      /* Jacobi weight for amg_smoother = 0 */
   uint64_t amg_seed;                     /* PMIS weight seed (default 3) */
-  int32_t use_graph;                     /* replay mgr_apply as a CUDA graph (default 1) */
-  int32_t reserved[7];
+  int32_t lean;                          /* 1: free the setup-only FP64 operators as soon as the setup
+                                            no longer needs them (the apply and the solve keep what
+                                            they read); their introspection then returns
+                                            MGR_ERR_STATE.  Default 0 */
+  int32_t spgemm_stage;                  /* SpGEMM products staged per batch of short rows (0: the
+                                            default 2^27; values <= 1024 also mean the default) */
+  int32_t reserved[6];                   /* must be zero */
 } mgr_options_t;
 
 typedef struct {
@@ -152,8 +157,8 @@ mgr_status_t mgr_memory_bytes(mgr_handle_t h, int64_t* bytes);
  * work buffers included (host out). */
 mgr_status_t mgr_memory_peak_bytes(mgr_handle_t h, int64_t* bytes);
 /* Statistics (host outs, each may be NULL): wall time of the last mgr_setup in milliseconds, kernel
- * launches issued by the last mgr_apply, kernel nodes of the captured apply graph (0 when not
- * captured), and the process-wide count of kernel launches issued by this library since load. */
+ * launches issued by the last mgr_apply, a reserved count that is always 0, and the process-wide
+ * count of kernel launches issued by this library since load. */
 mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_launches, int64_t* graph_nodes,
                            int64_t* total_launches);
 
@@ -161,10 +166,11 @@ mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_laun
  * launch of the named kernels and clears earlier totals, enable = 0 stops.  mgr_kernel_time returns
  * the launches and the summed device milliseconds recorded for `name` (synchronises).  Names:
  *   solve:  "bsr3_spmv_f64" (Krylov SpMV), "mdot", "mupdate" (Arnoldi), "global_relax",
- *           "bsr_resid_split" (level-0 residual), "frelax" (F-relaxation sweeps), "restrict"
- *           (coarse residual r_C - A_cf e_F), "interp" (e = P e_c), "amg0_rows" (smoothing and
- *           residual on the AMG level-0 operator), "amgc_rows" (the same on coarser AMG levels),
- *           "amg_restrict", "amg_prolong" (AMG transfers);
+ *           "bsr_resid_split" (level-0 residual); per MGR level l = 0..3: "frelax<l>" (F-relaxation
+ *           sweeps), "restrict<l>" (coarse residual r_C - A_cf e_F), "interp<l>" (e = P e_c); per AMG
+ *           level: "amg0_rows", "amg1_rows", "amg2_rows", "amgc_rows" (smoothing and residual passes,
+ *           levels 3 and coarser together), "amg0_restrict", "amg1_restrict", "amgc_restrict",
+ *           "amg0_prolong", "amg1_prolong", "amgc_prolong" (transfers, levels 2 and coarser together);
  *   setup:  "setup_total", "setup_mgr_level", "setup_mgr_rap", "setup_amg", "setup_amg_strength",
  *           "setup_amg_pmis", "setup_amg_extpi", "extpi_pattern", "extpi_weights",
  *           "setup_amg_transpose", "setup_amg_rap", "setup_dense_inverse", "setup_cast_alloc",
@@ -172,6 +178,10 @@ mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_laun
  *           "sym_fill_warp", "sym_block", "sym_bitmap".
  * Unknown names report 0 launches. */
 mgr_status_t mgr_profile(mgr_handle_t h, int enable);
+/* Restrict the recording to a comma-separated list of the names above (NULL or "" records every
+ * name); applies to the following mgr_profile(h, 1) session.  Recording fewer names keeps the event
+ * overhead out of the timed work. */
+mgr_status_t mgr_profile_select(mgr_handle_t h, const char* names);
 mgr_status_t mgr_kernel_time(mgr_handle_t h, const char* name, int64_t* launches, double* total_ms);
 /* Algorithmic bytes of the launches recorded for `name` since profiling was enabled (host out): for
  * the solve kernels, every input element read once and every output element written once (values,

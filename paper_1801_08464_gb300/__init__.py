@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
                 ("amg_max_levels", ctypes.c_int32), ("amg_max_coarse", ctypes.c_int32),
                 ("amg_smoother", ctypes.c_int32), ("amg_pre", ctypes.c_int32), ("amg_post", ctypes.c_int32),
                 ("amg_pmax", ctypes.c_int32), ("amg_omega", ctypes.c_double), ("amg_seed", ctypes.c_uint64),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("lean", ctypes.c_int32), ("spgemm_stage", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class Bsr3(ctypes.Structure):
@@ -62,7 +63,8 @@ class SolveInfo(ctypes.Structure):
 EXPORTS = ["mgr_status_string", "mgr_options_default", "mgr_create", "mgr_setup", "mgr_apply", "fgmres_solve",
            "mgr_destroy", "mgr_get_levels", "mgr_matrix_shape", "mgr_copy_matrix", "mgr_vector_len",
            "mgr_copy_vector", "mgr_memory_bytes", "mgr_memory_peak_bytes", "mgr_get_stats", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
-           "mgr_bsr3_outer_grad", "mgr_profile", "mgr_kernel_time", "mgr_kernel_bytes"]
+           "mgr_bsr3_outer_grad", "mgr_profile", "mgr_profile_select", "mgr_kernel_time",
+           "mgr_kernel_bytes"]
 
 
 def lib():
@@ -97,6 +99,7 @@ def lib():
         L.mgr_profile.argtypes = [vp, i32]
         L.mgr_kernel_time.argtypes = [vp, ctypes.c_char_p, P(i64), P(ctypes.c_double)]
         L.mgr_kernel_bytes.argtypes = [vp, ctypes.c_char_p, P(ctypes.c_double)]
+        L.mgr_profile_select.argtypes = [vp, ctypes.c_char_p]
         for name in EXPORTS:
             getattr(L, name).restype = ctypes.c_int if name not in ("mgr_status_string", "mgr_options_default") \
                 else getattr(L, name).restype
@@ -265,8 +268,12 @@ class MGR:
         _check(lib().mgr_copy_vector(self._h, kind, level, _ptr(out)), "mgr_copy_vector")
         return out[: n.value]
 
-    def profile(self, enable: bool = True):
-        """Start (clearing totals) or stop CUDA-event timing of the library's named kernels."""
+    def profile(self, enable: bool = True, only=None):
+        """Start (clearing totals) or stop CUDA-event timing of the library's named kernels; `only`
+        restricts the recording to the given names."""
+        if enable:
+            sel = ",".join(only) if only else None
+            _check(lib().mgr_profile_select(self._h, sel.encode() if sel else None), "mgr_profile_select")
         _check(lib().mgr_profile(self._h, 1 if enable else 0), "mgr_profile")
 
     def kernel_time(self, name: str):

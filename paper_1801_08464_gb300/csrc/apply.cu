@@ -136,7 +136,8 @@ struct Quad<double> {
 template <class T, class Epi>
 __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __restrict__ soff,
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
-                                                   const T* __restrict__ x, Epi epi) {
+                                                   const int32_t* __restrict__ perm, const T* __restrict__ x,
+                                                   Epi epi) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= nr) return;
   int64_t s = r / RS_C;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
     int4 c = __ldg(reinterpret_cast<const int4*>(cp + q * (RS_Q * RS_C)));
     sum += Quad<T>::dot(vp + q * (RS_Q * RS_C), c, x);
   }
-  epi(r, sum);
+  epi(perm ? (int64_t)perm[r] : r, sum);
 }
 
 template <class T, class Epi>
@@ -161,7 +162,8 @@ static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, co
                             (double)op.nr * epi.row_bytes());
   const int B = 256;
   if (op.sell) {
-    k_rows_sell<T, Epi><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, x, epi);
+    k_rows_sell<T, Epi><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
+                                                           epi);
     CU_LAUNCH();
     return;
   }
@@ -243,12 +245,13 @@ void launch_frelax_first(Ctx& c, int64_t nF, const int32_t* F, const T* src, con
 }
 template <class T>
 void launch_frelax_sweep(Ctx& c, const RowsOp<T>& Aff, const int32_t* F, const T* src, const T* minv, const T* eFi,
-                         T* eFo) {
-  run_rows(c, Aff, eFi, EpiFrelax<T>{F, src, minv, eFi, eFo}, "frelax");
+                         T* eFo, const char* name) {
+  run_rows(c, Aff, eFi, EpiFrelax<T>{F, src, minv, eFi, eFo}, name);
 }
 template <class T>
-void launch_restrict(Ctx& c, const RowsOp<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext) {
-  run_rows(c, Acf, eF, EpiRestrict<T>{C, r, rnext}, "restrict");
+void launch_restrict(Ctx& c, const RowsOp<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext,
+                     const char* name) {
+  run_rows(c, Acf, eF, EpiRestrict<T>{C, r, rnext}, name);
 }
 
 // interpolation: C dofs take ec[c] (a scatter over the C list), F dofs eF[f] + W_p[f,:] ec (a
@@ -277,13 +280,13 @@ struct EpiInterpF {
 
 template <class T, class TO>
 void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32_t* C, const RowsOp<T>& Wp,
-                   const T* eF, const T* ec, const T* base, TO* out) {
+                   const T* eF, const T* ec, const T* base, TO* out, const char* name) {
   if (nC > 0) {
-    ProfScope ps(c, "interp", (double)nC * (4.0 + sizeof(T) + (base ? sizeof(T) : 0) + sizeof(TO)));
+    ProfScope ps(c, name, (double)nC * (4.0 + sizeof(T) + (base ? sizeof(T) : 0) + sizeof(TO)));
     k_interp_c<T, TO><<<grid_for(nC, 256), 256, 0, c.s>>>(nC, C, ec, base, out);
     CU_LAUNCH();
   }
-  if (nF > 0) run_rows(c, Wp, ec, EpiInterpF<T, TO>{F, eF, base, out}, "interp");
+  if (nF > 0) run_rows(c, Wp, ec, EpiInterpF<T, TO>{F, eF, base, out}, name);
 }
 
 template <class T>
@@ -317,12 +320,12 @@ void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* 
   run_rows(c, A, xi, EpiJacobi<T>{d, b, xi, xo}, name);
 }
 template <class T>
-void launch_spmv(Ctx& c, const RowsOp<T>& A, const T* x, T* y) {
-  run_rows(c, A, x, EpiStore<T>{y}, "amg_restrict");
+void launch_spmv(Ctx& c, const RowsOp<T>& A, const T* x, T* y, const char* name) {
+  run_rows(c, A, x, EpiStore<T>{y}, name);
 }
 template <class T>
-void launch_prolong_add(Ctx& c, const RowsOp<T>& P, const T* xc, T* x) {
-  run_rows(c, P, xc, EpiAdd<T>{x}, "amg_prolong");
+void launch_prolong_add(Ctx& c, const RowsOp<T>& P, const T* xc, T* x, const char* name) {
+  run_rows(c, P, xc, EpiAdd<T>{x}, name);
 }
 
 // x = inv b with the FP64 dense inverse of the coarsest operator: one warp per row
@@ -359,21 +362,23 @@ void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b) {
   template void launch_bsr_resid_split<T>(Ctx&, const SellPattern&, const T*, const double*, const T*,            \
                                           const int32_t*, T*, T*);                                                 \
   template void launch_frelax_first<T>(Ctx&, int64_t, const int32_t*, const T*, const T*, T*);                     \
-  template void launch_frelax_sweep<T>(Ctx&, const RowsOp<T>&, const int32_t*, const T*, const T*, const T*, T*); \
-  template void launch_restrict<T>(Ctx&, const RowsOp<T>&, const int32_t*, const T*, const T*, T*);               \
+  template void launch_frelax_sweep<T>(Ctx&, const RowsOp<T>&, const int32_t*, const T*, const T*, const T*, T*,   \
+                                       const char*);                                                              \
+  template void launch_restrict<T>(Ctx&, const RowsOp<T>&, const int32_t*, const T*, const T*, T*, const char*);  \
   template void launch_interp<T, T>(Ctx&, int64_t, const int32_t*, int64_t, const int32_t*, const RowsOp<T>&,     \
-                                    const T*, const T*, const T*, T*);                                             \
+                                    const T*, const T*, const T*, T*, const char*);                                \
   template void launch_to_f64<T>(Ctx&, int64_t, const T*, double*);                                                \
   template void launch_scale<T>(Ctx&, int64_t, const T*, const T*, T*);                                            \
   template void launch_resid<T>(Ctx&, const RowsOp<T>&, const T*, const T*, T*, const char*);                     \
   template void launch_jacobi<T>(Ctx&, const RowsOp<T>&, const T*, const T*, const T*, T*, const char*);          \
-  template void launch_spmv<T>(Ctx&, const RowsOp<T>&, const T*, T*);                                             \
-  template void launch_prolong_add<T>(Ctx&, const RowsOp<T>&, const T*, T*);                                      \
+  template void launch_spmv<T>(Ctx&, const RowsOp<T>&, const T*, T*, const char*);                                \
+  template void launch_prolong_add<T>(Ctx&, const RowsOp<T>&, const T*, T*, const char*);                         \
   template void launch_dense_gemv<T>(Ctx&, int64_t, const double*, const T*, T*);
 INST(float)
 INST(double)
 #undef INST
 template void launch_interp<float, double>(Ctx&, int64_t, const int32_t*, int64_t, const int32_t*,
-                                           const RowsOp<float>&, const float*, const float*, const float*, double*);
+                                           const RowsOp<float>&, const float*, const float*, const float*, double*,
+                                           const char*);
 
 }  // namespace mgr

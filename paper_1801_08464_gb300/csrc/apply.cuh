@@ -37,14 +37,15 @@ void launch_frelax_first(Ctx& c, int64_t nF, const int32_t* F, const T* src, con
 // later sweeps: eFo = eFi + minv * (src - A_ff eFi)
 template <class T>
 void launch_frelax_sweep(Ctx& c, const RowsOp<T>& Aff, const int32_t* F, const T* src, const T* minv, const T* eFi,
-                         T* eFo);
+                         T* eFo, const char* name = "frelax");
 // rnext[c] = base_c - A_cf eF with base_c = r[C[c]] (C != nullptr) or rnext[c] (in place)
 template <class T>
-void launch_restrict(Ctx& c, const RowsOp<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext);
+void launch_restrict(Ctx& c, const RowsOp<T>& Acf, const int32_t* C, const T* r, const T* eF, T* rnext,
+                     const char* name = "restrict");
 // out[C[c]] = base + ec[c]; out[F[f]] = base + eF[f] + W_p[f,:] ec; base may be nullptr
 template <class T, class TO>
 void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32_t* C, const RowsOp<T>& Wp,
-                   const T* eF, const T* ec, const T* base, TO* out);
+                   const T* eF, const T* ec, const T* base, TO* out, const char* name = "interp");
 template <class T>
 void launch_to_f64(Ctx& c, int64_t n, const T* a, double* b);
 
@@ -58,9 +59,9 @@ template <class T>
 void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* xi, T* xo,
                    const char* name = "csr_rows");                                          // xo = xi + d (b - A xi)
 template <class T>
-void launch_spmv(Ctx& c, const RowsOp<T>& A, const T* x, T* y);                             // y = A x
+void launch_spmv(Ctx& c, const RowsOp<T>& A, const T* x, T* y, const char* name = "amg_restrict");  // y = A x
 template <class T>
-void launch_prolong_add(Ctx& c, const RowsOp<T>& P, const T* xc, T* x);                     // x += P xc
+void launch_prolong_add(Ctx& c, const RowsOp<T>& P, const T* xc, T* x, const char* name = "amg_prolong");  // x += P xc
 template <class T>
 void launch_dense_gemv(Ctx& c, int64_t n, const double* inv, const T* b, T* x);              // x = inv b (FP64)
 

@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <map>
+#include <set>
 #include <stdexcept>
 #include <vector>
 #include <string>
@@ -54,7 +55,9 @@ struct Prof {
     double bytes = 0.0;  // algorithmic bytes declared by the timed launches
   };
   std::map<std::string, Rec> recs;
+  std::set<std::string> only;  // when not empty, only these names are recorded
   std::vector<cudaEvent_t> pool;
+  bool wants(const char* n) const { return only.empty() || only.count(n) != 0; }
   cudaEvent_t get() {
     if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
     cudaEvent_t e;
@@ -89,6 +92,7 @@ struct Ctx {
   cudaStream_t s = nullptr;
   int* d_err = nullptr;        // device int, error bits
   int* h_pinned = nullptr;     // pinned host scratch (small readbacks)
+  int64_t spgemm_stage = 0;    // staged products per SpGEMM batch (0: the library default)
   int64_t bytes = 0;           // bytes currently allocated through this context
   int64_t peak = 0;
   int num_sms = 152;
@@ -100,8 +104,10 @@ struct ProfScope {
   cudaEvent_t e1 = nullptr;
   // bytes: the algorithmic bytes of the work inside the scope (each input element read once, each
   // output written once), summed per name for achieved-bandwidth figures
+  bool on = false;
   ProfScope(Ctx& ctx, const char* n, double bytes = 0.0) : c(ctx), name(n) {
-    if (!c.prof) return;
+    if (!c.prof || !c.prof->wants(n)) return;
+    on = true;
     cudaEvent_t e0 = c.prof->get();
     e1 = c.prof->get();
     cudaEventRecord(e0, c.s);
@@ -110,7 +116,7 @@ struct ProfScope {
     r.bytes += bytes;
   }
   ~ProfScope() {
-    if (!c.prof) return;
+    if (!on) return;
     cudaEventRecord(e1, c.s);
     c.prof->recs[name].b.push_back(e1);
   }

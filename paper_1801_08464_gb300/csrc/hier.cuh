@@ -1,5 +1,6 @@
 // hier.cuh -- device data of the MGR hierarchy and of the AMG coarse solver.
 #pragma once
+#include <functional>
 #include <vector>
 
 #include "common.cuh"
@@ -21,6 +22,7 @@ struct MgrLevel {
   RowsOp<float> Aff32, Acf32, Wp32;
   RowsOp<double> Aff64, Acf64, Wp64;
   DBuf<float> minv32;
+  bool cast = false;              // apply copies built
 };
 
 struct AmgLevel {
@@ -31,6 +33,7 @@ struct AmgLevel {
   RowsOp<float> A32, P32, R32;    // apply copies (working precision)
   RowsOp<double> A64, P64, R64;
   DBuf<float> dinv32;
+  bool cast = false;
 };
 
 struct AmgOpts {
@@ -40,9 +43,11 @@ struct AmgOpts {
   uint64_t seed = 3;
 };
 
-// Builds levels[0..] from A0 (copied) and the FP64 dense inverse of the coarsest operator.
-void amg_build(Ctx& c, const DCSR<double>& A0, const AmgOpts& o, std::vector<AmgLevel>& levels,
-               DBuf<double>& coarse_inv, int64_t& nco);
+// Builds levels[0..] from A0 (copied, or moved when take is set; its shape stays in A0) and the FP64
+// dense inverse of the coarsest operator.  done(level k), when given, is called once level k + 1 has
+// been built from level k (level k's matrices are not read again by the build).
+void amg_build(Ctx& c, DCSR<double>& A0, bool take, const AmgOpts& o, std::vector<AmgLevel>& levels,
+               DBuf<double>& coarse_inv, int64_t& nco, const std::function<void(AmgLevel&)>& done);
 
 // One reduction step at level l: fills L (splitting, W_p, W_r, P, R, split operators, scaling) and
 // the coarse operator Anext = R (A P) with the coarse markers.

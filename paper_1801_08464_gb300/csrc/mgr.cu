@@ -93,6 +93,15 @@ template <class T>
 inline T* P(DBuf<char>& b) { return reinterpret_cast<T*>(b.p); }
 
 // ---- apply -----------------------------------------------------------------------------------
+// timing names per level (levels beyond the table share the last name)
+static const char* lvl_name(const char* const* t, int n, int l) { return t[l < n ? l : n - 1]; }
+static const char* const kFrelax[] = {"frelax0", "frelax1", "frelax2", "frelax3"};
+static const char* const kRestrict[] = {"restrict0", "restrict1", "restrict2", "restrict3"};
+static const char* const kInterp[] = {"interp0", "interp1", "interp2", "interp3"};
+static const char* const kAmgRows[] = {"amg0_rows", "amg1_rows", "amg2_rows", "amgc_rows"};
+static const char* const kAmgRestrict[] = {"amg0_restrict", "amg1_restrict", "amgc_restrict"};
+static const char* const kAmgProlong[] = {"amg0_prolong", "amg1_prolong", "amgc_prolong"};
+
 template <class T>
 const T* frelax(mgr_handle_s& h, int l, const T* src, const int32_t* F) {
   MgrLevel& L = h.lev[l];
@@ -103,7 +112,7 @@ const T* frelax(mgr_handle_s& h, int l, const T* src, const int32_t* F) {
   launch_frelax_first<T>(h.c, L.nF, F, src, minv, a);
   const RowsOp<T>& Aff = tv<T>(L.Aff64, L.Aff32);
   for (int s = 1; s < L.sweeps; ++s) {
-    launch_frelax_sweep<T>(h.c, Aff, F, src, minv, a, b);
+    launch_frelax_sweep<T>(h.c, Aff, F, src, minv, a, b, lvl_name(kFrelax, 4, l));
     std::swap(a, b);
   }
   return a;
@@ -124,8 +133,7 @@ const T* vcycle(mgr_handle_s& h, int k, const T* b) {
   T* xa = P<T>(h.a_xa[k]);
   T* xb = P<T>(h.a_xb[k]);
   T* res = P<T>(h.a_res[k]);
-  // the level-0 operator (the pressure matrix) is timed apart from the coarser levels
-  const char* nm = (k == 0) ? "amg0_rows" : "amgc_rows";
+  const char* nm = lvl_name(kAmgRows, 4, k);
   launch_scale<T>(c, A.n, d, b, xa);
   for (int s = 1; s < h.o.amg_pre; ++s) {
     launch_jacobi<T>(c, Av, d, b, xa, xb, nm);
@@ -133,9 +141,9 @@ const T* vcycle(mgr_handle_s& h, int k, const T* b) {
   }
   launch_resid<T>(c, Av, xa, b, res, nm);
   T* bc = P<T>(h.a_b[k + 1]);
-  launch_spmv<T>(c, tv<T>(A.R64, A.R32), res, bc);
+  launch_spmv<T>(c, tv<T>(A.R64, A.R32), res, bc, lvl_name(kAmgRestrict, 3, k));
   const T* xc = vcycle<T>(h, k + 1, bc);
-  launch_prolong_add<T>(c, tv<T>(A.P64, A.P32), xc, xa);
+  launch_prolong_add<T>(c, tv<T>(A.P64, A.P32), xc, xa, lvl_name(kAmgProlong, 3, k));
   for (int s = 0; s < h.o.amg_post; ++s) {
     launch_jacobi<T>(c, Av, d, b, xa, xb, nm);
     std::swap(xa, xb);
@@ -167,21 +175,23 @@ void apply_t(mgr_handle_s& h, const double* r, double* z) {
   launch_bsr_resid_split<T>(c, h.sell, vals, r, e0, L0.map.p, r1, resF0);
   std::vector<const T*> eF(L);
   eF[0] = frelax<T>(h, 0, resF0, nullptr);
-  launch_restrict<T>(c, tv<T>(L0.Acf64, L0.Acf32), nullptr, nullptr, eF[0], r1);
+  launch_restrict<T>(c, tv<T>(L0.Acf64, L0.Acf32), nullptr, nullptr, eF[0], r1, kRestrict[0]);
   for (int l = 1; l < L; ++l) {
     MgrLevel& Ll = h.lev[l];
     const T* rl = P<T>(h.w_r[l]);
     eF[l] = frelax<T>(h, l, rl, Ll.F.p);
-    launch_restrict<T>(c, tv<T>(Ll.Acf64, Ll.Acf32), Ll.C.p, rl, eF[l], P<T>(h.w_r[l + 1]));
+    launch_restrict<T>(c, tv<T>(Ll.Acf64, Ll.Acf32), Ll.C.p, rl, eF[l], P<T>(h.w_r[l + 1]),
+                       lvl_name(kRestrict, 4, l));
   }
   const T* ec = vcycle<T>(h, 0, P<T>(h.w_r[L]));
   for (int l = L - 1; l >= 1; --l) {
     MgrLevel& Ll = h.lev[l];
     T* el = P<T>(h.w_e[l]);
-    launch_interp<T, T>(c, Ll.nF, Ll.F.p, Ll.nC, Ll.C.p, tv<T>(Ll.Wp64, Ll.Wp32), eF[l], ec, nullptr, el);
+    launch_interp<T, T>(c, Ll.nF, Ll.F.p, Ll.nC, Ll.C.p, tv<T>(Ll.Wp64, Ll.Wp32), eF[l], ec, nullptr, el,
+                        lvl_name(kInterp, 4, l));
     ec = el;
   }
-  launch_interp<T, double>(c, L0.nF, L0.F.p, L0.nC, L0.C.p, tv<T>(L0.Wp64, L0.Wp32), eF[0], ec, e0, z);
+  launch_interp<T, double>(c, L0.nF, L0.F.p, L0.nC, L0.C.p, tv<T>(L0.Wp64, L0.Wp32), eF[0], ec, e0, z, kInterp[0]);
   h.apply_launches = (int64_t)(g_launch_count - l0);
 }
 
@@ -226,6 +236,48 @@ void alloc_work(mgr_handle_s& h) {
   }
 }
 
+// Frees the buffers of a setup-only matrix; its shape stays for introspection.
+void release_csr(DCSR<double>& M) {
+  M.rp.release();
+  M.ci.release();
+  M.v.release();
+}
+
+// The apply operators of MGR level l in the working precision (SELL or CSR copies of A_ff, A_cf, W_p).
+void cast_mgr_level(mgr_handle_s& h, MgrLevel& L) {
+  if (L.cast) return;
+  Ctx& c = h.c;
+  if (h.o.precision == MGR_PREC_MIXED) {
+    rowsop_build<float>(c, L.Aff, L.Aff32);
+    rowsop_build<float>(c, L.Acf, L.Acf32);
+    rowsop_build<float>(c, L.Wp, L.Wp32);
+    L.minv32.alloc(c, L.nF + 1);
+    launch_cast_f32(c, L.nF, L.minv.p, L.minv32.p);
+  } else {
+    rowsop_build<double>(c, L.Aff, L.Aff64);
+    rowsop_build<double>(c, L.Acf, L.Acf64);
+    rowsop_build<double>(c, L.Wp, L.Wp64);
+  }
+  L.cast = true;
+}
+
+void cast_amg_level(mgr_handle_s& h, AmgLevel& G) {
+  if (G.cast) return;
+  Ctx& c = h.c;
+  if (h.o.precision == MGR_PREC_MIXED) {
+    rowsop_build<float>(c, G.A, G.A32);
+    rowsop_build<float>(c, G.P, G.P32);
+    rowsop_build<float>(c, G.R, G.R32);
+    G.dinv32.alloc(c, G.n);
+    launch_cast_f32(c, G.n, G.dinv.p, G.dinv32.p);
+  } else {
+    rowsop_build<double>(c, G.A, G.A64);
+    rowsop_build<double>(c, G.P, G.P64);
+    rowsop_build<double>(c, G.R, G.R64);
+  }
+  G.cast = true;
+}
+
 void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
   Ctx& c = h.c;
   int64_t nv = 9 * SELL_C * h.sell.slots;
@@ -239,34 +291,8 @@ void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
     h.val64.alloc(c, nv);
     sell_fill_values<double, double>(c, h.sell, A.values, h.val64.p);
   }
-  for (int l = 0; l < h.L; ++l) {
-    MgrLevel& L = h.lev[l];
-    if (mixed) {
-      rowsop_build<float>(c, L.Aff, L.Aff32);
-      rowsop_build<float>(c, L.Acf, L.Acf32);
-      rowsop_build<float>(c, L.Wp, L.Wp32);
-      L.minv32.alloc(c, L.nF + 1);
-      launch_cast_f32(c, L.nF, L.minv.p, L.minv32.p);
-    } else {
-      rowsop_build<double>(c, L.Aff, L.Aff64);
-      rowsop_build<double>(c, L.Acf, L.Acf64);
-      rowsop_build<double>(c, L.Wp, L.Wp64);
-    }
-  }
-  for (size_t k = 0; k + 1 < h.amg.size(); ++k) {
-    AmgLevel& G = h.amg[k];
-    if (mixed) {
-      rowsop_build<float>(c, G.A, G.A32);
-      rowsop_build<float>(c, G.P, G.P32);
-      rowsop_build<float>(c, G.R, G.R32);
-      G.dinv32.alloc(c, G.n);
-      launch_cast_f32(c, G.n, G.dinv.p, G.dinv32.p);
-    } else {
-      rowsop_build<double>(c, G.A, G.A64);
-      rowsop_build<double>(c, G.P, G.P64);
-      rowsop_build<double>(c, G.R, G.R64);
-    }
-  }
+  for (int l = 0; l < h.L; ++l) cast_mgr_level(h, h.lev[l]);
+  for (size_t k = 0; k + 1 < h.amg.size(); ++k) cast_amg_level(h, h.amg[k]);
 }
 
 void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
@@ -278,6 +304,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   h.cinv.release();
   h.val32.release(); h.val64.release(); h.binv32.release();
   ProfScope ps_all(c, "setup_total");
+  c.spgemm_stage = h.o.spgemm_stage;
   bsr3_validate(c, A, marker);
   h.nb = A.nb;
   h.nnzb = A.nnzb;
@@ -317,9 +344,20 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     mgr_reduce_level(c, h.lev[l], l, lo, h.lev[l + 1].A, mk_next);
     h.lev[l + 1].n = h.lev[l].nC;
     h.lev[l + 1].mk = std::move(mk_next);
+    if (h.o.lean) {  // the level's FP64 operators are not read again
+      MgrLevel& Lv = h.lev[l];
+      cast_mgr_level(h, Lv);
+      release_csr(Lv.A);
+      release_csr(Lv.Wp);
+      release_csr(Lv.Wr);
+      release_csr(Lv.P);
+      release_csr(Lv.R);
+      release_csr(Lv.Aff);
+      release_csr(Lv.Acf);
+    }
   }
   // coarse solve on the last level
-  const DCSR<double>& Ac = h.lev[L].A;
+  DCSR<double>& Ac = h.lev[L].A;
   if (h.o.coarse_solver == 1) {
     if (Ac.nr > 4096) throw Error(MGR_ERR_UNSUPPORTED, "dense coarse solve limited to 4096 rows");
     h.coarse_dense = true;
@@ -339,7 +377,19 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     ao.omega = h.o.amg_omega;
     ao.seed = h.o.amg_seed;
     ProfScope ps(c, "setup_amg");
-    amg_build(c, Ac, ao, h.amg, h.cinv, h.nco);
+    if (h.o.lean) {
+      // the AMG takes the pressure operator over, and each level's FP64 matrices are freed once the
+      // next level is built
+      amg_build(c, h.lev[L].A, true, ao, h.amg, h.cinv, h.nco, [&](AmgLevel& G) {
+        cast_amg_level(h, G);
+        release_csr(G.A);
+        release_csr(G.P);
+        release_csr(G.R);
+        release_csr(G.S);
+      });
+    } else {
+      amg_build(c, h.lev[L].A, false, ao, h.amg, h.cinv, h.nco, nullptr);
+    }
   }
   {
     ProfScope ps(c, "setup_cast_alloc");
@@ -588,7 +638,6 @@ void mgr_options_default(mgr_options_t* o) {
   o->amg_pmax = 0;
   o->amg_omega = 1.0;
   o->amg_seed = 3;
-  o->use_graph = 1;
 }
 
 static mgr_status_t check_options(const mgr_options_t& o) {
@@ -694,7 +743,7 @@ mgr_status_t mgr_matrix_shape(mgr_handle_t h, int kind, int level, int64_t* nr, 
   if (!h || !nr || !nc || !nnz) return MGR_ERR_INVALID_ARG;
   if (!h->ready) return MGR_ERR_STATE;
   const DCSR<double>* m = pick_matrix(*h, kind, level);
-  if (!m || m->rp.p == nullptr) return MGR_ERR_INVALID_ARG;
+  if (!m || (m->rp.p == nullptr && !(h->o.lean && m->nr > 0))) return MGR_ERR_INVALID_ARG;
   *nr = m->nr; *nc = m->nc; *nnz = m->nnz;
   return MGR_OK;
 }
@@ -703,7 +752,8 @@ mgr_status_t mgr_copy_matrix(mgr_handle_t h, int kind, int level, int64_t* rowpt
   if (!h || !rowptr || !col) return MGR_ERR_INVALID_ARG;
   if (!h->ready) return MGR_ERR_STATE;
   const DCSR<double>* m = pick_matrix(*h, kind, level);
-  if (!m || m->rp.p == nullptr) return MGR_ERR_INVALID_ARG;
+  if (!m) return MGR_ERR_INVALID_ARG;
+  if (m->rp.p == nullptr) return (h->o.lean && m->nr > 0) ? MGR_ERR_STATE : MGR_ERR_INVALID_ARG;
   return guarded(h, [&] {
     Ctx& c = h->c;
     CU(cudaMemcpyAsync(rowptr, m->rp.p, sizeof(int64_t) * (m->nr + 1), cudaMemcpyDeviceToDevice, c.s));
@@ -713,7 +763,6 @@ mgr_status_t mgr_copy_matrix(mgr_handle_t h, int kind, int level, int64_t* rowpt
       else { k_fill_one<<<grid_for(m->nnz, 256), 256, 0, c.s>>>(m->nnz, val); CU_LAUNCH(); }
     }
     CU(cudaStreamSynchronize(c.s));
-      CU_LAUNCH();
   });
 }
 
@@ -743,11 +792,10 @@ mgr_status_t mgr_copy_vector(mgr_handle_t h, int kind, int level, double* out) {
         case 0: CU(cudaMemcpyAsync(out, h->lev[level].minv.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, c.s)); break;
         case 1: CU(cudaMemcpyAsync(out, h->amg[level].dinv.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, c.s)); break;
         case 2: CU(cudaMemcpyAsync(out, h->binv.p, sizeof(double) * len, cudaMemcpyDeviceToDevice, c.s)); break;
-        case 3: k_to_double<int32_t><<<g, 256, 0, c.s>>>(len, h->lev[level].F.p, out); break;
-        case 4: k_to_double<int32_t><<<g, 256, 0, c.s>>>(len, h->lev[level].C.p, out); break;
-        case 5: k_to_double<int8_t><<<g, 256, 0, c.s>>>(len, h->amg[level].cf.p, out); break;
+        case 3: k_to_double<int32_t><<<g, 256, 0, c.s>>>(len, h->lev[level].F.p, out); CU_LAUNCH(); break;
+        case 4: k_to_double<int32_t><<<g, 256, 0, c.s>>>(len, h->lev[level].C.p, out); CU_LAUNCH(); break;
+        case 5: k_to_double<int8_t><<<g, 256, 0, c.s>>>(len, h->amg[level].cf.p, out); CU_LAUNCH(); break;
       }
-      CU_LAUNCH();
     }
     CU(cudaStreamSynchronize(c.s));
   });
@@ -764,6 +812,25 @@ mgr_status_t mgr_profile(mgr_handle_t h, int enable) {
       h->c.prof = h->prof;
     } else {
       h->c.prof = nullptr;
+    }
+  });
+}
+
+mgr_status_t mgr_profile_select(mgr_handle_t h, const char* names) {
+  if (!h) return MGR_ERR_INVALID_ARG;
+  return guarded(h, [&] {
+    if (!h->prof) h->prof = new Prof();
+    h->prof->only.clear();
+    if (!names) return;
+    std::string cur;
+    for (const char* p = names;; ++p) {
+      if (*p == ',' || *p == '\0') {
+        if (!cur.empty()) h->prof->only.insert(cur);
+        cur.clear();
+        if (*p == '\0') break;
+      } else if (*p != ' ') {
+        cur.push_back(*p);
+      }
     }
   });
 }

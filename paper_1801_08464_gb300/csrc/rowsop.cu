@@ -3,23 +3,57 @@
 
 namespace mgr {
 
-__global__ void k_rs_width(int64_t nr, const int64_t* rp, int64_t nslices, int64_t* width) {
+// slice widths (longest row of each slice, rounded up to a multiple of RS_Q); rows in slice order
+// are perm[r] when perm is given
+__global__ void k_rs_width(int64_t nr, const int64_t* rp, const int32_t* perm, int64_t nslices, int64_t* width) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= nslices) return;
   int64_t w = 0, e = (s + 1) * RS_C < nr ? (s + 1) * RS_C : nr;
-  for (int64_t r = s * RS_C; r < e; ++r) w = max(w, rp[r + 1] - rp[r]);
+  for (int64_t r = s * RS_C; r < e; ++r) {
+    int64_t o = perm ? perm[r] : r;
+    w = max(w, rp[o + 1] - rp[o]);
+  }
   width[s] = (w + RS_Q - 1) / RS_Q * RS_Q;
+}
+
+// order the rows of each window of RS_SIGMA rows by decreasing length, equal lengths by row index
+// (one block per window: bitonic sort of (length, row) keys in shared memory)
+__global__ void __launch_bounds__(RS_SIGMA) k_rs_sort(int64_t nr, const int64_t* rp, int32_t* perm) {
+  __shared__ unsigned long long key[RS_SIGMA];
+  int64_t r0 = (int64_t)blockIdx.x * RS_SIGMA;
+  int t = threadIdx.x;
+  int64_t r = r0 + t;
+  if (r < nr) {
+    unsigned long long len = (unsigned long long)(rp[r + 1] - rp[r]);
+    // ascending sort of (max_len - len, index) = descending length, ascending index
+    key[t] = ((0xFFFFFFFFull - (len > 0xFFFFFFFFull ? 0xFFFFFFFFull : len)) << 32) | (unsigned long long)t;
+  } else {
+    key[t] = ~0ull;
+  }
+  __syncthreads();
+  for (int k = 2; k <= RS_SIGMA; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      int x = t ^ j;
+      if (x > t) {
+        bool up = (t & k) == 0;
+        unsigned long long a = key[t], b = key[x];
+        if ((a > b) == up) { key[t] = b; key[x] = a; }
+      }
+      __syncthreads();
+    }
+  if (r < nr) perm[r] = (int32_t)(r0 + (int64_t)(key[t] & 0xFFFFFFFFull));
 }
 
 template <class T>
 __global__ void k_rs_fill(int64_t nr, int64_t npad, const int64_t* rp, const int32_t* ci, const double* v,
-                          const int64_t* soff, int32_t* scol, T* sval) {
+                          const int32_t* perm, const int64_t* soff, int32_t* scol, T* sval) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= npad) return;
   int64_t s = r / RS_C;
   int t = (int)(r - s * RS_C);
   int64_t b0 = soff[s], w = soff[s + 1] - b0;
-  int64_t k0 = r < nr ? rp[r] : 0, len = r < nr ? rp[r + 1] - k0 : 0;
+  int64_t o0 = r < nr ? (perm ? perm[r] : r) : 0;
+  int64_t k0 = r < nr ? rp[o0] : 0, len = r < nr ? rp[o0 + 1] - k0 : 0;
   for (int64_t j = 0; j < w; ++j) {
     int64_t o = b0 * RS_C + (j / RS_Q) * (RS_Q * RS_C) + t * RS_Q + (j % RS_Q);
     if (j < len) { scol[o] = ci[k0 + j]; sval[o] = (T)v[k0 + j]; }
@@ -40,23 +74,33 @@ void rowsop_build(Ctx& c, const DCSR<double>& A, RowsOp<T>& op) {
   op.nnz = A.nnz;
   op.sell = false;
   op.slots = 0;
-  if (A.nr > 0 && A.nnz > 0) {
+  if (A.nr >= RS_MIN_ROWS && A.nnz > 0) {
     int64_t ns = (A.nr + RS_C - 1) / RS_C;
     DBuf<int64_t> width(c, ns + 1);
-    k_rs_width<<<grid_for(ns, 256), 256, 0, c.s>>>(A.nr, A.rp, ns, width.p);
-    CU_LAUNCH();
     op.soff.alloc(c, ns + 1);
+    k_rs_width<<<grid_for(ns, 256), 256, 0, c.s>>>(A.nr, A.rp, nullptr, ns, width.p);
+    CU_LAUNCH();
     op.slots = counts_to_rowptr(c, width.p, op.soff.p, ns);
+    if ((double)(op.slots * RS_C) > RS_SORT_PAD * (double)A.nnz) {
+      op.perm.alloc(c, A.nr);
+      k_rs_sort<<<(unsigned)((A.nr + RS_SIGMA - 1) / RS_SIGMA), RS_SIGMA, 0, c.s>>>(A.nr, A.rp, op.perm.p);
+      CU_LAUNCH();
+      k_rs_width<<<grid_for(ns, 256), 256, 0, c.s>>>(A.nr, A.rp, op.perm.p, ns, width.p);
+      CU_LAUNCH();
+      op.slots = counts_to_rowptr(c, width.p, op.soff.p, ns);
+    }
     if ((double)(op.slots * RS_C) <= RS_MAX_PAD * (double)A.nnz) {
       op.sell = true;
       op.scol.alloc(c, op.slots * RS_C);
       op.sval.alloc(c, op.slots * RS_C);
       int64_t np = ns * RS_C;
-      k_rs_fill<T><<<grid_for(np, 256), 256, 0, c.s>>>(A.nr, np, A.rp, A.ci, A.v, op.soff.p, op.scol.p, op.sval.p);
+      k_rs_fill<T><<<grid_for(np, 256), 256, 0, c.s>>>(A.nr, np, A.rp, A.ci, A.v, op.perm.p, op.soff.p, op.scol.p,
+                                                      op.sval.p);
       CU_LAUNCH();
       return;
     }
     op.soff.release();
+    op.perm.release();
   }
   DCSR<T>& B = op.csr;
   B.nr = A.nr; B.nc = A.nc; B.nnz = A.nnz;

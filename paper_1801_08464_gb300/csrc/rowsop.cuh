@@ -10,8 +10,13 @@
 // which keep more bytes in flight per thread than one 4-byte load per slot.  Slices of 8 rather
 // than 32 keep the padding of the pressure-level operators (rows of 25 to 63 entries side by side)
 // near 10 %.
-// CSR: kept when the slices would pad more than 30 % above the nonzeros (rows of very different
-// lengths side by side); the vector-CSR kernel (TPR lanes per row) runs those.
+// Sorted slices: when rows of very different lengths sit side by side (AMG operators and transfers,
+// the coarse-level couplings), the rows are first ordered by decreasing length within windows of
+// RS_SIGMA consecutive rows (stable), so a slice holds rows of similar length; perm[r] is then the
+// operator row stored at slice position r.  Windows keep the rows of a slice close together, so
+// their x gathers and outputs stay local.
+// CSR: kept for operators with fewer than RS_MIN_ROWS rows, and when even the sorted slices would pad
+// more than 30 % above the nonzeros; the vector-CSR kernel (TPR lanes per row) runs those.
 #pragma once
 #include "common.cuh"
 
@@ -20,6 +25,11 @@ namespace mgr {
 constexpr int RS_C = 8;
 constexpr int RS_Q = 4;  // slots per group
 constexpr double RS_MAX_PAD = 1.3;
+constexpr double RS_SORT_PAD = 1.1;  // above this padding the rows are ordered by length
+constexpr int RS_SIGMA = 256;
+// one thread per row needs rows to fill the GPU (152 SMs x 2048 threads); smaller operators keep CSR
+// and the vector kernel, which puts up to 32 lanes on each row
+constexpr int64_t RS_MIN_ROWS = 256 * 1024;
 
 template <class T>
 struct RowsOp {
@@ -28,6 +38,7 @@ struct RowsOp {
   // SELL-8 with 4-slot groups
   int64_t slots = 0;
   DBuf<int64_t> soff;
+  DBuf<int32_t> perm;  // empty when rows keep their order
   DBuf<int32_t> scol;
   DBuf<T> sval;
   // CSR

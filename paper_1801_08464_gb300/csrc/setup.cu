@@ -675,11 +675,19 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
   CU_LAUNCH();
 }
 
-void amg_build(Ctx& c, const DCSR<double>& A0, const AmgOpts& o, std::vector<AmgLevel>& lv, DBuf<double>& cinv,
-               int64_t& nco) {
+void amg_build(Ctx& c, DCSR<double>& A0, bool take, const AmgOpts& o, std::vector<AmgLevel>& lv,
+               DBuf<double>& cinv, int64_t& nco, const std::function<void(AmgLevel&)>& done) {
   lv.clear();
   lv.emplace_back();
-  copy_csr(c, A0, lv[0].A);
+  if (take) {
+    DCSR<double>& D = lv[0].A;
+    D.nr = A0.nr; D.nc = A0.nc; D.nnz = A0.nnz;
+    D.rp = std::move(A0.rp);
+    D.ci = std::move(A0.ci);
+    D.v = std::move(A0.v);
+  } else {
+    copy_csr(c, A0, lv[0].A);
+  }
   lv[0].n = A0.nr;
   int maxlev = o.max_levels;
   const int B = 256;
@@ -729,6 +737,7 @@ void amg_build(Ctx& c, const DCSR<double>& A0, const AmgOpts& o, std::vector<Amg
     }
     next.n = nC;
     lv.push_back(std::move(next));
+    if (done) done(lv[k]);
     ++k;
   }
   nco = lv.back().n;

@@ -198,6 +198,7 @@ __device__ __forceinline__ uint32_t hash32(int32_t k) { return (uint32_t)k * 265
 // sized to twice the row's candidate count, then sort the distinct keys.
 constexpr int SYM_SORT = 128;
 constexpr int FUSE_CAP = 1024;  // rows with up to FUSE_CAP products take the fused (one-pass) kernels
+constexpr int64_t SPGEMM_STAGE = 128ll << 20;  // staged products per batch of fused rows
 
 template <int MODE>
 __global__ void __launch_bounds__(32 * SYM_WARPS) k_sym_warp(int64_t m, const int64_t* arp, const int32_t* aci,
@@ -306,10 +307,12 @@ __global__ void k_sym_block(const int32_t* rows, const int64_t* arp, const int32
   if (threadIdx.x == 0) ucount = 0;
   __syncthreads();
   int64_t a0 = arp[i], a1 = arp[i + 1];
-  // flatten (p, q) pairs: threads walk the A row; each thread inserts strided B entries
-  for (int64_t p = a0; p < a1; ++p) {
+  // warp w takes the A entries w, w + nwarps, ...; its lanes insert the selected B row (set union:
+  // order irrelevant), so short B rows still keep most lanes busy
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int64_t p = a0 + (threadIdx.x >> 5); p < a1; p += nwarp) {
     int32_t k = aci[p];
-    for (int64_t q = brp[k] + threadIdx.x; q < brp[k + 1]; q += blockDim.x) {
+    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
       int32_t key = bci[q];
       uint32_t h = hash32(key) & (SYM_BHASH - 1);
       while (true) {
@@ -343,6 +346,69 @@ __global__ void k_sym_block(const int32_t* rows, const int64_t* arp, const int32
   for (int t = threadIdx.x; t < u; t += blockDim.x) cci[o + t] = K[t];
 }
 
+// Rows with more than SYM_BCAP products when C has more than SYM_BITS columns: a block-wide hash of
+// SYM_GHASH slots holding at most SYM_GCAP distinct columns (a row with more sets EBIT_CAPACITY and
+// is left empty).  Probing is bounded by the table size, so a full table ends the insertion.
+constexpr int SYM_GHASH = 32768;
+constexpr int SYM_GCAP = 16384;
+
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_sym_bighash(const int32_t* rows, const int64_t* arp, const int32_t* aci,
+                                                      const int64_t* brp, const int32_t* bci, int64_t* cnt,
+                                                      const int64_t* crp, int32_t* cci, int* err) {
+  extern __shared__ int32_t smem[];
+  int32_t* T = smem;               // SYM_GHASH
+  int32_t* K = smem + SYM_GHASH;   // SYM_GCAP
+  __shared__ int ucount, full;
+  int64_t i = rows[blockIdx.x];
+  for (int t = threadIdx.x; t < SYM_GHASH; t += blockDim.x) T[t] = -1;
+  if (threadIdx.x == 0) { ucount = 0; full = 0; }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int64_t p = arp[i] + (threadIdx.x >> 5); p < arp[i + 1]; p += nwarp) {
+    int32_t k = aci[p];
+    for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
+      int32_t key = bci[q];
+      uint32_t h = hash32(key) & (SYM_GHASH - 1);
+      int probes = 0;
+      while (true) {
+        int32_t prev = atomicCAS(&T[h], -1, key);
+        if (prev == -1) { atomicAdd(&ucount, 1); break; }
+        if (prev == key) break;
+        h = (h + 1) & (SYM_GHASH - 1);
+        if (++probes >= SYM_GHASH) { full = 1; break; }
+      }
+    }
+  }
+  __syncthreads();
+  int u = ucount;
+  if (full || u > SYM_GCAP) {
+    if (threadIdx.x == 0) {
+      atomicOr(err, EBIT_CAPACITY);
+      if (MODE == 0) cnt[i] = 0;
+    }
+    return;
+  }
+  if (MODE == 0) {
+    if (threadIdx.x == 0) cnt[i] = u;
+    return;
+  }
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < SYM_GHASH; t += blockDim.x) {
+    int32_t key = T[t];
+    if (key >= 0) K[atomicAdd(&base, 1)] = key;
+  }
+  __syncthreads();
+  int n2 = next_pow2(u);
+  for (int t = u + threadIdx.x; t < n2; t += blockDim.x) K[t] = INT_MAX;
+  __syncthreads();
+  block_bitonic_keys(K, n2);
+  int64_t o = crp[i];
+  for (int t = threadIdx.x; t < u; t += blockDim.x) cci[o + t] = K[t];
+}
+
 // bitmap over the columns [0, nc), nc <= SYM_BITS; 1024 threads, each owning consecutive words
 template <int MODE>
 __global__ void __launch_bounds__(1024) k_sym_bitmap(const int32_t* rows, int64_t nc, const int64_t* arp,
@@ -354,11 +420,14 @@ __global__ void __launch_bounds__(1024) k_sym_bitmap(const int32_t* rows, int64_
   int64_t i = rows[blockIdx.x];
   for (int t = threadIdx.x; t < nw; t += blockDim.x) bits[t] = 0u;
   __syncthreads();
-  for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
-    int32_t k = aci[p];
-    for (int64_t q = brp[k] + threadIdx.x; q < brp[k + 1]; q += blockDim.x) {
-      int32_t key = bci[q];
-      atomicOr(&bits[key >> 5], 1u << (key & 31));
+  {
+    const int ln = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int64_t p = arp[i] + (threadIdx.x >> 5); p < arp[i + 1]; p += nwarp) {
+      int32_t k = aci[p];
+      for (int64_t q = brp[k] + ln; q < brp[k + 1]; q += 32) {
+        int32_t key = bci[q];
+        atomicOr(&bits[key >> 5], 1u << (key & 31));
+      }
     }
   }
   __syncthreads();
@@ -427,9 +496,8 @@ static void sym_pass(Ctx& c, int mode, const DCSR<double>& A, const DCSR<double>
       CU_LAUNCH();
     }
   }
-  if (nbig > 0) {
+  if (nbig > 0 && B.nc <= SYM_BITS) {
     ProfScope ps3(c, "sym_bitmap");
-    if (B.nc > SYM_BITS) throw Error(MGR_ERR_UNSUPPORTED, "spgemm: a row with > 8192 products and > 2^20 columns");
     size_t sh = sizeof(uint32_t) * (size_t)((B.nc + 31) / 32);
     if (mode == 0) {
       CU(cudaFuncSetAttribute(k_sym_bitmap<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
@@ -438,6 +506,19 @@ static void sym_pass(Ctx& c, int mode, const DCSR<double>& A, const DCSR<double>
     } else {
       CU(cudaFuncSetAttribute(k_sym_bitmap<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
       k_sym_bitmap<1><<<nbig, 1024, sh, c.s>>>(big, B.nc, A.rp, A.ci, B.rp, B.ci, nullptr, C.rp, C.ci);
+      CU_LAUNCH();
+    }
+  } else if (nbig > 0) {
+    ProfScope ps3(c, "sym_bitmap");
+    size_t sh = sizeof(int32_t) * (SYM_GHASH + SYM_GCAP);
+    if (mode == 0) {
+      CU(cudaFuncSetAttribute(k_sym_bighash<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      k_sym_bighash<0><<<nbig, 1024, sh, c.s>>>(big, A.rp, A.ci, B.rp, B.ci, cnt, nullptr, nullptr, c.d_err);
+      CU_LAUNCH();
+      check_errors(c, "spgemm: long rows");
+    } else {
+      CU(cudaFuncSetAttribute(k_sym_bighash<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      k_sym_bighash<1><<<nbig, 1024, sh, c.s>>>(big, A.rp, A.ci, B.rp, B.ci, nullptr, C.rp, C.ci, c.d_err);
       CU_LAUNCH();
     }
   }
@@ -605,7 +686,7 @@ __global__ void __launch_bounds__(32 * FH_WARPS) k_spgemm_fused_hash(
     const int32_t* __restrict__ rows, const int* __restrict__ nrows, const int64_t* __restrict__ arp,
     const int32_t* __restrict__ aci, const double* __restrict__ av, const int64_t* __restrict__ brp,
     const int32_t* __restrict__ bci, const double* __restrict__ bv, const int64_t* __restrict__ ub,
-    const int64_t* __restrict__ soff, int32_t* __restrict__ scol, double* __restrict__ sval,
+    const int64_t* __restrict__ soff, int64_t sbase, int32_t* __restrict__ scol, double* __restrict__ sval,
     int64_t* __restrict__ cnt) {
   __shared__ int32_t hk[FH_WARPS][FH_SLOTS];
   __shared__ double hv[FH_WARPS][FH_SLOTS];
@@ -673,7 +754,7 @@ __global__ void __launch_bounds__(32 * FH_WARPS) k_spgemm_fused_hash(
         }
         __syncwarp();
       }
-    int64_t o = soff[i];
+    int64_t o = soff[i] - sbase;
     for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
     if (lane == 0) cnt[i] = u;
     __syncwarp();
@@ -693,7 +774,7 @@ constexpr int FZ_CAPA = 128;
 constexpr int FZ_SLOTS = 512;
 
 __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
-    int64_t m, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
+    int64_t r0, int64_t m, int64_t sbase, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
     const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
     const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
     double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ rest, int* __restrict__ nrest) {
@@ -704,7 +785,7 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
   __shared__ double sa[FZ_WARPS][FZ_CAPA];
   __shared__ double gv[FZ_WARPS][32];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t i = (int64_t)blockIdx.x * FZ_WARPS + w;
+  int64_t i = r0 + (int64_t)blockIdx.x * FZ_WARPS + w;
   if (i >= m) return;
   int U = (int)ub[i];
   int64_t a0 = arp[i];
@@ -818,7 +899,7 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
       }
       __syncwarp();
     }
-  int64_t o = soff[i];
+  int64_t o = soff[i] - sbase;
   for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
   if (lane == 0) cnt[i] = u;
 }
@@ -837,6 +918,36 @@ __global__ void k_spgemm_fused_copy(int64_t m, const int64_t* __restrict__ ub, c
     cv[c0 + t] = sval[o + t];
   }
 }
+// Batches of the fused rows: batch b starts at the first row whose staging offset reaches
+// b * budget (offsets grow by at most FUSE_CAP < budget per row, so every batch has a first row).
+__global__ void k_batch_starts(int64_t m, const int64_t* soff, int64_t budget, int64_t* bstart, int64_t* bbase) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  int64_t b = soff[i] / budget;
+  if (i == 0 || soff[i - 1] / budget != b) { bstart[b] = i; bbase[b] = soff[i]; }
+}
+__global__ void k_batch_counts(int64_t i0, int64_t i1, const int64_t* ub, const int64_t* cnt, int64_t* pc) {
+  int64_t i = i0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < i1) pc[i - i0] = ub[i] <= FUSE_CAP ? cnt[i] : 0;
+}
+// staged rows of one batch -> packed (exact sizes), and packed -> their rows of C
+__global__ void k_batch_pack(int64_t i0, int64_t i1, const int64_t* ub, const int64_t* soff, int64_t sbase,
+                             const int32_t* scol, const double* sval, const int64_t* poff, int32_t* pcol, double* pval) {
+  int64_t i = i0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3);
+  int sub = threadIdx.x & 7;
+  if (i >= i1 || ub[i] > FUSE_CAP) return;
+  int64_t o = soff[i] - sbase, d = poff[i - i0], L = poff[i - i0 + 1] - d;
+  for (int64_t t = sub; t < L; t += 8) { pcol[d + t] = scol[o + t]; pval[d + t] = sval[o + t]; }
+}
+__global__ void k_batch_unpack(int64_t i0, int64_t i1, const int64_t* ub, const int64_t* poff, const int32_t* pcol,
+                               const double* pval, const int64_t* crp, int32_t* cci, double* cv) {
+  int64_t i = i0 + ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3);
+  int sub = threadIdx.x & 7;
+  if (i >= i1 || ub[i] > FUSE_CAP) return;
+  int64_t d = poff[i - i0], c0 = crp[i], L = crp[i + 1] - c0;
+  for (int64_t t = sub; t < L; t += 8) { cci[c0 + t] = pcol[d + t]; cv[c0 + t] = pval[d + t]; }
+}
+
 __global__ void k_small_ub(int64_t m, const int64_t* ub, int64_t* us) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < m) us[i] = ub[i] <= FUSE_CAP ? ub[i] : 0;
@@ -872,21 +983,70 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
   int hc[2];
   CU(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, c.s));
   CU(cudaStreamSynchronize(c.s));
-  DBuf<int32_t> scol(c, nstage + 1);
-  DBuf<double> sval(c, nstage + 1);
-  {
-    ProfScope ps2(c, "fused_small");
-    DBuf<int32_t> rest(c, m);
-    DBuf<int> nrest(c, 1);
-    CU(cudaMemsetAsync(nrest.p, 0, sizeof(int), c.s));
-    k_spgemm_fused_chunk<<<grid_for(m, FZ_WARPS), 32 * FZ_WARPS, 0, c.s>>>(m, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p,
-                                                                           soff.p, scol.p, sval.p, cnt.p, rest.p,
-                                                                           nrest.p);
+  // the fused rows are staged (up to their product count each) in batches of at most
+  // stage + FUSE_CAP entries; with several batches, each is packed to its exact size before
+  // the next one is staged, so the transient memory follows the output, not the product count
+  const int64_t stage = c.spgemm_stage > FUSE_CAP ? c.spgemm_stage : SPGEMM_STAGE;
+  const int64_t nbatch = nstage / stage + 1;
+  std::vector<int64_t> bst(nbatch + 1, m), bbase(nbatch + 1, nstage);
+  if (nbatch > 1) {
+    DBuf<int64_t> dbs(c, nbatch), dbb(c, nbatch);
+    fill_i64(c, dbs.p, m, nbatch);  // a batch without a first row stays empty
+    fill_i64(c, dbb.p, nstage, nbatch);
+    k_batch_starts<<<grid_for(m, 256), 256, 0, c.s>>>(m, soff.p, stage, dbs.p, dbb.p);
     CU_LAUNCH();
-    // 4 blocks of 48 KB shared memory per SM on 152 SMs, 4 rounds
-    k_spgemm_fused_hash<<<grid_for(m, FH_WARPS, 152 * 16), 32 * FH_WARPS, 0, c.s>>>(
-        rest.p, nrest.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p);
-    CU_LAUNCH();
+    CU(cudaMemcpyAsync(bst.data(), dbs.p, sizeof(int64_t) * nbatch, cudaMemcpyDeviceToHost, c.s));
+    CU(cudaMemcpyAsync(bbase.data(), dbb.p, sizeof(int64_t) * nbatch, cudaMemcpyDeviceToHost, c.s));
+    CU(cudaStreamSynchronize(c.s));
+    for (int64_t b = nbatch - 1; b >= 0; --b) {
+      bst[b] = std::min(bst[b], bst[b + 1]);
+      bbase[b] = std::min(bbase[b], bbase[b + 1]);
+    }
+  } else {
+    bst[0] = 0;
+    bbase[0] = 0;
+  }
+  int64_t cap = 0;
+  for (int64_t b = 0; b < nbatch; ++b) cap = std::max(cap, bbase[b + 1] - bbase[b]);
+  DBuf<int32_t> scol(c, cap + 1);
+  DBuf<double> sval(c, cap + 1);
+  std::vector<DBuf<int64_t>> poff(nbatch > 1 ? nbatch : 0);
+  std::vector<DBuf<int32_t>> pcol(poff.size());
+  std::vector<DBuf<double>> pval(poff.size());
+  DBuf<int32_t> rest(c, m);
+  DBuf<int> nrest(c, 1);
+  for (int64_t b = 0; b < nbatch; ++b) {
+    const int64_t i0 = bst[b], i1 = bst[b + 1], base = bbase[b];
+    if (i1 <= i0) continue;
+    {
+      ProfScope ps2(c, "fused_small");
+      CU(cudaMemsetAsync(nrest.p, 0, sizeof(int), c.s));
+      k_spgemm_fused_chunk<<<grid_for(i1 - i0, FZ_WARPS), 32 * FZ_WARPS, 0, c.s>>>(
+          i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, rest.p, nrest.p);
+      CU_LAUNCH();
+      // 4 blocks of 48 KB shared memory per SM on 152 SMs, 4 rounds
+      k_spgemm_fused_hash<<<grid_for(i1 - i0, FH_WARPS, 152 * 16), 32 * FH_WARPS, 0, c.s>>>(
+          rest.p, nrest.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, base, scol.p, sval.p, cnt.p);
+      CU_LAUNCH();
+    }
+    if (nbatch > 1) {
+      ProfScope ps3(c, "fused_copy");
+      int64_t nr = i1 - i0;
+      DBuf<int64_t> pc(c, nr + 1);
+      k_batch_counts<<<grid_for(nr, 256), 256, 0, c.s>>>(i0, i1, ub.p, cnt.p, pc.p);
+      CU_LAUNCH();
+      poff[b].alloc(c, nr + 1);
+      int64_t tot = counts_to_rowptr(c, pc.p, poff[b].p, nr);
+      pcol[b].alloc(c, tot + 1);
+      pval[b].alloc(c, tot + 1);
+      k_batch_pack<<<grid_for(nr * 8, 256), 256, 0, c.s>>>(i0, i1, ub.p, soff.p, base, scol.p, sval.p, poff[b].p,
+                                                           pcol[b].p, pval[b].p);
+      CU_LAUNCH();
+    }
+  }
+  if (nbatch > 1) {  // the staging is no longer needed
+    scol.release();
+    sval.release();
   }
   sym_pass(c, 0, A, B, ub.p, mid.p, hc[0], big.p, hc[1], cnt.p, C, 1);
   C.nnz = counts_to_rowptr(c, cnt.p, C.rp.p, m);
@@ -895,8 +1055,21 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
   sym_pass(c, 1, A, B, ub.p, mid.p, hc[0], big.p, hc[1], nullptr, C, 1);
   {
     ProfScope ps3(c, "fused_copy");
-    k_spgemm_fused_copy<<<grid_for(m * 8, 256), 256, 0, c.s>>>(m, ub.p, soff.p, scol.p, sval.p, C.rp.p, C.ci.p, C.v.p);
-    CU_LAUNCH();
+    if (nbatch == 1) {
+      k_spgemm_fused_copy<<<grid_for(m * 8, 256), 256, 0, c.s>>>(m, ub.p, soff.p, scol.p, sval.p, C.rp.p, C.ci.p,
+                                                                   C.v.p);
+      CU_LAUNCH();
+    } else {
+      for (int64_t b = 0; b < nbatch; ++b) {
+        const int64_t i0 = bst[b], i1 = bst[b + 1];
+        if (i1 <= i0) continue;
+        k_batch_unpack<<<grid_for((i1 - i0) * 8, 256), 256, 0, c.s>>>(i0, i1, ub.p, poff[b].p, pcol[b].p, pval[b].p,
+                                                                       C.rp.p, C.ci.p, C.v.p);
+        CU_LAUNCH();
+        pcol[b].release();
+        pval[b].release();
+      }
+    }
   }
   ProfScope ps4(c, "spgemm_numeric");
   k_spgemm_numeric_expand<<<grid_for(C.nr, NX_WARPS), 32 * NX_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci,

@@ -1,7 +1,8 @@
 """Full-size workloads on the GPU.
 
 64^3 (786,432 unknowns, FP64, AMG coarse solve): the whole hierarchy against the oracle, splittings
-and patterns bit for bit, and the solve to 1e-8.
+and patterns bit for bit, one preconditioner application against the oracle's, and the solve to
+1e-8.
 128^3 (6,291,456 unknowns, FP32 hierarchy / FP64 Krylov, the benchmark's launch configuration):
 properties that hold at any size -- level sizes 3N-M, 2N-M, N, the level-1 operator on sampled rows
 against its closed form A_cc - A_cf C33^-1 A_fc, the explicit residual of the returned solution.
@@ -38,6 +39,10 @@ def test_64cube_full_parity_fp64():
         compare_csr(m.scipy(mg.MAT_AMG_P, k), o.scipy(oracle.MAT_AMG_P, k), what=f"AMG P_{k}")
         compare_csr(m.scipy(mg.MAT_AMG_A, k + 1), o.scipy(oracle.MAT_AMG_A, k + 1), what=f"AMG A_{k+1}")
     b = ncpgen.normals(p.n, 2)
+    # one preconditioner application (operators of >= 256K rows run in the sliced layouts here)
+    z = m.apply(torch.as_tensor(b, device="cuda")).cpu().numpy()
+    zo = o.apply(b)
+    assert np.linalg.norm(z - zo) <= 1e-9 * np.linalg.norm(zo)
     x, info = m.fgmres(A, torch.as_tensor(b, device="cuda"), rtol=1e-8)
     assert info["converged"]
     xg = x.cpu().numpy()

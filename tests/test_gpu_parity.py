@@ -228,3 +228,75 @@ def test_error_statuses():
     x, info = m.fgmres(A, b, rtol=1e-14, maxit=2, raise_on_fail=False)
     assert info["status"] == 3 and info["iterations"] == 2 and info["relres_true"] < 1.0
     m.close()
+
+
+def _hier_arrays(m, mg):
+    """Every matrix of a GPU hierarchy as scipy CSR, keyed by (kind, level)."""
+    L, na = m.levels()
+    out = {}
+    for l in range(L + 1):
+        out[(mg.MAT_LEVEL, l)] = m.scipy(mg.MAT_LEVEL, l)
+    for l in range(L):
+        for kind in (mg.MAT_WP, mg.MAT_WR, mg.MAT_P, mg.MAT_R):
+            out[(kind, l)] = m.scipy(kind, l)
+    for k in range(na):
+        out[(mg.MAT_AMG_A, k)] = m.scipy(mg.MAT_AMG_A, k)
+        if k < na - 1:
+            for kind in (mg.MAT_AMG_P, mg.MAT_AMG_R, mg.MAT_AMG_S):
+                out[(kind, k)] = m.scipy(kind, k)
+    return out
+
+
+@pytest.mark.parametrize("name", list(PARITY))
+def test_batched_spgemm_and_lean_setup(name):
+    """Products staged in batches of 2048 (many batches per product, packed between batches) give
+    the hierarchy of the single-batch path bit for bit; the lean setup (FP64 setup operators freed as
+    soon as they are used) gives the same preconditioner and solve bit for bit, keeps the level shapes
+    and reports MGR_ERR_STATE for the freed matrices.  Non-injective restriction at level 2, so the
+    products are larger than with the defaults."""
+    import paper_1801_08464_gb300 as mg
+    import torch
+    p = ncpgen.make_problem(PARITY[name])
+    A, mk = to_gpu(p)
+    opts = OPTION_SETS["jacobi_trunc"]
+    ref = mg.MGR(**opts)
+    ref.setup(A, mk)
+    bat = mg.MGR(spgemm_stage=2048, **opts)
+    bat.setup(A, mk)
+    h1, h2 = _hier_arrays(ref, mg), _hier_arrays(bat, mg)
+    assert h1.keys() == h2.keys()
+    for key in h1:
+        a, b = h1[key], h2[key]
+        assert np.array_equal(a.indptr, b.indptr) and np.array_equal(a.indices, b.indices), key
+        assert np.array_equal(a.data, b.data), key
+    r = torch.as_tensor(ncpgen.normals(p.n, 2), device="cuda")
+    for prec in ("fp64", "mixed"):
+        full = mg.MGR(precision=prec, **opts)
+        full.setup(A, mk)
+        lean = mg.MGR(precision=prec, lean=1, spgemm_stage=2048, **opts)
+        lean.setup(A, mk)
+        assert torch.equal(full.apply(r), lean.apply(r)), prec
+        x1, i1 = full.fgmres(A, r, rtol=1e-8)
+        x2, i2 = lean.fgmres(A, r, rtol=1e-8)
+        assert i1["iterations"] == i2["iterations"] and torch.equal(x1, x2), prec
+        L, na = lean.levels()
+        assert [bench_shape(lean, mg.MAT_LEVEL, l) for l in range(L + 1)] == \
+            [bench_shape(full, mg.MAT_LEVEL, l) for l in range(L + 1)]
+        with pytest.raises(mg.MgrError) as e:
+            lean.matrix(mg.MAT_LEVEL, 1)
+        assert e.value.code == 8  # MGR_ERR_STATE
+        assert lean.memory_bytes() < full.memory_bytes()
+        full.close()
+        lean.close()
+    ref.close()
+    bat.close()
+
+
+def bench_shape(m, kind, lev):
+    import ctypes
+
+    import paper_1801_08464_gb300 as mg
+    nr, nc, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rc = mg.lib().mgr_matrix_shape(m._h, kind, lev, ctypes.byref(nr), ctypes.byref(nc), ctypes.byref(nnz))
+    assert rc == 0
+    return nr.value, nc.value, nnz.value
