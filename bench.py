@@ -40,7 +40,10 @@ SOLVE_KERNELS = ("bsr3_spmv_f64", "mdot", "mupdate", "global_relax", "bsr_resid_
 SETUP_KERNELS = ("setup_total", "setup_mgr_level", "setup_mgr_rap", "setup_amg", "setup_amg_strength",
                  "setup_amg_pmis", "setup_amg_extpi", "extpi_pattern", "extpi_weights", "setup_amg_transpose",
                  "setup_amg_rap", "setup_dense_inverse", "setup_cast_alloc", "spgemm", "fused_small", "fused_copy",
-                 "spgemm_numeric", "sym_ub", "sym_count_warp", "sym_fill_warp", "sym_block", "sym_bitmap")
+                 "spgemm_numeric", "sym_ub", "sym_count_warp", "sym_fill_warp", "sym_block", "sym_bitmap",
+                 "rap_mgr0_AP", "rap_mgr0_RAP", "rap_mgr1_AP", "rap_mgr1_RAP", "rap_mgr2_AP", "rap_mgr2_RAP",
+                 "rap_amg0_AP", "rap_amg0_PtAP", "rap_amg1_AP", "rap_amg1_PtAP", "rap_amgc_AP", "rap_amgc_PtAP",
+                 "spgemm_extpi")
 KERNEL_NAMES = SOLVE_KERNELS + SETUP_KERNELS
 # DRAM bytes over algorithmic bytes of one launch, from one ncu capture of the kernel on an 80^3
 # instance of the workload (dram__bytes_read.sum + dram__bytes_write.sum); the traffic of a full-size
@@ -296,6 +299,12 @@ def main():
             rk[k] = {"launches": n_k, "ms": t_k, "achieved_gbs": gbs, "frac": gbs / peak,
                      "bytes_per_launch": by_k / n_k}
     out["kernel_bandwidth"] = rk
+    sb = {}
+    for k in SETUP_KERNELS:
+        n_k, t_k, by_k = kt.get(k, (0, 0.0, 0.0))
+        if n_k and by_k and t_k > 0:
+            sb[k] = {"calls": n_k, "ms": t_k, "achieved_gbs": by_k / (t_k * 1e-3) / 1e9}
+    out["setup_bandwidth"] = sb
     if kt_dom:
         k, (n_k, t_k, by_k) = kt_dom
         per_launch = by_k / n_k

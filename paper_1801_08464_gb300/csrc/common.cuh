@@ -122,6 +122,12 @@ struct ProfScope {
   }
 };
 
+// Adds algorithmic bytes to the record of `name` when the name is being profiled (for work whose
+// size is known only after its launches were issued).
+inline void prof_add_bytes(Ctx& c, const char* name, double bytes) {
+  if (c.prof && c.prof->wants(name)) c.prof->recs[name].bytes += bytes;
+}
+
 void* dev_alloc(Ctx& c, size_t bytes);
 void dev_free(Ctx& c, void* p, size_t bytes);
 
@@ -227,7 +233,8 @@ void bsr3_validate(Ctx& c, const mgr_bsr3_t& A, const int8_t* marker);  // throw
 void bsr3_to_csr(Ctx& c, const mgr_bsr3_t& A, DCSR<double>& out);        // exact zeros dropped
 void bsr3_block_inverse(Ctx& c, const mgr_bsr3_t& A, double* binv);      // sets EBIT_SINGULAR
 // C = A * B: structural pattern, each entry summed in ascending intermediate index.
-void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C);
+// C = A B (Gustavson order); `name` labels the call in the per-kernel timing
+void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C, const char* name = "spgemm");
 // Pattern of C = A * B only (values left unallocated), same pattern rules.
 void spgemm_symbolic(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C);
 void transpose(Ctx& c, const DCSR<double>& A, DCSR<double>& T);          // rows sorted by column

@@ -229,15 +229,18 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
   // row c of R (A P) is 0.0 + 1 * (A P)_{C[c]}; a Gustavson sum that starts at +0.0 never ends at -0.0,
   // so that equals (A P)_{C[c]} bit for bit, and only the C rows of A enter the product.
   {
+    static const char* const kAP[] = {"rap_mgr0_AP", "rap_mgr1_AP", "rap_mgr2_AP", "rap_mgr3_AP"};
+    static const char* const kRAP[] = {"rap_mgr0_RAP", "rap_mgr1_RAP", "rap_mgr2_RAP", "rap_mgr3_RAP"};
+    const int li = l < 3 ? l : 3;
     ProfScope ps(c, "setup_mgr_rap");
     if (o.restrict_type == 1) {
       DCSR<double> AP;
-      spgemm(c, A, L.P, AP);
-      spgemm(c, L.R, AP, Anext);
+      spgemm(c, A, L.P, AP, kAP[li]);
+      spgemm(c, L.R, AP, Anext, kRAP[li]);
     } else {
       DCSR<double> AC;
       csr_gather_rows(c, A, L.C.p, nC, AC);
-      spgemm(c, AC, L.P, Anext);
+      spgemm(c, AC, L.P, Anext, kRAP[li]);
     }
   }
   mk_next.alloc(c, nC);
@@ -403,12 +406,13 @@ constexpr int EXT_CAP = 256;
 __global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* srp,
                                 const int32_t* sci, const int8_t* cf, const int32_t* cidx, const int32_t* cfine,
                                 const int64_t* prp, const int32_t* pci, double* pv, double* den_g, double* q_g,
-                                int8_t* rowzero) {
+                                int8_t* rowzero, const int8_t* only) {
   __shared__ double s_wt[EXT_WARPS][EXT_CAP], s_kt[EXT_WARPS][EXT_CAP];
   __shared__ int8_t s_wf[EXT_WARPS][EXT_CAP], s_kf[EXT_WARPS][EXT_CAP];
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (i >= n) return;
+  if (only && !only[i]) return;
   if (cf[i] == 1) {
     if (lane == 0) { pv[prp[i]] = 1.0; rowzero[i] = 0; }
     return;
@@ -507,6 +511,132 @@ __global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, con
     }
     pv[t] = (at != 0.0) ? -dv(num, at) : 0.0;
   }
+}
+
+// The same weights with the row's interpolation columns (fine indices, ascending) and running
+// numerators in shared memory: a warp walks the strong F neighbours k in ascending order; for each k
+// its lanes test the entries of row k against the staged columns in parallel, lane 0 adds den_k's
+// terms in row order from the lanes' shuffled values, and the lanes then add q_k a_kl to the
+// numerators of the distinct columns l of row k (__syncwarp between successive k).  Every sum is
+// formed in the order of k_extpi_weights, so the weights are identical bit for bit.  Rows with more
+// than EXT_PCAP interpolation columns are left to k_extpi_weights (flag `rest`).
+constexpr int EXT_PCAP = 512;
+
+__device__ __forceinline__ int find_sh(const int32_t* a, int n, int32_t key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return (lo < n && a[lo] == key) ? lo : -1;
+}
+
+__global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights_sh(
+    int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
+    const int64_t* __restrict__ srp, const int32_t* __restrict__ sci, const int8_t* __restrict__ cf,
+    const int32_t* __restrict__ cfine, const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
+    double* __restrict__ pv, int8_t* __restrict__ rowzero, int8_t* __restrict__ rest) {
+  __shared__ int32_t s_pf[EXT_WARPS][EXT_PCAP];
+  __shared__ double s_num[EXT_WARPS][EXT_PCAP];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * EXT_WARPS + w;
+  if (i >= n) return;
+  if (cf[i] == 1) {
+    if (lane == 0) { pv[prp[i]] = 1.0; rowzero[i] = 0; rest[i] = 0; }
+    return;
+  }
+  const int64_t p0 = prp[i], np64 = prp[i + 1] - p0;
+  if (np64 > EXT_PCAP) {
+    if (lane == 0) rest[i] = 1;
+    return;
+  }
+  const int np = (int)np64;
+  int32_t* pf = s_pf[w];
+  double* num = s_num[w];
+  const int64_t r0 = rp[i], r1 = rp[i + 1];
+  const int64_t s0 = srp[i], s1 = srp[i + 1];
+  // staged columns (fine indices, ascending) and numerators starting at a_ij
+  for (int t = lane; t < np; t += 32) pf[t] = cfine[pci[p0 + t]];
+  __syncwarp();
+  for (int t = lane; t < np; t += 32) num[t] = csr_get(rp, ci, v, i, pf[t]);
+  // at = a_ii, then the weak neighbours outside Chat_i in row order
+  double at = 0.0;
+  if (lane == 0) at = csr_get(rp, ci, v, i, (int32_t)i);
+  for (int64_t b = r0; b < r1; b += 32) {
+    int64_t q = b + lane;
+    bool lump = false;
+    double val = 0.0;
+    if (q < r1) {
+      int32_t nn = ci[q];
+      val = v[q];
+      lump = nn != i && find_i32(sci, s0, s1, nn) < 0 && find_sh(pf, np, nn) < 0;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, lump);
+    while (m) {
+      int l = __ffs(m) - 1;
+      double x = __shfl_sync(0xffffffffu, val, l);
+      if (lane == 0) at = dd(at, x);
+      m &= m - 1;
+    }
+  }
+  __syncwarp();
+  // strong F neighbours in ascending order
+  for (int64_t p = s0; p < s1; ++p) {
+    const int32_t k = sci[p];
+    if (cf[k] == 1) continue;
+    const int64_t k0 = rp[k], k1 = rp[k + 1];
+    // a_kk and a_ki (lanes scan row k)
+    double akk = 0.0, aki = 0.0;
+    for (int64_t b = k0; b < k1; b += 32) {
+      int64_t q = b + lane;
+      int32_t l = q < k1 ? ci[q] : -1;
+      double x = q < k1 ? v[q] : 0.0;
+      unsigned mk = __ballot_sync(0xffffffffu, l == k), mi = __ballot_sync(0xffffffffu, l == (int32_t)i);
+      if (mk) akk = __shfl_sync(0xffffffffu, x, __ffs(mk) - 1);
+      if (mi) aki = __shfl_sync(0xffffffffu, x, __ffs(mi) - 1);
+    }
+    // den_k in row order
+    double den = 0.0;
+    for (int64_t b = k0; b < k1; b += 32) {
+      int64_t q = b + lane;
+      bool in = false;
+      double x = 0.0;
+      if (q < k1) {
+        int32_t l = ci[q];
+        x = v[q];
+        in = (l == (int32_t)i || find_sh(pf, np, l) >= 0) && opposite(x, akk);
+      }
+      unsigned m = __ballot_sync(0xffffffffu, in);
+      while (m) {
+        int l = __ffs(m) - 1;
+        double y = __shfl_sync(0xffffffffu, x, l);
+        if (lane == 0) den = dd(den, y);
+        m &= m - 1;
+      }
+    }
+    den = __shfl_sync(0xffffffffu, den, 0);
+    const double aik = csr_get(rp, ci, v, i, k);
+    if (den != 0.0) {
+      const double qk = dv(aik, den);
+      if (lane == 0 && opposite(aki, akk)) at = dd(at, dm(qk, aki));
+      // numerators: distinct columns of row k land on distinct slots
+      for (int64_t b = k0; b < k1; b += 32) {
+        int64_t q = b + lane;
+        if (q < k1) {
+          int32_t l = ci[q];
+          double x = v[q];
+          int t = find_sh(pf, np, l);
+          if (t >= 0 && opposite(x, akk)) num[t] = dd(num[t], dm(qk, x));
+        }
+      }
+    } else if (lane == 0) {
+      at = dd(at, aik);
+    }
+    __syncwarp();
+  }
+  at = __shfl_sync(0xffffffffu, at, 0);
+  if (lane == 0) { rowzero[i] = (at == 0.0); rest[i] = 0; }
+  for (int t = lane; t < np; t += 32) pv[p0 + t] = (at != 0.0) ? -dv(num[t], at) : 0.0;
 }
 
 // Keep / truncation: an empty-flagged row keeps nothing; with pmax > 0 a longer F row keeps its pmax
@@ -650,7 +780,7 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
   fill_f64(c, T.v.p, 1.0, T.nnz);
   {
     ProfScope ps(c, "extpi_pattern");
-    spgemm(c, M, T, Q);
+    spgemm(c, M, T, Q, "spgemm_extpi");
   }
   DCSR<double> Pf;
   {
@@ -662,10 +792,14 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
     CU_LAUNCH();
   }
   DBuf<double> den(c, S.nnz + 1), q(c, S.nnz + 1), scale(c, n);
-  DBuf<int8_t> rowzero(c, n), keep(c, Pf.nnz + 1);
+  DBuf<int8_t> rowzero(c, n), keep(c, Pf.nnz + 1), rest(c, n);
   ProfScope psw(c, "extpi_weights");
+  k_extpi_weights_sh<<<grid_for(n, EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p,
+                                                                         cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p,
+                                                                         rest.p);
+  CU_LAUNCH();
   k_extpi_weights<<<grid_for(n * 32, 32 * EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp,
-                                                           Pf.ci, Pf.v, den.p, q.p, rowzero.p);
+                                                           Pf.ci, Pf.v, den.p, q.p, rowzero.p, rest.p);
   CU_LAUNCH();
   DBuf<int64_t> cnt(c, n + 1);
   k_ptrunc<<<grid_for(n * 32, 128), 128, 0, c.s>>>(n, cf.p, Pf.rp, Pf.v, rowzero.p, pmax, keep.p, scale.p, cnt.p);
@@ -732,8 +866,11 @@ void amg_build(Ctx& c, DCSR<double>& A0, bool take, const AmgOpts& o, std::vecto
     {
       ProfScope ps(c, "setup_amg_rap");
       DCSR<double> AP;
-      spgemm(c, L.A, L.P, AP);
-      spgemm(c, L.R, AP, next.A);
+      static const char* const kAP[] = {"rap_amg0_AP", "rap_amg1_AP", "rap_amgc_AP"};
+      static const char* const kPAP[] = {"rap_amg0_PtAP", "rap_amg1_PtAP", "rap_amgc_PtAP"};
+      const int ki = k < 2 ? k : 2;
+      spgemm(c, L.A, L.P, AP, kAP[ki]);
+      spgemm(c, L.R, AP, next.A, kPAP[ki]);
     }
     next.n = nC;
     lv.push_back(std::move(next));

@@ -761,6 +761,48 @@ __global__ void __launch_bounds__(32 * FH_WARPS) k_spgemm_fused_hash(
   }
 }
 
+// Fused product for rows with at most TT_CAP products, one thread per row: the products are taken
+// in (k, q) order and merged into a short sorted list in shared memory (a new column is inserted
+// with 0.0 + its product, a repeated column adds its product), so every entry is summed from 0.0 in
+// ascending k exactly as in the warp kernels, with no hashing and no sort pass.
+constexpr int TT_CAP = 32;
+constexpr int TT_THREADS = 64;
+
+__global__ void __launch_bounds__(TT_THREADS) k_spgemm_tiny(
+    int64_t r0, int64_t r1, int64_t sbase, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+    const double* __restrict__ av, const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
+    const double* __restrict__ bv, const int64_t* __restrict__ ub, const int64_t* __restrict__ soff,
+    int32_t* __restrict__ scol, double* __restrict__ sval, int64_t* __restrict__ cnt) {
+  __shared__ int32_t sc[TT_CAP][TT_THREADS];
+  __shared__ double sv[TT_CAP][TT_THREADS];
+  const int t = threadIdx.x;
+  const int64_t i = r0 + (int64_t)blockIdx.x * TT_THREADS + t;
+  if (i >= r1) return;
+  if (ub[i] > TT_CAP) return;
+  int u = 0;
+  for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
+    const int32_t k = aci[p];
+    const double a = av[p];
+    for (int64_t q = brp[k]; q < brp[k + 1]; ++q) {
+      const int32_t j = bci[q];
+      const double prod = __dmul_rn(a, bv[q]);
+      int pos = u;
+      while (pos > 0 && sc[pos - 1][t] > j) --pos;
+      if (pos > 0 && sc[pos - 1][t] == j) {
+        sv[pos - 1][t] = __dadd_rn(sv[pos - 1][t], prod);
+      } else {
+        for (int e = u; e > pos; --e) { sc[e][t] = sc[e - 1][t]; sv[e][t] = sv[e - 1][t]; }
+        sc[pos][t] = j;
+        sv[pos][t] = __dadd_rn(0.0, prod);
+        ++u;
+      }
+    }
+  }
+  const int64_t o = soff[i] - sbase;
+  for (int e = 0; e < u; ++e) { scol[o + e] = sc[e][t]; sval[o + e] = sv[e][t]; }
+  cnt[i] = u;
+}
+
 // Fused product for rows with at most FUSE_CAP products and FZ_CAPA entries in A (the common case):
 // products are taken 32 at a time in (k, q) order, i.e. ascending intermediate index k (lane t holds
 // product t0 + t; its A entry comes from a scan of the B row lengths kept in shared memory, and the
@@ -788,6 +830,7 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
   int64_t i = r0 + (int64_t)blockIdx.x * FZ_WARPS + w;
   if (i >= m) return;
   int U = (int)ub[i];
+  if (U <= TT_CAP) return;  // k_spgemm_tiny
   int64_t a0 = arp[i];
   int na = (int)(arp[i + 1] - a0);
   if (U > FZ_SLOTS / 2 || na > FZ_CAPA) {  // the row goes to the larger kernels
@@ -953,7 +996,7 @@ __global__ void k_small_ub(int64_t m, const int64_t* ub, int64_t* us) {
   if (i < m) us[i] = ub[i] <= FUSE_CAP ? ub[i] : 0;
 }
 
-void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C) {
+void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C, const char* name) {
   if (A.nc != B.nr) throw Error(MGR_ERR_INVALID_ARG, "spgemm: inner dimensions differ");
   int64_t m = A.nr;
   C.nr = m;
@@ -967,6 +1010,7 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
     return;
   }
   ProfScope ps(c, "spgemm");
+  ProfScope psn(c, name);
   DBuf<int64_t> ub(c, m), cnt(c, m + 1), us(c, m + 1);
   DBuf<int32_t> mid(c, m), big(c, m);
   DBuf<int> counters(c, 2);
@@ -1021,6 +1065,9 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
     {
       ProfScope ps2(c, "fused_small");
       CU(cudaMemsetAsync(nrest.p, 0, sizeof(int), c.s));
+      k_spgemm_tiny<<<grid_for(i1 - i0, TT_THREADS), TT_THREADS, 0, c.s>>>(i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci,
+                                                                           B.v, ub.p, soff.p, scol.p, sval.p, cnt.p);
+      CU_LAUNCH();
       k_spgemm_fused_chunk<<<grid_for(i1 - i0, FZ_WARPS), 32 * FZ_WARPS, 0, c.s>>>(
           i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, rest.p, nrest.p);
       CU_LAUNCH();
@@ -1070,6 +1117,12 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
         pval[b].release();
       }
     }
+  }
+  if (c.prof && c.prof->wants(name)) {
+    // algorithmic bytes of the product: A once, one B entry (column, value) per product, C written
+    DBuf<int64_t> pp(c, m + 1);
+    int64_t products = counts_to_rowptr(c, ub.p, pp.p, m);
+    prof_add_bytes(c, name, 12.0 * (double)(A.nnz + products + C.nnz) + 16.0 * (double)(m + 1));
   }
   ProfScope ps4(c, "spgemm_numeric");
   k_spgemm_numeric_expand<<<grid_for(C.nr, NX_WARPS), 32 * NX_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci,
