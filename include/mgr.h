@@ -83,7 +83,10 @@ typedef struct {
                                             MGR_ERR_STATE.  Default 0 */
   int32_t spgemm_stage;                  /* SpGEMM products staged per batch of short rows (0: the
                                             default 2^27; values <= 1024 also mean the default) */
-  int32_t reserved[6];                   /* must be zero */
+  int32_t adjoint;                       /* 1: the setup also builds the transposed operators of the
+                                            preconditioner, for mgr_apply_transpose and
+                                            fgmres_solve_transpose (default 0) */
+  int32_t reserved[5];                   /* must be zero */
 } mgr_options_t;
 
 typedef struct {
@@ -136,6 +139,19 @@ mgr_status_t fgmres_solve(mgr_handle_t h, const mgr_bsr3_t* A, const double* b, 
 
 /* Release the handle and all its device memory (synchronises its stream).  NULL is accepted. */
 mgr_status_t mgr_destroy(mgr_handle_t h);
+
+/* ---- transposed solves (adjoint) ----------------------------------------------------------------
+ * For a handle set up on A with options.adjoint = 1.  z = M^-T r, the exact transpose of mgr_apply's
+ * operator M^-1 (up to rounding): the levels in reverse roles (P_l^T = S_C + W_p^T S_F restricts, the
+ * F-relaxation sweeps run with A_ff^T, the coarse residual is formed with A_cf^T, the V-cycle is
+ * V(post, pre) with A_k^T, and the global relaxation closes with z = g + B^T (y - A^T g)).  It is the
+ * natural preconditioner of A^T x = b: (A^T M^-T) = (M^-1 A)^T keeps the spectrum of the forward
+ * preconditioned operator.  MGR_ERR_STATE without options.adjoint. */
+mgr_status_t mgr_apply_transpose(mgr_handle_t h, const double* r, double* z);
+/* Solves A^T x = b (A the matrix given to mgr_setup, with its values as passed now) by FGMRES(m)
+ * right-preconditioned with M^-T; arguments, stopping rule and statuses as fgmres_solve. */
+mgr_status_t fgmres_solve_transpose(mgr_handle_t h, const mgr_bsr3_t* A, const double* b, double* x, double rtol,
+                                    int restart, int maxit, mgr_solve_info_t* info);
 
 /* ---- introspection (for parity tests and reporting) ------------------------------------------ */
 /* Matrix kinds: 0 level operator A_l (l = 0..L), 1 W_p(l), 2 W_r(l), 3 P(l), 4 R(l) (l < L),

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("amg_smoother", ctypes.c_int32), ("amg_pre", ctypes.c_int32), ("amg_post", ctypes.c_int32),
                 ("amg_pmax", ctypes.c_int32), ("amg_omega", ctypes.c_double), ("amg_seed", ctypes.c_uint64),
                 ("lean", ctypes.c_int32), ("spgemm_stage", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("adjoint", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Bsr3(ctypes.Structure):
@@ -61,6 +61,7 @@ class SolveInfo(ctypes.Structure):
 
 
 EXPORTS = ["mgr_status_string", "mgr_options_default", "mgr_create", "mgr_setup", "mgr_apply", "fgmres_solve",
+           "mgr_apply_transpose", "fgmres_solve_transpose",
            "mgr_destroy", "mgr_get_levels", "mgr_matrix_shape", "mgr_copy_matrix", "mgr_vector_len",
            "mgr_copy_vector", "mgr_memory_bytes", "mgr_memory_peak_bytes", "mgr_get_stats", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
            "mgr_bsr3_outer_grad", "mgr_profile", "mgr_profile_select", "mgr_kernel_time",
@@ -84,6 +85,8 @@ def lib():
         L.mgr_setup.argtypes = [vp, P(Bsr3), vp]
         L.mgr_apply.argtypes = [vp, vp, vp]
         L.fgmres_solve.argtypes = [vp, P(Bsr3), vp, vp, ctypes.c_double, i32, i32, P(SolveInfo)]
+        L.mgr_apply_transpose.argtypes = [vp, vp, vp]
+        L.fgmres_solve_transpose.argtypes = [vp, P(Bsr3), vp, vp, ctypes.c_double, i32, i32, P(SolveInfo)]
         L.mgr_destroy.argtypes = [vp]
         L.mgr_get_levels.argtypes = [vp, P(i32), P(i32)]
         L.mgr_matrix_shape.argtypes = [vp, i32, i32, P(i64), P(i64), P(i64)]
@@ -216,7 +219,18 @@ class MGR:
         _check(lib().mgr_apply(self._h, _ptr(r), _ptr(z)), "mgr_apply")
         return z
 
-    def fgmres(self, A: BSR3, b, x=None, rtol=1e-8, restart=30, maxit=1000, history=False, raise_on_fail=True):
+    def apply_transpose(self, r, z=None):
+        """z = M^-T r (needs options adjoint=1 at setup)."""
+        import torch
+        if z is None:
+            z = torch.empty_like(r)
+        _check(lib().mgr_apply_transpose(self._h, _ptr(r), _ptr(z)), "mgr_apply_transpose")
+        return z
+
+    def fgmres(self, A: BSR3, b, x=None, rtol=1e-8, restart=30, maxit=1000, history=False, raise_on_fail=True,
+               transpose=False):
+        """Solve A x = b (or A^T x = b with transpose=True and a handle set up with adjoint=1) by
+        FGMRES(restart) right-preconditioned with M^-1 (M^-T); x is the initial guess and the output."""
         import numpy as np
         import torch
         if x is None:
@@ -227,15 +241,15 @@ class MGR:
             hist = np.zeros(maxit + 2)
             info.history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             info.history_cap = maxit + 2
-        rc = lib().fgmres_solve(self._h, ctypes.byref(A.c()), _ptr(b), _ptr(x), rtol, restart, maxit,
-                                ctypes.byref(info))
+        fn = lib().fgmres_solve_transpose if transpose else lib().fgmres_solve
+        rc = fn(self._h, ctypes.byref(A.c()), _ptr(b), _ptr(x), rtol, restart, maxit, ctypes.byref(info))
         out = dict(status=rc, iterations=info.iterations, restarts=info.restarts, converged=bool(info.converged),
                    relres_true=info.relres_true, relres_est=info.relres_est, bnorm=info.bnorm,
                    solve_ms=info.solve_ms)
         if history:
             out["history"] = hist[: info.iterations + 1].copy()
         if raise_on_fail and rc not in (0,):
-            raise MgrError(rc, "fgmres_solve")
+            raise MgrError(rc, "fgmres_solve_transpose" if transpose else "fgmres_solve")
         return x, out
 
     def levels(self):

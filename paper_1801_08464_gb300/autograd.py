@@ -1,13 +1,15 @@
 """Adjoint differentiation of x = A(theta)^-1 b through the MGR-preconditioned solve.
 
-Forward: mgr_setup(A, cf_marker) and fgmres_solve(A, b).  Backward, for an upstream gradient
-g = dL/dx: transpose the blocks of A (mgr_bsr3_transpose), build an MGR hierarchy for A^T with the
-same cf_marker, solve A^T lambda = g with FGMRES, then dL/db = lambda and
-dL/dA_ij = -lambda_i x_j on the stored block pattern (mgr_bsr3_outer_grad).  Each hierarchy is
-released as soon as its solve returns, so the forward and the adjoint never hold device memory at
-the same time.
+Forward: mgr_setup(A, cf_marker) with the transposed operators built too (options.adjoint = 1) and
+fgmres_solve(A, b).  Backward, for an upstream gradient g = dL/dx: the same hierarchy solves
+A^T lambda = g by fgmres_solve_transpose, right-preconditioned with M^-T, the transpose of the
+forward preconditioner (A^T M^-T = (M^-1 A)^T keeps the forward spectrum); then dL/db = lambda and
+dL/dA_ij = -lambda_i x_j on the stored block pattern (mgr_bsr3_outer_grad).  The hierarchy lives from
+the forward call until the backward call returns (or until the graph is freed).
 """
 from __future__ import annotations
+
+import ctypes
 
 import torch
 
@@ -21,6 +23,14 @@ def _record(stats, key, m, info):
     stats[key] = d
 
 
+def _with_adjoint(opts):
+    from . import Options
+    o = Options()
+    ctypes.memmove(ctypes.byref(o), ctypes.byref(opts), ctypes.sizeof(Options))
+    o.adjoint = 1
+    return o
+
+
 class MgrSolve(torch.autograd.Function):
     """x = A^-1 b with A = BSR3(rowptr, colind, values); differentiable in values and b."""
 
@@ -28,35 +38,34 @@ class MgrSolve(torch.autograd.Function):
     def forward(ctx, values, b, rowptr, colind, cf_marker, opts, rtol, restart, maxit, stats):
         from . import BSR3, MGR
         A = BSR3(rowptr, colind, values.detach().reshape(-1, 3, 3).contiguous())
-        m = MGR(opts)
+        m = MGR(_with_adjoint(opts))
         m.setup(A, cf_marker)
         x, info = m.fgmres(A, b.detach().contiguous(), rtol=rtol, restart=restart, maxit=maxit)
         _record(stats, "forward", m, info)
-        m.close()
-        ctx.save_for_backward(values, x, rowptr, colind, cf_marker)
-        ctx.opts, ctx.rtol, ctx.restart, ctx.maxit, ctx.stats = opts, rtol, restart, maxit, stats
+        ctx.save_for_backward(values, x, rowptr, colind)
+        ctx.m = m
+        ctx.rtol, ctx.restart, ctx.maxit, ctx.stats = rtol, restart, maxit, stats
         ctx.forward_info = info
         return x
 
     @staticmethod
     def backward(ctx, gx):
-        from . import BSR3, MGR, bsr3_outer_grad, bsr3_transpose
-        values, x, rowptr, colind, cf_marker = ctx.saved_tensors
+        from . import BSR3, bsr3_outer_grad
+        values, x, rowptr, colind = ctx.saved_tensors
         A = BSR3(rowptr, colind, values.detach().reshape(-1, 3, 3).contiguous())
-        At = bsr3_transpose(A)
-        m = MGR(ctx.opts)
-        m.setup(At, cf_marker)
-        lam, info = m.fgmres(At, gx.contiguous(), rtol=ctx.rtol, restart=ctx.restart, maxit=ctx.maxit)
+        m = ctx.m
+        lam, info = m.fgmres(A, gx.contiguous(), rtol=ctx.rtol, restart=ctx.restart, maxit=ctx.maxit,
+                             transpose=True)
         _record(ctx.stats, "adjoint", m, info)
         m.close()
-        del At
+        ctx.m = None
         gvals = bsr3_outer_grad(A, lam, x).reshape(values.shape)
         return gvals, lam, None, None, None, None, None, None, None, None
 
 
 def mgr_solve(values, b, rowptr, colind, cf_marker, opts=None, rtol=1e-8, restart=30, maxit=1000, stats=None):
     """Differentiable x = A^-1 b.  If `stats` is a dict, it receives the forward solve's info (and,
-    after backward, the adjoint solve's) with setup time and the handle's peak device bytes."""
+    after backward, the adjoint solve's) with the setup time and the handle's peak device bytes."""
     from . import options
     o = opts if opts is not None else options()
     return MgrSolve.apply(values, b, rowptr, colind, cf_marker, o, rtol, restart, maxit, stats)

@@ -289,6 +289,94 @@ void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32
   if (nF > 0) run_rows(c, Wp, ec, EpiInterpF<T, TO>{F, eF, base, out}, name);
 }
 
+// ---- the transposed preconditioner (M^-T) ------------------------------------------------------
+template <class T>
+struct EpiGatherAdd {  // out[c] = y[C[c]] + s   (P^T y = y_C + W_p^T y_F)
+  const int32_t* C; const T* y; T* out;
+  __device__ void operator()(int64_t c, T s) const { out[c] = y[C[c]] + s; }
+  double row_bytes() const { return 4.0 + 2.0 * sizeof(T); }
+};
+template <class T>
+void launch_gather_add(Ctx& c, const RowsOp<T>& WpT, const int32_t* C, const T* y, T* out, const char* name) {
+  run_rows(c, WpT, y, EpiGatherAdd<T>{C, y, out}, name);
+}
+
+// g[C[c]] = tc[c] for c < nC, g[F[f]] = gF[f] for f < nF
+template <class T>
+__global__ void k_scatter_cf(int64_t nC, const int32_t* C, const T* tc, int64_t nF, const int32_t* F, const T* gF,
+                             T* g) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < nC) g[C[t]] = tc[t];
+  else if (t < nC + nF) g[F[t - nC]] = gF[t - nC];
+}
+template <class T>
+void launch_scatter_cf(Ctx& c, int64_t nC, const int32_t* C, const T* tc, int64_t nF, const int32_t* F, const T* gF,
+                       T* g) {
+  if (nC + nF <= 0) return;
+  ProfScope ps(c, "scatter_cf", (double)(nC + nF) * (4.0 + 2.0 * sizeof(T)));
+  k_scatter_cf<T><<<grid_for(nC + nF, 256), 256, 0, c.s>>>(nC, C, tc, nF, F, gF, g);
+  CU_LAUNCH();
+}
+
+// level-0 finish of M^-T with the global relaxation: z = g + B^T (y - A^T g), blocks of B^T given
+template <class T>
+struct EpiGRT {
+  const double* y; const T* g; const T* bt; double* z;
+  __device__ void operator()(int64_t I, T s0, T s1, T s2) const {
+    T r0 = (T)y[3 * I] - s0, r1 = (T)y[3 * I + 1] - s1, r2 = (T)y[3 * I + 2] - s2;
+    const T* b = bt + 9 * I;
+    z[3 * I + 0] = (double)(g[3 * I + 0] + (b[0] * r0 + b[1] * r1 + b[2] * r2));
+    z[3 * I + 1] = (double)(g[3 * I + 1] + (b[3] * r0 + b[4] * r1 + b[5] * r2));
+    z[3 * I + 2] = (double)(g[3 * I + 2] + (b[6] * r0 + b[7] * r1 + b[8] * r2));
+  }
+};
+template <class T>
+void launch_bsr_grt(Ctx& c, const SellPattern& S, const T* valsT, const double* y, const T* g, const T* bt,
+                    double* z) {
+  ProfScope ps(c, "global_relax_t", (double)S.nnzb_real * (9 * sizeof(T) + 4) + 8.0 * (S.nb + 1) +
+                                        (double)S.nb * (3 * sizeof(T) + 24 + 3 * sizeof(T) + 9 * sizeof(T) + 24));
+  launch_bsr_sell<T, T>(c, S, valsT, g, EpiGRT<T>{y, g, bt, z});
+}
+
+template <class T>
+__global__ void k_transpose_blocks(int64_t nb, const T* b, T* bt) {
+  int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= nb) return;
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) bt[9 * I + 3 * p + q] = b[9 * I + 3 * q + p];
+}
+template <class T>
+void launch_transpose_blocks(Ctx& c, int64_t nb, const T* b, T* bt) {
+  if (nb <= 0) return;
+  k_transpose_blocks<T><<<grid_for(nb, 256), 256, 0, c.s>>>(nb, b, bt);
+  CU_LAUNCH();
+}
+
+__global__ void k_dense_transpose(int64_t n, const double* a, double* at) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  int64_t i = t / n, j = t - i * n;
+  at[j * n + i] = a[t];
+}
+void launch_dense_transpose(Ctx& c, int64_t n, const double* a, double* at) {
+  if (n <= 0) return;
+  k_dense_transpose<<<grid_for(n * n, 256), 256, 0, c.s>>>(n, a, at);
+  CU_LAUNCH();
+}
+
+// columns j of a CSR matrix replaced by map[j]
+__global__ void k_map_cols(int64_t nnz, int32_t* ci, const int32_t* map) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < nnz) ci[k] = map[ci[k]];
+}
+void launch_map_cols(Ctx& c, int64_t nnz, int32_t* ci, const int32_t* map) {
+  if (nnz <= 0) return;
+  k_map_cols<<<grid_for(nnz, 256), 256, 0, c.s>>>(nnz, ci, map);
+  CU_LAUNCH();
+}
+
 template <class T>
 __global__ void k_to_f64(int64_t n, const T* a, double* b) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -373,6 +461,10 @@ void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b) {
   template void launch_jacobi<T>(Ctx&, const RowsOp<T>&, const T*, const T*, const T*, T*, const char*);          \
   template void launch_spmv<T>(Ctx&, const RowsOp<T>&, const T*, T*, const char*);                                \
   template void launch_prolong_add<T>(Ctx&, const RowsOp<T>&, const T*, T*, const char*);                         \
+  template void launch_gather_add<T>(Ctx&, const RowsOp<T>&, const int32_t*, const T*, T*, const char*);            \
+  template void launch_scatter_cf<T>(Ctx&, int64_t, const int32_t*, const T*, int64_t, const int32_t*, const T*, T*);  \
+  template void launch_bsr_grt<T>(Ctx&, const SellPattern&, const T*, const double*, const T*, const T*, double*);   \
+  template void launch_transpose_blocks<T>(Ctx&, int64_t, const T*, T*);                                             \
   template void launch_dense_gemv<T>(Ctx&, int64_t, const double*, const T*, T*);
 INST(float)
 INST(double)

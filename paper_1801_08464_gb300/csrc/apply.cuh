@@ -48,6 +48,19 @@ void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32
                    const T* eF, const T* ec, const T* base, TO* out, const char* name = "interp");
 template <class T>
 void launch_to_f64(Ctx& c, int64_t n, const T* a, double* b);
+// pieces of the transposed preconditioner M^-T
+template <class T>
+void launch_gather_add(Ctx& c, const RowsOp<T>& WpT, const int32_t* C, const T* y, T* out, const char* name);
+template <class T>
+void launch_scatter_cf(Ctx& c, int64_t nC, const int32_t* C, const T* tc, int64_t nF, const int32_t* F, const T* gF,
+                       T* g);
+template <class T>
+void launch_bsr_grt(Ctx& c, const SellPattern& S, const T* valsT, const double* y, const T* g, const T* bt,
+                    double* z);
+template <class T>
+void launch_transpose_blocks(Ctx& c, int64_t nb, const T* b, T* bt);
+void launch_dense_transpose(Ctx& c, int64_t n, const double* a, double* at);
+void launch_map_cols(Ctx& c, int64_t nnz, int32_t* ci, const int32_t* map);
 
 // ---- AMG -------------------------------------------------------------------------------------
 template <class T>
@@ -95,5 +108,6 @@ void launch_nrm2sq(Ctx& c, int64_t n, const double* x, double* part, double* out
 // adjoint helpers
 void launch_bsr3_outer_grad(Ctx& c, const mgr_bsr3_t& A, const double* lam, const double* x, double* g);
 void launch_bsr3_transpose(Ctx& c, const mgr_bsr3_t& A, int64_t* rpt, int32_t* cit, double* vt);
+void launch_bsr3_transpose_pattern(Ctx& c, const mgr_bsr3_t& A, int64_t* rpt, int32_t* cit, int64_t* src);
 
 }  // namespace mgr

@@ -28,6 +28,11 @@ void sell_build_pattern(Ctx& c, int64_t nb, int64_t nnzb, const int64_t* rowptr,
 // Scatters BSR values (9 per block, row-major) into the sliced value layout (slots * 32 * 9).
 template <class TS, class TD>
 void sell_fill_values(Ctx& c, const SellPattern& S, const TS* values, TD* out);
+// For the layout of A^T: src[] (positions in A^T's block order) replaced by perm[src] (A's blocks),
+// and values filled with each source block transposed.
+void sell_compose_src(Ctx& c, SellPattern& S, const int64_t* perm);
+template <class TS, class TD>
+void sell_fill_values_t(Ctx& c, const SellPattern& S, const TS* values, TD* out);
 
 // Product over the sliced layout: one thread per block row; epi(I, s0, s1, s2) gets the row sums.
 template <class T, class TX, class Epi>

@@ -23,6 +23,10 @@ struct MgrLevel {
   RowsOp<double> Aff64, Acf64, Wp64;
   DBuf<float> minv32;
   bool cast = false;              // apply copies built
+  // transposed operators of M^-T (built when the handle serves transposed solves): W_p^T with its
+  // columns as level dof numbers, A_cf^T, A_ff^T
+  RowsOp<float> WpT32, AcfT32, AffT32;
+  RowsOp<double> WpT64, AcfT64, AffT64;
 };
 
 struct AmgLevel {
@@ -34,6 +38,8 @@ struct AmgLevel {
   RowsOp<double> A64, P64, R64;
   DBuf<float> dinv32;
   bool cast = false;
+  RowsOp<float> AT32;             // A^T for the transposed V-cycle (when built)
+  RowsOp<double> AT64;
 };
 
 struct AmgOpts {

@@ -375,4 +375,32 @@ void launch_bsr3_transpose(Ctx& c, const mgr_bsr3_t& A, int64_t* rpt, int32_t* c
   CU(cudaStreamSynchronize(c.s));
 }
 
+// Pattern of A^T (row pointers, block columns ascending) and, per transposed block, the index of its
+// source block in A.
+__global__ void k_bsort_src(int64_t nb, const int64_t* trp, int32_t* tci, int64_t* src) {
+  int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (J >= nb) return;
+  int64_t b = trp[J], e = trp[J + 1];
+  for (int64_t a = b + 1; a < e; ++a) {
+    int32_t key = tci[a];
+    int64_t s = src[a];
+    int64_t t = a - 1;
+    while (t >= b && tci[t] > key) { tci[t + 1] = tci[t]; src[t + 1] = src[t]; --t; }
+    tci[t + 1] = key;
+    src[t + 1] = s;
+  }
+}
+void launch_bsr3_transpose_pattern(Ctx& c, const mgr_bsr3_t& A, int64_t* rpt, int32_t* cit, int64_t* src) {
+  DBuf<unsigned long long> cnt(c, A.nb + 1);
+  CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (A.nb + 1), c.s));
+  k_bcol_count<<<grid_for(A.nnzb, 256, 8192), 256, 0, c.s>>>(A.nnzb, A.colind, cnt.p);
+  CU_LAUNCH();
+  scan_excl_i64(c, reinterpret_cast<const int64_t*>(cnt.p), rpt, A.nb);
+  CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (A.nb + 1), c.s));
+  k_bscatter<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.colind, rpt, cnt.p, cit, src);
+  CU_LAUNCH();
+  k_bsort_src<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, rpt, cit, src);
+  CU_LAUNCH();
+}
+
 }  // namespace mgr

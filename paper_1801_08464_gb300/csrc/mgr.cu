@@ -51,6 +51,12 @@ struct mgr_handle_s {
   double setup_ms = 0.0;
   int64_t apply_launches = 0;
   Prof* prof = nullptr;
+  // transposed preconditioner M^-T (options.adjoint = 1)
+  bool has_t = false;
+  SellPattern sellT;              // A^T's pattern in the sliced layout; src holds A's block index
+  DBuf<float> valT32, binvT32;
+  DBuf<double> valT64, binvT64, kry_valsT, cinvT;
+  std::vector<DBuf<char>> w_u;
 };
 
 namespace {
@@ -103,14 +109,15 @@ static const char* const kAmgRestrict[] = {"amg0_restrict", "amg1_restrict", "am
 static const char* const kAmgProlong[] = {"amg0_prolong", "amg1_prolong", "amgc_prolong"};
 
 template <class T>
-const T* frelax(mgr_handle_s& h, int l, const T* src, const int32_t* F) {
+const T* frelax(mgr_handle_s& h, int l, const T* src, const int32_t* F, bool transposed = false) {
   MgrLevel& L = h.lev[l];
   T* a = P<T>(h.w_eF[l]);
   T* b = P<T>(h.w_eF2[l]);
   if (L.nF == 0) return a;
   const T* minv = pick_ptr<T>(L.minv, L.minv32);
   launch_frelax_first<T>(h.c, L.nF, F, src, minv, a);
-  const RowsOp<T>& Aff = tv<T>(L.Aff64, L.Aff32);
+  // the transpose of the sweeps sum_i (I - D^-1 A_ff)^i D^-1 is the same sweeps with A_ff^T
+  const RowsOp<T>& Aff = transposed ? tv<T>(L.AffT64, L.AffT32) : tv<T>(L.Aff64, L.Aff32);
   for (int s = 1; s < L.sweeps; ++s) {
     launch_frelax_sweep<T>(h.c, Aff, F, src, minv, a, b, lvl_name(kFrelax, 4, l));
     std::swap(a, b);
@@ -118,33 +125,38 @@ const T* frelax(mgr_handle_s& h, int l, const T* src, const int32_t* F) {
   return a;
 }
 
+// One V(pre, post) cycle from a zero guess on AMG level k.  transposed: the cycle's transpose, i.e.
+// V(post, pre) with A_k^T in the smoothing and residual passes, the same transfers (R = P^T) and the
+// transposed coarsest inverse.
 template <class T>
-const T* vcycle(mgr_handle_s& h, int k, const T* b) {
+const T* vcycle(mgr_handle_s& h, int k, const T* b, bool transposed = false) {
   Ctx& c = h.c;
   int last = (int)h.amg.size() - 1;
   if (k == last || h.coarse_dense) {
     T* x = P<T>(h.a_xa[k]);
-    launch_dense_gemv<T>(c, h.nco, h.cinv.p, b, x);
+    launch_dense_gemv<T>(c, h.nco, transposed ? h.cinvT.p : h.cinv.p, b, x);
     return x;
   }
   AmgLevel& A = h.amg[k];
-  const RowsOp<T>& Av = tv<T>(A.A64, A.A32);
+  const RowsOp<T>& Av = transposed ? tv<T>(A.AT64, A.AT32) : tv<T>(A.A64, A.A32);
+  const int npre = transposed ? h.o.amg_post : h.o.amg_pre;
+  const int npost = transposed ? h.o.amg_pre : h.o.amg_post;
   const T* d = pick_ptr<T>(A.dinv, A.dinv32);
   T* xa = P<T>(h.a_xa[k]);
   T* xb = P<T>(h.a_xb[k]);
   T* res = P<T>(h.a_res[k]);
   const char* nm = lvl_name(kAmgRows, 4, k);
   launch_scale<T>(c, A.n, d, b, xa);
-  for (int s = 1; s < h.o.amg_pre; ++s) {
+  for (int s = 1; s < npre; ++s) {
     launch_jacobi<T>(c, Av, d, b, xa, xb, nm);
     std::swap(xa, xb);
   }
   launch_resid<T>(c, Av, xa, b, res, nm);
   T* bc = P<T>(h.a_b[k + 1]);
   launch_spmv<T>(c, tv<T>(A.R64, A.R32), res, bc, lvl_name(kAmgRestrict, 3, k));
-  const T* xc = vcycle<T>(h, k + 1, bc);
+  const T* xc = vcycle<T>(h, k + 1, bc, transposed);
   launch_prolong_add<T>(c, tv<T>(A.P64, A.P32), xc, xa, lvl_name(kAmgProlong, 3, k));
-  for (int s = 0; s < h.o.amg_post; ++s) {
+  for (int s = 0; s < npost; ++s) {
     launch_jacobi<T>(c, Av, d, b, xa, xb, nm);
     std::swap(xa, xb);
   }
@@ -195,6 +207,52 @@ void apply_t(mgr_handle_s& h, const double* r, double* z) {
   h.apply_launches = (int64_t)(g_launch_count - l0);
 }
 
+// The transposed preconditioner.  With s = (I - A B) r, the apply above is
+//   M^-1 = B + [S_F^T Phi S_F + P_0 N_1 (S_C - A_cf Phi S_F)] (I - A B)
+// (B the block-diagonal relaxation, Phi the F-relaxation, P_0 = S_C^T + S_F^T W_p, N_1 the map of the
+// levels below), so
+//   M^-T y = g + B^T (y - A^T g),  g = S_C^T t_C + S_F^T Phi^T (y_F - A_cf^T t_C),  t_C = N_1^T (P_0^T y)
+// with P_0^T y = y_C + W_p^T y_F; each level applies the same formula recursively and the last one
+// the transposed V-cycle.
+template <class T>
+const T* level_t(mgr_handle_s& h, int l, const T* y) {
+  Ctx& c = h.c;
+  if (l == h.L) return vcycle<T>(h, 0, y, true);
+  MgrLevel& Lv = h.lev[l];
+  T* ecin = P<T>(h.w_r[l + 1]);
+  launch_gather_add<T>(c, tv<T>(Lv.WpT64, Lv.WpT32), Lv.C.p, y, ecin, lvl_name(kRestrict, 4, l));
+  const T* tc = level_t<T>(h, l + 1, ecin);
+  T* u = P<T>(h.w_u[l]);
+  launch_restrict<T>(c, tv<T>(Lv.AcfT64, Lv.AcfT32), Lv.F.p, y, tc, u, lvl_name(kRestrict, 4, l));
+  const T* gF = frelax<T>(h, l, u, nullptr, true);
+  T* g = P<T>(h.w_e[l]);
+  launch_scatter_cf<T>(c, Lv.nC, Lv.C.p, tc, Lv.nF, Lv.F.p, gF, g);
+  return g;
+}
+
+template <class T>
+void apply_tt(mgr_handle_s& h, const double* y, double* z) {
+  Ctx& c = h.c;
+  unsigned long long l0 = g_launch_count;
+  int64_t n = 3 * h.nb;
+  T* yin = P<T>(h.w_tmp_in);
+  if constexpr (std::is_same<T, float>::value) launch_cast_f32(c, n, y, yin);
+  else CU(cudaMemcpyAsync(yin, y, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.s));
+  const T* g = (h.L == 0) ? vcycle<T>(h, 0, yin, true) : level_t<T>(h, 0, yin);
+  if (h.L > 0 && h.o.global_relax) {
+    launch_bsr_grt<T>(c, h.sellT, pick_ptr<T>(h.valT64, h.valT32), y, g, pick_ptr<T>(h.binvT64, h.binvT32), z);
+  } else {
+    launch_to_f64<T>(c, n, g, z);
+  }
+  h.apply_launches = (int64_t)(g_launch_count - l0);
+}
+
+void do_apply_t(mgr_handle_s& h, const double* r, double* z) {
+  if (!h.has_t) throw Error(MGR_ERR_STATE, "the handle was set up without options.adjoint");
+  if (h.o.precision == MGR_PREC_MIXED) apply_tt<float>(h, r, z);
+  else apply_tt<double>(h, r, z);
+}
+
 void do_apply(mgr_handle_s& h, const double* r, double* z) {
   if (h.o.precision == MGR_PREC_MIXED) apply_t<float>(h, r, z);
   else apply_t<double>(h, r, z);
@@ -224,6 +282,11 @@ void alloc_work(mgr_handle_s& h) {
     }
   }
   h.w_resF0.alloc(c, es * ((L > 0 ? h.lev[0].nF : 0) + 1));
+  h.w_u.clear();
+  if (h.o.adjoint) {
+    h.w_u.resize(L + 1);
+    for (int l = 0; l < L; ++l) h.w_u[l].alloc(c, es * (h.lev[l].nF + 1));
+  }
   size_t na = std::max<size_t>(h.amg.size(), 1);
   h.a_b.clear(); h.a_xa.clear(); h.a_xb.clear(); h.a_res.clear();
   h.a_b.resize(na); h.a_xa.resize(na); h.a_xb.resize(na); h.a_res.resize(na);
@@ -258,6 +321,25 @@ void cast_mgr_level(mgr_handle_s& h, MgrLevel& L) {
     rowsop_build<double>(c, L.Acf, L.Acf64);
     rowsop_build<double>(c, L.Wp, L.Wp64);
   }
+  if (h.o.adjoint) {
+    // W_p^T (its columns renumbered from F positions to level dofs, so it reads the level vector),
+    // A_cf^T, A_ff^T
+    DCSR<double> WpT, AcfT, AffT;
+    transpose(c, L.Wp, WpT);
+    launch_map_cols(c, WpT.nnz, WpT.ci.p, L.F.p);
+    WpT.nc = L.n;
+    transpose(c, L.Acf, AcfT);
+    transpose(c, L.Aff, AffT);
+    if (h.o.precision == MGR_PREC_MIXED) {
+      rowsop_build<float>(c, WpT, L.WpT32);
+      rowsop_build<float>(c, AcfT, L.AcfT32);
+      rowsop_build<float>(c, AffT, L.AffT32);
+    } else {
+      rowsop_build<double>(c, WpT, L.WpT64);
+      rowsop_build<double>(c, AcfT, L.AcfT64);
+      rowsop_build<double>(c, AffT, L.AffT64);
+    }
+  }
   L.cast = true;
 }
 
@@ -274,6 +356,12 @@ void cast_amg_level(mgr_handle_s& h, AmgLevel& G) {
     rowsop_build<double>(c, G.A, G.A64);
     rowsop_build<double>(c, G.P, G.P64);
     rowsop_build<double>(c, G.R, G.R64);
+  }
+  if (h.o.adjoint) {
+    DCSR<double> AT;
+    transpose(c, G.A, AT);
+    if (h.o.precision == MGR_PREC_MIXED) rowsop_build<float>(c, AT, G.AT32);
+    else rowsop_build<double>(c, AT, G.AT64);
   }
   G.cast = true;
 }
@@ -293,6 +381,30 @@ void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
   }
   for (int l = 0; l < h.L; ++l) cast_mgr_level(h, h.lev[l]);
   for (size_t k = 0; k + 1 < h.amg.size(); ++k) cast_amg_level(h, h.amg[k]);
+  if (h.o.adjoint) {
+    // A^T in the sliced layout (its src renumbered to A's blocks, values transposed block by block),
+    // the transposed diagonal-block inverses and the transposed coarsest inverse
+    DBuf<int64_t> rpt(c, h.nb + 1), srcT(c, h.nnzb);
+    DBuf<int32_t> cit(c, h.nnzb);
+    launch_bsr3_transpose_pattern(c, A, rpt.p, cit.p, srcT.p);
+    sell_build_pattern(c, h.nb, h.nnzb, rpt.p, cit.p, h.sellT);
+    sell_compose_src(c, h.sellT, srcT.p);
+    int64_t nvt = 9 * SELL_C * h.sellT.slots;
+    if (mixed) {
+      h.valT32.alloc(c, nvt);
+      sell_fill_values_t<double, float>(c, h.sellT, A.values, h.valT32.p);
+      h.binvT32.alloc(c, 9 * h.nb);
+      launch_transpose_blocks<float>(c, h.nb, h.binv32.p, h.binvT32.p);
+    } else {
+      h.valT64.alloc(c, nvt);
+      sell_fill_values_t<double, double>(c, h.sellT, A.values, h.valT64.p);
+      h.binvT64.alloc(c, 9 * h.nb);
+      launch_transpose_blocks<double>(c, h.nb, h.binv.p, h.binvT64.p);
+    }
+    h.cinvT.alloc(c, (size_t)h.nco * h.nco);
+    launch_dense_transpose(c, h.nco, h.cinv.p, h.cinvT.p);
+    h.has_t = true;
+  }
 }
 
 void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
@@ -303,6 +415,9 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   h.amg.clear();
   h.cinv.release();
   h.val32.release(); h.val64.release(); h.binv32.release();
+  h.has_t = false;
+  h.valT32.release(); h.valT64.release(); h.binvT32.release(); h.binvT64.release(); h.cinvT.release();
+  h.kry_valsT.release();
   ProfScope ps_all(c, "setup_total");
   c.spgemm_stage = h.o.spgemm_stage;
   bsr3_validate(c, A, marker);
@@ -418,8 +533,9 @@ void ensure_krylov(mgr_handle_s& h, int m, int64_t n) {
   h.kry_ld = ld;
 }
 
+// tr: solve A^T x = b with the transposed preconditioner M^-T (right-preconditioned by it).
 mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, double* x, double rtol, int m, int maxit,
-                       mgr_solve_info_t* info) {
+                       mgr_solve_info_t* info, bool tr = false) {
   auto t0 = std::chrono::steady_clock::now();
   Ctx& c = h.c;
   int64_t n = 3 * A.nb;
@@ -435,11 +551,14 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
   double* V = h.V.p;
   double* Z = h.Z.p;
   const int64_t ld = h.kry_ld;
-  // A's values in the sliced layout (the pattern is the one given to mgr_setup)
-  h.kry_vals.alloc(c, 9 * SELL_C * h.sell.slots);
-  sell_fill_values<double, double>(c, h.sell, A.values, h.kry_vals.p);
+  // A's (or A^T's) values in the sliced layout (the pattern is the one given to mgr_setup)
+  const SellPattern& SP = tr ? h.sellT : h.sell;
+  DBuf<double>& KV = tr ? h.kry_valsT : h.kry_vals;
+  KV.alloc(c, 9 * SELL_C * SP.slots);
+  if (tr) sell_fill_values_t<double, double>(c, SP, A.values, KV.p);
+  else sell_fill_values<double, double>(c, SP, A.values, KV.p);
   auto spmv = [&](const double* xx, const double* sub, double* yy) {
-    launch_sell_spmv_f64(c, h.sell, h.kry_vals.p, xx, sub, yy);
+    launch_sell_spmv_f64(c, SP, KV.p, xx, sub, yy);
   };
   double* dsc = h.dsc.p;
   mgr_status_t st = MGR_OK;
@@ -476,7 +595,8 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
         double* vj = V + (int64_t)j * ld;
         double* zj = Z + (int64_t)j * ld;
         double* w = V + (int64_t)(j + 1) * ld;
-        do_apply(h, vj, zj);
+        if (tr) do_apply_t(h, vj, zj);
+        else do_apply(h, vj, zj);
         spmv(zj, nullptr, w);
         // classical Gram-Schmidt: h = V^T w and w.w in one pass; the norm of w - V h follows from
         // Pythagoras; when it drops below 1/sqrt(2) of ||w|| a second pass re-orthogonalises
@@ -705,6 +825,23 @@ mgr_status_t fgmres_solve(mgr_handle_t h, const mgr_bsr3_t* A, const double* b, 
   if (A->nb != h->nb || A->nnzb != h->nnzb || !A->rowptr || !A->colind || !A->values) return MGR_ERR_INVALID_ARG;
   mgr_status_t st = MGR_OK;
   mgr_status_t g = guarded(h, [&] { st = do_fgmres(*h, *A, b, x, rtol, restart, maxit, info); });
+  return g != MGR_OK ? g : st;
+}
+
+mgr_status_t mgr_apply_transpose(mgr_handle_t h, const double* r, double* z) {
+  if (!h || !r || !z) return MGR_ERR_INVALID_ARG;
+  if (!h->ready || !h->has_t) return MGR_ERR_STATE;
+  return guarded(h, [&] { do_apply_t(*h, r, z); });
+}
+
+mgr_status_t fgmres_solve_transpose(mgr_handle_t h, const mgr_bsr3_t* A, const double* b, double* x, double rtol,
+                                    int restart, int maxit, mgr_solve_info_t* info) {
+  if (!h || !A || !b || !x || restart < 1 || restart > KRY_MAXV || maxit < 0 || !(rtol >= 0.0))
+    return MGR_ERR_INVALID_ARG;
+  if (!h->ready || !h->has_t) return MGR_ERR_STATE;
+  if (A->nb != h->nb || A->nnzb != h->nnzb || !A->rowptr || !A->colind || !A->values) return MGR_ERR_INVALID_ARG;
+  mgr_status_t st = MGR_OK;
+  mgr_status_t g = guarded(h, [&] { st = do_fgmres(*h, *A, b, x, rtol, restart, maxit, info, true); });
   return g != MGR_OK ? g : st;
 }
 

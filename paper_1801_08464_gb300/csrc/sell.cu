@@ -73,4 +73,41 @@ void sell_fill_values(Ctx& c, const SellPattern& S, const TS* values, TD* out) {
 template void sell_fill_values<double, double>(Ctx&, const SellPattern&, const double*, double*);
 template void sell_fill_values<double, float>(Ctx&, const SellPattern&, const double*, float*);
 
+__global__ void k_sell_compose(int64_t n, int64_t* src, const int64_t* perm) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx < n && src[idx] >= 0) src[idx] = perm[src[idx]];
+}
+void sell_compose_src(Ctx& c, SellPattern& S, const int64_t* perm) {
+  int64_t n = S.slots * SELL_C;
+  if (n <= 0) return;
+  k_sell_compose<<<grid_for(n, 256), 256, 0, c.s>>>(n, S.src.p, perm);
+  CU_LAUNCH();
+}
+
+template <class TS, class TD>
+__global__ void k_sell_fill_values_t(int64_t n, const int64_t* __restrict__ src, const TS* __restrict__ v,
+                                     TD* __restrict__ out) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= n) return;
+  int64_t slot = idx / SELL_C;
+  int t = (int)(idx - slot * SELL_C);
+  int64_t k = src[idx];
+  TD* o = out + slot * 9 * SELL_C + t;
+#pragma unroll
+  for (int p = 0; p < 3; ++p)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) o[(3 * p + q) * SELL_C] = k >= 0 ? (TD)v[9 * k + 3 * q + p] : TD(0);
+}
+
+template <class TS, class TD>
+void sell_fill_values_t(Ctx& c, const SellPattern& S, const TS* values, TD* out) {
+  int64_t n = S.slots * SELL_C;
+  if (n <= 0) return;
+  k_sell_fill_values_t<TS, TD><<<grid_for(n, 256), 256, 0, c.s>>>(n, S.src.p, values, out);
+  CU_LAUNCH();
+}
+
+template void sell_fill_values_t<double, double>(Ctx&, const SellPattern&, const double*, double*);
+template void sell_fill_values_t<double, float>(Ctx&, const SellPattern&, const double*, float*);
+
 }  // namespace mgr

@@ -1,4 +1,4 @@
-"""The adjoint workload at full size on the GPU.
+"""The adjoint workloads at full size on the GPU.
 
 64^3 adjoint (786,432 unknowns, FP32 hierarchy / FP64 Krylov): the gradient of L = w . x with respect
 to the BSR values, from the MGR-preconditioned A^T solve, against central finite differences of
@@ -76,3 +76,4 @@ def test_adjoint_64cube_finite_differences():
     print(f"64^3 adjoint: forward {stats['forward']['iterations']} it, adjoint {stats['adjoint']['iterations']} it, "
           f"worst FD relative error {worst:.2e}")
     assert worst <= 1e-5, worst
+
