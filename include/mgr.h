@@ -144,12 +144,15 @@ mgr_status_t mgr_destroy(mgr_handle_t h);
  * For a handle set up on A with options.adjoint = 1.  z = M^-T r, the exact transpose of mgr_apply's
  * operator M^-1 (up to rounding): the levels in reverse roles (P_l^T = S_C + W_p^T S_F restricts, the
  * F-relaxation sweeps run with A_ff^T, the coarse residual is formed with A_cf^T, the V-cycle is
- * V(post, pre) with A_k^T, and the global relaxation closes with z = g + B^T (y - A^T g)).  It is the
- * natural preconditioner of A^T x = b: (A^T M^-T) = (M^-1 A)^T keeps the spectrum of the forward
- * preconditioned operator.  MGR_ERR_STATE without options.adjoint. */
+ * V(post, pre) with A_k^T, and the global relaxation closes with z = g + B^T (y - A^T g)).
+ * MGR_ERR_STATE without options.adjoint. */
 mgr_status_t mgr_apply_transpose(mgr_handle_t h, const double* r, double* z);
-/* Solves A^T x = b (A the matrix given to mgr_setup, with its values as passed now) by FGMRES(m)
- * right-preconditioned with M^-T; arguments, stopping rule and statuses as fgmres_solve. */
+/* Solves A^T x = b (A the matrix given to mgr_setup, with its values as passed now) by GMRES(m) on
+ * M^-T A^T x = M^-T b: the preconditioner on the left makes the operator (A M^-1)^T, the transpose of
+ * the forward solve's, which keeps its spectrum and conditioning (with M^-T on the right, restarted
+ * GMRES stalls on layered workloads whose forward solve converges).  Each restart cycle begins from
+ * the true residual and convergence is declared on ||b - A^T x|| <= rtol ||b||; arguments and
+ * statuses as fgmres_solve. */
 mgr_status_t fgmres_solve_transpose(mgr_handle_t h, const mgr_bsr3_t* A, const double* b, double* x, double rtol,
                                     int restart, int maxit, mgr_solve_info_t* info);
 

@@ -229,8 +229,9 @@ class MGR:
 
     def fgmres(self, A: BSR3, b, x=None, rtol=1e-8, restart=30, maxit=1000, history=False, raise_on_fail=True,
                transpose=False):
-        """Solve A x = b (or A^T x = b with transpose=True and a handle set up with adjoint=1) by
-        FGMRES(restart) right-preconditioned with M^-1 (M^-T); x is the initial guess and the output."""
+        """Solve A x = b by FGMRES(restart) right-preconditioned with M^-1, or, with transpose=True on a
+        handle set up with adjoint=1, A^T x = b by GMRES(restart) left-preconditioned with M^-T; x is
+        the initial guess and the output."""
         import numpy as np
         import torch
         if x is None:

@@ -533,7 +533,12 @@ void ensure_krylov(mgr_handle_s& h, int m, int64_t n) {
   h.kry_ld = ld;
 }
 
-// tr: solve A^T x = b with the transposed preconditioner M^-T (right-preconditioned by it).
+// tr: solve A^T x = b with the transposed preconditioner M^-T, applied from the left: GMRES(m) on
+// M^-T A^T x = M^-T b, the transpose of the forward right-preconditioned operator A M^-1 (with M^-T on
+// the right, (M^-1 A)^T, restarted GMRES stalls on the layered workloads where the forward solve
+// converges).  Each cycle starts from the true residual; the inner iteration stops when the
+// preconditioned residual estimate reaches rtol ||b|| scaled by the preconditioned-to-true ratio at
+// the cycle start, and the true residual decides convergence.
 mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, double* x, double rtol, int m, int maxit,
                        mgr_solve_info_t* info, bool tr = false) {
   auto t0 = std::chrono::steady_clock::now();
@@ -585,19 +590,35 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
     // (A M^-1 v_j is close to v_j, inside the basis); below 0.1 the Givens estimate was seen to run
     // ahead of the true residual on a 2-D case and force a restart.
     const double eta = 0.3;
+    const bool left = tr;
     while (!loc.converged) {
-      launch_scal(c, n, 1.0 / beta, V, V);
+      double scale = 1.0;  // true / preconditioned residual norm at the cycle start (left)
+      double beta_k = beta;
+      if (left) {
+        CU(cudaMemcpyAsync(Z, V, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.s));
+        do_apply_t(h, Z, V);
+        launch_nrm2sq(c, n, V, h.part.p, dsc);
+        rd(dsc, 1);
+        beta_k = std::sqrt(hp[0]);
+        if (!(beta_k > 0.0) || !std::isfinite(beta_k)) { st = MGR_ERR_BREAKDOWN; break; }
+        scale = beta / beta_k;
+      }
+      launch_scal(c, n, 1.0 / beta_k, V, V);
       std::fill(g.begin(), g.end(), 0.0);
-      g[0] = beta;
+      g[0] = beta_k;
       int k = 0;
       bool stop = false;
       for (int j = 0; j < m && it < maxit; ++j) {
         double* vj = V + (int64_t)j * ld;
         double* zj = Z + (int64_t)j * ld;
         double* w = V + (int64_t)(j + 1) * ld;
-        if (tr) do_apply_t(h, vj, zj);
-        else do_apply(h, vj, zj);
-        spmv(zj, nullptr, w);
+        if (left) {
+          spmv(vj, nullptr, Z);  // Z's first column as scratch: the left form needs no Z basis
+          do_apply_t(h, Z, w);
+        } else {
+          do_apply(h, vj, zj);
+          spmv(zj, nullptr, w);
+        }
         // classical Gram-Schmidt: h = V^T w and w.w in one pass; the norm of w - V h follows from
         // Pythagoras; when it drops below 1/sqrt(2) of ||w|| a second pass re-orthogonalises
         launch_mdot(c, n, V, ld, j + 1, w, true, h.part.p, dsc);
@@ -640,8 +661,8 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
         g[j] = cs[j] * g[j];
         ++it;
         k = j + 1;
-        if (info && info->history && it < info->history_cap) info->history[it] = std::fabs(g[j + 1]) / bnorm;
-        if (std::fabs(g[j + 1]) <= rtol * bnorm || nw == 0.0) break;
+        if (info && info->history && it < info->history_cap) info->history[it] = scale * std::fabs(g[j + 1]) / bnorm;
+        if (scale * std::fabs(g[j + 1]) <= rtol * bnorm || nw == 0.0) break;
       }
       if (stop) break;
       for (int i = k - 1; i >= 0; --i) {
@@ -652,9 +673,9 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
       if (k > 0) {
         memcpy(hp + 200, y.data(), sizeof(double) * k);
         CU(cudaMemcpyAsync(dsc + 200, hp + 200, sizeof(double) * k, cudaMemcpyHostToDevice, c.s));
-        launch_xupdate(c, n, Z, ld, k, dsc + 200, x);
+        launch_xupdate(c, n, left ? V : Z, ld, k, dsc + 200, x);
       }
-      loc.relres_est = (k > 0) ? std::fabs(g[k]) / bnorm : beta / bnorm;
+      loc.relres_est = (k > 0) ? scale * std::fabs(g[k]) / bnorm : beta / bnorm;
       spmv(x, b, V);
       launch_nrm2sq(c, n, V, h.part.p, dsc);
       rd(dsc, 1);

@@ -673,6 +673,31 @@ __global__ void __launch_bounds__(32 * NUM_WARPS) k_spgemm_numeric(int64_t m, co
   }
 }
 
+// Stores the u distinct (column, value) pairs K[0..u), V[0..u) (any order, u <= 128) at
+// ocol/oval in ascending column order: each lane holds up to 4 pairs and counts, in one pass over the
+// keys (broadcast shared-memory reads), how many are smaller; that count is the pair's position.
+__device__ __forceinline__ void warp_rank_store128(const int32_t* K, const double* V, int u, int lane,
+                                                   int32_t* ocol, double* oval) {
+  int32_t key[4];
+  int r[4];
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    int t = lane + 32 * h;
+    key[h] = t < u ? K[t] : INT_MAX;
+    r[h] = 0;
+  }
+  for (int j = 0; j < u; ++j) {
+    int32_t kj = K[j];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) r[h] += (kj < key[h]);
+  }
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    int t = lane + 32 * h;
+    if (t < u) { ocol[r[h]] = key[h]; oval[r[h]] = V[t]; }
+  }
+}
+
 // Fused product for the rows with at most FUSE_CAP products that k_spgemm_fused_chunk left (long A
 // rows or more than FZ_SLOTS / 2 products; it lists them): the A row is walked in ascending
 // order (ascending k); the products of one A entry have distinct columns, so the lanes add them to a
@@ -923,6 +948,12 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
     __syncwarp();
   }
   int u = base;
+  int64_t o = soff[i] - sbase;
+  if (u <= 128) {
+    warp_rank_store128(K, Vv, u, lane, scol + o, sval + o);
+    if (lane == 0) cnt[i] = u;
+    return;
+  }
   int n2 = 1;
   while (n2 < u) n2 <<= 1;
   for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
@@ -942,7 +973,6 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
       }
       __syncwarp();
     }
-  int64_t o = soff[i] - sbase;
   for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
   if (lane == 0) cnt[i] = u;
 }

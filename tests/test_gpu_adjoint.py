@@ -35,8 +35,8 @@ def test_block_transpose_and_outer_grad_kernels():
     assert np.array_equal(g, ref)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_adjoint_matches_dense_adjoint(precision):
+@pytest.mark.parametrize("precision,adjoint", [("fp64", "transpose"), ("mixed", "transpose"), ("fp64", "rebuild")])
+def test_adjoint_matches_dense_adjoint(precision, adjoint):
     import paper_1801_08464_gb300 as mg
     import torch
     p = ncpgen.make_problem(CFG8)
@@ -49,7 +49,7 @@ def test_adjoint_matches_dense_adjoint(precision):
     ci = torch.as_tensor(p.colind, device="cuda")
     mk = torch.as_tensor(p.cf_marker, device="cuda")
     opts = mg.options(precision=precision)
-    x = mg.mgr_solve(vals, bt, rp, ci, mk, opts, rtol=1e-12, maxit=2000)
+    x = mg.mgr_solve(vals, bt, rp, ci, mk, opts, rtol=1e-12, maxit=2000, adjoint=adjoint)
     loss = (x * torch.as_tensor(w, device="cuda")).sum()
     loss.backward()
     assert rel(x.detach().cpu().numpy(), xd) <= 1e-9
