@@ -99,13 +99,15 @@ __global__ void __launch_bounds__(256) k_rows(int64_t nr, const int64_t* __restr
   int sub = (int)(gt % TPR);
   bool ok = r < nr;
   T s = 0;
+  typename Epi::Pre pre{};
+  if (ok && sub == 0) pre = epi.pre(r);  // the epilogue's loads overlap the row's
   if (ok) {
     int64_t k1 = rp[r + 1];
     for (int64_t k = rp[r] + sub; k < k1; k += TPR) s += v[k] * ldg(x + ci[k]);
   }
 #pragma unroll
   for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
-  if (ok && sub == 0) epi(r, s);
+  if (ok && sub == 0) epi.post(r, s, pre);
 }
 
 // SELL form: one thread per row, slots walked four at a time (padding slots add 0 * x[0])
@@ -142,6 +144,8 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
   if (r >= nr) return;
   int64_t s = r / RS_C;
   int t = (int)(r - s * RS_C);
+  const int64_t row = perm ? (int64_t)perm[r] : r;
+  const typename Epi::Pre pre = epi.pre(row);  // the epilogue's loads overlap the row's
   int64_t j0 = soff[s], nq = (soff[s + 1] - j0) / RS_Q;
   const int32_t* cp = col + j0 * RS_C + t * RS_Q;
   const T* vp = val + j0 * RS_C + t * RS_Q;
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
     int4 c = __ldg(reinterpret_cast<const int4*>(cp + q * (RS_Q * RS_C)));
     sum += Quad<T>::dot(vp + q * (RS_Q * RS_C), c, x);
   }
-  epi(perm ? (int64_t)perm[r] : r, sum);
+  epi.post(row, sum, pre);
 }
 
 template <class T, class Epi>
@@ -187,46 +191,54 @@ static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, co
   }
 }
 
+// Row epilogues: pre(row) loads what the epilogue needs before the row's product is formed, post(row,
+// s, pre) finishes with the product s.
 template <class T>
 struct EpiFrelax {  // eFo[f] = eFi[f] + minv[f] (src_f - s)
   const int32_t* F; const T* src; const T* minv; const T* eFi; T* eFo;
-  __device__ void operator()(int64_t f, T s) const {
-    T b = F ? src[F[f]] : src[f];
-    eFo[f] = eFi[f] + minv[f] * (b - s);
-  }
+  struct Pre { T b, m, e; };
+  __device__ Pre pre(int64_t f) const { return {F ? src[F[f]] : src[f], minv[f], eFi[f]}; }
+  __device__ void post(int64_t f, T s, const Pre& p) const { eFo[f] = p.e + p.m * (p.b - s); }
   double row_bytes() const { return (F ? 4 : 0) + 4.0 * sizeof(T); }
 };
 template <class T>
 struct EpiRestrict {  // rnext[c] = base_c - s
   const int32_t* C; const T* r; T* rnext;
-  __device__ void operator()(int64_t c, T s) const {
-    T b = C ? r[C[c]] : rnext[c];
-    rnext[c] = b - s;
-  }
+  struct Pre { T b; };
+  __device__ Pre pre(int64_t c) const { return {C ? r[C[c]] : rnext[c]}; }
+  __device__ void post(int64_t c, T s, const Pre& p) const { rnext[c] = p.b - s; }
   double row_bytes() const { return (C ? 4 : 0) + 2.0 * sizeof(T); }
 };
 template <class T>
 struct EpiResid {
   const T* b; T* res;
-  __device__ void operator()(int64_t i, T s) const { res[i] = b[i] - s; }
+  struct Pre { T b; };
+  __device__ Pre pre(int64_t i) const { return {b[i]}; }
+  __device__ void post(int64_t i, T s, const Pre& p) const { res[i] = p.b - s; }
   double row_bytes() const { return 2.0 * sizeof(T); }
 };
 template <class T>
 struct EpiJacobi {
   const T* d; const T* b; const T* xi; T* xo;
-  __device__ void operator()(int64_t i, T s) const { xo[i] = xi[i] + d[i] * (b[i] - s); }
+  struct Pre { T d, b, x; };
+  __device__ Pre pre(int64_t i) const { return {d[i], b[i], xi[i]}; }
+  __device__ void post(int64_t i, T s, const Pre& p) const { xo[i] = p.x + p.d * (p.b - s); }
   double row_bytes() const { return 4.0 * sizeof(T); }
 };
 template <class T>
 struct EpiStore {
   T* y;
-  __device__ void operator()(int64_t i, T s) const { y[i] = s; }
+  struct Pre {};
+  __device__ Pre pre(int64_t) const { return {}; }
+  __device__ void post(int64_t i, T s, const Pre&) const { y[i] = s; }
   double row_bytes() const { return 1.0 * sizeof(T); }
 };
 template <class T>
 struct EpiAdd {
   T* y;
-  __device__ void operator()(int64_t i, T s) const { y[i] += s; }
+  struct Pre { T y; };
+  __device__ Pre pre(int64_t i) const { return {y[i]}; }
+  __device__ void post(int64_t i, T s, const Pre& p) const { y[i] = p.y + s; }
   double row_bytes() const { return 2.0 * sizeof(T); }
 };
 
@@ -269,11 +281,15 @@ __global__ void k_interp_c(int64_t nC, const int32_t* __restrict__ C, const T* _
 template <class T, class TO>
 struct EpiInterpF {
   const int32_t* F; const T* eF; const T* base; TO* out;
-  __device__ void operator()(int64_t f, T s) const {
+  struct Pre { int32_t d; T e, b; };
+  __device__ Pre pre(int64_t f) const {
     int32_t d = F[f];
-    T v = eF[f] + s;
-    if (base) v += base[d];
-    out[d] = (TO)v;
+    return {d, eF[f], base ? base[d] : T(0)};
+  }
+  __device__ void post(int64_t, T s, const Pre& p) const {
+    T v = p.e + s;
+    if (base) v += p.b;
+    out[p.d] = (TO)v;
   }
   double row_bytes() const { return 4.0 + sizeof(T) + (base ? sizeof(T) : 0) + sizeof(TO); }
 };
@@ -293,7 +309,9 @@ void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32
 template <class T>
 struct EpiGatherAdd {  // out[c] = y[C[c]] + s   (P^T y = y_C + W_p^T y_F)
   const int32_t* C; const T* y; T* out;
-  __device__ void operator()(int64_t c, T s) const { out[c] = y[C[c]] + s; }
+  struct Pre { T y; };
+  __device__ Pre pre(int64_t c) const { return {y[C[c]]}; }
+  __device__ void post(int64_t c, T s, const Pre& p) const { out[c] = p.y + s; }
   double row_bytes() const { return 4.0 + 2.0 * sizeof(T); }
 };
 template <class T>

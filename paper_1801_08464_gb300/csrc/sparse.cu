@@ -760,27 +760,31 @@ __global__ void __launch_bounds__(32 * FH_WARPS) k_spgemm_fused_hash(
       __syncwarp();
     }
     int u = base;
-    int n2 = 1;
-    while (n2 < u) n2 <<= 1;
-    for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
-    __syncwarp();
-    for (int k2 = 2; k2 <= n2; k2 <<= 1)
-      for (int j = k2 >> 1; j > 0; j >>= 1) {
-        for (int t = lane; t < n2; t += 32) {
-          int x = t ^ j;
-          if (x > t) {
-            bool up = (t & k2) == 0;
-            int32_t ka = K[t], kb = K[x];
-            if ((ka > kb) == up) {
-              K[t] = kb; K[x] = ka;
-              double va = Vv[t]; Vv[t] = Vv[x]; Vv[x] = va;
+    int64_t o = soff[i] - sbase;
+    if (u <= 128) {
+      warp_rank_store128(K, Vv, u, lane, scol + o, sval + o);
+    } else {
+      int n2 = 1;
+      while (n2 < u) n2 <<= 1;
+      for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
+      __syncwarp();
+      for (int k2 = 2; k2 <= n2; k2 <<= 1)
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+          for (int t = lane; t < n2; t += 32) {
+            int x = t ^ j;
+            if (x > t) {
+              bool up = (t & k2) == 0;
+              int32_t ka = K[t], kb = K[x];
+              if ((ka > kb) == up) {
+                K[t] = kb; K[x] = ka;
+                double va = Vv[t]; Vv[t] = Vv[x]; Vv[x] = va;
+              }
             }
           }
+          __syncwarp();
         }
-        __syncwarp();
-      }
-    int64_t o = soff[i] - sbase;
-    for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
+      for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
+    }
     if (lane == 0) cnt[i] = u;
     __syncwarp();
   }
