@@ -135,7 +135,7 @@ struct Quad<double> {
   }
 };
 
-template <class T, class Epi>
+template <class T, class Epi, int Q>
 __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __restrict__ soff,
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
                                                    const int32_t* __restrict__ perm, const T* __restrict__ x,
@@ -146,14 +146,19 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
   int t = (int)(r - s * RS_C);
   const int64_t row = perm ? (int64_t)perm[r] : r;
   const typename Epi::Pre pre = epi.pre(row);  // the epilogue's loads overlap the row's
-  int64_t j0 = soff[s], nq = (soff[s + 1] - j0) / RS_Q;
-  const int32_t* cp = col + j0 * RS_C + t * RS_Q;
-  const T* vp = val + j0 * RS_C + t * RS_Q;
+  int64_t j0 = soff[s], nq = (soff[s + 1] - j0) / Q;
+  const int32_t* cp = col + j0 * RS_C + t * Q;
+  const T* vp = val + j0 * RS_C + t * Q;
   T sum = 0;
+  if constexpr (Q == 4) {
 #pragma unroll 2
-  for (int64_t q = 0; q < nq; ++q) {
-    int4 c = __ldg(reinterpret_cast<const int4*>(cp + q * (RS_Q * RS_C)));
-    sum += Quad<T>::dot(vp + q * (RS_Q * RS_C), c, x);
+    for (int64_t q = 0; q < nq; ++q) {
+      int4 c = __ldg(reinterpret_cast<const int4*>(cp + q * (4 * RS_C)));
+      sum += Quad<T>::dot(vp + q * (4 * RS_C), c, x);
+    }
+  } else {
+#pragma unroll 4
+    for (int64_t j = 0; j < nq; ++j) sum += vp[j * RS_C] * ldg(x + cp[j * RS_C]);
   }
   epi.post(row, sum, pre);
 }
@@ -166,8 +171,12 @@ static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, co
                             (double)op.nr * epi.row_bytes());
   const int B = 256;
   if (op.sell) {
-    k_rows_sell<T, Epi><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
-                                                           epi);
+    if (op.q == 4)
+      k_rows_sell<T, Epi, 4><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
+                                                                epi);
+    else
+      k_rows_sell<T, Epi, 1><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
+                                                                epi);
     CU_LAUNCH();
     return;
   }

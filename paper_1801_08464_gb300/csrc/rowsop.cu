@@ -3,9 +3,10 @@
 
 namespace mgr {
 
-// slice widths (longest row of each slice, rounded up to a multiple of RS_Q); rows in slice order
-// are perm[r] when perm is given
-__global__ void k_rs_width(int64_t nr, const int64_t* rp, const int32_t* perm, int64_t nslices, int64_t* width) {
+// slice widths (longest row of each slice, rounded up to a multiple of q); rows in slice order are
+// perm[r] when perm is given
+__global__ void k_rs_width(int64_t nr, const int64_t* rp, const int32_t* perm, int q, int64_t nslices,
+                           int64_t* width) {
   int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= nslices) return;
   int64_t w = 0, e = (s + 1) * RS_C < nr ? (s + 1) * RS_C : nr;
@@ -13,7 +14,7 @@ __global__ void k_rs_width(int64_t nr, const int64_t* rp, const int32_t* perm, i
     int64_t o = perm ? perm[r] : r;
     w = max(w, rp[o + 1] - rp[o]);
   }
-  width[s] = (w + RS_Q - 1) / RS_Q * RS_Q;
+  width[s] = (w + q - 1) / q * q;
 }
 
 // order the rows of each window of RS_SIGMA rows by decreasing length, equal lengths by row index
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(RS_SIGMA) k_rs_sort(int64_t nr, const int64_t*
 
 template <class T>
 __global__ void k_rs_fill(int64_t nr, int64_t npad, const int64_t* rp, const int32_t* ci, const double* v,
-                          const int32_t* perm, const int64_t* soff, int32_t* scol, T* sval) {
+                          const int32_t* perm, int q, const int64_t* soff, int32_t* scol, T* sval) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= npad) return;
   int64_t s = r / RS_C;
@@ -55,7 +56,7 @@ __global__ void k_rs_fill(int64_t nr, int64_t npad, const int64_t* rp, const int
   int64_t o0 = r < nr ? (perm ? perm[r] : r) : 0;
   int64_t k0 = r < nr ? rp[o0] : 0, len = r < nr ? rp[o0 + 1] - k0 : 0;
   for (int64_t j = 0; j < w; ++j) {
-    int64_t o = b0 * RS_C + (j / RS_Q) * (RS_Q * RS_C) + t * RS_Q + (j % RS_Q);
+    int64_t o = b0 * RS_C + (j / q) * (q * RS_C) + t * q + (j % q);
     if (j < len) { scol[o] = ci[k0 + j]; sval[o] = (T)v[k0 + j]; }
     else { scol[o] = 0; sval[o] = T(0); }  // column 0 exists in every operator with nonzeros
   }
@@ -78,14 +79,15 @@ void rowsop_build(Ctx& c, const DCSR<double>& A, RowsOp<T>& op) {
     int64_t ns = (A.nr + RS_C - 1) / RS_C;
     DBuf<int64_t> width(c, ns + 1);
     op.soff.alloc(c, ns + 1);
-    k_rs_width<<<grid_for(ns, 256), 256, 0, c.s>>>(A.nr, A.rp, nullptr, ns, width.p);
+    op.q = ((double)A.nnz >= RS_QUAD_MIN_AVG * (double)A.nr) ? RS_Q : 1;
+    k_rs_width<<<grid_for(ns, 256), 256, 0, c.s>>>(A.nr, A.rp, nullptr, op.q, ns, width.p);
     CU_LAUNCH();
     op.slots = counts_to_rowptr(c, width.p, op.soff.p, ns);
     if ((double)(op.slots * RS_C) > RS_SORT_PAD * (double)A.nnz) {
       op.perm.alloc(c, A.nr);
       k_rs_sort<<<(unsigned)((A.nr + RS_SIGMA - 1) / RS_SIGMA), RS_SIGMA, 0, c.s>>>(A.nr, A.rp, op.perm.p);
       CU_LAUNCH();
-      k_rs_width<<<grid_for(ns, 256), 256, 0, c.s>>>(A.nr, A.rp, op.perm.p, ns, width.p);
+      k_rs_width<<<grid_for(ns, 256), 256, 0, c.s>>>(A.nr, A.rp, op.perm.p, op.q, ns, width.p);
       CU_LAUNCH();
       op.slots = counts_to_rowptr(c, width.p, op.soff.p, ns);
     }
@@ -94,8 +96,8 @@ void rowsop_build(Ctx& c, const DCSR<double>& A, RowsOp<T>& op) {
       op.scol.alloc(c, op.slots * RS_C);
       op.sval.alloc(c, op.slots * RS_C);
       int64_t np = ns * RS_C;
-      k_rs_fill<T><<<grid_for(np, 256), 256, 0, c.s>>>(A.nr, np, A.rp, A.ci, A.v, op.perm.p, op.soff.p, op.scol.p,
-                                                      op.sval.p);
+      k_rs_fill<T><<<grid_for(np, 256), 256, 0, c.s>>>(A.nr, np, A.rp, A.ci, A.v, op.perm.p, op.q, op.soff.p,
+                                                      op.scol.p, op.sval.p);
       CU_LAUNCH();
       return;
     }

@@ -1,13 +1,16 @@
 // rowsop.cuh -- scalar sparse operators of the preconditioner apply, in one of two layouts.
 //
-// SELL-8 (sliced ELL) with slots in groups of 4: rows are grouped in slices of 8 consecutive rows;
-// slice s holds W_s slots (its longest row, rounded up to a multiple of 4) starting at slot B_s (a
-// multiple of 4).  Slot j of row t (t = row within the slice) is stored at
-//   (B_s * 8) + (j / 4) * 32 + t * 4 + (j % 4)
-// in col[] and val[] (padding: column 0, value 0).  So one thread per row reads its slots four at a
-// time as one 16-byte load of columns and one 16-byte (FP32) or two 16-byte (FP64) loads of values,
-// and the 8 rows of a slice read one contiguous 128-byte line per group: few, wide, fully used loads,
-// which keep more bytes in flight per thread than one 4-byte load per slot.  Slices of 8 rather
+// SELL-8 (sliced ELL) with slots in groups of q (4, or 1 for operators with short rows): rows are
+// grouped in slices of 8 consecutive rows; slice s holds W_s slots (its longest row, rounded up to a
+// multiple of q) starting at slot B_s (a multiple of q).  Slot j of row t (t = row within the slice)
+// is stored at
+//   (B_s * 8) + (j / q) * 8q + t * q + (j % q)
+// in col[] and val[] (padding: column 0, value 0).  With q = 4 one thread per row reads its slots
+// four at a time as one 16-byte load of columns and one 16-byte (FP32) or two 16-byte (FP64) loads
+// of values, and the 8 rows of a slice read one contiguous 128-byte line per group: few, wide, fully
+// used loads, which keep more bytes in flight per thread than one 4-byte load per slot.  Rows of a
+// few entries (transfers, restrictions: 1 to 7 entries) keep q = 1, which pads nothing once the
+// rows are ordered by length.  Slices of 8 rather
 // than 32 keep the padding of the pressure-level operators (rows of 25 to 63 entries side by side)
 // near 10 %.
 // Sorted slices: when rows of very different lengths sit side by side (AMG operators and transfers,
@@ -23,7 +26,8 @@
 namespace mgr {
 
 constexpr int RS_C = 8;
-constexpr int RS_Q = 4;  // slots per group
+constexpr int RS_Q = 4;  // slots per group for operators with long rows
+constexpr double RS_QUAD_MIN_AVG = 8.0;  // average row length from which the 4-slot groups pay
 constexpr double RS_MAX_PAD = 1.3;
 constexpr double RS_SORT_PAD = 1.1;  // above this padding the rows are ordered by length
 constexpr int RS_SIGMA = 256;
@@ -37,6 +41,7 @@ struct RowsOp {
   bool sell = false;
   // SELL-8 with 4-slot groups
   int64_t slots = 0;
+  int q = RS_Q;        // slots per group: RS_Q, or 1 for short rows (where groups of 4 would pad)
   DBuf<int64_t> soff;
   DBuf<int32_t> perm;  // empty when rows keep their order
   DBuf<int32_t> scol;
