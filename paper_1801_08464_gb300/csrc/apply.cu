@@ -182,16 +182,17 @@ static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, co
   }
   const DCSR<T>& M = op.csr;
   double avg = M.nr ? (double)M.nnz / (double)M.nr : 0.0;
-  if (avg <= 2.5) {
+  // lanes per row: about four entries per lane or more
+  if (avg <= 5.0) {
     k_rows<T, 2, Epi><<<grid_for(M.nr * 2, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
-  } else if (avg <= 6.0) {
+  } else if (avg <= 12.0) {
     k_rows<T, 4, Epi><<<grid_for(M.nr * 4, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
-  } else if (avg <= 12.0) {
+  } else if (avg <= 24.0) {
     k_rows<T, 8, Epi><<<grid_for(M.nr * 8, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
-  } else if (avg <= 40.0) {
+  } else if (avg <= 128.0) {
     k_rows<T, 16, Epi><<<grid_for(M.nr * 16, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
   } else {

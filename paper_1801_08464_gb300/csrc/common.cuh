@@ -236,7 +236,6 @@ void bsr3_block_inverse(Ctx& c, const mgr_bsr3_t& A, double* binv);      // sets
 // C = A B (Gustavson order); `name` labels the call in the per-kernel timing
 void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C, const char* name = "spgemm");
 // Pattern of C = A * B only (values left unallocated), same pattern rules.
-void spgemm_symbolic(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C);
 void transpose(Ctx& c, const DCSR<double>& A, DCSR<double>& T);          // rows sorted by column
 // Sort each row segment [rp[i], rp[i+1]) of (ci, v) by ci (keys unique within a row).
 void sort_rows(Ctx& c, int64_t nr, const int64_t* rp, int32_t* ci, double* v);

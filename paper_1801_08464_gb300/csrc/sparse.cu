@@ -130,20 +130,6 @@ void bsr3_block_inverse(Ctx& c, const mgr_bsr3_t& A, double* binv) {
 
 // ---------------------------------------------------------------------------------------------
 // Sorting helpers (bitonic networks in shared memory).
-__device__ __forceinline__ void warp_bitonic_keys(int32_t* key, int n, int lane) {
-  for (int k = 2; k <= n; k <<= 1)
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = lane; t < n; t += 32) {
-        int x = t ^ j;
-        if (x > t) {
-          bool up = (t & k) == 0;
-          int32_t a = key[t], b = key[x];
-          if ((a > b) == up) { key[t] = b; key[x] = a; }
-        }
-      }
-      __syncwarp();
-    }
-}
 __device__ __forceinline__ void block_bitonic_keys(int32_t* key, int n) {
   for (int k = 2; k <= n; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
@@ -165,13 +151,13 @@ __device__ __forceinline__ int next_pow2(int x) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// SpGEMM symbolic: the pattern of row i of C is the sorted union of the columns of the rows of B
-// selected by row i of A.  Three kernels by per-row work bound ub_i = sum of the B row lengths:
-// a warp with a shared-memory hash table (ub <= SYM_WCAP), a block with a larger table
-// (ub <= SYM_BCAP), and a block with a bitmap over the columns of C (nc <= SYM_BITS).
-constexpr int SYM_WCAP = 1024;
-constexpr int SYM_WHASH = 2048;
-constexpr int SYM_WARPS = 4;
+// SpGEMM.  Rows with at most FUSE_CAP products (ub_i = sum of the B row lengths selected by row i of
+// A) are formed in one pass by the fused kernels below.  Longer rows take a symbolic pass (the
+// sorted union of the selected B rows' columns: a block with a shared hash table for
+// ub <= SYM_BCAP, a block with a bitmap over the columns of C for nc <= SYM_BITS, else a bounded
+// 32K-slot hash) and a numeric pass.
+constexpr int FUSE_CAP = 2048;  // rows with up to FUSE_CAP products take the fused (one-pass) kernels
+constexpr int64_t SPGEMM_STAGE = 128ll << 20;  // staged products per batch of fused rows
 constexpr int SYM_BCAP = 8192;
 constexpr int SYM_BHASH = 16384;
 constexpr int64_t SYM_BITS = 1 << 20;
@@ -187,113 +173,10 @@ __global__ void k_spgemm_ub(int64_t m, const int64_t* arp, const int32_t* aci, c
   }
   ub[i] = s;
   if (s > SYM_BCAP) big[atomicAdd(n_big, 1)] = (int32_t)i;
-  else if (s > SYM_WCAP) mid[atomicAdd(n_mid, 1)] = (int32_t)i;
+  else if (s > FUSE_CAP) mid[atomicAdd(n_mid, 1)] = (int32_t)i;
 }
 
 __device__ __forceinline__ uint32_t hash32(int32_t k) { return (uint32_t)k * 2654435761u; }
-
-// MODE 0: count unique columns into cnt[i]; MODE 1: write the sorted unique columns at crp[i].
-// Rows with at most SYM_SORT candidates copy them into shared memory, sort them (bitonic) and keep
-// the first of each run of equal columns; longer rows (up to SYM_WCAP) insert into a hash table
-// sized to twice the row's candidate count, then sort the distinct keys.
-constexpr int SYM_SORT = 128;
-constexpr int FUSE_CAP = 1024;  // rows with up to FUSE_CAP products take the fused (one-pass) kernels
-constexpr int64_t SPGEMM_STAGE = 128ll << 20;  // staged products per batch of fused rows
-
-template <int MODE>
-__global__ void __launch_bounds__(32 * SYM_WARPS) k_sym_warp(int64_t m, const int64_t* arp, const int32_t* aci,
-                                                              const int64_t* brp, const int32_t* bci,
-                                                              const int64_t* ub, int64_t* cnt, const int64_t* crp,
-                                                              int32_t* cci, int skip_small) {
-  __shared__ int32_t tab[SYM_WARPS][SYM_WHASH];
-  __shared__ int ucount[SYM_WARPS];
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t i = (int64_t)blockIdx.x * SYM_WARPS + w;
-  if (i >= m) return;
-  int U = (int)ub[i];
-  if (U > SYM_WCAP) return;  // handled by the block / bitmap kernels
-  if (skip_small && U <= FUSE_CAP) return;  // handled by the fused kernel
-  int32_t* T = tab[w];
-  int64_t a0 = arp[i], a1 = arp[i + 1];
-  if (U <= SYM_SORT) {
-    // lane p copies the B row selected by A entry p to its offset (exclusive scan of the lengths), so
-    // the rows are gathered in parallel rather than one after another
-    int carry = 0;
-    for (int64_t p0 = a0; p0 < a1; p0 += 32) {
-      int64_t p = p0 + lane;
-      int64_t b0 = 0;
-      int len = 0;
-      if (p < a1) {
-        int32_t k = aci[p];
-        b0 = brp[k];
-        len = (int)(brp[k + 1] - b0);
-      }
-      int x = len;
-      for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      int off = carry + x - len;
-      for (int q = 0; q < len; ++q) T[off + q] = bci[b0 + q];
-      carry += __shfl_sync(0xffffffffu, x, 31);
-    }
-    int n2 = next_pow2(U);
-    for (int t = U + lane; t < n2; t += 32) T[t] = INT_MAX;
-    __syncwarp();
-    warp_bitonic_keys(T, n2, lane);
-    int64_t o = (MODE == 1) ? crp[i] : 0;
-    int u = 0;
-    for (int t0 = 0; t0 < U; t0 += 32) {
-      int t = t0 + lane;
-      bool first = t < U && (t == 0 || T[t] != T[t - 1]);
-      unsigned msk = __ballot_sync(0xffffffffu, first);
-      if (MODE == 1 && first) cci[o + u + __popc(msk & ((1u << lane) - 1))] = T[t];
-      u += __popc(msk);
-    }
-    if (MODE == 0 && lane == 0) cnt[i] = u;
-    return;
-  }
-  int H = next_pow2(2 * U);
-  for (int t = lane; t < H; t += 32) T[t] = -1;
-  if (lane == 0) ucount[w] = 0;
-  __syncwarp();
-  // lane p inserts the B row selected by A entry p (rows handled in parallel)
-  for (int64_t p = a0 + lane; p < a1; p += 32) {
-    int32_t k = aci[p];
-    for (int64_t q = brp[k]; q < brp[k + 1]; ++q) {
-      int32_t key = bci[q];
-      uint32_t h = hash32(key) & (H - 1);
-      while (true) {
-        int32_t prev = atomicCAS(&T[h], -1, key);
-        if (prev == -1) { atomicAdd(&ucount[w], 1); break; }
-        if (prev == key) break;
-        h = (h + 1) & (H - 1);
-      }
-    }
-  }
-  __syncwarp();
-  int u = ucount[w];
-  if (MODE == 0) {
-    if (lane == 0) cnt[i] = u;
-    return;
-  }
-  // in-place compaction: a chunk is read into registers before any write, and every write goes to a
-  // position below the end of the chunk being read
-  int base = 0;
-  for (int t = 0; t < H; t += 32) {
-    int32_t key = (t + lane < H) ? T[t + lane] : -1;
-    unsigned msk = __ballot_sync(0xffffffffu, key >= 0);
-    if (key >= 0) T[base + __popc(msk & ((1u << lane) - 1))] = key;
-    base += __popc(msk);
-    __syncwarp();
-  }
-  int n2 = next_pow2(u);
-  for (int t = u + lane; t < n2; t += 32) T[t] = INT_MAX;
-  __syncwarp();
-  warp_bitonic_keys(T, n2, lane);
-  int64_t o = crp[i];
-  for (int t = lane; t < u; t += 32) cci[o + t] = T[t];
-}
 
 template <int MODE>
 __global__ void k_sym_block(const int32_t* rows, const int64_t* arp, const int32_t* aci, const int64_t* brp,
@@ -472,17 +355,11 @@ __global__ void __launch_bounds__(1024) k_sym_bitmap(const int32_t* rows, int64_
   }
 }
 
-static void sym_pass(Ctx& c, int mode, const DCSR<double>& A, const DCSR<double>& B, const int64_t* ub,
-                     const int32_t* mid, int nmid, const int32_t* big, int nbig, int64_t* cnt, DCSR<double>& C,
-                     int skip_small = 0) {
-  int64_t m = A.nr;
-  unsigned g = grid_for(m, SYM_WARPS);
-  ProfScope ps(c, mode == 0 ? "sym_count_warp" : "sym_fill_warp");
-  if (mode == 0)
-    k_sym_warp<0><<<g, 32 * SYM_WARPS, 0, c.s>>>(m, A.rp, A.ci, B.rp, B.ci, ub, cnt, nullptr, nullptr, skip_small);
-  else
-    k_sym_warp<1><<<g, 32 * SYM_WARPS, 0, c.s>>>(m, A.rp, A.ci, B.rp, B.ci, ub, nullptr, C.rp, C.ci, skip_small);
-  CU_LAUNCH();
+// Symbolic pass for the rows with more than FUSE_CAP products: count (mode 0) or write the sorted
+// distinct columns (mode 1) of the listed rows.
+static void sym_pass(Ctx& c, int mode, const DCSR<double>& A, const DCSR<double>& B, const int32_t* mid, int nmid,
+                     const int32_t* big, int nbig, int64_t* cnt, DCSR<double>& C) {
+  ProfScope ps(c, mode == 0 ? "sym_count" : "sym_fill");
   if (nmid > 0) {
     ProfScope ps2(c, "sym_block");
     size_t sh = sizeof(int32_t) * (SYM_BHASH + SYM_BCAP);
@@ -522,37 +399,6 @@ static void sym_pass(Ctx& c, int mode, const DCSR<double>& A, const DCSR<double>
       CU_LAUNCH();
     }
   }
-}
-
-void spgemm_symbolic(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C) {
-  if (A.nc != B.nr) throw Error(MGR_ERR_INVALID_ARG, "spgemm: inner dimensions differ");
-  ProfScope ps(c, "spgemm_symbolic");
-  int64_t m = A.nr;
-  C.nr = m;
-  C.nc = B.nc;
-  C.rp.alloc(c, m + 1);
-  if (m == 0) {
-    fill_i64(c, C.rp.p, 0, 1);
-    C.nnz = 0;
-    C.ci.alloc(c, 0);
-    return;
-  }
-  DBuf<int64_t> ub(c, m), cnt(c, m);
-  DBuf<int32_t> mid(c, m), big(c, m);
-  DBuf<int> counters(c, 2);
-  CU(cudaMemsetAsync(counters.p, 0, 2 * sizeof(int), c.s));
-  {
-    ProfScope ps(c, "sym_ub");
-    k_spgemm_ub<<<grid_for(m, 256), 256, 0, c.s>>>(m, A.rp, A.ci, B.rp, ub.p, counters.p, mid.p, counters.p + 1, big.p);
-  }
-  CU_LAUNCH();
-  int hc[2];
-  CU(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, c.s));
-  CU(cudaStreamSynchronize(c.s));
-  sym_pass(c, 0, A, B, ub.p, mid.p, hc[0], big.p, hc[1], cnt.p, C);
-  C.nnz = counts_to_rowptr(c, cnt.p, C.rp.p, m);
-  C.ci.alloc(c, C.nnz);
-  sym_pass(c, 1, A, B, ub.p, mid.p, hc[0], big.p, hc[1], nullptr, C);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -703,10 +549,12 @@ __device__ __forceinline__ void warp_rank_store128(const int32_t* K, const doubl
 // order (ascending k); the products of one A entry have distinct columns, so the lanes add them to a
 // shared-memory hash table (column -> running sum) without conflicts, and __syncwarp orders successive
 // k.  Each sum therefore starts from 0.0 and adds its products in ascending k (Gustavson's order).
-// The distinct columns are then compacted, sorted (bitonic, values carried) and staged.
-constexpr int FH_WARPS = 2;
-constexpr int FH_SLOTS = 2 * FUSE_CAP;
+// The distinct columns are then compacted, sorted (rank placement up to 128, else bitonic, values
+// carried) and staged.  Two shapes: 2 warps with 2048 slots each for rows of at most FH_CAP
+// products, one warp with 4096 slots for the rest up to FUSE_CAP (48 KB of shared memory either way).
+constexpr int FH_CAP = 1024;
 
+template <int FH_WARPS, int FH_SLOTS>
 __global__ void __launch_bounds__(32 * FH_WARPS) k_spgemm_fused_hash(
     const int32_t* __restrict__ rows, const int* __restrict__ nrows, const int64_t* __restrict__ arp,
     const int32_t* __restrict__ aci, const double* __restrict__ av, const int64_t* __restrict__ brp,
@@ -848,7 +696,8 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
     int64_t r0, int64_t m, int64_t sbase, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
     const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
     const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
-    double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ rest, int* __restrict__ nrest) {
+    double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ rest, int* __restrict__ nrest,
+    int32_t* __restrict__ rest2, int* __restrict__ nrest2) {
   __shared__ int32_t hk[FZ_WARPS][FZ_SLOTS];
   __shared__ double hv[FZ_WARPS][FZ_SLOTS];
   __shared__ int32_t sst[FZ_WARPS][FZ_CAPA + 1];
@@ -863,7 +712,10 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
   int64_t a0 = arp[i];
   int na = (int)(arp[i + 1] - a0);
   if (U > FZ_SLOTS / 2 || na > FZ_CAPA) {  // the row goes to the larger kernels
-    if (U <= FUSE_CAP && lane == 0) rest[atomicAdd(nrest, 1)] = (int32_t)i;
+    if (lane == 0) {
+      if (U <= FH_CAP) rest[atomicAdd(nrest, 1)] = (int32_t)i;
+      else if (U <= FUSE_CAP) rest2[atomicAdd(nrest2, 1)] = (int32_t)i;
+    }
     return;
   }
   int32_t* K = hk[w];
@@ -1091,23 +943,27 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
   std::vector<DBuf<int64_t>> poff(nbatch > 1 ? nbatch : 0);
   std::vector<DBuf<int32_t>> pcol(poff.size());
   std::vector<DBuf<double>> pval(poff.size());
-  DBuf<int32_t> rest(c, m);
-  DBuf<int> nrest(c, 1);
+  DBuf<int32_t> rest(c, m), rest2(c, m);
+  DBuf<int> nrest(c, 2);
   for (int64_t b = 0; b < nbatch; ++b) {
     const int64_t i0 = bst[b], i1 = bst[b + 1], base = bbase[b];
     if (i1 <= i0) continue;
     {
       ProfScope ps2(c, "fused_small");
-      CU(cudaMemsetAsync(nrest.p, 0, sizeof(int), c.s));
+      CU(cudaMemsetAsync(nrest.p, 0, 2 * sizeof(int), c.s));
       k_spgemm_tiny<<<grid_for(i1 - i0, TT_THREADS), TT_THREADS, 0, c.s>>>(i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci,
                                                                            B.v, ub.p, soff.p, scol.p, sval.p, cnt.p);
       CU_LAUNCH();
       k_spgemm_fused_chunk<<<grid_for(i1 - i0, FZ_WARPS), 32 * FZ_WARPS, 0, c.s>>>(
-          i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, rest.p, nrest.p);
+          i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, rest.p, nrest.p,
+          rest2.p, nrest.p + 1);
       CU_LAUNCH();
-      // 4 blocks of 48 KB shared memory per SM on 152 SMs, 4 rounds
-      k_spgemm_fused_hash<<<grid_for(i1 - i0, FH_WARPS, 152 * 16), 32 * FH_WARPS, 0, c.s>>>(
+      // a fixed grid over each list: 4 blocks of 48 KB shared memory per SM on 152 SMs, 4 rounds
+      k_spgemm_fused_hash<2, 2 * FH_CAP><<<grid_for(i1 - i0, 2, 152 * 16), 64, 0, c.s>>>(
           rest.p, nrest.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, base, scol.p, sval.p, cnt.p);
+      CU_LAUNCH();
+      k_spgemm_fused_hash<1, 2 * FUSE_CAP><<<grid_for(i1 - i0, 1, 152 * 16), 32, 0, c.s>>>(
+          rest2.p, nrest.p + 1, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, base, scol.p, sval.p, cnt.p);
       CU_LAUNCH();
     }
     if (nbatch > 1) {
@@ -1129,11 +985,11 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
     scol.release();
     sval.release();
   }
-  sym_pass(c, 0, A, B, ub.p, mid.p, hc[0], big.p, hc[1], cnt.p, C, 1);
+  sym_pass(c, 0, A, B, mid.p, hc[0], big.p, hc[1], cnt.p, C);
   C.nnz = counts_to_rowptr(c, cnt.p, C.rp.p, m);
   C.ci.alloc(c, C.nnz);
   C.v.alloc(c, C.nnz);
-  sym_pass(c, 1, A, B, ub.p, mid.p, hc[0], big.p, hc[1], nullptr, C, 1);
+  sym_pass(c, 1, A, B, mid.p, hc[0], big.p, hc[1], nullptr, C);
   {
     ProfScope ps3(c, "fused_copy");
     if (nbatch == 1) {

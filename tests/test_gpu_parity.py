@@ -59,6 +59,7 @@ def test_setup_parity(name, optname):
     np.testing.assert_allclose(m.vector(mg.VEC_BINV, 0).cpu().numpy(), o.vec(oracle.VEC_BINV, 0), rtol=1e-13,
                                atol=1e-13 * np.abs(o.vec(oracle.VEC_BINV, 0)).max())
     print(f"{name}/{optname}: fraction of bit-identical setup values {np.mean(same):.6f}")
+    assert min(same) == 1.0, "setup values are computed by the same IEEE operations as the oracle's"
     m.close()
 
 
