@@ -258,6 +258,37 @@ __global__ void k_strength(int64_t n, const int64_t* rp, const int32_t* ci, cons
   int lane = threadIdx.x & 31;
   if (i >= n) return;
   int64_t b = rp[i], e = rp[i + 1];
+  int64_t count = 0, out = (MODE == 1) ? srp[i] : 0;
+  if (e - b <= 64) {
+    // the row (at most 64 entries) is read once into registers, two entries per lane
+    const int64_t k0 = b + lane, k1 = b + 32 + lane;
+    const int32_t c0 = k0 < e ? ci[k0] : -1, c1 = k1 < e ? ci[k1] : -1;
+    const double v0 = k0 < e ? v[k0] : 0.0, v1 = k1 < e ? v[k1] : 0.0;
+    double d = (c0 == (int32_t)i) ? v0 : ((c1 == (int32_t)i) ? v1 : 0.0);
+    for (int o = 16; o > 0; o >>= 1) {
+      double t = __shfl_xor_sync(0xffffffffu, d, o);
+      if (t != 0.0) d = t;
+    }
+    const double s = (d >= 0.0) ? 1.0 : -1.0;
+    double m = 0.0;
+    if (c0 >= 0 && c0 != (int32_t)i) m = fmax(m, -dm(s, v0));
+    if (c1 >= 0 && c1 != (int32_t)i) m = fmax(m, -dm(s, v1));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (m > 0.0) {
+      const double thr = dm(theta, m);
+      const bool st0 = c0 >= 0 && c0 != (int32_t)i && -dm(s, v0) >= thr;
+      const bool st1 = c1 >= 0 && c1 != (int32_t)i && -dm(s, v1) >= thr;
+      const unsigned m0 = __ballot_sync(0xffffffffu, st0), m1 = __ballot_sync(0xffffffffu, st1);
+      if (MODE == 1) {
+        const unsigned below = (1u << lane) - 1;
+        if (st0) sci[out + __popc(m0 & below)] = c0;
+        if (st1) sci[out + __popc(m0) + __popc(m1 & below)] = c1;
+      }
+      count = __popc(m0) + __popc(m1);
+    }
+    if (MODE == 0 && lane == 0) cnt[i] = count;
+    return;
+  }
   double d = 0.0;
   for (int64_t k = b + lane; k < e; k += 32)
     if (ci[k] == i) d = v[k];
@@ -273,7 +304,6 @@ __global__ void k_strength(int64_t n, const int64_t* rp, const int32_t* ci, cons
       if (x > m) m = x;
     }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  int64_t count = 0, out = (MODE == 1) ? srp[i] : 0;
   if (m > 0.0) {
     double thr = dm(theta, m);
     for (int64_t k0 = b; k0 < e; k0 += 32) {
