@@ -193,8 +193,8 @@ mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_laun
  *   setup:  "setup_total", "setup_mgr_level", "setup_mgr_rap", "setup_amg", "setup_amg_strength",
  *           "setup_amg_pmis", "setup_amg_extpi", "extpi_pattern", "extpi_weights",
  *           "setup_amg_transpose", "setup_amg_rap", "setup_dense_inverse", "setup_cast_alloc",
- *           "spgemm", "fused_small", "fused_copy", "spgemm_numeric", "sym_ub", "sym_count_warp",
- *           "sym_fill_warp", "sym_block", "sym_bitmap"; per product: "rap_mgr<l>_AP",
+ *           "spgemm", "fused_small", "fused_copy", "spgemm_numeric", "sym_ub", "sym_count",
+ *           "sym_fill", "sym_block", "sym_bitmap"; per product: "rap_mgr<l>_AP",
  *           "rap_mgr<l>_RAP" (l = 0..2), "rap_amg0_AP", "rap_amg0_PtAP", "rap_amg1_AP", "rap_amg1_PtAP",
  *           "rap_amgc_AP", "rap_amgc_PtAP" (AMG levels 2 and coarser together), "spgemm_extpi".
  * Unknown names report 0 launches. */

@@ -620,7 +620,7 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
           spmv(zj, nullptr, w);
         }
         // classical Gram-Schmidt: h = V^T w and w.w in one pass; the norm of w - V h follows from
-        // Pythagoras; when it drops below 1/sqrt(2) of ||w|| a second pass re-orthogonalises
+        // Pythagoras; when it drops below eta ||w|| a second pass re-orthogonalises
         launch_mdot(c, n, V, ld, j + 1, w, true, h.part.p, dsc);
         launch_pyth_scale(c, j + 1, dsc, dsc + j + 1, dsc + 64);
         rd(dsc, 66);
