@@ -62,7 +62,9 @@ typedef struct {
 typedef struct {
   int32_t precision;                     /* mgr_precision_t; MIXED = FP32 hierarchy, FP64 Krylov */
   int32_t global_relax;                  /* Algorithm step (1) at the finest level (default 1) */
-  int32_t frelax_type[MGR_MAX_LEVELS];   /* 0 omega-Jacobi, 1 l1-Jacobi (defaults 0, 1, 1) */
+  int32_t frelax_type[MGR_MAX_LEVELS];   /* 0 omega-Jacobi, 1 l1-Jacobi, 2 one AMG V(1,1)-cycle on
+                                            A_ff per sweep (section 6.2; the AMG settings below,
+                                            PMIS seed amg_seed + 7919 (l + 1)); defaults 0, 1, 1 */
   int32_t frelax_sweeps[MGR_MAX_LEVELS]; /* F-relaxation sweeps (defaults 1, 2, 2) */
   double frelax_omega[MGR_MAX_LEVELS];   /* Jacobi weight (default 1) */
   int32_t restrict_type[MGR_MAX_LEVELS]; /* 0 injective W_r = 0, 1 W_r = -A_cf D_ff^-1 (eqs.

@@ -44,7 +44,7 @@
 
 typedef struct {
   int32_t global_relax;        /* Algorithm step (1) at the finest level */
-  int32_t frelax_type[MAXLEV]; /* 0: omega-Jacobi, 1: l1-Jacobi */
+  int32_t frelax_type[MAXLEV]; /* 0: omega-Jacobi, 1: l1-Jacobi, 2: AMG V(1,1)-cycle on A_ff */
   int32_t frelax_sweeps[MAXLEV];
   double frelax_omega[MAXLEV];
   int32_t restrict_type[MAXLEV]; /* 0: injective W_r = 0; 1: W_r = -A_cf D_ff^-1 */
@@ -586,6 +586,7 @@ typedef struct {
   csr_t Wp, Wr, P, R;
   double* aff_lu;     /* ideal mode: dense LU of A_ff */
   int32_t* aff_piv;
+  void* famg;         /* frelax_type 2: AMG hierarchy on A_ff (amg_t) */
 } olev_t;
 
 typedef struct {
@@ -642,6 +643,7 @@ static void lev_free(olev_t* l) {
   csr_free(&l->A); csr_free(&l->Wp); csr_free(&l->Wr); csr_free(&l->P); csr_free(&l->R);
   free(l->mk); free(l->F); free(l->C); free(l->cidx); free(l->fidx); free(l->minv);
   free(l->aff_lu); free(l->aff_piv);
+  amg_free((amg_t*)l->famg);
   memset(l, 0, sizeof *l);
 }
 
@@ -694,6 +696,35 @@ static int reduce_level(omgr_t* m, int l) {
     } else {
       L->minv[f] = o->frelax_omega[l] / d;
     }
+  }
+  /* frelax_type 2 (section 6.2): the F-relaxation is one AMG V(1,1)-cycle on A_ff (F rows and
+   * columns, in F order), built with the same AMG settings and a PMIS seed of its own per level */
+  if (o->frelax_type[l] == 2 && !o->ideal && nF > 0) {
+    csr_t Aff;
+    int64_t cnt = 0;
+    for (int64_t f = 0; f < nF; ++f) {
+      int64_t i = L->F[f];
+      for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) cnt += (L->fidx[A->ci[k]] >= 0);
+    }
+    csr_alloc(&Aff, nF, nF, cnt);
+    int64_t q = 0;
+    for (int64_t f = 0; f < nF; ++f) {
+      int64_t i = L->F[f];
+      for (int64_t k = A->rp[i]; k < A->rp[i + 1]; ++k) {
+        int32_t g = L->fidx[A->ci[k]];
+        if (g >= 0) { Aff.ci[q] = g; Aff.v[q] = A->v[k]; ++q; }
+      }
+      Aff.rp[f + 1] = q;
+    }
+    oopts_t of = *o;
+    of.amg_seed = o->amg_seed + 7919ull * (uint64_t)(l + 1);
+    of.amg_pre = 1;
+    of.amg_post = 1;
+    amg_t* g = NULL;
+    int rc = amg_setup(&Aff, &of, &g);
+    csr_free(&Aff);
+    if (rc) { free(dff); return rc; }
+    L->famg = g;
   }
   /* W_p (nF x nC) */
   if (!o->ideal) {
@@ -872,6 +903,11 @@ static void level_solve(const omgr_t* m, int l, const double* r, double* e) {
     if (m->o.ideal) {
       lu_solve(L->nF, L->aff_lu, L->aff_piv, rf);
       for (int64_t f = 0; f < L->nF; ++f) e[L->F[f]] += rf[f];
+    } else if (L->famg) {
+      double* ef = (double*)xmalloc(sizeof(double) * (size_t)L->nF);
+      amg_vcycle((const amg_t*)L->famg, 0, rf, ef);
+      for (int64_t f = 0; f < L->nF; ++f) e[L->F[f]] += ef[f];
+      free(ef);
     } else {
       for (int64_t f = 0; f < L->nF; ++f) e[L->F[f]] += L->minv[f] * rf[f];
     }

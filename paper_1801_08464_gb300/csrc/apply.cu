@@ -315,6 +315,30 @@ void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32
   if (nF > 0) run_rows(c, Wp, ec, EpiInterpF<T, TO>{F, eF, base, out}, name);
 }
 
+// dst[f] = src[idx[f]], and y += x
+template <class T>
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ idx, const T* __restrict__ src, T* __restrict__ dst) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f < n) dst[f] = src[idx[f]];
+}
+template <class T>
+void launch_gather(Ctx& c, int64_t n, const int32_t* idx, const T* src, T* dst) {
+  if (n <= 0) return;
+  k_gather<T><<<grid_for(n, 256), 256, 0, c.s>>>(n, idx, src, dst);
+  CU_LAUNCH();
+}
+template <class T>
+__global__ void k_axpy1(int64_t n, const T* __restrict__ x, T* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] += x[i];
+}
+template <class T>
+void launch_axpy(Ctx& c, int64_t n, const T* x, T* y) {
+  if (n <= 0) return;
+  k_axpy1<T><<<grid_for(n, 256), 256, 0, c.s>>>(n, x, y);
+  CU_LAUNCH();
+}
+
 // ---- the transposed preconditioner (M^-T) ------------------------------------------------------
 template <class T>
 struct EpiGatherAdd {  // out[c] = y[C[c]] + s   (P^T y = y_C + W_p^T y_F)
@@ -493,6 +517,8 @@ void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b) {
   template void launch_scatter_cf<T>(Ctx&, int64_t, const int32_t*, const T*, int64_t, const int32_t*, const T*, T*);  \
   template void launch_bsr_grt<T>(Ctx&, const SellPattern&, const T*, const double*, const T*, const T*, double*);   \
   template void launch_transpose_blocks<T>(Ctx&, int64_t, const T*, T*);                                             \
+  template void launch_gather<T>(Ctx&, int64_t, const int32_t*, const T*, T*);                                       \
+  template void launch_axpy<T>(Ctx&, int64_t, const T*, T*);                                                         \
   template void launch_dense_gemv<T>(Ctx&, int64_t, const double*, const T*, T*);
 INST(float)
 INST(double)

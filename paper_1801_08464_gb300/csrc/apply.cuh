@@ -60,6 +60,10 @@ void launch_bsr_grt(Ctx& c, const SellPattern& S, const T* valsT, const double* 
 template <class T>
 void launch_transpose_blocks(Ctx& c, int64_t nb, const T* b, T* bt);
 void launch_dense_transpose(Ctx& c, int64_t n, const double* a, double* at);
+template <class T>
+void launch_gather(Ctx& c, int64_t n, const int32_t* idx, const T* src, T* dst);  // dst[f] = src[idx[f]]
+template <class T>
+void launch_axpy(Ctx& c, int64_t n, const T* x, T* y);                            // y += x
 void launch_map_cols(Ctx& c, int64_t nnz, int32_t* ci, const int32_t* map);
 
 // ---- AMG -------------------------------------------------------------------------------------

@@ -8,6 +8,19 @@
 
 namespace mgr {
 
+struct AmgLevel {
+  int64_t n = 0;
+  DCSR<double> A, P, R, S;        // operator, interpolation, restriction = P^T, strength pattern
+  DBuf<int8_t> cf;                // 1 = C, -1 = F
+  DBuf<double> dinv;              // smoother scaling
+  RowsOp<float> A32, P32, R32;    // apply copies (working precision)
+  RowsOp<double> A64, P64, R64;
+  DBuf<float> dinv32;
+  bool cast = false;
+  RowsOp<float> AT32;             // A^T for the transposed V-cycle (when built)
+  RowsOp<double> AT64;
+};
+
 // One reduction level of section 5: F = {marker == l}, C = {marker > l} among the level's dofs.
 struct MgrLevel {
   int64_t n = 0, nF = 0, nC = 0;
@@ -27,20 +40,16 @@ struct MgrLevel {
   // columns as level dof numbers, A_cf^T, A_ff^T
   RowsOp<float> WpT32, AcfT32, AffT32;
   RowsOp<double> WpT64, AcfT64, AffT64;
+  // frelax_type 2 (section 6.2): the F-relaxation is an AMG V(1,1)-cycle on A_ff per sweep; its
+  // hierarchy, coarsest inverse (and transpose) and work buffers
+  std::vector<AmgLevel> famg;
+  DBuf<double> fcinv, fcinvT;
+  int64_t fnco = 0;
+  std::vector<DBuf<char>> fa_b, fa_xa, fa_xb, fa_res;
+  DBuf<char> w_fsrc, w_fres;
 };
 
-struct AmgLevel {
-  int64_t n = 0;
-  DCSR<double> A, P, R, S;        // operator, interpolation, restriction = P^T, strength pattern
-  DBuf<int8_t> cf;                // 1 = C, -1 = F
-  DBuf<double> dinv;              // smoother scaling
-  RowsOp<float> A32, P32, R32;    // apply copies (working precision)
-  RowsOp<double> A64, P64, R64;
-  DBuf<float> dinv32;
-  bool cast = false;
-  RowsOp<float> AT32;             // A^T for the transposed V-cycle (when built)
-  RowsOp<double> AT64;
-};
+
 
 struct AmgOpts {
   double theta = 0.25;

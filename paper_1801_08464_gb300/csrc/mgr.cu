@@ -109,11 +109,35 @@ static const char* const kAmgRestrict[] = {"amg0_restrict", "amg1_restrict", "am
 static const char* const kAmgProlong[] = {"amg0_prolong", "amg1_prolong", "amgc_prolong"};
 
 template <class T>
+const T* vcycle_ref(mgr_handle_s& h, MgrLevel& L, const T* b, bool transposed);
+
+template <class T>
 const T* frelax(mgr_handle_s& h, int l, const T* src, const int32_t* F, bool transposed = false) {
   MgrLevel& L = h.lev[l];
   T* a = P<T>(h.w_eF[l]);
   T* b = P<T>(h.w_eF2[l]);
   if (L.nF == 0) return a;
+  if (!L.famg.empty()) {
+    // frelax_type 2: e_F = V(src_F), then e_F += V(src_F - A_ff e_F) for further sweeps (with A_ff^T
+    // and the transposed cycle in M^-T: the same recurrence, transposed term by term)
+    const T* sF = src;
+    if (F) {
+      T* gsrc = P<T>(L.w_fsrc);
+      launch_gather<T>(h.c, L.nF, F, src, gsrc);
+      sF = gsrc;
+    }
+    const T* v = vcycle_ref<T>(h, L, sF, transposed);
+    if (L.sweeps <= 1) return v;
+    CU(cudaMemcpyAsync(a, v, sizeof(T) * L.nF, cudaMemcpyDeviceToDevice, h.c.s));
+    const RowsOp<T>& Aop = transposed ? tv<T>(L.AffT64, L.AffT32) : tv<T>(L.Aff64, L.Aff32);
+    T* rres = P<T>(L.w_fres);
+    for (int s = 1; s < L.sweeps; ++s) {
+      launch_resid<T>(h.c, Aop, a, sF, rres, lvl_name(kFrelax, 4, l));
+      const T* dv = vcycle_ref<T>(h, L, rres, transposed);
+      launch_axpy<T>(h.c, L.nF, dv, a);
+    }
+    return a;
+  }
   const T* minv = pick_ptr<T>(L.minv, L.minv32);
   launch_frelax_first<T>(h.c, L.nF, F, src, minv, a);
   // the transpose of the sweeps sum_i (I - D^-1 A_ff)^i D^-1 is the same sweeps with A_ff^T
@@ -125,42 +149,70 @@ const T* frelax(mgr_handle_s& h, int l, const T* src, const int32_t* F, bool tra
   return a;
 }
 
+// An AMG hierarchy with its coarsest inverse and work buffers: the coarse-grid solver of the last
+// MGR level, or the A_ff solver of an F-relaxation (frelax_type 2).
+struct AmgRef {
+  std::vector<AmgLevel>* lv;
+  const double* cinv;
+  const double* cinvT;
+  int64_t nco;
+  bool dense;
+  std::vector<DBuf<char>>* b;
+  std::vector<DBuf<char>>* xa;
+  std::vector<DBuf<char>>* xb;
+  std::vector<DBuf<char>>* res;
+  int pre, post;
+  bool coarse;  // timing names of the coarse solver (else "famg_*")
+};
+static AmgRef coarse_ref(mgr_handle_s& h) {
+  return {&h.amg, h.cinv.p, h.cinvT.p, h.nco, h.coarse_dense, &h.a_b, &h.a_xa, &h.a_xb, &h.a_res,
+          h.o.amg_pre, h.o.amg_post, true};
+}
+static AmgRef famg_ref(MgrLevel& L) {
+  return {&L.famg, L.fcinv.p, L.fcinvT.p, L.fnco, false, &L.fa_b, &L.fa_xa, &L.fa_xb, &L.fa_res, 1, 1, false};
+}
+
 // One V(pre, post) cycle from a zero guess on AMG level k.  transposed: the cycle's transpose, i.e.
 // V(post, pre) with A_k^T in the smoothing and residual passes, the same transfers (R = P^T) and the
 // transposed coarsest inverse.
 template <class T>
-const T* vcycle(mgr_handle_s& h, int k, const T* b, bool transposed = false) {
+const T* vcycle(mgr_handle_s& h, const AmgRef& g, int k, const T* b, bool transposed = false) {
   Ctx& c = h.c;
-  int last = (int)h.amg.size() - 1;
-  if (k == last || h.coarse_dense) {
-    T* x = P<T>(h.a_xa[k]);
-    launch_dense_gemv<T>(c, h.nco, transposed ? h.cinvT.p : h.cinv.p, b, x);
+  int last = (int)g.lv->size() - 1;
+  if (k == last || g.dense) {
+    T* x = P<T>((*g.xa)[k]);
+    launch_dense_gemv<T>(c, g.nco, transposed ? g.cinvT : g.cinv, b, x);
     return x;
   }
-  AmgLevel& A = h.amg[k];
+  AmgLevel& A = (*g.lv)[k];
   const RowsOp<T>& Av = transposed ? tv<T>(A.AT64, A.AT32) : tv<T>(A.A64, A.A32);
-  const int npre = transposed ? h.o.amg_post : h.o.amg_pre;
-  const int npost = transposed ? h.o.amg_pre : h.o.amg_post;
+  const int npre = transposed ? g.post : g.pre;
+  const int npost = transposed ? g.pre : g.post;
   const T* d = pick_ptr<T>(A.dinv, A.dinv32);
-  T* xa = P<T>(h.a_xa[k]);
-  T* xb = P<T>(h.a_xb[k]);
-  T* res = P<T>(h.a_res[k]);
-  const char* nm = lvl_name(kAmgRows, 4, k);
+  T* xa = P<T>((*g.xa)[k]);
+  T* xb = P<T>((*g.xb)[k]);
+  T* res = P<T>((*g.res)[k]);
+  const char* nm = g.coarse ? lvl_name(kAmgRows, 4, k) : "famg_rows";
   launch_scale<T>(c, A.n, d, b, xa);
   for (int s = 1; s < npre; ++s) {
     launch_jacobi<T>(c, Av, d, b, xa, xb, nm);
     std::swap(xa, xb);
   }
   launch_resid<T>(c, Av, xa, b, res, nm);
-  T* bc = P<T>(h.a_b[k + 1]);
-  launch_spmv<T>(c, tv<T>(A.R64, A.R32), res, bc, lvl_name(kAmgRestrict, 3, k));
-  const T* xc = vcycle<T>(h, k + 1, bc, transposed);
-  launch_prolong_add<T>(c, tv<T>(A.P64, A.P32), xc, xa, lvl_name(kAmgProlong, 3, k));
+  T* bc = P<T>((*g.b)[k + 1]);
+  launch_spmv<T>(c, tv<T>(A.R64, A.R32), res, bc, g.coarse ? lvl_name(kAmgRestrict, 3, k) : "famg_transfer");
+  const T* xc = vcycle<T>(h, g, k + 1, bc, transposed);
+  launch_prolong_add<T>(c, tv<T>(A.P64, A.P32), xc, xa, g.coarse ? lvl_name(kAmgProlong, 3, k) : "famg_transfer");
   for (int s = 0; s < npost; ++s) {
     launch_jacobi<T>(c, Av, d, b, xa, xb, nm);
     std::swap(xa, xb);
   }
   return xa;
+}
+
+template <class T>
+const T* vcycle_ref(mgr_handle_s& h, MgrLevel& L, const T* b, bool transposed) {
+  return vcycle<T>(h, famg_ref(L), 0, b, transposed);
 }
 
 template <class T>
@@ -172,7 +224,7 @@ void apply_t(mgr_handle_s& h, const double* r, double* z) {
     T* rin = P<T>(h.w_tmp_in);
     if constexpr (std::is_same<T, float>::value) launch_cast_f32(c, 3 * h.nb, r, rin);
     else CU(cudaMemcpyAsync(rin, r, sizeof(double) * 3 * h.nb, cudaMemcpyDeviceToDevice, c.s));
-    const T* e = vcycle<T>(h, 0, rin);
+    const T* e = vcycle<T>(h, coarse_ref(h), 0, rin);
     launch_to_f64<T>(c, 3 * h.nb, e, z);
     h.apply_launches = (int64_t)(g_launch_count - l0);
     return;
@@ -195,7 +247,7 @@ void apply_t(mgr_handle_s& h, const double* r, double* z) {
     launch_restrict<T>(c, tv<T>(Ll.Acf64, Ll.Acf32), Ll.C.p, rl, eF[l], P<T>(h.w_r[l + 1]),
                        lvl_name(kRestrict, 4, l));
   }
-  const T* ec = vcycle<T>(h, 0, P<T>(h.w_r[L]));
+  const T* ec = vcycle<T>(h, coarse_ref(h), 0, P<T>(h.w_r[L]));
   for (int l = L - 1; l >= 1; --l) {
     MgrLevel& Ll = h.lev[l];
     T* el = P<T>(h.w_e[l]);
@@ -217,7 +269,7 @@ void apply_t(mgr_handle_s& h, const double* r, double* z) {
 template <class T>
 const T* level_t(mgr_handle_s& h, int l, const T* y) {
   Ctx& c = h.c;
-  if (l == h.L) return vcycle<T>(h, 0, y, true);
+  if (l == h.L) return vcycle<T>(h, coarse_ref(h), 0, y, true);
   MgrLevel& Lv = h.lev[l];
   T* ecin = P<T>(h.w_r[l + 1]);
   launch_gather_add<T>(c, tv<T>(Lv.WpT64, Lv.WpT32), Lv.C.p, y, ecin, lvl_name(kRestrict, 4, l));
@@ -238,7 +290,7 @@ void apply_tt(mgr_handle_s& h, const double* y, double* z) {
   T* yin = P<T>(h.w_tmp_in);
   if constexpr (std::is_same<T, float>::value) launch_cast_f32(c, n, y, yin);
   else CU(cudaMemcpyAsync(yin, y, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.s));
-  const T* g = (h.L == 0) ? vcycle<T>(h, 0, yin, true) : level_t<T>(h, 0, yin);
+  const T* g = (h.L == 0) ? vcycle<T>(h, coarse_ref(h), 0, yin, true) : level_t<T>(h, 0, yin);
   if (h.L > 0 && h.o.global_relax) {
     launch_bsr_grt<T>(c, h.sellT, pick_ptr<T>(h.valT64, h.valT32), y, g, pick_ptr<T>(h.binvT64, h.binvT32), z);
   } else {
@@ -282,6 +334,22 @@ void alloc_work(mgr_handle_s& h) {
     }
   }
   h.w_resF0.alloc(c, es * ((L > 0 ? h.lev[0].nF : 0) + 1));
+  for (int l = 0; l < L; ++l) {
+    MgrLevel& Lv = h.lev[l];
+    size_t nf = Lv.famg.size();
+    Lv.fa_b.clear(); Lv.fa_xa.clear(); Lv.fa_xb.clear(); Lv.fa_res.clear();
+    if (nf == 0) continue;
+    Lv.fa_b.resize(nf); Lv.fa_xa.resize(nf); Lv.fa_xb.resize(nf); Lv.fa_res.resize(nf);
+    for (size_t k = 0; k < nf; ++k) {
+      int64_t nk = Lv.famg[k].n;
+      Lv.fa_b[k].alloc(c, es * nk);
+      Lv.fa_xa[k].alloc(c, es * nk);
+      Lv.fa_xb[k].alloc(c, es * nk);
+      Lv.fa_res[k].alloc(c, es * nk);
+    }
+    Lv.w_fsrc.alloc(c, es * (Lv.nF + 1));
+    Lv.w_fres.alloc(c, es * (Lv.nF + 1));
+  }
   h.w_u.clear();
   if (h.o.adjoint) {
     h.w_u.resize(L + 1);
@@ -379,7 +447,10 @@ void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
     h.val64.alloc(c, nv);
     sell_fill_values<double, double>(c, h.sell, A.values, h.val64.p);
   }
-  for (int l = 0; l < h.L; ++l) cast_mgr_level(h, h.lev[l]);
+  for (int l = 0; l < h.L; ++l) {
+    cast_mgr_level(h, h.lev[l]);
+    for (size_t k = 0; k + 1 < h.lev[l].famg.size(); ++k) cast_amg_level(h, h.lev[l].famg[k]);
+  }
   for (size_t k = 0; k + 1 < h.amg.size(); ++k) cast_amg_level(h, h.amg[k]);
   if (h.o.adjoint) {
     // A^T in the sliced layout (its src renumbered to A's blocks, values transposed block by block),
@@ -404,6 +475,47 @@ void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
     h.cinvT.alloc(c, (size_t)h.nco * h.nco);
     launch_dense_transpose(c, h.nco, h.cinv.p, h.cinvT.p);
     h.has_t = true;
+  }
+}
+
+AmgOpts amg_opts(const mgr_options_t& o) {
+  AmgOpts ao;
+  ao.theta = o.amg_theta;
+  ao.max_levels = o.amg_max_levels;
+  ao.max_coarse = o.amg_max_coarse;
+  ao.smoother = o.amg_smoother;
+  ao.pre = o.amg_pre;
+  ao.post = o.amg_post;
+  ao.pmax = o.amg_pmax;
+  ao.omega = o.amg_omega;
+  ao.seed = o.amg_seed;
+  return ao;
+}
+
+// frelax_type 2: the AMG hierarchy of the level's A_ff (same settings as the coarse solver, V(1,1),
+// PMIS seed amg_seed + 7919 (l + 1)) with its coarsest inverse (and transpose for M^-T)
+void build_famg(mgr_handle_s& h, int l) {
+  Ctx& c = h.c;
+  MgrLevel& L = h.lev[l];
+  if (L.nF == 0) return;
+  AmgOpts af = amg_opts(h.o);
+  af.seed = h.o.amg_seed + 7919ull * (uint64_t)(l + 1);
+  af.pre = af.post = 1;
+  ProfScope ps(c, "setup_famg");
+  if (h.o.lean) {
+    amg_build(c, L.Aff, false, af, L.famg, L.fcinv, L.fnco, [&](AmgLevel& G) {
+      cast_amg_level(h, G);
+      release_csr(G.A);
+      release_csr(G.P);
+      release_csr(G.R);
+      release_csr(G.S);
+    });
+  } else {
+    amg_build(c, L.Aff, false, af, L.famg, L.fcinv, L.fnco, nullptr);
+  }
+  if (h.o.adjoint) {
+    L.fcinvT.alloc(c, (size_t)L.fnco * L.fnco);
+    launch_dense_transpose(c, L.fnco, L.fcinv.p, L.fcinvT.p);
   }
 }
 
@@ -459,6 +571,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     mgr_reduce_level(c, h.lev[l], l, lo, h.lev[l + 1].A, mk_next);
     h.lev[l + 1].n = h.lev[l].nC;
     h.lev[l + 1].mk = std::move(mk_next);
+    if (h.o.frelax_type[l] == 2) build_famg(h, l);
     if (h.o.lean) {  // the level's FP64 operators are not read again
       MgrLevel& Lv = h.lev[l];
       cast_mgr_level(h, Lv);
@@ -481,16 +594,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     check_errors(c, "dense coarse inverse");
   } else {
     h.coarse_dense = false;
-    AmgOpts ao;
-    ao.theta = h.o.amg_theta;
-    ao.max_levels = h.o.amg_max_levels;
-    ao.max_coarse = h.o.amg_max_coarse;
-    ao.smoother = h.o.amg_smoother;
-    ao.pre = h.o.amg_pre;
-    ao.post = h.o.amg_post;
-    ao.pmax = h.o.amg_pmax;
-    ao.omega = h.o.amg_omega;
-    ao.seed = h.o.amg_seed;
+    const AmgOpts ao = amg_opts(h.o);
     ProfScope ps(c, "setup_amg");
     if (h.o.lean) {
       // the AMG takes the pressure operator over, and each level's FP64 matrices are freed once the
@@ -785,7 +889,7 @@ static mgr_status_t check_options(const mgr_options_t& o) {
   if (o.precision != MGR_PREC_FP64 && o.precision != MGR_PREC_MIXED) return MGR_ERR_INVALID_ARG;
   for (int l = 0; l < MGR_MAX_LEVELS; ++l) {
     if (o.frelax_sweeps[l] < 1 || o.frelax_sweeps[l] > 64) return MGR_ERR_INVALID_ARG;
-    if (o.frelax_type[l] < 0 || o.frelax_type[l] > 1) return MGR_ERR_INVALID_ARG;
+    if (o.frelax_type[l] < 0 || o.frelax_type[l] > 2) return MGR_ERR_INVALID_ARG;
     if (o.restrict_type[l] < 0 || o.restrict_type[l] > 1) return MGR_ERR_INVALID_ARG;
   }
   if (o.apply_full_R != 0) return MGR_ERR_UNSUPPORTED;

@@ -105,8 +105,8 @@ def test_adjoint_matches_finite_differences():
     assert worst <= 1e-5, worst
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_transposed_preconditioner_is_the_transpose(precision):
+@pytest.mark.parametrize("precision,frelax", [("fp64", [0, 1, 1]), ("mixed", [0, 1, 1]), ("fp64", [0, 2, 2])])
+def test_transposed_preconditioner_is_the_transpose(precision, frelax):
     """mgr_apply_transpose is the transpose of mgr_apply's operator: the dense matrices of both, built
     column by column on a small 3-level problem with a multi-level AMG, agree to rounding."""
     import paper_1801_08464_gb300 as mg
@@ -114,7 +114,8 @@ def test_transposed_preconditioner_is_the_transpose(precision):
     p = ncpgen.make_problem(ncpgen.GridConfig(6, 5, 4, sigma=1.0, layer_contrast=1e-2, absent_frac=0.4, absent_mode=1,
                                               seed=4))
     A, mk = to_gpu(p)
-    m = mg.MGR(precision=precision, adjoint=1, amg_max_coarse=8, restrict_type=[1, 1, 0])
+    m = mg.MGR(precision=precision, adjoint=1, amg_max_coarse=8, restrict_type=[1, 1, 0], frelax_type=frelax,
+               frelax_sweeps=[1, 2, 2])
     m.setup(A, mk)
     L, na = m.levels()
     assert L == 3 and na >= 3

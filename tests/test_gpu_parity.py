@@ -14,6 +14,11 @@ from gpu_common import PARITY, compare_csr, rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
+# The paper's phase-transition setting (section 6.2): non-injective R at all levels, one AMG
+# V(1,1)-cycle on A_ff as the F-relaxation of levels 2 and 3, V(2,2) on the coarse system.
+PAPER_62 = dict(frelax_type=[0, 2, 2], frelax_sweeps=[1, 1, 1], restrict_type=[1, 1, 1], amg_pre=2, amg_post=2,
+                amg_max_coarse=16)
+
 OPTION_SETS = {
     "default": {},
     "jacobi_trunc": dict(frelax_type=[0, 0, 0], frelax_omega=[1.0, 0.8, 0.8], amg_theta=0.5, amg_pmax=4,
@@ -64,10 +69,11 @@ def test_setup_parity(name, optname):
 
 
 @pytest.mark.parametrize("name", list(PARITY))
-def test_apply_parity_fp64(name):
+@pytest.mark.parametrize("optname", ["default", "paper_62"])
+def test_apply_parity_fp64(name, optname):
     import torch
     p = ncpgen.make_problem(PARITY[name])
-    A, mk, m, o = _pair(p)
+    A, mk, m, o = _pair(p, **(PAPER_62 if optname == "paper_62" else {}))
     for seed in (2, 7):
         r = ncpgen.normals(p.n, seed)
         z = m.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
@@ -94,10 +100,11 @@ def test_global_relaxation_step(name):
 
 
 @pytest.mark.parametrize("name", list(PARITY))
-def test_fgmres_parity_fp64(name):
+@pytest.mark.parametrize("optname", ["default", "paper_62"])
+def test_fgmres_parity_fp64(name, optname):
     import torch
     p = ncpgen.make_problem(PARITY[name])
-    A, mk, m, o = _pair(p)
+    A, mk, m, o = _pair(p, **(PAPER_62 if optname == "paper_62" else {}))
     b = ncpgen.normals(p.n, 2)
     bt = torch.as_tensor(b, device="cuda")
     Asp = p.to_scipy()

@@ -379,3 +379,30 @@ def test_strength_threshold(wy, strong):
     ny_links = int((np.abs(S.row - S.col) == nx).sum())
     assert ny_links == (2 * nx * (ny - 1) if strong else 0)
     assert int((np.abs(S.row - S.col) == 1).sum()) == 2 * (nx - 1) * ny
+
+
+@pytest.mark.parametrize("cfg", TINY)
+@pytest.mark.parametrize("rtype", [0, 1])
+def test_amg_frelaxation_exact_limit_is_two_level_formula(cfg, rtype):
+    """F-relaxation by AMG (frelax_type 2, section 6.2): when the AMG on A_ff is a single dense level
+    (amg_max_coarse >= nF) the F-solve is exact, and with an exact coarse solve and no global
+    relaxation one apply of the one-level MGR (markers 0 and 1 only) is the two-level multiplicative
+    formula z_F = A_ff^-1 r_F + W_p e_c, z_C = e_c, e_c = A_c^-1 (r_C - A_cf A_ff^-1 r_F),
+    with A_c = R A P the oracle's own coarse operator (checked separately by P2-P4)."""
+    p = ncpgen.make_problem(cfg)
+    marker = np.where(p.cf_marker == 0, 0, 1).astype(np.int8)  # one reduction: the Henry rows
+    o = oracle.OracleMGR(p.rowptr, p.colind, p.values, marker, frelax_type=[2], frelax_sweeps=[1],
+                         restrict_type=[rtype], global_relax=0, coarse_solver=1, amg_max_coarse=100000)
+    assert o.info()[0] == 1
+    A = p.to_scipy().toarray()
+    F, C = np.nonzero(marker == 0)[0], np.nonzero(marker == 1)[0]
+    Ac = o.scipy(oracle.MAT_LEVEL, 1).toarray()
+    Wp = o.scipy(oracle.MAT_WP, 0).toarray()
+    r = ncpgen.normals(p.n, 3)
+    eF = np.linalg.solve(A[np.ix_(F, F)], r[F])
+    ec = np.linalg.solve(Ac, r[C] - A[np.ix_(C, F)] @ eF)
+    z = np.empty(p.n)
+    z[C] = ec
+    z[F] = eF + Wp @ ec
+    zo = o.apply(r)
+    assert np.linalg.norm(zo - z) <= 1e-10 * np.linalg.norm(z)
