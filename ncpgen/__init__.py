@@ -39,7 +39,11 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("sigma", ctypes.c_double), ("layer_contrast", ctypes.c_double),
                 ("absent_frac", ctypes.c_double), ("absent_mode", ctypes.c_int32),
-                ("pad_", ctypes.c_int32), ("seed", ctypes.c_uint64), ("phi", ctypes.c_double)]
+                ("pad_", ctypes.c_int32), ("seed", ctypes.c_uint64), ("phi", ctypes.c_double),
+                ("closure", ctypes.c_int32), ("state_mode", ctypes.c_int32), ("vg_n", ctypes.c_double),
+                ("s_lr", ctypes.c_double), ("s_gr", ctypes.c_double), ("p_r", ctypes.c_double),
+                ("s_l1", ctypes.c_double), ("s_l2", ctypes.c_double), ("closed", ctypes.c_int32),
+                ("pad2_", ctypes.c_int32)]
 
 
 def _load():
@@ -49,7 +53,8 @@ def _load():
         P = ctypes.POINTER
         lib.ncp_count.argtypes = [P(_Cfg), P(ctypes.c_int64), P(ctypes.c_int64)]
         lib.ncp_build.argtypes = [P(_Cfg)] + [ctypes.c_void_p] * 6
-        lib.ncp_residual.argtypes = [P(_Cfg), ctypes.c_void_p, ctypes.c_void_p]
+        lib.ncp_residual.argtypes = [P(_Cfg), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.ncp_jacobian.argtypes = [P(_Cfg)] + [ctypes.c_void_p] * 6
         lib.ncp_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
         lib.ncp_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
         lib.ncp_cf_marker.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
@@ -69,14 +74,27 @@ class GridConfig:
     absent_mode: int = 0          # 0 = i.i.d. cells, 1 = seeded blob
     seed: int = 1
     phi: float = 0.3
+    closure: int = 0              # 0 = Corey n = 2 + linear P_c, 1 = Van Genuchten (regularised P_c)
+    state_mode: int = 0           # 0 = seeded state, 1 = two sub-domains at s_l1 / s_l2 (section 6.1)
+    vg_n: float = 1.54
+    s_lr: float = 0.01
+    s_gr: float = 0.0
+    p_r: float = 2.0
+    s_l1: float = 0.962
+    s_l2: float = 0.842
+    closed: int = 0               # 1 = no-flow boundary everywhere
 
     def _c(self) -> _Cfg:
         return _Cfg(self.nx, self.ny, self.nz, self.sigma, self.layer_contrast, self.absent_frac,
-                    self.absent_mode, 0, self.seed, self.phi)
+                    self.absent_mode, 0, self.seed, self.phi, self.closure, self.state_mode, self.vg_n,
+                    self.s_lr, self.s_gr, self.p_r, self.s_l1, self.s_l2, self.closed, 0)
 
 
 # The five workloads: 32x32 plain FP64; 64^3 FP64 with AMG; 128^3 mixed precision (headline);
-# 64^3 adjoint; 256^3 mixed precision forward + adjoint.
+# 64^3 adjoint; 256^3 mixed precision forward + adjoint.  Then the unsaturated two-level family of
+# section 6.1 (Van Genuchten closures with n = 1.54, S_lr = 0.01, S_gr = 0, entry pressure 2 in
+# units of the 1e6 Pa liquid pressure; homogeneous permeability; closed boundary; gas present
+# everywhere; sub-domains at S_l = 0.962 and 0.842) on its four meshes.
 WORKLOADS = {
     "ncp2d_32x32": GridConfig(32, 32, 1, sigma=1.0, absent_frac=0.3, absent_mode=0),
     "ncp3d_64": GridConfig(64, 64, 64, sigma=2.0, absent_frac=0.5, absent_mode=1),
@@ -84,6 +102,9 @@ WORKLOADS = {
     "ncp3d_64_adjoint": GridConfig(64, 64, 64, sigma=2.0, absent_frac=0.5, absent_mode=1),
     "ncp3d_256_layered": GridConfig(256, 256, 256, sigma=2.0, layer_contrast=1e-6, absent_frac=0.5, absent_mode=1),
 }
+for _nx, _ny in ((200, 10), (400, 20), (800, 40), (1600, 80)):
+    WORKLOADS[f"unsat2d_{_nx}x{_ny}"] = GridConfig(_nx, _ny, 1, sigma=0.0, absent_frac=0.0, closure=1, state_mode=1,
+                                                  closed=1)
 
 
 @dataclasses.dataclass
@@ -134,14 +155,55 @@ def make_problem(cfg: GridConfig) -> Problem:
     return Problem(cfg, nb, rowptr, colind, values, gp, marker, state, perm)
 
 
-def residual(cfg: GridConfig, u: np.ndarray) -> np.ndarray:
-    """Nonlinear residual R(u) (for finite-difference checks of the Jacobian)."""
+def residual(cfg: GridConfig, u: np.ndarray, u_old: np.ndarray | None = None) -> np.ndarray:
+    """Nonlinear residual R(u) of one backward Euler step; u_old (optional) is the previous time
+    level, whose mass is subtracted."""
     lib = _load()
     u = np.ascontiguousarray(u, np.float64).reshape(-1)
+    uo = None if u_old is None else np.ascontiguousarray(u_old, np.float64).reshape(-1)
     R = np.empty_like(u)
-    if lib.ncp_residual(ctypes.byref(cfg._c()), u.ctypes.data, R.ctypes.data) != 0:
+    if lib.ncp_residual(ctypes.byref(cfg._c()), u.ctypes.data, None if uo is None else uo.ctypes.data,
+                        R.ctypes.data) != 0:
         raise RuntimeError("ncp_residual failed")
     return R
+
+
+def jacobian(cfg: GridConfig, u: np.ndarray, want_residual: bool = False, u_old: np.ndarray | None = None):
+    """BSR Jacobian (rowptr, colind, values) at an arbitrary state u, with the configuration's
+    permeability and the active-set rule of the constraint rows; also R(u) when asked (u_old: the
+    previous time level, as in `residual`)."""
+    lib = _load()
+    c = cfg._c()
+    nb, nnzb = ctypes.c_int64(), ctypes.c_int64()
+    if lib.ncp_count(ctypes.byref(c), ctypes.byref(nb), ctypes.byref(nnzb)) != 0:
+        raise ValueError(f"invalid grid config {cfg}")
+    nb, nnzb = nb.value, nnzb.value
+    u = np.ascontiguousarray(u, np.float64).reshape(-1)
+    if u.size != 3 * nb:
+        raise ValueError("state size does not match the grid")
+    rowptr = np.empty(nb + 1, np.int64)
+    colind = np.empty(nnzb, np.int32)
+    values = np.empty((nnzb, 3, 3), np.float64)
+    R = np.empty(3 * nb, np.float64) if want_residual else None
+    uo = None if u_old is None else np.ascontiguousarray(u_old, np.float64).reshape(-1)
+    rc = lib.ncp_jacobian(ctypes.byref(c), u.ctypes.data, None if uo is None else uo.ctypes.data,
+                          rowptr.ctypes.data, colind.ctypes.data, values.ctypes.data,
+                          R.ctypes.data if R is not None else None)
+    if rc != 0:
+        raise RuntimeError(f"ncp_jacobian failed ({rc})")
+    return (rowptr, colind, values, R) if want_residual else (rowptr, colind, values)
+
+
+def newton_system(cfg: GridConfig, u: np.ndarray, u_old: np.ndarray | None = None):
+    """The linear system of one semi-smooth Newton step at u (section 3.1): the BSR Jacobian, R(u),
+    the cf_marker of the step's active set and the active set itself (True where a constraint row
+    takes the G branch, i.e. the gas phase is present)."""
+    rowptr, colind, values, R = jacobian(cfg, u, want_residual=True, u_old=u_old)
+    rows = np.repeat(np.arange(rowptr.shape[0] - 1), np.diff(rowptr))
+    d = values[rows == colind]
+    active = d[:, 2, 2] == -1.0  # G' = (C_h, C_h P_c', -1); F' = (0, -1, 0)
+    marker = cf_marker(active.astype(np.int8))
+    return rowptr, colind, values, R, marker, active
 
 
 def normals(n: int, seed: int, stream: int = 2) -> np.ndarray:

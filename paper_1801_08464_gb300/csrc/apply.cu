@@ -163,6 +163,55 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
   epi.post(row, sum, pre);
 }
 
+// SELL form with H threads per row (4-slot groups): thread h of a row takes groups h, h + H, ...;
+// the 8 rows of a slice and their H threads are 8H consecutive lanes, so one step of a slice reads
+// H consecutive 128-byte lines; partial sums meet by shuffles across lanes 8 and 16 apart.  Used
+// when one thread per row would leave the GPU with few waves of long rows (a tail).
+template <class T, class Epi, int H>
+__global__ void __launch_bounds__(256) k_rows_sell_split(int64_t nr, const int64_t* __restrict__ soff,
+                                                         const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                         const int32_t* __restrict__ perm, const T* __restrict__ x,
+                                                         Epi epi) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t s = g / (RS_C * H);
+  const int u = (int)(g - s * (RS_C * H));
+  const int h = u / RS_C, t = u % RS_C;
+  const int64_t r = s * RS_C + t;
+  const bool ok = r < nr;
+  const int64_t row = ok ? (perm ? (int64_t)perm[r] : r) : 0;
+  typename Epi::Pre pre{};
+  if (ok && h == 0) pre = epi.pre(row);
+  T sum = 0;
+  if (ok) {
+    const int64_t j0 = soff[s], nq = (soff[s + 1] - j0) / 4;
+    const int32_t* cp = col + j0 * RS_C + t * 4;
+    const T* vp = val + j0 * RS_C + t * 4;
+#pragma unroll 2
+    for (int64_t q = h; q < nq; q += H) {
+      int4 c = __ldg(reinterpret_cast<const int4*>(cp + q * (4 * RS_C)));
+      sum += Quad<T>::dot(vp + q * (4 * RS_C), c, x);
+    }
+  }
+  if (H >= 2) sum += __shfl_xor_sync(0xffffffffu, sum, 8);
+  if (H >= 4) sum += __shfl_xor_sync(0xffffffffu, sum, 16);
+  if (ok && h == 0) epi.post(row, sum, pre);
+}
+
+// threads the device keeps resident at once (SMs x 2048)
+static int64_t device_threads() {
+  static int64_t cached[64] = {0};
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int sms = 0, per = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CU(cudaDeviceGetAttribute(&per, cudaDevAttrMaxThreadsPerMultiProcessor, dev));
+    cached[dev] = (int64_t)sms * per;
+  }
+  return cached[dev];
+}
+
 template <class T, class Epi>
 static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, const char* name = "csr_rows") {
   if (op.nr <= 0) return;
@@ -171,9 +220,20 @@ static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, co
                             (double)op.nr * epi.row_bytes());
   const int B = 256;
   if (op.sell) {
+    // threads per row: enough for six waves of resident threads, at most 4
+    const int64_t slices = (op.nr + RS_C - 1) / RS_C;
+    int H = 1;
     if (op.q == 4)
+      while (H < 4 && op.nr * H < 6 * device_threads()) H *= 2;
+    if (op.q == 4 && H == 1)
       k_rows_sell<T, Epi, 4><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
                                                                 epi);
+    else if (op.q == 4 && H == 2)
+      k_rows_sell_split<T, Epi, 2><<<grid_for(slices * RS_C * 2, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p,
+                                                                                    op.sval.p, op.perm.p, x, epi);
+    else if (op.q == 4)
+      k_rows_sell_split<T, Epi, 4><<<grid_for(slices * RS_C * 4, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p,
+                                                                                    op.sval.p, op.perm.p, x, epi);
     else
       k_rows_sell<T, Epi, 1><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
                                                                 epi);

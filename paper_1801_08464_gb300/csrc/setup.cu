@@ -543,14 +543,21 @@ __global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, con
   }
 }
 
-// The same weights with the row's interpolation columns (fine indices, ascending) and running
-// numerators in shared memory: a warp walks the strong F neighbours k in ascending order; for each k
-// its lanes test the entries of row k against the staged columns in parallel, lane 0 adds den_k's
-// terms in row order from the lanes' shuffled values, and the lanes then add q_k a_kl to the
-// numerators of the distinct columns l of row k (__syncwarp between successive k).  Every sum is
-// formed in the order of k_extpi_weights, so the weights are identical bit for bit.  Rows with more
-// than EXT_PCAP interpolation columns are left to k_extpi_weights (flag `rest`).
-constexpr int EXT_PCAP = 512;
+// The same weights with the row's interpolation columns (fine indices, ascending), its strength
+// row, its strong F neighbours with a_ik, and running numerators in shared memory.  One pass over row
+// i sets the numerators to a_ij, adds the lumped weak entries to at = a_ii in row order (lane 0, from
+// the lanes' shuffled values) and lists the strong F neighbours in ascending order.  The warp then
+// walks that list; a neighbour row k of up to 64 entries is loaded once into registers (two per
+// lane), its entries are tested against the staged columns in parallel, lane 0 adds den_k's terms
+// in row order, and the lanes add q_k a_kl to the numerators of the distinct columns l of row k
+// (__syncwarp between successive k).  a_kk comes from the diagonal array.  Every sum is formed in
+// the order of k_extpi_weights, so the weights are identical bit for bit.
+// The kernel is bound by the latency of its chains of dependent loads, so the shared-memory stage is
+// kept small (PCAP interpolation columns, KCAP strong neighbours per row) for many resident warps: a
+// first launch with small caps takes the rows that fit, a second launch with large caps the rows
+// flagged by the first (rest = 1), and k_extpi_weights the rows beyond those (rest = 2).
+constexpr int EXT_PCAP_S = 32, EXT_KCAP_S = 16;
+constexpr int EXT_PCAP_L = 512, EXT_KCAP_L = 128;
 
 __device__ __forceinline__ int find_sh(const int32_t* a, int n, int32_t key) {
   int lo = 0, hi = n;
@@ -561,111 +568,157 @@ __device__ __forceinline__ int find_sh(const int32_t* a, int n, int32_t key) {
   return (lo < n && a[lo] == key) ? lo : -1;
 }
 
-__global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights_sh(
+// lane 0 adds the values x of the lanes in mask m to s, in lane order
+__device__ __forceinline__ double ordered_add(unsigned m, double x, double s) {
+  const int lane = threadIdx.x & 31;
+  while (m) {
+    int l = __ffs(m) - 1;
+    double y = __shfl_sync(0xffffffffu, x, l);
+    if (lane == 0) s = dd(s, y);
+    m &= m - 1;
+  }
+  return s;
+}
+
+__global__ void k_diag(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                       const double* __restrict__ v, double* __restrict__ d) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  d[i] = csr_get(rp, ci, v, i, (int32_t)i);
+}
+
+// pass 0: every row (C rows, and F rows within the small caps; others get rest = 1);
+// pass 1: the rows with rest == 1 (within the large caps; others get rest = 2).
+template <int PCAP, int KCAP, int MINB>
+__global__ void __launch_bounds__(32 * EXT_WARPS, MINB) k_extpi_weights_sh(
     int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
-    const int64_t* __restrict__ srp, const int32_t* __restrict__ sci, const int8_t* __restrict__ cf,
-    const int32_t* __restrict__ cfine, const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
-    double* __restrict__ pv, int8_t* __restrict__ rowzero, int8_t* __restrict__ rest) {
-  __shared__ int32_t s_pf[EXT_WARPS][EXT_PCAP];
-  __shared__ double s_num[EXT_WARPS][EXT_PCAP];
+    const double* __restrict__ diag, const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
+    const int8_t* __restrict__ cf, const int32_t* __restrict__ cfine, const int64_t* __restrict__ prp,
+    const int32_t* __restrict__ pci, double* __restrict__ pv, int8_t* __restrict__ rowzero, int8_t* __restrict__ rest,
+    int pass) {
+  __shared__ int32_t s_pf[EXT_WARPS][PCAP];
+  __shared__ double s_num[EXT_WARPS][PCAP];
+  __shared__ int32_t s_s[EXT_WARPS][KCAP];
+  __shared__ int32_t s_k[EXT_WARPS][KCAP];
+  __shared__ double s_aik[EXT_WARPS][KCAP];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = (int64_t)blockIdx.x * EXT_WARPS + w;
   if (i >= n) return;
+  if (pass == 1 && rest[i] != 1) return;
   if (cf[i] == 1) {
     if (lane == 0) { pv[prp[i]] = 1.0; rowzero[i] = 0; rest[i] = 0; }
     return;
   }
   const int64_t p0 = prp[i], np64 = prp[i + 1] - p0;
-  if (np64 > EXT_PCAP) {
-    if (lane == 0) rest[i] = 1;
+  const int64_t s0 = srp[i], ns64 = srp[i + 1] - s0;
+  if (np64 > PCAP || ns64 > KCAP) {
+    if (lane == 0) rest[i] = (int8_t)(pass + 1);
     return;
   }
-  const int np = (int)np64;
+  const int np = (int)np64, ns = (int)ns64;
   int32_t* pf = s_pf[w];
   double* num = s_num[w];
-  const int64_t r0 = rp[i], r1 = rp[i + 1];
-  const int64_t s0 = srp[i], s1 = srp[i + 1];
-  // staged columns (fine indices, ascending) and numerators starting at a_ij
-  for (int t = lane; t < np; t += 32) pf[t] = cfine[pci[p0 + t]];
+  int32_t* sr = s_s[w];
+  for (int t = lane; t < np; t += 32) {
+    pf[t] = cfine[pci[p0 + t]];
+    num[t] = 0.0;
+  }
+  for (int t = lane; t < ns; t += 32) sr[t] = sci[s0 + t];
   __syncwarp();
-  for (int t = lane; t < np; t += 32) num[t] = csr_get(rp, ci, v, i, pf[t]);
-  // at = a_ii, then the weak neighbours outside Chat_i in row order
-  double at = 0.0;
-  if (lane == 0) at = csr_get(rp, ci, v, i, (int32_t)i);
+  // row i: numerators a_ij, lumped weak entries (at = a_ii first), strong F neighbours listed
+  const int64_t r0 = rp[i], r1 = rp[i + 1];
+  double at = diag[i];
+  int nk = 0;
   for (int64_t b = r0; b < r1; b += 32) {
     int64_t q = b + lane;
-    bool lump = false;
+    bool lump = false, sf = false;
+    int32_t nn = -1;
     double val = 0.0;
     if (q < r1) {
-      int32_t nn = ci[q];
+      nn = ci[q];
       val = v[q];
-      lump = nn != i && find_i32(sci, s0, s1, nn) < 0 && find_sh(pf, np, nn) < 0;
+      int t = find_sh(pf, np, nn);
+      if (t >= 0) num[t] = val;
+      bool strong = find_sh(sr, ns, nn) >= 0;
+      lump = nn != i && !strong && t < 0;
+      sf = strong && cf[nn] != 1;
     }
-    unsigned m = __ballot_sync(0xffffffffu, lump);
-    while (m) {
-      int l = __ffs(m) - 1;
-      double x = __shfl_sync(0xffffffffu, val, l);
-      if (lane == 0) at = dd(at, x);
-      m &= m - 1;
+    at = ordered_add(__ballot_sync(0xffffffffu, lump), val, at);
+    unsigned ms = __ballot_sync(0xffffffffu, sf);
+    if (sf) {
+      int pos = nk + __popc(ms & ((1u << lane) - 1u));
+      s_k[w][pos] = nn;
+      s_aik[w][pos] = val;
     }
+    nk += __popc(ms);
   }
   __syncwarp();
-  // strong F neighbours in ascending order
-  for (int64_t p = s0; p < s1; ++p) {
-    const int32_t k = sci[p];
-    if (cf[k] == 1) continue;
+  for (int p = 0; p < nk; ++p) {
+    const int32_t k = s_k[w][p];
+    const double aik = s_aik[w][p];
+    const double akk = diag[k];
     const int64_t k0 = rp[k], k1 = rp[k + 1];
-    // a_kk and a_ki (lanes scan row k)
-    double akk = 0.0, aki = 0.0;
-    for (int64_t b = k0; b < k1; b += 32) {
-      int64_t q = b + lane;
-      int32_t l = q < k1 ? ci[q] : -1;
-      double x = q < k1 ? v[q] : 0.0;
-      unsigned mk = __ballot_sync(0xffffffffu, l == k), mi = __ballot_sync(0xffffffffu, l == (int32_t)i);
-      if (mk) akk = __shfl_sync(0xffffffffu, x, __ffs(mk) - 1);
-      if (mi) aki = __shfl_sync(0xffffffffu, x, __ffs(mi) - 1);
-    }
-    // den_k in row order
-    double den = 0.0;
-    for (int64_t b = k0; b < k1; b += 32) {
-      int64_t q = b + lane;
-      bool in = false;
-      double x = 0.0;
-      if (q < k1) {
-        int32_t l = ci[q];
-        x = v[q];
-        in = (l == (int32_t)i || find_sh(pf, np, l) >= 0) && opposite(x, akk);
+    double den = 0.0, aki = 0.0;
+    if (k1 - k0 <= 64) {
+      int32_t la = -1, lb = -1;
+      double xa = 0.0, xb = 0.0;
+      if (k0 + lane < k1) { la = ci[k0 + lane]; xa = v[k0 + lane]; }
+      if (k0 + 32 + lane < k1) { lb = ci[k0 + 32 + lane]; xb = v[k0 + 32 + lane]; }
+      const int ta = la >= 0 ? find_sh(pf, np, la) : -1;
+      const int tb = lb >= 0 ? find_sh(pf, np, lb) : -1;
+      const bool oa = opposite(xa, akk), ob = opposite(xb, akk);
+      unsigned mi = __ballot_sync(0xffffffffu, la == (int32_t)i);
+      if (mi) aki = __shfl_sync(0xffffffffu, xa, __ffs(mi) - 1);
+      mi = __ballot_sync(0xffffffffu, lb == (int32_t)i);
+      if (mi) aki = __shfl_sync(0xffffffffu, xb, __ffs(mi) - 1);
+      den = ordered_add(__ballot_sync(0xffffffffu, (la == (int32_t)i || ta >= 0) && oa), xa, den);
+      den = ordered_add(__ballot_sync(0xffffffffu, (lb == (int32_t)i || tb >= 0) && ob), xb, den);
+      den = __shfl_sync(0xffffffffu, den, 0);
+      if (den != 0.0) {
+        const double qk = dv(aik, den);
+        if (lane == 0 && opposite(aki, akk)) at = dd(at, dm(qk, aki));
+        if (ta >= 0 && oa) num[ta] = dd(num[ta], dm(qk, xa));
+        if (tb >= 0 && ob) num[tb] = dd(num[tb], dm(qk, xb));
+      } else if (lane == 0) {
+        at = dd(at, aik);
       }
-      unsigned m = __ballot_sync(0xffffffffu, in);
-      while (m) {
-        int l = __ffs(m) - 1;
-        double y = __shfl_sync(0xffffffffu, x, l);
-        if (lane == 0) den = dd(den, y);
-        m &= m - 1;
-      }
-    }
-    den = __shfl_sync(0xffffffffu, den, 0);
-    const double aik = csr_get(rp, ci, v, i, k);
-    if (den != 0.0) {
-      const double qk = dv(aik, den);
-      if (lane == 0 && opposite(aki, akk)) at = dd(at, dm(qk, aki));
-      // numerators: distinct columns of row k land on distinct slots
+    } else {
       for (int64_t b = k0; b < k1; b += 32) {
         int64_t q = b + lane;
+        bool in = false;
+        double x = 0.0;
         if (q < k1) {
           int32_t l = ci[q];
-          double x = v[q];
-          int t = find_sh(pf, np, l);
-          if (t >= 0 && opposite(x, akk)) num[t] = dd(num[t], dm(qk, x));
+          x = v[q];
+          if (l == (int32_t)i) aki = x;
+          in = (l == (int32_t)i || find_sh(pf, np, l) >= 0) && opposite(x, akk);
         }
+        den = ordered_add(__ballot_sync(0xffffffffu, in), x, den);
       }
-    } else if (lane == 0) {
-      at = dd(at, aik);
+      den = __shfl_sync(0xffffffffu, den, 0);
+      unsigned mi = __ballot_sync(0xffffffffu, aki != 0.0);
+      aki = mi ? __shfl_sync(0xffffffffu, aki, __ffs(mi) - 1) : 0.0;
+      if (den != 0.0) {
+        const double qk = dv(aik, den);
+        if (lane == 0 && opposite(aki, akk)) at = dd(at, dm(qk, aki));
+        for (int64_t b = k0; b < k1; b += 32) {
+          int64_t q = b + lane;
+          if (q < k1) {
+            int32_t l = ci[q];
+            double x = v[q];
+            int t = find_sh(pf, np, l);
+            if (t >= 0 && opposite(x, akk)) num[t] = dd(num[t], dm(qk, x));
+          }
+        }
+      } else if (lane == 0) {
+        at = dd(at, aik);
+      }
     }
     __syncwarp();
   }
   at = __shfl_sync(0xffffffffu, at, 0);
   if (lane == 0) { rowzero[i] = (at == 0.0); rest[i] = 0; }
+  __syncwarp();
   for (int t = lane; t < np; t += 32) pv[p0 + t] = (at != 0.0) ? -dv(num[t], at) : 0.0;
 }
 
@@ -824,9 +877,14 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
   DBuf<double> den(c, S.nnz + 1), q(c, S.nnz + 1), scale(c, n);
   DBuf<int8_t> rowzero(c, n), keep(c, Pf.nnz + 1), rest(c, n);
   ProfScope psw(c, "extpi_weights");
-  k_extpi_weights_sh<<<grid_for(n, EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p,
-                                                                         cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p,
-                                                                         rest.p);
+  DBuf<double> diag(c, n);
+  k_diag<<<grid_for(n, B), B, 0, c.s>>>(n, A.rp, A.ci, A.v, diag.p);
+  CU_LAUNCH();
+  k_extpi_weights_sh<EXT_PCAP_S, EXT_KCAP_S, 12><<<grid_for(n, EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(
+      n, A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p, cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p, 0);
+  CU_LAUNCH();
+  k_extpi_weights_sh<EXT_PCAP_L, EXT_KCAP_L, 1><<<grid_for(n, EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(
+      n, A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p, cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p, 1);
   CU_LAUNCH();
   k_extpi_weights<<<grid_for(n * 32, 32 * EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp,
                                                            Pf.ci, Pf.v, den.p, q.p, rowzero.p, rest.p);

@@ -11,7 +11,13 @@ PARITY = {
     "ncp3d_16": ncpgen.GridConfig(16, 16, 16, sigma=2.0, absent_frac=0.5, absent_mode=1, seed=1),
     "ragged_13x7x9": ncpgen.GridConfig(13, 7, 9, sigma=1.0, layer_contrast=1e-4, absent_frac=0.4, absent_mode=1,
                                        seed=3),
+    # the two-level unsaturated case of section 6.1 (Van Genuchten closures, gas present everywhere)
+    "unsat2d_200x10": ncpgen.WORKLOADS["unsat2d_200x10"],
 }
+
+# Section 6.1's two-level setting: injective R (W_r = 0) at both reductions, three relaxation sweeps
+# on the saturation block (l1-Jacobi in place of the paper's Gauss-Seidel), V(2,2) on the pressure.
+UNSAT = dict(restrict_type=[0, 0], frelax_type=[1, 1], frelax_sweeps=[1, 3], amg_pre=2, amg_post=2)
 
 
 def to_gpu(p):

@@ -10,7 +10,7 @@ import pytest
 
 import ncpgen
 import oracle
-from gpu_common import PARITY, compare_csr, rel, to_gpu
+from gpu_common import PARITY, UNSAT, compare_csr, rel, to_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -23,7 +23,9 @@ OPTION_SETS = {
     "default": {},
     "jacobi_trunc": dict(frelax_type=[0, 0, 0], frelax_omega=[1.0, 0.8, 0.8], amg_theta=0.5, amg_pmax=4,
                          amg_smoother=0, amg_omega=0.8, restrict_type=[1, 1, 0], frelax_sweeps=[1, 3, 2]),
+    "unsat_two_level": UNSAT,
 }
+NAMED = {"default": {}, "paper_62": PAPER_62, "unsat_two_level": UNSAT}
 
 
 def _pair(p, **opts):
@@ -69,11 +71,11 @@ def test_setup_parity(name, optname):
 
 
 @pytest.mark.parametrize("name", list(PARITY))
-@pytest.mark.parametrize("optname", ["default", "paper_62"])
+@pytest.mark.parametrize("optname", list(NAMED))
 def test_apply_parity_fp64(name, optname):
     import torch
     p = ncpgen.make_problem(PARITY[name])
-    A, mk, m, o = _pair(p, **(PAPER_62 if optname == "paper_62" else {}))
+    A, mk, m, o = _pair(p, **NAMED[optname])
     for seed in (2, 7):
         r = ncpgen.normals(p.n, seed)
         z = m.apply(torch.as_tensor(r, device="cuda")).cpu().numpy()
@@ -100,11 +102,11 @@ def test_global_relaxation_step(name):
 
 
 @pytest.mark.parametrize("name", list(PARITY))
-@pytest.mark.parametrize("optname", ["default", "paper_62"])
+@pytest.mark.parametrize("optname", list(NAMED))
 def test_fgmres_parity_fp64(name, optname):
     import torch
     p = ncpgen.make_problem(PARITY[name])
-    A, mk, m, o = _pair(p, **(PAPER_62 if optname == "paper_62" else {}))
+    A, mk, m, o = _pair(p, **NAMED[optname])
     b = ncpgen.normals(p.n, 2)
     bt = torch.as_tensor(b, device="cuda")
     Asp = p.to_scipy()
@@ -186,8 +188,15 @@ def test_edge_cases_all_present_all_absent_tiny():
     cases = [ncpgen.GridConfig(8, 8, 1, absent_frac=0.0, seed=41), ncpgen.GridConfig(8, 8, 1, absent_frac=1.0, seed=41),
              ncpgen.GridConfig(2, 2, 1, absent_frac=0.5, seed=3), ncpgen.GridConfig(1, 1, 1, absent_frac=0.0, seed=3),
              ncpgen.GridConfig(3, 1, 2, absent_frac=0.5, absent_mode=1, seed=4)]
-    for cfg in cases:
-        p = ncpgen.make_problem(cfg)
+    # the generator's markers, then the all-present case with P_l kept at marker 3 (an empty third
+    # reduction)
+    probs = [ncpgen.make_problem(cfg) for cfg in cases]
+    q = probs[0]
+    mk3 = q.cf_marker.copy()
+    mk3[0::3] = 3
+    probs.append(ncpgen.Problem(q.cfg, q.nb, q.rowptr, q.colind, q.values, q.gas_present, mk3, q.state, q.perm))
+    for p in probs:
+        cfg = p.cfg
         A, mk, m, o = _pair(p)
         L, na = m.levels()
         assert (L, na) == o.info()
