@@ -88,7 +88,12 @@ typedef struct {
   int32_t adjoint;                       /* 1: the setup also builds the transposed operators of the
                                             preconditioner, for mgr_apply_transpose and
                                             fgmres_solve_transpose (default 0) */
-  int32_t reserved[5];                   /* must be zero */
+  int32_t apply_graph;                   /* the forward apply replayed as a CUDA graph (captured at the
+                                            second apply after a setup, on fixed input/output buffers
+                                            with device copies around each replay): 0 auto (systems
+                                            of at most 2^21 unknowns, where the apply is bound by its
+                                            launches), 1 always, -1 never.  Profiling disables it */
+  int32_t reserved[4];                   /* must be zero */
 } mgr_options_t;
 
 typedef struct {
@@ -178,7 +183,8 @@ mgr_status_t mgr_memory_bytes(mgr_handle_t h, int64_t* bytes);
  * work buffers included (host out). */
 mgr_status_t mgr_memory_peak_bytes(mgr_handle_t h, int64_t* bytes);
 /* Statistics (host outs, each may be NULL): wall time of the last mgr_setup in milliseconds, kernel
- * launches issued by the last mgr_apply, a reserved count that is always 0, and the process-wide
+ * launches issued by the last mgr_apply, the kernel launches in the captured apply graph (0 while
+ * the apply is launched directly), and the process-wide
  * count of kernel launches issued by this library since load. */
 mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_launches, int64_t* graph_nodes,
                            int64_t* total_launches);

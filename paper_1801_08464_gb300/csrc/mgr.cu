@@ -57,6 +57,13 @@ struct mgr_handle_s {
   DBuf<float> valT32, binvT32;
   DBuf<double> valT64, binvT64, kry_valsT, cinvT;
   std::vector<DBuf<char>> w_u;
+  // the forward apply as a CUDA graph (options.apply_graph), valid until the next setup
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  DBuf<double> g_in, g_out;  // the graph's fixed input and output
+  int64_t g_launches = 0;    // kernel launches captured in it
+  int applies = 0;           // forward applies since the setup
+  bool graph_failed = false;
 };
 
 namespace {
@@ -305,8 +312,81 @@ void do_apply_t(mgr_handle_s& h, const double* r, double* z) {
   else apply_tt<double>(h, r, z);
 }
 
+// Systems of at most this many unknowns replay the forward apply as a CUDA graph by default: their
+// apply is a chain of small kernels bound by launch overhead.
+constexpr int64_t APPLY_GRAPH_AUTO_MAX = int64_t(1) << 21;
+
+void reset_graph(mgr_handle_s& h) {
+  if (h.gexec) {
+    cudaStreamSynchronize(h.c.s);  // no replay in flight
+    cudaGraphExecDestroy(h.gexec);
+  }
+  h.gexec = nullptr;
+  h.g_launches = 0;
+  h.applies = 0;
+  h.graph_failed = false;
+}
+
+bool graph_wanted(const mgr_handle_s& h) {
+  if (h.c.prof || h.graph_failed || h.o.apply_graph < 0) return false;
+  return h.o.apply_graph > 0 || 3 * h.nb <= APPLY_GRAPH_AUTO_MAX;
+}
+
+// Capture one forward apply from g_in to g_out on a private stream (the caller's stream may be the
+// legacy default stream, which cannot capture); on any failure the handle keeps launching directly.
+template <class T>
+void capture_apply(mgr_handle_s& h) {
+  Ctx& c = h.c;
+  const int64_t n = 3 * h.nb;
+  h.g_in.alloc(c, n);
+  h.g_out.alloc(c, n);
+  if (!h.gstream) CU(cudaStreamCreateWithFlags(&h.gstream, cudaStreamNonBlocking));
+  cudaStream_t s0 = c.s;
+  const unsigned long long l0 = g_launch_count;
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(h.gstream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+  if (ok) {
+    c.s = h.gstream;
+    try {
+      apply_t<T>(h, h.g_in.p, h.g_out.p);
+    } catch (...) {
+      ok = false;
+    }
+    c.s = s0;
+    ok = (cudaStreamEndCapture(h.gstream, &graph) == cudaSuccess) && ok && graph;
+  }
+  g_launch_count = l0;  // nothing ran
+  if (ok) ok = cudaGraphInstantiate(&h.gexec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    h.gexec = nullptr;
+    h.graph_failed = true;
+    cudaGetLastError();
+    return;
+  }
+  h.g_launches = h.apply_launches;
+}
+
 void do_apply(mgr_handle_s& h, const double* r, double* z) {
-  if (h.o.precision == MGR_PREC_MIXED) apply_t<float>(h, r, z);
+  const bool mixed = h.o.precision == MGR_PREC_MIXED;
+  // the first apply after a setup runs directly (it also settles the launch-shape caches); the
+  // second captures the graph, and later ones replay it
+  if (graph_wanted(h) && h.applies++ >= 1) {
+    if (!h.gexec) {
+      if (mixed) capture_apply<float>(h);
+      else capture_apply<double>(h);
+    }
+    if (h.gexec) {
+      Ctx& c = h.c;
+      const size_t bytes = sizeof(double) * 3 * h.nb;
+      CU(cudaMemcpyAsync(h.g_in.p, r, bytes, cudaMemcpyDeviceToDevice, c.s));
+      CU(cudaGraphLaunch(h.gexec, c.s));
+      g_launch_count += (unsigned long long)h.g_launches;
+      CU(cudaMemcpyAsync(z, h.g_out.p, bytes, cudaMemcpyDeviceToDevice, c.s));
+      return;
+    }
+  }
+  if (mixed) apply_t<float>(h, r, z);
   else apply_t<double>(h, r, z);
 }
 
@@ -523,6 +603,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   auto t0 = std::chrono::steady_clock::now();
   Ctx& c = h.c;
   h.ready = false;
+  reset_graph(h);
   h.lev.clear();
   h.amg.clear();
   h.cinv.release();
@@ -896,6 +977,7 @@ static mgr_status_t check_options(const mgr_options_t& o) {
   if (o.amg_pre < 1 || o.amg_post < 0 || o.amg_max_levels < 1 || o.amg_max_coarse < 1 || o.amg_max_coarse > 4096)
     return MGR_ERR_INVALID_ARG;
   if (o.amg_smoother < 0 || o.amg_smoother > 1 || o.amg_pmax < 0) return MGR_ERR_INVALID_ARG;
+  if (o.apply_graph < -1 || o.apply_graph > 1) return MGR_ERR_INVALID_ARG;
   return MGR_OK;
 }
 
@@ -974,6 +1056,9 @@ mgr_status_t mgr_destroy(mgr_handle_t h) {
   if (!h) return MGR_OK;
   mgr_status_t st = guarded(h, [&] {
     CU(cudaStreamSynchronize(h->c.s));
+    reset_graph(*h);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
+    h->gstream = nullptr;
     h->lev.clear();
     h->amg.clear();
   });
@@ -1138,7 +1223,7 @@ mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_laun
   if (!h) return setup_ms || apply_launches || graph_nodes ? MGR_ERR_INVALID_ARG : MGR_OK;
   if (setup_ms) *setup_ms = h->setup_ms;
   if (apply_launches) *apply_launches = h->apply_launches;
-  if (graph_nodes) *graph_nodes = 0;
+  if (graph_nodes) *graph_nodes = h->gexec ? h->g_launches : 0;
   return MGR_OK;
 }
 

@@ -7,6 +7,8 @@
 
 #include "hier.cuh"
 
+#include <climits>
+
 namespace mgr {
 
 __device__ __forceinline__ double dm(double a, double b) { return __dmul_rn(a, b); }
@@ -251,6 +253,40 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
 // ===================================== AMG (coarse solve) =====================================
 // Strength: with s = +1 if a_ii >= 0 else -1, j != i is strong iff -s a_ij >= theta m where
 // m = max(0, max_{k != i} -s a_ik) > 0.  A warp per row; MODE 0 counts, MODE 1 writes in order.
+// Everything but theta * m is done on the bit patterns with integer instructions (the FP64 pipe is
+// the scarce resource): -s a_ij is a_ij with its sign bit flipped when s = +1, and doubles compare
+// like the integers dkey() maps them to (NaN entries are neither strong nor part of the maximum, as
+// with IEEE comparisons).  The results are those of the comparisons in FP64 exactly.
+constexpr long long DMAG = 0x7FFFFFFFFFFFFFFFLL, DINF = 0x7FF0000000000000LL, DSIGN = (long long)0x8000000000000000ULL;
+
+__device__ __forceinline__ long long dkey(long long b) { return b ^ ((b >> 63) & DMAG); }
+
+// key of -s a for the entry's bits (LLONG_MIN for NaN: never the maximum, never strong)
+__device__ __forceinline__ long long strength_key(double a, bool spos) {
+  long long b = __double_as_longlong(a);
+  if ((b & DMAG) > DINF) return LLONG_MIN;
+  return dkey(spos ? (b ^ DSIGN) : b);
+}
+
+// s = +1 iff a_ii >= 0 (true for -0.0, false for NaN)
+__device__ __forceinline__ bool diag_nonneg(double d) {
+  long long b = __double_as_longlong(d);
+  return (b & DMAG) == 0 || (b >= 0 && (b & DMAG) <= DINF);
+}
+
+__device__ __forceinline__ long long warp_max_ll(long long x) {
+  for (int o = 16; o > 0; o >>= 1) {
+    long long t = __shfl_xor_sync(0xffffffffu, x, o);
+    x = t > x ? t : x;
+  }
+  return x;
+}
+
+// x >= thr for thr = theta * m >= 0 (thr == 0 admits both zeros)
+__device__ __forceinline__ bool key_ge_thr(long long kx, long long kthr) {
+  return kx >= kthr || (kthr == 0 && kx == -1);
+}
+
 template <int MODE>
 __global__ void k_strength(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, double theta, int64_t* cnt,
                            const int64_t* srp, int32_t* sci) {
@@ -264,20 +300,21 @@ __global__ void k_strength(int64_t n, const int64_t* rp, const int32_t* ci, cons
     const int64_t k0 = b + lane, k1 = b + 32 + lane;
     const int32_t c0 = k0 < e ? ci[k0] : -1, c1 = k1 < e ? ci[k1] : -1;
     const double v0 = k0 < e ? v[k0] : 0.0, v1 = k1 < e ? v[k1] : 0.0;
-    double d = (c0 == (int32_t)i) ? v0 : ((c1 == (int32_t)i) ? v1 : 0.0);
-    for (int o = 16; o > 0; o >>= 1) {
-      double t = __shfl_xor_sync(0xffffffffu, d, o);
-      if (t != 0.0) d = t;
-    }
-    const double s = (d >= 0.0) ? 1.0 : -1.0;
-    double m = 0.0;
-    if (c0 >= 0 && c0 != (int32_t)i) m = fmax(m, -dm(s, v0));
-    if (c1 >= 0 && c1 != (int32_t)i) m = fmax(m, -dm(s, v1));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (m > 0.0) {
-      const double thr = dm(theta, m);
-      const bool st0 = c0 >= 0 && c0 != (int32_t)i && -dm(s, v0) >= thr;
-      const bool st1 = c1 >= 0 && c1 != (int32_t)i && -dm(s, v1) >= thr;
+    double d = 0.0;
+    const unsigned md0 = __ballot_sync(0xffffffffu, c0 == (int32_t)i), md1 = __ballot_sync(0xffffffffu, c1 == (int32_t)i);
+    if (md0) d = __shfl_sync(0xffffffffu, v0, __ffs(md0) - 1);
+    else if (md1) d = __shfl_sync(0xffffffffu, v1, __ffs(md1) - 1);
+    const bool spos = diag_nonneg(d);
+    const long long kx0 = (c0 >= 0 && c0 != (int32_t)i) ? strength_key(v0, spos) : LLONG_MIN;
+    const long long kx1 = (c1 >= 0 && c1 != (int32_t)i) ? strength_key(v1, spos) : LLONG_MIN;
+    long long km = kx0 > kx1 ? kx0 : kx1;
+    km = km > 0 ? km : 0;
+    km = warp_max_ll(km);
+    if (km > 0) {
+      const double thr = dm(theta, __longlong_as_double(km));  // km > 0: the key is the bits
+      const long long kthr = dkey(__double_as_longlong(thr));
+      const bool st0 = kx0 != LLONG_MIN && key_ge_thr(kx0, kthr);
+      const bool st1 = kx1 != LLONG_MIN && key_ge_thr(kx1, kthr);
       const unsigned m0 = __ballot_sync(0xffffffffu, st0), m1 = __ballot_sync(0xffffffffu, st1);
       if (MODE == 1) {
         const unsigned below = (1u << lane) - 1;
@@ -290,26 +327,30 @@ __global__ void k_strength(int64_t n, const int64_t* rp, const int32_t* ci, cons
     return;
   }
   double d = 0.0;
-  for (int64_t k = b + lane; k < e; k += 32)
-    if (ci[k] == i) d = v[k];
-  for (int o = 16; o > 0; o >>= 1) {
-    double t = __shfl_xor_sync(0xffffffffu, d, o);
-    if (t != 0.0) d = t;
+  for (int64_t k0 = b; k0 < e; k0 += 32) {
+    const int64_t k = k0 + lane;
+    const bool hit = k < e && ci[k] == i;
+    const unsigned mh = __ballot_sync(0xffffffffu, hit);
+    if (mh) d = __shfl_sync(0xffffffffu, hit ? v[k] : 0.0, __ffs(mh) - 1);
   }
-  double s = (d >= 0.0) ? 1.0 : -1.0;
-  double m = 0.0;
+  const bool spos = diag_nonneg(d);
+  long long km = 0;
   for (int64_t k = b + lane; k < e; k += 32)
     if (ci[k] != i) {
-      double x = -dm(s, v[k]);
-      if (x > m) m = x;
+      const long long kx = strength_key(v[k], spos);
+      km = kx > km ? kx : km;
     }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (m > 0.0) {
-    double thr = dm(theta, m);
+  km = warp_max_ll(km);
+  if (km > 0) {
+    const double thr = dm(theta, __longlong_as_double(km));
+    const long long kthr = dkey(__double_as_longlong(thr));
     for (int64_t k0 = b; k0 < e; k0 += 32) {
       int64_t k = k0 + lane;
       bool strong = false;
-      if (k < e && ci[k] != i) strong = (-dm(s, v[k]) >= thr);
+      if (k < e && ci[k] != i) {
+        const long long kx = strength_key(v[k], spos);
+        strong = kx != LLONG_MIN && key_ge_thr(kx, kthr);
+      }
       unsigned msk = __ballot_sync(0xffffffffu, strong);
       if (MODE == 1 && strong) sci[out + __popc(msk & ((1u << lane) - 1))] = ci[k];
       count += __popc(msk);
@@ -345,14 +386,16 @@ __global__ void k_pmis_select(int64_t n, const int64_t* srp, const int32_t* sci,
   if (i >= n) return;
   nc[i] = 0;
   if (st[i] != 0) return;
-  double wi = w[i];
+  // the weights are positive doubles, which order like their bit patterns: integer comparisons
+  const long long* wb = reinterpret_cast<const long long*>(w);
+  const long long wi = wb[i];
   for (int pass = 0; pass < 2; ++pass) {
     const int64_t* rp = pass ? trp : srp;
     const int32_t* ci = pass ? tci : sci;
     for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
       int32_t j = ci[k];
       if (j == i || st[j] != 0) continue;
-      double wj = w[j];
+      const long long wj = wb[j];
       if (wj > wi || (wj == wi && j > i)) return;
     }
   }
@@ -423,6 +466,14 @@ __global__ void k_pfull_fill(int64_t n, const int8_t* cf, const int32_t* cidx, c
 }
 
 __device__ __forceinline__ bool opposite(double a, double d) { return (d > 0.0 && a < 0.0) || (d < 0.0 && a > 0.0); }
+
+// opposite() on the bit patterns, with integer instructions: both nonzero, neither NaN, signs differ
+__device__ __forceinline__ bool opposite_bits(double a, double d) {
+  const long long ia = __double_as_longlong(a), id = __double_as_longlong(d);
+  const long long mag = 0x7FFFFFFFFFFFFFFFLL, inf = 0x7FF0000000000000LL;
+  const long long ma = ia & mag, md = id & mag;
+  return ma != 0 && md != 0 && ma <= inf && md <= inf && (ia ^ id) < 0;
+}
 
 // Extended+i weights (De Sterck, Falgout, Nolting & Yang 2008), one warp per F row; the pattern
 // (Chat_i, coarse indices, ascending) is already in P.  Per strong F neighbour k (position p in S_i):
@@ -552,11 +603,8 @@ __global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, con
 // in row order, and the lanes add q_k a_kl to the numerators of the distinct columns l of row k
 // (__syncwarp between successive k).  a_kk comes from the diagonal array.  Every sum is formed in
 // the order of k_extpi_weights, so the weights are identical bit for bit.
-// The kernel is bound by the latency of its chains of dependent loads, so the shared-memory stage is
-// kept small (PCAP interpolation columns, KCAP strong neighbours per row) for many resident warps: a
-// first launch with small caps takes the rows that fit, a second launch with large caps the rows
-// flagged by the first (rest = 1), and k_extpi_weights the rows beyond those (rest = 2).
-constexpr int EXT_PCAP_S = 32, EXT_KCAP_S = 16;
+// It takes the rows that k_extpi_weights_row leaves (rest = 1) within its caps (PCAP interpolation
+// columns, KCAP strong neighbours); k_extpi_weights takes the rows beyond those (rest = 2).
 constexpr int EXT_PCAP_L = 512, EXT_KCAP_L = 128;
 
 __device__ __forceinline__ int find_sh(const int32_t* a, int n, int32_t key) {
@@ -587,8 +635,94 @@ __global__ void k_diag(int64_t n, const int64_t* __restrict__ rp, const int32_t*
   d[i] = csr_get(rp, ci, v, i, (int32_t)i);
 }
 
-// pass 0: every row (C rows, and F rows within the small caps; others get rest = 1);
-// pass 1: the rows with rest == 1 (within the large caps; others get rest = 2).
+// One thread per row.  The instructions of the FP64 pipe are the scarce resource here (GB300 issues
+// about one FP64 warp instruction per 16 SM cycles, whatever its active lanes), and most of the
+// arithmetic of a row is sequential (the sums in row order), so each thread takes one row and every
+// FP64 warp instruction advances 32 rows.  Membership tests are merge walks of sorted lists (row i
+// against its strength row and its interpolation columns; row k against the columns).  The
+// interpolation columns and numerators sit in shared memory ([slot][thread]); rows with more than
+// EXT_PCAP_T columns are flagged rest = 1 for the warp kernel below.
+constexpr int EXT_TPB = 128, EXT_PCAP_T = 16;
+
+__global__ void __launch_bounds__(EXT_TPB) k_extpi_weights_row(
+    int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
+    const double* __restrict__ diag, const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
+    const int8_t* __restrict__ cf, const int32_t* __restrict__ cfine, const int64_t* __restrict__ prp,
+    const int32_t* __restrict__ pci, double* __restrict__ pv, int8_t* __restrict__ rowzero, int8_t* __restrict__ rest) {
+  __shared__ int32_t s_pf[EXT_PCAP_T][EXT_TPB];
+  __shared__ double s_num[EXT_PCAP_T][EXT_TPB];
+  const int64_t i = blockIdx.x * (int64_t)EXT_TPB + threadIdx.x;
+  if (i >= n) return;
+  const int tx = threadIdx.x;
+  if (cf[i] == 1) { pv[prp[i]] = 1.0; rowzero[i] = 0; rest[i] = 0; return; }
+  const int64_t p0 = prp[i];
+  const int64_t np64 = prp[i + 1] - p0;
+  if (np64 > EXT_PCAP_T) { rest[i] = 1; return; }
+  const int np = (int)np64;
+  for (int t = 0; t < np; ++t) {
+    s_pf[t][tx] = cfine[pci[p0 + t]];
+    s_num[t][tx] = 0.0;
+  }
+  const int64_t r0 = rp[i], r1 = rp[i + 1], s0 = srp[i], s1 = srp[i + 1];
+  // row i: numerators a_ij, then at = a_ii plus the lumped weak entries in row order
+  double at = diag[i];
+  {
+    int64_t sp = s0;
+    int t = 0;
+    for (int64_t q = r0; q < r1; ++q) {
+      const int32_t nn = ci[q];
+      const double x = v[q];
+      while (sp < s1 && sci[sp] < nn) ++sp;
+      const bool strong = sp < s1 && sci[sp] == nn;
+      while (t < np && s_pf[t][tx] < nn) ++t;
+      const bool inp = t < np && s_pf[t][tx] == nn;
+      if (inp) s_num[t][tx] = x;
+      if (nn != (int32_t)i && !strong && !inp) at = dd(at, x);
+    }
+  }
+  // strong F neighbours k in ascending order (a_ik by a merge walk over row i)
+  int64_t q = r0;
+  for (int64_t sp = s0; sp < s1; ++sp) {
+    const int32_t k = sci[sp];
+    while (q < r1 && ci[q] < k) ++q;
+    if (cf[k] == 1) continue;
+    const double aik = (q < r1 && ci[q] == k) ? v[q] : 0.0;
+    const double akk = diag[k];
+    const int64_t k0 = rp[k], k1 = rp[k + 1];
+    double den = 0.0, aki = 0.0;
+    {
+      int t = 0;
+      for (int64_t u = k0; u < k1; ++u) {
+        const int32_t l = ci[u];
+        const double x = v[u];
+        while (t < np && s_pf[t][tx] < l) ++t;
+        const bool inp = t < np && s_pf[t][tx] == l;
+        if (l == (int32_t)i) aki = x;
+        if ((l == (int32_t)i || inp) && opposite_bits(x, akk)) den = dd(den, x);
+      }
+    }
+    if (den != 0.0) {
+      const double qk = dv(aik, den);
+      if (opposite_bits(aki, akk)) at = dd(at, dm(qk, aki));
+      int t = 0;
+      for (int64_t u = k0; u < k1; ++u) {
+        const int32_t l = ci[u];
+        while (t < np && s_pf[t][tx] < l) ++t;
+        if (t < np && s_pf[t][tx] == l) {
+          const double x = v[u];
+          if (opposite_bits(x, akk)) s_num[t][tx] = dd(s_num[t][tx], dm(qk, x));
+        }
+      }
+    } else {
+      at = dd(at, aik);
+    }
+  }
+  rowzero[i] = (at == 0.0);
+  rest[i] = 0;
+  for (int t = 0; t < np; ++t) pv[p0 + t] = (at != 0.0) ? -dv(s_num[t][tx], at) : 0.0;
+}
+
+// pass 1: the rows with rest == 1 (within the caps; others get rest = 2).
 template <int PCAP, int KCAP, int MINB>
 __global__ void __launch_bounds__(32 * EXT_WARPS, MINB) k_extpi_weights_sh(
     int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
@@ -880,8 +1014,8 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
   DBuf<double> diag(c, n);
   k_diag<<<grid_for(n, B), B, 0, c.s>>>(n, A.rp, A.ci, A.v, diag.p);
   CU_LAUNCH();
-  k_extpi_weights_sh<EXT_PCAP_S, EXT_KCAP_S, 12><<<grid_for(n, EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(
-      n, A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p, cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p, 0);
+  k_extpi_weights_row<<<grid_for(n, EXT_TPB), EXT_TPB, 0, c.s>>>(n, A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p,
+                                                                 cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p);
   CU_LAUNCH();
   k_extpi_weights_sh<EXT_PCAP_L, EXT_KCAP_L, 1><<<grid_for(n, EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(
       n, A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p, cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p, 1);
