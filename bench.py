@@ -403,7 +403,7 @@ def main():
     if rap:
         t_s = sum(sb[k]["ms"] for k in rap)
         by_s = sum(kt[k][2] for k in rap)
-        out["roofline_setup"] = {"kernel": "spgemm (k_spgemm_tiny, k_spgemm_fused_chunk, k_spgemm_fused_hash)",
+        out["roofline_setup"] = {"kernel": "spgemm (k_spgemm_tiny, k_spgemm_fused_chunk, k_spgemm_chunk_list)",
                                  "bound": "issue", "ms": t_s, "achieved_gbs": by_s / (t_s * 1e-3) / 1e9,
                                  "frac_of_hbm": by_s / (t_s * 1e-3) / 1e9 / peak, "calls": sum(sb[k]["calls"] for k in rap)}
     if kt_dom:

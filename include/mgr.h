@@ -93,7 +93,10 @@ typedef struct {
                                             with device copies around each replay): 0 auto (systems
                                             of at most 2^21 unknowns, where the apply is bound by its
                                             launches), 1 always, -1 never.  Profiling disables it */
-  int32_t reserved[4];                   /* must be zero */
+  int32_t pdl;                           /* 0: the apply and Krylov kernels use programmatic dependent
+                                            launch (each may start while its predecessor drains and
+                                            waits for it before touching memory); -1: plain launches */
+  int32_t reserved[3];                   /* must be zero */
 } mgr_options_t;
 
 typedef struct {

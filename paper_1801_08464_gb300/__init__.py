@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
                 ("amg_smoother", ctypes.c_int32), ("amg_pre", ctypes.c_int32), ("amg_post", ctypes.c_int32),
                 ("amg_pmax", ctypes.c_int32), ("amg_omega", ctypes.c_double), ("amg_seed", ctypes.c_uint64),
                 ("lean", ctypes.c_int32), ("spgemm_stage", ctypes.c_int32),
-                ("adjoint", ctypes.c_int32), ("apply_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("adjoint", ctypes.c_int32), ("apply_graph", ctypes.c_int32), ("pdl", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class Bsr3(ctypes.Structure):

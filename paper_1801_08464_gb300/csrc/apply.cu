@@ -13,6 +13,7 @@ __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
 // ============================== level 0: 3x3 blocks =============================================
 template <class T>
 __global__ void k_global_relax(int64_t nb, const T* __restrict__ binv, const double* __restrict__ r, T* __restrict__ e0) {
+  pdl_wait();
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nb) return;
   T r0 = (T)r[3 * I], r1 = (T)r[3 * I + 1], r2 = (T)r[3 * I + 2];
@@ -25,7 +26,7 @@ __global__ void k_global_relax(int64_t nb, const T* __restrict__ binv, const dou
 template <class T>
 void launch_global_relax(Ctx& c, int64_t nb, const T* binv, const double* r, T* e0) {
   ProfScope ps(c, "global_relax", (double)nb * (9 * sizeof(T) + 24 + 3 * sizeof(T)));
-  k_global_relax<T><<<grid_for(nb, 256), 256, 0, c.s>>>(nb, binv, r, e0);
+  launch_pdl(c, k_global_relax<T>, grid_for(nb, 256), 256, 0, nb, binv, r, e0);
   CU_LAUNCH();
 }
 
@@ -36,6 +37,7 @@ __global__ void __launch_bounds__(256) k_bsr_resid_split(int64_t nb, const int64
                                                          const double* __restrict__ r, const T* __restrict__ e0,
                                                          const int32_t* __restrict__ map, T* __restrict__ rnext,
                                                          T* __restrict__ resF) {
+  pdl_wait();
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nb) return;
   T s0 = 0, s1 = 0, s2 = 0;
@@ -83,7 +85,7 @@ void launch_bsr_resid_split(Ctx& c, const SellPattern& S, const T* vals, const d
   if (e0) {
     launch_bsr_sell<T, T>(c, S, vals, e0, EpiSplit<T>{r, map, rnext, resF});
   } else {
-    k_bsr_resid_split<T><<<grid_for(S.nb, 256), 256, 0, c.s>>>(S.nb, nullptr, nullptr, vals, r, e0, map, rnext, resF);
+    launch_pdl(c, k_bsr_resid_split<T>, grid_for(S.nb, 256), 256, 0, S.nb, nullptr, nullptr, vals, r, e0, map, rnext, resF);
     CU_LAUNCH();
   }
 }
@@ -94,6 +96,7 @@ void launch_bsr_resid_split(Ctx& c, const SellPattern& S, const T* vals, const d
 template <class T, int TPR, class Epi>
 __global__ void __launch_bounds__(256) k_rows(int64_t nr, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                               const T* __restrict__ v, const T* __restrict__ x, Epi epi) {
+  pdl_wait();
   int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t r = gt / TPR;
   int sub = (int)(gt % TPR);
@@ -140,6 +143,7 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
                                                    const int32_t* __restrict__ col, const T* __restrict__ val,
                                                    const int32_t* __restrict__ perm, const T* __restrict__ x,
                                                    Epi epi) {
+  pdl_wait();
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= nr) return;
   int64_t s = r / RS_C;
@@ -172,6 +176,7 @@ __global__ void __launch_bounds__(256) k_rows_sell_split(int64_t nr, const int64
                                                          const int32_t* __restrict__ col, const T* __restrict__ val,
                                                          const int32_t* __restrict__ perm, const T* __restrict__ x,
                                                          Epi epi) {
+  pdl_wait();
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t s = g / (RS_C * H);
   const int u = (int)(g - s * (RS_C * H));
@@ -223,19 +228,20 @@ static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, co
     // threads per row: enough for six waves of resident threads, at most 4
     const int64_t slices = (op.nr + RS_C - 1) / RS_C;
     int H = 1;
+    // (each thread keeps at least two 4-slot groups of an average row)
     if (op.q == 4)
-      while (H < 4 && op.nr * H < 6 * device_threads()) H *= 2;
+      while (H < 4 && op.nr * H < 6 * device_threads() && (double)op.nnz >= 8.0 * 2 * H * (double)op.nr) H *= 2;
     if (op.q == 4 && H == 1)
-      k_rows_sell<T, Epi, 4><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
+      launch_pdl(c, k_rows_sell<T, Epi, 4>, grid_for(op.nr, B), B, 0, op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
                                                                 epi);
     else if (op.q == 4 && H == 2)
-      k_rows_sell_split<T, Epi, 2><<<grid_for(slices * RS_C * 2, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p,
+      launch_pdl(c, k_rows_sell_split<T, Epi, 2>, grid_for(slices * RS_C * 2, B), B, 0, op.nr, op.soff.p, op.scol.p,
                                                                                     op.sval.p, op.perm.p, x, epi);
     else if (op.q == 4)
-      k_rows_sell_split<T, Epi, 4><<<grid_for(slices * RS_C * 4, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p,
+      launch_pdl(c, k_rows_sell_split<T, Epi, 4>, grid_for(slices * RS_C * 4, B), B, 0, op.nr, op.soff.p, op.scol.p,
                                                                                     op.sval.p, op.perm.p, x, epi);
     else
-      k_rows_sell<T, Epi, 1><<<grid_for(op.nr, B), B, 0, c.s>>>(op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
+      launch_pdl(c, k_rows_sell<T, Epi, 1>, grid_for(op.nr, B), B, 0, op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
                                                                 epi);
     CU_LAUNCH();
     return;
@@ -244,19 +250,19 @@ static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, co
   double avg = M.nr ? (double)M.nnz / (double)M.nr : 0.0;
   // lanes per row: about four entries per lane or more
   if (avg <= 5.0) {
-    k_rows<T, 2, Epi><<<grid_for(M.nr * 2, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    launch_pdl(c, k_rows<T, 2, Epi>, grid_for(M.nr * 2, B), B, 0, M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
   } else if (avg <= 12.0) {
-    k_rows<T, 4, Epi><<<grid_for(M.nr * 4, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    launch_pdl(c, k_rows<T, 4, Epi>, grid_for(M.nr * 4, B), B, 0, M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
   } else if (avg <= 24.0) {
-    k_rows<T, 8, Epi><<<grid_for(M.nr * 8, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    launch_pdl(c, k_rows<T, 8, Epi>, grid_for(M.nr * 8, B), B, 0, M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
   } else if (avg <= 128.0) {
-    k_rows<T, 16, Epi><<<grid_for(M.nr * 16, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    launch_pdl(c, k_rows<T, 16, Epi>, grid_for(M.nr * 16, B), B, 0, M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
   } else {
-    k_rows<T, 32, Epi><<<grid_for(M.nr * 32, B), B, 0, c.s>>>(M.nr, M.rp, M.ci, M.v, x, epi);
+    launch_pdl(c, k_rows<T, 32, Epi>, grid_for(M.nr * 32, B), B, 0, M.nr, M.rp, M.ci, M.v, x, epi);
     CU_LAUNCH();
   }
 }
@@ -314,6 +320,7 @@ struct EpiAdd {
 
 template <class T>
 __global__ void k_frelax_first(int64_t nF, const int32_t* F, const T* src, const T* minv, T* eF) {
+  pdl_wait();
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= nF) return;
   eF[f] = minv[f] * (F ? src[F[f]] : src[f]);
@@ -322,7 +329,7 @@ __global__ void k_frelax_first(int64_t nF, const int32_t* F, const T* src, const
 template <class T>
 void launch_frelax_first(Ctx& c, int64_t nF, const int32_t* F, const T* src, const T* minv, T* eF) {
   if (nF <= 0) return;
-  k_frelax_first<T><<<grid_for(nF, 256), 256, 0, c.s>>>(nF, F, src, minv, eF);
+  launch_pdl(c, k_frelax_first<T>, grid_for(nF, 256), 256, 0, nF, F, src, minv, eF);
   CU_LAUNCH();
 }
 template <class T>
@@ -341,6 +348,7 @@ void launch_restrict(Ctx& c, const RowsOp<T>& Acf, const int32_t* C, const T* r,
 template <class T, class TO>
 __global__ void k_interp_c(int64_t nC, const int32_t* __restrict__ C, const T* __restrict__ ec,
                            const T* __restrict__ base, TO* __restrict__ out) {
+  pdl_wait();
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= nC) return;
   int32_t d = C[c];
@@ -369,7 +377,7 @@ void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32
                    const T* eF, const T* ec, const T* base, TO* out, const char* name) {
   if (nC > 0) {
     ProfScope ps(c, name, (double)nC * (4.0 + sizeof(T) + (base ? sizeof(T) : 0) + sizeof(TO)));
-    k_interp_c<T, TO><<<grid_for(nC, 256), 256, 0, c.s>>>(nC, C, ec, base, out);
+    launch_pdl(c, k_interp_c<T, TO>, grid_for(nC, 256), 256, 0, nC, C, ec, base, out);
     CU_LAUNCH();
   }
   if (nF > 0) run_rows(c, Wp, ec, EpiInterpF<T, TO>{F, eF, base, out}, name);
@@ -378,24 +386,26 @@ void launch_interp(Ctx& c, int64_t nF, const int32_t* F, int64_t nC, const int32
 // dst[f] = src[idx[f]], and y += x
 template <class T>
 __global__ void k_gather(int64_t n, const int32_t* __restrict__ idx, const T* __restrict__ src, T* __restrict__ dst) {
+  pdl_wait();
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f < n) dst[f] = src[idx[f]];
 }
 template <class T>
 void launch_gather(Ctx& c, int64_t n, const int32_t* idx, const T* src, T* dst) {
   if (n <= 0) return;
-  k_gather<T><<<grid_for(n, 256), 256, 0, c.s>>>(n, idx, src, dst);
+  launch_pdl(c, k_gather<T>, grid_for(n, 256), 256, 0, n, idx, src, dst);
   CU_LAUNCH();
 }
 template <class T>
 __global__ void k_axpy1(int64_t n, const T* __restrict__ x, T* __restrict__ y) {
+  pdl_wait();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) y[i] += x[i];
 }
 template <class T>
 void launch_axpy(Ctx& c, int64_t n, const T* x, T* y) {
   if (n <= 0) return;
-  k_axpy1<T><<<grid_for(n, 256), 256, 0, c.s>>>(n, x, y);
+  launch_pdl(c, k_axpy1<T>, grid_for(n, 256), 256, 0, n, x, y);
   CU_LAUNCH();
 }
 
@@ -417,6 +427,7 @@ void launch_gather_add(Ctx& c, const RowsOp<T>& WpT, const int32_t* C, const T* 
 template <class T>
 __global__ void k_scatter_cf(int64_t nC, const int32_t* C, const T* tc, int64_t nF, const int32_t* F, const T* gF,
                              T* g) {
+  pdl_wait();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t < nC) g[C[t]] = tc[t];
   else if (t < nC + nF) g[F[t - nC]] = gF[t - nC];
@@ -426,7 +437,7 @@ void launch_scatter_cf(Ctx& c, int64_t nC, const int32_t* C, const T* tc, int64_
                        T* g) {
   if (nC + nF <= 0) return;
   ProfScope ps(c, "scatter_cf", (double)(nC + nF) * (4.0 + 2.0 * sizeof(T)));
-  k_scatter_cf<T><<<grid_for(nC + nF, 256), 256, 0, c.s>>>(nC, C, tc, nF, F, gF, g);
+  launch_pdl(c, k_scatter_cf<T>, grid_for(nC + nF, 256), 256, 0, nC, C, tc, nF, F, gF, g);
   CU_LAUNCH();
 }
 
@@ -452,6 +463,7 @@ void launch_bsr_grt(Ctx& c, const SellPattern& S, const T* valsT, const double* 
 
 template <class T>
 __global__ void k_transpose_blocks(int64_t nb, const T* b, T* bt) {
+  pdl_wait();
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nb) return;
 #pragma unroll
@@ -462,11 +474,12 @@ __global__ void k_transpose_blocks(int64_t nb, const T* b, T* bt) {
 template <class T>
 void launch_transpose_blocks(Ctx& c, int64_t nb, const T* b, T* bt) {
   if (nb <= 0) return;
-  k_transpose_blocks<T><<<grid_for(nb, 256), 256, 0, c.s>>>(nb, b, bt);
+  launch_pdl(c, k_transpose_blocks<T>, grid_for(nb, 256), 256, 0, nb, b, bt);
   CU_LAUNCH();
 }
 
 __global__ void k_dense_transpose(int64_t n, const double* a, double* at) {
+  pdl_wait();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= n * n) return;
   int64_t i = t / n, j = t - i * n;
@@ -474,41 +487,44 @@ __global__ void k_dense_transpose(int64_t n, const double* a, double* at) {
 }
 void launch_dense_transpose(Ctx& c, int64_t n, const double* a, double* at) {
   if (n <= 0) return;
-  k_dense_transpose<<<grid_for(n * n, 256), 256, 0, c.s>>>(n, a, at);
+  launch_pdl(c, k_dense_transpose, grid_for(n * n, 256), 256, 0, n, a, at);
   CU_LAUNCH();
 }
 
 // columns j of a CSR matrix replaced by map[j]
 __global__ void k_map_cols(int64_t nnz, int32_t* ci, const int32_t* map) {
+  pdl_wait();
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k < nnz) ci[k] = map[ci[k]];
 }
 void launch_map_cols(Ctx& c, int64_t nnz, int32_t* ci, const int32_t* map) {
   if (nnz <= 0) return;
-  k_map_cols<<<grid_for(nnz, 256), 256, 0, c.s>>>(nnz, ci, map);
+  launch_pdl(c, k_map_cols, grid_for(nnz, 256), 256, 0, nnz, ci, map);
   CU_LAUNCH();
 }
 
 template <class T>
 __global__ void k_to_f64(int64_t n, const T* a, double* b) {
+  pdl_wait();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) b[i] = (double)a[i];
 }
 template <class T>
 void launch_to_f64(Ctx& c, int64_t n, const T* a, double* b) {
-  k_to_f64<T><<<grid_for(n, 256), 256, 0, c.s>>>(n, a, b);
+  launch_pdl(c, k_to_f64<T>, grid_for(n, 256), 256, 0, n, a, b);
   CU_LAUNCH();
 }
 
 // ============================== AMG V-cycle pieces ==============================================
 template <class T>
 __global__ void k_scale_vec(int64_t n, const T* d, const T* b, T* x) {
+  pdl_wait();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) x[i] = d[i] * b[i];
 }
 template <class T>
 void launch_scale(Ctx& c, int64_t n, const T* d, const T* b, T* x) {
-  k_scale_vec<T><<<grid_for(n, 256), 256, 0, c.s>>>(n, d, b, x);
+  launch_pdl(c, k_scale_vec<T>, grid_for(n, 256), 256, 0, n, d, b, x);
   CU_LAUNCH();
 }
 template <class T>
@@ -531,6 +547,7 @@ void launch_prolong_add(Ctx& c, const RowsOp<T>& P, const T* xc, T* x, const cha
 // x = inv b with the FP64 dense inverse of the coarsest operator: one warp per row
 template <class T>
 __global__ void k_dense_gemv(int64_t n, const double* __restrict__ inv, const T* __restrict__ b, T* __restrict__ x) {
+  pdl_wait();
   int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (i >= n) return;
@@ -542,17 +559,18 @@ __global__ void k_dense_gemv(int64_t n, const double* __restrict__ inv, const T*
 template <class T>
 void launch_dense_gemv(Ctx& c, int64_t n, const double* inv, const T* b, T* x) {
   if (n <= 0) return;
-  k_dense_gemv<T><<<grid_for(n * 32, 256), 256, 0, c.s>>>(n, inv, b, x);
+  launch_pdl(c, k_dense_gemv<T>, grid_for(n * 32, 256), 256, 0, n, inv, b, x);
   CU_LAUNCH();
 }
 
 __global__ void k_cast_f32(int64_t n, const double* a, float* b) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
 }
 void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b) {
   if (n <= 0) return;
-  k_cast_f32<<<grid_for(n, 256, 8192), 256, 0, c.s>>>(n, a, b);
+  launch_pdl(c, k_cast_f32, grid_for(n, 256, 8192), 256, 0, n, a, b);
   CU_LAUNCH();
 }
 

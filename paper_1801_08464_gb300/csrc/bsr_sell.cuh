@@ -39,6 +39,7 @@ template <class T, class TX, class Epi>
 __global__ void __launch_bounds__(256) k_bsr_sell(int64_t nb, const int64_t* __restrict__ soff,
                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
                                                   const TX* __restrict__ x, Epi epi) {
+  pdl_wait();
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nb) return;
   int64_t s = I / SELL_C;
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(256) k_bsr_sell(int64_t nb, const int64_t* __r
 
 template <class T, class TX, class Epi>
 inline void launch_bsr_sell(Ctx& c, const SellPattern& S, const T* val, const TX* x, const Epi& epi) {
-  k_bsr_sell<T, TX, Epi><<<grid_for(S.nb, 256), 256, 0, c.s>>>(S.nb, S.soff.p, S.col.p, val, x, epi);
+  launch_pdl(c, k_bsr_sell<T, TX, Epi>, grid_for(S.nb, 256), 256, 0, S.nb, S.soff.p, S.col.p, val, x, epi);
   CU_LAUNCH();
 }
 

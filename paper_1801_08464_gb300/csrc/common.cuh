@@ -96,6 +96,7 @@ struct Ctx {
   int64_t bytes = 0;           // bytes currently allocated through this context
   int64_t peak = 0;
   int num_sms = 152;
+  bool pdl = true;             // programmatic dependent launch for the kernels launched with launch_pdl
 };
 
 struct ProfScope {
@@ -180,6 +181,36 @@ T read_scalar(Ctx& c, const T* dptr) {
   return h;
 }
 void check_errors(Ctx& c, const char* phase);  // reads d_err, throws on set bits, clears it
+
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be scheduled while its
+// predecessor in the stream still runs (the launch latency of a chain of short dependent kernels
+// overlaps the previous one).  Such a kernel calls pdl_wait() before it touches global memory: it
+// returns once the predecessor grid has completed and its writes are visible (at once for a kernel
+// launched without the attribute), and then lets the next kernel be scheduled; that kernel can start
+// only after every block of this one has passed this point, so all of this grid is resident or done
+// by then.
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(Ctx& c, void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                       const Args&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = c.pdl ? 1 : 0;
+  cuda_check(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...), "kernel launch", __FILE__, __LINE__);
+}
 
 inline unsigned grid_for(int64_t n, int block, int64_t cap = (1ll << 30)) {
   int64_t g = (n + block - 1) / block;

@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(256) k_bsr3_spmv_f64(int64_t nb, const int64_t
                                                        const int32_t* __restrict__ ci, const double* __restrict__ v,
                                                        const double* __restrict__ x, const double* __restrict__ sub,
                                                        double* __restrict__ y) {
+  pdl_wait();
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nb) return;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
@@ -44,7 +45,7 @@ struct EpiSpmvF64 {  // y = A x, or y = sub - A x
 };
 
 void launch_bsr3_spmv_f64(Ctx& c, const mgr_bsr3_t& A, const double* x, const double* sub, double* y) {
-  k_bsr3_spmv_f64<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.colind, A.values, x, sub, y);
+  launch_pdl(c, k_bsr3_spmv_f64, grid_for(A.nb, 256), 256, 0, A.nb, A.rowptr, A.colind, A.values, x, sub, y);
   CU_LAUNCH();
 }
 
@@ -85,6 +86,7 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NA], int na, do
 __global__ void __launch_bounds__(KT) k_mdot(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
                                              const double* __restrict__ w, int ww, int ng, int nx, int64_t chunk,
                                              double* __restrict__ part) {
+  pdl_wait();
   int g = blockIdx.x % ng;
   int x = blockIdx.x / ng;
   int k0 = g * MD_VEC;
@@ -140,6 +142,7 @@ __global__ void __launch_bounds__(KT) k_mdot(int64_t n, const double* __restrict
 // out[k] = sum over the nx partials of k, in a fixed order (a warp per k, strided lanes, then a
 // fixed shuffle tree)
 __global__ void k_reduce_parts(int nx, int na, const double* __restrict__ part, double* __restrict__ out) {
+  pdl_wait();
   int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
   if (k >= na) return;
@@ -189,10 +192,10 @@ void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const 
   int64_t chunk;
   int nx = md_nx(n, ng, &chunk);
   ProfScope ps(c, "mdot", 8.0 * (nv + 1) * n);
-  k_mdot<<<ng * nx, KT, 0, c.s>>>(n, V, ldv, nv, w, ww, ng, nx, chunk, part);
+  launch_pdl(c, k_mdot, ng * nx, KT, 0, n, V, ldv, nv, w, ww, ng, nx, chunk, part);
   CU_LAUNCH();
   int na = nv + ww;
-  k_reduce_parts<<<(na + 7) / 8, 256, 0, c.s>>>(nx, na, part, out);
+  launch_pdl(c, k_reduce_parts, (na + 7) / 8, 256, 0, nx, na, part, out);
   CU_LAUNCH();
 }
 
@@ -201,6 +204,7 @@ void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const 
 __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
                                                 const double* __restrict__ h, const double* __restrict__ sp,
                                                 const double* w, double* vout, double* __restrict__ part) {
+  pdl_wait();
   __shared__ double sh_h[KRY_MAXV];
   if (threadIdx.x < nv) sh_h[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
@@ -238,16 +242,17 @@ void launch_mupdate(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, con
   if (nv > KRY_MAXV) throw Error(MGR_ERR_UNSUPPORTED, "update with more than 32 vectors");
   ProfScope ps(c, "mupdate", 8.0 * (nv + 2) * n);
   const int grid = one_wave((const void*)k_mupdate);
-  k_mupdate<<<grid, KT, 0, c.s>>>(n, V, ldv, nv, h, scale, w, vout, out ? part : nullptr);
+  launch_pdl(c, k_mupdate, grid, KT, 0, n, V, ldv, nv, h, scale, w, vout, out ? part : nullptr);
   CU_LAUNCH();
   if (out) {
-    k_reduce_parts<<<1, 32, 0, c.s>>>(grid, 1, part, out);
+    launch_pdl(c, k_reduce_parts, 1, 32, 0, grid, 1, part, out);
     CU_LAUNCH();
   }
 }
 
 // s_out = 1 / sqrt(ww - sum_k h_k^2): the Pythagorean norm of w - V h for orthonormal V
 __global__ void k_pyth_scale(int nv, const double* __restrict__ h, const double* __restrict__ ww, double* out) {
+  pdl_wait();
   if (threadIdx.x != 0) return;
   double s = *ww;
   for (int k = 0; k < nv; ++k) s -= h[k] * h[k];
@@ -255,33 +260,36 @@ __global__ void k_pyth_scale(int nv, const double* __restrict__ h, const double*
   out[1] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
 }
 void launch_pyth_scale(Ctx& c, int nv, const double* h, const double* ww, double* out) {
-  k_pyth_scale<<<1, 32, 0, c.s>>>(nv, h, ww, out);
+  launch_pdl(c, k_pyth_scale, 1, 32, 0, nv, h, ww, out);
   CU_LAUNCH();
 }
 
 __global__ void __launch_bounds__(KT) k_nrm2sq(int64_t n, const double* __restrict__ x, double* __restrict__ part) {
+  pdl_wait();
   double acc[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)KT + threadIdx.x; i < n; i += (int64_t)gridDim.x * KT) acc[0] += x[i] * x[i];
   block_reduce_store<1>(acc, 1, part);
 }
 void launch_nrm2sq(Ctx& c, int64_t n, const double* x, double* part, double* out) {
-  k_nrm2sq<<<KRY_GRID, KT, 0, c.s>>>(n, x, part);
+  launch_pdl(c, k_nrm2sq, KRY_GRID, KT, 0, n, x, part);
   CU_LAUNCH();
-  k_reduce_parts<<<1, 32, 0, c.s>>>(KRY_GRID, 1, part, out);
+  launch_pdl(c, k_reduce_parts, 1, 32, 0, KRY_GRID, 1, part, out);
   CU_LAUNCH();
 }
 
 __global__ void k_scal(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i];
 }
 void launch_scal(Ctx& c, int64_t n, double alpha, const double* x, double* y) {
-  k_scal<<<grid_for(n, 256, 4 * 1024), 256, 0, c.s>>>(n, alpha, x, y);
+  launch_pdl(c, k_scal, grid_for(n, 256, 4 * 1024), 256, 0, n, alpha, x, y);
   CU_LAUNCH();
 }
 
 __global__ void k_xupdate(int64_t n, const double* __restrict__ Z, int64_t ldz, int nz, const double* __restrict__ y,
                           double* __restrict__ x) {
+  pdl_wait();
   __shared__ double sy[KRY_MAXV];
   if (threadIdx.x < nz) sy[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
@@ -296,7 +304,7 @@ __global__ void k_xupdate(int64_t n, const double* __restrict__ Z, int64_t ldz, 
 void launch_xupdate(Ctx& c, int64_t n, const double* Z, int64_t ldz, int nz, const double* y, double* x) {
   for (int k0 = 0; k0 < nz; k0 += KRY_MAXV) {
     int m = nz - k0 < KRY_MAXV ? nz - k0 : KRY_MAXV;
-    k_xupdate<<<grid_for(n, 256, 4 * 1024), 256, 0, c.s>>>(n, Z + k0 * ldz, ldz, m, y + k0, x);
+    launch_pdl(c, k_xupdate, grid_for(n, 256, 4 * 1024), 256, 0, n, Z + k0 * ldz, ldz, m, y + k0, x);
     CU_LAUNCH();
   }
 }
@@ -305,6 +313,7 @@ void launch_xupdate(Ctx& c, int64_t n, const double* Z, int64_t ldz, int nz, con
 // g[9k + 3p + q] = -lam[3I+p] x[3J+q]
 __global__ void k_outer_grad(int64_t nb, const int64_t* rp, const int32_t* ci, const double* lam, const double* x,
                              double* g) {
+  pdl_wait();
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nb) return;
   double l0 = lam[3 * I], l1 = lam[3 * I + 1], l2 = lam[3 * I + 2];
@@ -318,16 +327,18 @@ __global__ void k_outer_grad(int64_t nb, const int64_t* rp, const int32_t* ci, c
   }
 }
 void launch_bsr3_outer_grad(Ctx& c, const mgr_bsr3_t& A, const double* lam, const double* x, double* g) {
-  k_outer_grad<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.colind, lam, x, g);
+  launch_pdl(c, k_outer_grad, grid_for(A.nb, 256), 256, 0, A.nb, A.rowptr, A.colind, lam, x, g);
   CU_LAUNCH();
 }
 
 __global__ void k_bcol_count(int64_t nnzb, const int32_t* ci, unsigned long long* cnt) {
+  pdl_wait();
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnzb; k += (int64_t)gridDim.x * blockDim.x)
     atomicAdd(&cnt[ci[k]], 1ull);
 }
 __global__ void k_bscatter(int64_t nb, const int64_t* rp, const int32_t* ci, const int64_t* trp, unsigned long long* slot,
                            int32_t* tci, int64_t* src) {
+  pdl_wait();
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (I >= nb) return;
   for (int64_t k = rp[I]; k < rp[I + 1]; ++k) {
@@ -340,6 +351,7 @@ __global__ void k_bscatter(int64_t nb, const int64_t* rp, const int32_t* ci, con
 // sort each transposed block row by column (insertion sort: block rows are short), then copy the
 // transposed 3x3 blocks
 __global__ void k_bsort_fill(int64_t nb, const int64_t* trp, int32_t* tci, int64_t* src, const double* v, double* vt) {
+  pdl_wait();
   int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (J >= nb) return;
   int64_t b = trp[J], e = trp[J + 1];
@@ -364,13 +376,13 @@ void launch_bsr3_transpose(Ctx& c, const mgr_bsr3_t& A, int64_t* rpt, int32_t* c
   DBuf<unsigned long long> cnt(c, A.nb + 1);
   DBuf<int64_t> src(c, A.nnzb);
   CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (A.nb + 1), c.s));
-  k_bcol_count<<<grid_for(A.nnzb, 256, 8192), 256, 0, c.s>>>(A.nnzb, A.colind, cnt.p);
+  launch_pdl(c, k_bcol_count, grid_for(A.nnzb, 256, 8192), 256, 0, A.nnzb, A.colind, cnt.p);
   CU_LAUNCH();
   scan_excl_i64(c, reinterpret_cast<const int64_t*>(cnt.p), rpt, A.nb);
   CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (A.nb + 1), c.s));
-  k_bscatter<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.colind, rpt, cnt.p, cit, src.p);
+  launch_pdl(c, k_bscatter, grid_for(A.nb, 256), 256, 0, A.nb, A.rowptr, A.colind, rpt, cnt.p, cit, src.p);
   CU_LAUNCH();
-  k_bsort_fill<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, rpt, cit, src.p, A.values, vt);
+  launch_pdl(c, k_bsort_fill, grid_for(A.nb, 256), 256, 0, A.nb, rpt, cit, src.p, A.values, vt);
   CU_LAUNCH();
   CU(cudaStreamSynchronize(c.s));
 }
@@ -378,6 +390,7 @@ void launch_bsr3_transpose(Ctx& c, const mgr_bsr3_t& A, int64_t* rpt, int32_t* c
 // Pattern of A^T (row pointers, block columns ascending) and, per transposed block, the index of its
 // source block in A.
 __global__ void k_bsort_src(int64_t nb, const int64_t* trp, int32_t* tci, int64_t* src) {
+  pdl_wait();
   int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (J >= nb) return;
   int64_t b = trp[J], e = trp[J + 1];
@@ -393,13 +406,13 @@ __global__ void k_bsort_src(int64_t nb, const int64_t* trp, int32_t* tci, int64_
 void launch_bsr3_transpose_pattern(Ctx& c, const mgr_bsr3_t& A, int64_t* rpt, int32_t* cit, int64_t* src) {
   DBuf<unsigned long long> cnt(c, A.nb + 1);
   CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (A.nb + 1), c.s));
-  k_bcol_count<<<grid_for(A.nnzb, 256, 8192), 256, 0, c.s>>>(A.nnzb, A.colind, cnt.p);
+  launch_pdl(c, k_bcol_count, grid_for(A.nnzb, 256, 8192), 256, 0, A.nnzb, A.colind, cnt.p);
   CU_LAUNCH();
   scan_excl_i64(c, reinterpret_cast<const int64_t*>(cnt.p), rpt, A.nb);
   CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * (A.nb + 1), c.s));
-  k_bscatter<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.colind, rpt, cnt.p, cit, src);
+  launch_pdl(c, k_bscatter, grid_for(A.nb, 256), 256, 0, A.nb, A.rowptr, A.colind, rpt, cnt.p, cit, src);
   CU_LAUNCH();
-  k_bsort_src<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, rpt, cit, src);
+  launch_pdl(c, k_bsort_src, grid_for(A.nb, 256), 256, 0, A.nb, rpt, cit, src);
   CU_LAUNCH();
 }
 

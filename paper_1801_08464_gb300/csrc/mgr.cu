@@ -978,6 +978,7 @@ static mgr_status_t check_options(const mgr_options_t& o) {
     return MGR_ERR_INVALID_ARG;
   if (o.amg_smoother < 0 || o.amg_smoother > 1 || o.amg_pmax < 0) return MGR_ERR_INVALID_ARG;
   if (o.apply_graph < -1 || o.apply_graph > 1) return MGR_ERR_INVALID_ARG;
+  if (o.pdl < -1 || o.pdl > 0) return MGR_ERR_INVALID_ARG;
   return MGR_OK;
 }
 
@@ -992,6 +993,7 @@ mgr_status_t mgr_create(mgr_handle_t* out, const mgr_options_t* opt, void* strea
   st = guarded(h, [&] {
     CU(cudaGetDevice(&h->device));
     h->c.s = static_cast<cudaStream_t>(stream);
+    h->c.pdl = h->o.pdl >= 0;
     int sms = 0;
     CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
     h->c.num_sms = sms;

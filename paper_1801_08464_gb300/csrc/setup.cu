@@ -642,9 +642,12 @@ __global__ void k_diag(int64_t n, const int64_t* __restrict__ rp, const int32_t*
 // against its strength row and its interpolation columns; row k against the columns).  The
 // interpolation columns and numerators sit in shared memory ([slot][thread]); rows with more than
 // EXT_PCAP_T columns are flagged rest = 1 for the warp kernel below.
-constexpr int EXT_TPB = 128, EXT_PCAP_T = 16;
+constexpr int EXT_TPB = 128, EXT_PCAP_T = 8;
 
-__global__ void __launch_bounds__(EXT_TPB) k_extpi_weights_row(
+// Its loads are one stream per thread, so L1 must hold many rows: the shared stage is kept small
+// (EXT_PCAP_T slots per thread; about 3 % of the F rows of a pressure-like operator have more
+// interpolation columns and take the warp kernel) and the registers are capped for 12 blocks per SM.
+__global__ void __launch_bounds__(EXT_TPB, 12) k_extpi_weights_row(
     int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
     const double* __restrict__ diag, const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
     const int8_t* __restrict__ cf, const int32_t* __restrict__ cfine, const int64_t* __restrict__ prp,

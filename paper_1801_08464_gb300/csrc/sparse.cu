@@ -544,100 +544,6 @@ __device__ __forceinline__ void warp_rank_store128(const int32_t* K, const doubl
   }
 }
 
-// Fused product for the rows with at most FUSE_CAP products that k_spgemm_fused_chunk left (long A
-// rows or more than FZ_SLOTS / 2 products; it lists them): the A row is walked in ascending
-// order (ascending k); the products of one A entry have distinct columns, so the lanes add them to a
-// shared-memory hash table (column -> running sum) without conflicts, and __syncwarp orders successive
-// k.  Each sum therefore starts from 0.0 and adds its products in ascending k (Gustavson's order).
-// The distinct columns are then compacted, sorted (rank placement up to 128, else bitonic, values
-// carried) and staged.  Two shapes: 2 warps with 2048 slots each for rows of at most FH_CAP
-// products, one warp with 4096 slots for the rest up to FUSE_CAP (48 KB of shared memory either way).
-constexpr int FH_CAP = 1024;
-
-template <int FH_WARPS, int FH_SLOTS>
-__global__ void __launch_bounds__(32 * FH_WARPS) k_spgemm_fused_hash(
-    const int32_t* __restrict__ rows, const int* __restrict__ nrows, const int64_t* __restrict__ arp,
-    const int32_t* __restrict__ aci, const double* __restrict__ av, const int64_t* __restrict__ brp,
-    const int32_t* __restrict__ bci, const double* __restrict__ bv, const int64_t* __restrict__ ub,
-    const int64_t* __restrict__ soff, int64_t sbase, int32_t* __restrict__ scol, double* __restrict__ sval,
-    int64_t* __restrict__ cnt) {
-  __shared__ int32_t hk[FH_WARPS][FH_SLOTS];
-  __shared__ double hv[FH_WARPS][FH_SLOTS];
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t nr = *nrows;
-  // a fixed grid walks the list of rows left by k_spgemm_fused_chunk
-  for (int64_t r = (int64_t)blockIdx.x * FH_WARPS + w; r < nr; r += (int64_t)gridDim.x * FH_WARPS) {
-    const int64_t i = rows[r];
-    int U = (int)ub[i];
-    int32_t* K = hk[w];
-    double* Vv = hv[w];
-    int H = 1;
-    while (H < 2 * U) H <<= 1;
-    for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
-    __syncwarp();
-    for (int64_t p = arp[i]; p < arp[i + 1]; ++p) {
-      int32_t k = aci[p];
-      double a = av[p];
-      for (int64_t q = brp[k] + lane; q < brp[k + 1]; q += 32) {
-        int32_t key = bci[q];
-        double prod = __dmul_rn(a, bv[q]);
-        uint32_t h = hash32(key) & (H - 1);
-        while (true) {
-          int32_t prev = atomicCAS(&K[h], -1, key);
-          if (prev == -1 || prev == key) break;
-          h = (h + 1) & (H - 1);
-        }
-        Vv[h] = __dadd_rn(Vv[h], prod);
-      }
-      __syncwarp();
-    }
-    // compaction of the occupied slots to the front (order irrelevant: sorted next)
-    int base = 0;
-    for (int t0 = 0; t0 < H; t0 += 32) {
-      int t = t0 + lane;
-      int32_t key = t < H ? K[t] : -1;
-      double v = t < H ? Vv[t] : 0.0;
-      unsigned msk = __ballot_sync(0xffffffffu, key >= 0);
-      __syncwarp();
-      if (key >= 0) {
-        int pos = base + __popc(msk & ((1u << lane) - 1));
-        K[pos] = key;
-        Vv[pos] = v;
-      }
-      base += __popc(msk);
-      __syncwarp();
-    }
-    int u = base;
-    int64_t o = soff[i] - sbase;
-    if (u <= 128) {
-      warp_rank_store128(K, Vv, u, lane, scol + o, sval + o);
-    } else {
-      int n2 = 1;
-      while (n2 < u) n2 <<= 1;
-      for (int t = u + lane; t < n2; t += 32) K[t] = INT_MAX;
-      __syncwarp();
-      for (int k2 = 2; k2 <= n2; k2 <<= 1)
-        for (int j = k2 >> 1; j > 0; j >>= 1) {
-          for (int t = lane; t < n2; t += 32) {
-            int x = t ^ j;
-            if (x > t) {
-              bool up = (t & k2) == 0;
-              int32_t ka = K[t], kb = K[x];
-              if ((ka > kb) == up) {
-                K[t] = kb; K[x] = ka;
-                double va = Vv[t]; Vv[t] = Vv[x]; Vv[x] = va;
-              }
-            }
-          }
-          __syncwarp();
-        }
-      for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
-    }
-    if (lane == 0) cnt[i] = u;
-    __syncwarp();
-  }
-}
-
 // Fused product for rows with at most TT_CAP products, one thread per row: the products are taken
 // in (k, q) order and merged into a short sorted list in shared memory (a new column is inserted
 // with 0.0 + its product, a repeated column adds its product), so every entry is summed from 0.0 in
@@ -680,113 +586,107 @@ __global__ void __launch_bounds__(TT_THREADS) k_spgemm_tiny(
   cnt[i] = u;
 }
 
-// Fused product for rows with at most FUSE_CAP products and FZ_CAPA entries in A (the common case):
-// products are taken 32 at a time in (k, q) order, i.e. ascending intermediate index k (lane t holds
-// product t0 + t; its A entry comes from a scan of the B row lengths kept in shared memory, and the
-// next chunk's loads are issued before the current chunk is added).  Lanes holding the same column
-// form a group (__match_any_sync); the group's lowest lane adds the group's products in lane order
-// to the column's running sum in a row-sized shared hash table.  Every sum therefore starts at 0.0
-// and adds its products in ascending k (Gustavson's order).  Only the distinct columns are then
-// sorted (bitonic, sums carried) and staged.
-constexpr int FZ_WARPS = 4;
-constexpr int FZ_CAPA = 128;
-constexpr int FZ_SLOTS = 512;
+// Fused product of one row (a warp), the common case of the setup products: products are taken 32
+// at a time in (k, q) order, i.e. ascending intermediate index k (lane t holds product t0 + t; its A
+// entry comes from a scan of the B row lengths kept in shared memory, and the next chunk's loads are
+// issued before the current chunk is added).  The A row is taken in batches of CAPA entries (the
+// scan's capacity), in order.  Lanes holding the same column form a group (__match_any_sync); the
+// group's lowest lane adds the group's products in lane order to the column's running sum in a
+// row-sized shared hash table.  Every sum therefore starts at 0.0 and adds its products in ascending
+// k (Gustavson's order).  Only the distinct columns are then sorted (rank placement up to 128, else
+// bitonic, sums carried) and staged at scol/sval + o.
+struct ChunkSmem {
+  int32_t* K;     // [slots] hash keys
+  double* V;      // [slots] running sums
+  int32_t* sst;   // [capa + 1] product offsets of the batch's A entries
+  int64_t* sbg;   // [capa] B row starts
+  double* sa;     // [capa] A values
+  double* gv;     // [32] the chunk's products
+};
 
-__global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
-    int64_t r0, int64_t m, int64_t sbase, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
-    const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
-    const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
-    double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ rest, int* __restrict__ nrest,
-    int32_t* __restrict__ rest2, int* __restrict__ nrest2) {
-  __shared__ int32_t hk[FZ_WARPS][FZ_SLOTS];
-  __shared__ double hv[FZ_WARPS][FZ_SLOTS];
-  __shared__ int32_t sst[FZ_WARPS][FZ_CAPA + 1];
-  __shared__ int64_t sbg[FZ_WARPS][FZ_CAPA];
-  __shared__ double sa[FZ_WARPS][FZ_CAPA];
-  __shared__ double gv[FZ_WARPS][32];
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int64_t i = r0 + (int64_t)blockIdx.x * FZ_WARPS + w;
-  if (i >= m) return;
-  int U = (int)ub[i];
-  if (U <= TT_CAP) return;  // k_spgemm_tiny
-  int64_t a0 = arp[i];
-  int na = (int)(arp[i + 1] - a0);
-  if (U > FZ_SLOTS / 2 || na > FZ_CAPA) {  // the row goes to the larger kernels
-    if (lane == 0) {
-      if (U <= FH_CAP) rest[atomicAdd(nrest, 1)] = (int32_t)i;
-      else if (U <= FUSE_CAP) rest2[atomicAdd(nrest2, 1)] = (int32_t)i;
-    }
-    return;
-  }
-  int32_t* K = hk[w];
-  double* Vv = hv[w];
+template <int SLOTS, int CAPA>
+__device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __restrict__ arp,
+                                          const int32_t* __restrict__ aci, const double* __restrict__ av,
+                                          const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
+                                          const double* __restrict__ bv, int64_t o, int32_t* __restrict__ scol,
+                                          double* __restrict__ sval, int64_t* __restrict__ cnt, const ChunkSmem& sm) {
+  const int lane = threadIdx.x & 31;
+  int32_t* K = sm.K;
+  double* Vv = sm.V;
   int H = 32;
   while (H < 2 * U) H <<= 1;
   for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
-  int carry = 0;
-  for (int p0 = 0; p0 < na; p0 += 32) {
-    int p = p0 + lane;
-    int len = 0;
-    if (p < na) {
-      int32_t k = aci[a0 + p];
-      int64_t b0 = brp[k];
-      len = (int)(brp[k + 1] - b0);
-      sbg[w][p] = b0;
-      sa[w][p] = av[a0 + p];
+  const int64_t a0 = arp[i], a1 = arp[i + 1];
+  for (int64_t pb = a0; pb < a1; pb += CAPA) {
+    const int na = (int)((a1 - pb) < CAPA ? (a1 - pb) : CAPA);
+    __syncwarp();
+    int carry = 0;
+    for (int p0 = 0; p0 < na; p0 += 32) {
+      int p = p0 + lane;
+      int len = 0;
+      if (p < na) {
+        int32_t k = aci[pb + p];
+        int64_t b0 = brp[k];
+        len = (int)(brp[k + 1] - b0);
+        sm.sbg[p] = b0;
+        sm.sa[p] = av[pb + p];
+      }
+      int x = len;
+      for (int of = 1; of < 32; of <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, of);
+        if (lane >= of) x += y;
+      }
+      if (p < na) sm.sst[p] = carry + x - len;
+      carry += __shfl_sync(0xffffffffu, x, 31);
     }
-    int x = len;
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    if (lane == 0) sm.sst[na] = carry;
+    __syncwarp();
+    const int Ub = carry;
+    // product t of the batch -> (column, value)
+    auto fetch = [&](int t, int32_t& col, double& val) {
+      col = -1 - lane;
+      val = 0.0;
+      if (t < Ub) {
+        int lo = 0, hi = na;
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if (sm.sst[mid] <= t) lo = mid; else hi = mid;
+        }
+        int64_t q = sm.sbg[lo] + (t - sm.sst[lo]);
+        col = bci[q];
+        val = __dmul_rn(sm.sa[lo], bv[q]);
+      }
+    };
+    int32_t ncol;
+    double nval;
+    fetch(lane, ncol, nval);
+    for (int t0 = 0; t0 < Ub; t0 += 32) {
+      int32_t col = ncol;
+      double val = nval;
+      if (t0 + 32 < Ub) fetch(t0 + 32 + lane, ncol, nval);
+      unsigned grp = __match_any_sync(0xffffffffu, col);
+      sm.gv[lane] = val;
+      __syncwarp();
+      if (col >= 0 && lane == __ffs(grp) - 1) {
+        uint32_t h = hash32(col) & (H - 1);
+        while (true) {
+          int32_t prev = atomicCAS(&K[h], -1, col);
+          if (prev == -1 || prev == col) break;
+          h = (h + 1) & (H - 1);
+        }
+        double acc = Vv[h];
+        unsigned g = grp;
+        while (g) {
+          int l = __ffs(g) - 1;
+          acc = __dadd_rn(acc, sm.gv[l]);
+          g &= g - 1;
+        }
+        Vv[h] = acc;
+      }
+      __syncwarp();
     }
-    if (p < na) sst[w][p] = carry + x - len;
-    carry += __shfl_sync(0xffffffffu, x, 31);
   }
-  if (lane == 0) sst[w][na] = carry;
   __syncwarp();
-  // product t -> (column, value); loads for the next chunk are issued before this chunk is added
-  auto fetch = [&](int t, int32_t& col, double& val) {
-    col = -1 - lane;
-    val = 0.0;
-    if (t < U) {
-      int lo = 0, hi = na;
-      while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (sst[w][mid] <= t) lo = mid; else hi = mid;
-      }
-      int64_t q = sbg[w][lo] + (t - sst[w][lo]);
-      col = bci[q];
-      val = __dmul_rn(sa[w][lo], bv[q]);
-    }
-  };
-  int32_t ncol;
-  double nval;
-  fetch(lane, ncol, nval);
-  for (int t0 = 0; t0 < U; t0 += 32) {
-    int32_t col = ncol;
-    double val = nval;
-    if (t0 + 32 < U) fetch(t0 + 32 + lane, ncol, nval);
-    unsigned grp = __match_any_sync(0xffffffffu, col);
-    gv[w][lane] = val;
-    __syncwarp();
-    if (col >= 0 && lane == __ffs(grp) - 1) {
-      uint32_t h = hash32(col) & (H - 1);
-      while (true) {
-        int32_t prev = atomicCAS(&K[h], -1, col);
-        if (prev == -1 || prev == col) break;
-        h = (h + 1) & (H - 1);
-      }
-      double acc = Vv[h];
-      unsigned g = grp;
-      while (g) {
-        int l = __ffs(g) - 1;
-        acc = __dadd_rn(acc, gv[w][l]);
-        g &= g - 1;
-      }
-      Vv[h] = acc;
-    }
-    __syncwarp();
-  }
   // compact the occupied slots, sort them by column, stage
   int base = 0;
   for (int t0 = 0; t0 < H; t0 += 32) {
@@ -803,11 +703,11 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
     base += __popc(msk);
     __syncwarp();
   }
-  int u = base;
-  int64_t o = soff[i] - sbase;
+  const int u = base;
   if (u <= 128) {
     warp_rank_store128(K, Vv, u, lane, scol + o, sval + o);
     if (lane == 0) cnt[i] = u;
+    __syncwarp();
     return;
   }
   int n2 = 1;
@@ -831,6 +731,94 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
     }
   for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
   if (lane == 0) cnt[i] = u;
+  __syncwarp();
+}
+
+// The rows of a batch with TT_CAP < U <= FZ_SLOTS / 2 and at most FZ_CAPA A entries; the others with
+// U <= FUSE_CAP are listed by product count for the list kernels below (lists 0, 1, 2: U up to 512,
+// 1024, 2048).
+constexpr int FZ_WARPS = 4;
+constexpr int FZ_CAPA = 128;
+constexpr int FZ_SLOTS = 512;
+
+__global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
+    int64_t r0, int64_t m, int64_t sbase, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
+    const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
+    const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
+    double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ lists, int64_t list_stride,
+    int* __restrict__ nlist) {
+  __shared__ int32_t hk[FZ_WARPS][FZ_SLOTS];
+  __shared__ double hv[FZ_WARPS][FZ_SLOTS];
+  __shared__ int32_t sst[FZ_WARPS][FZ_CAPA + 1];
+  __shared__ int64_t sbg[FZ_WARPS][FZ_CAPA];
+  __shared__ double sa[FZ_WARPS][FZ_CAPA];
+  __shared__ double gv[FZ_WARPS][32];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t i = r0 + (int64_t)blockIdx.x * FZ_WARPS + w;
+  if (i >= m) return;
+  int U = (int)ub[i];
+  if (U <= TT_CAP) return;  // k_spgemm_tiny
+  int na = (int)(arp[i + 1] - arp[i]);
+  if (U > FZ_SLOTS / 2 || na > FZ_CAPA) {  // the row goes to a list kernel
+    if (lane == 0 && U <= FUSE_CAP) {
+      const int l = U <= 512 ? 0 : (U <= 1024 ? 1 : 2);
+      lists[l * list_stride + atomicAdd(&nlist[l], 1)] = (int32_t)i;
+    }
+    return;
+  }
+  ChunkSmem sm{hk[w], hv[w], sst[w], sbg[w], sa[w], gv[w]};
+  chunk_row<FZ_SLOTS, FZ_CAPA>(i, U, arp, aci, av, brp, bci, bv, soff[i] - sbase, scol, sval, cnt, sm);
+}
+
+// The listed rows, W warps per block with SLOTS hash slots each (dynamic shared memory), a fixed grid
+// walking the list.
+template <int SLOTS, int CAPA>
+constexpr size_t chunk_warp_bytes() {
+  return ((size_t)SLOTS * 8 + (size_t)CAPA * 16 + 32 * 8 + (size_t)SLOTS * 4 + (size_t)(CAPA + 1) * 4 + 15) / 16 * 16;
+}
+
+template <int W, int SLOTS, int CAPA>
+__global__ void __launch_bounds__(32 * W, 2) k_spgemm_chunk_list(
+    const int32_t* __restrict__ rows, const int* __restrict__ nrows, int64_t sbase, const int64_t* __restrict__ arp,
+    const int32_t* __restrict__ aci, const double* __restrict__ av, const int64_t* __restrict__ brp,
+    const int32_t* __restrict__ bci, const double* __restrict__ bv, const int64_t* __restrict__ ub,
+    const int64_t* __restrict__ soff, int32_t* __restrict__ scol, double* __restrict__ sval,
+    int64_t* __restrict__ cnt) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int w = threadIdx.x >> 5;
+  unsigned char* base = dsm + (size_t)w * chunk_warp_bytes<SLOTS, CAPA>();
+  ChunkSmem sm;
+  sm.V = reinterpret_cast<double*>(base);
+  sm.sbg = reinterpret_cast<int64_t*>(base + (size_t)SLOTS * 8);
+  sm.sa = reinterpret_cast<double*>(base + (size_t)SLOTS * 8 + (size_t)CAPA * 8);
+  sm.gv = reinterpret_cast<double*>(base + (size_t)SLOTS * 8 + (size_t)CAPA * 16);
+  sm.K = reinterpret_cast<int32_t*>(base + (size_t)SLOTS * 8 + (size_t)CAPA * 16 + 32 * 8);
+  sm.sst = reinterpret_cast<int32_t*>(base + (size_t)SLOTS * 12 + (size_t)CAPA * 16 + 32 * 8);
+  const int64_t nr = *nrows;
+  for (int64_t r = (int64_t)blockIdx.x * W + w; r < nr; r += (int64_t)gridDim.x * W) {
+    const int64_t i = rows[r];
+    chunk_row<SLOTS, CAPA>(i, (int)ub[i], arp, aci, av, brp, bci, bv, soff[i] - sbase, scol, sval, cnt, sm);
+  }
+}
+
+template <int W, int SLOTS, int CAPA>
+static void launch_chunk_list(Ctx& c, const int32_t* rows, const int* nrows, int64_t sbase, const DCSR<double>& A,
+                              const DCSR<double>& B, const int64_t* ub, const int64_t* soff, int32_t* scol,
+                              double* sval, int64_t* cnt, int64_t max_rows) {
+  const size_t bytes = (size_t)W * chunk_warp_bytes<SLOTS, CAPA>();
+  static int set_dev = -1;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (set_dev != dev) {
+    CU(cudaFuncSetAttribute(k_spgemm_chunk_list<W, SLOTS, CAPA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)bytes));
+    set_dev = dev;
+  }
+  // a fixed grid: the list's length is known on the device only
+  const unsigned grid = grid_for(max_rows, W, (int64_t)c.num_sms * 8);
+  k_spgemm_chunk_list<W, SLOTS, CAPA><<<grid, 32 * W, bytes, c.s>>>(rows, nrows, sbase, A.rp, A.ci, A.v, B.rp, B.ci,
+                                                                    B.v, ub, soff, scol, sval, cnt);
+  CU_LAUNCH();
 }
 
 // copy the staged columns and values of the fused rows to their final place in C
@@ -943,28 +931,25 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
   std::vector<DBuf<int64_t>> poff(nbatch > 1 ? nbatch : 0);
   std::vector<DBuf<int32_t>> pcol(poff.size());
   std::vector<DBuf<double>> pval(poff.size());
-  DBuf<int32_t> rest(c, m), rest2(c, m);
-  DBuf<int> nrest(c, 2);
+  DBuf<int32_t> lists(c, 3 * m);
+  DBuf<int> nlist(c, 3);
   for (int64_t b = 0; b < nbatch; ++b) {
     const int64_t i0 = bst[b], i1 = bst[b + 1], base = bbase[b];
     if (i1 <= i0) continue;
     {
       ProfScope ps2(c, "fused_small");
-      CU(cudaMemsetAsync(nrest.p, 0, 2 * sizeof(int), c.s));
+      CU(cudaMemsetAsync(nlist.p, 0, 3 * sizeof(int), c.s));
       k_spgemm_tiny<<<grid_for(i1 - i0, TT_THREADS), TT_THREADS, 0, c.s>>>(i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci,
                                                                            B.v, ub.p, soff.p, scol.p, sval.p, cnt.p);
       CU_LAUNCH();
       k_spgemm_fused_chunk<<<grid_for(i1 - i0, FZ_WARPS), 32 * FZ_WARPS, 0, c.s>>>(
-          i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, rest.p, nrest.p,
-          rest2.p, nrest.p + 1);
+          i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, lists.p, m, nlist.p);
       CU_LAUNCH();
-      // a fixed grid over each list: 4 blocks of 48 KB shared memory per SM on 152 SMs, 4 rounds
-      k_spgemm_fused_hash<2, 2 * FH_CAP><<<grid_for(i1 - i0, 2, 152 * 16), 64, 0, c.s>>>(
-          rest.p, nrest.p, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, base, scol.p, sval.p, cnt.p);
-      CU_LAUNCH();
-      k_spgemm_fused_hash<1, 2 * FUSE_CAP><<<grid_for(i1 - i0, 1, 152 * 16), 32, 0, c.s>>>(
-          rest2.p, nrest.p + 1, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, base, scol.p, sval.p, cnt.p);
-      CU_LAUNCH();
+      launch_chunk_list<4, 1024, 256>(c, lists.p, nlist.p, base, A, B, ub.p, soff.p, scol.p, sval.p, cnt.p, i1 - i0);
+      launch_chunk_list<2, 2048, 256>(c, lists.p + m, nlist.p + 1, base, A, B, ub.p, soff.p, scol.p, sval.p, cnt.p,
+                                      i1 - i0);
+      launch_chunk_list<1, 4096, 512>(c, lists.p + 2 * m, nlist.p + 2, base, A, B, ub.p, soff.p, scol.p, sval.p,
+                                      cnt.p, i1 - i0);
     }
     if (nbatch > 1) {
       ProfScope ps3(c, "fused_copy");

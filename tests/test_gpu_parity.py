@@ -351,3 +351,24 @@ def test_apply_graph_replay_matches_direct(precision):
     assert mg_graph.stats()["graph_nodes"] == 0
     mg_graph.close()
     mg_direct.close()
+
+
+def test_programmatic_dependent_launch_matches_plain():
+    """Kernels launched with programmatic dependent launch (the default) give the plainly launched
+    results bit for bit: apply and FGMRES, mixed precision, on a multi-level hierarchy."""
+    import torch
+
+    import paper_1801_08464_gb300 as mg
+    p = ncpgen.make_problem(PARITY["ncp3d_16"])
+    A, mk = to_gpu(p)
+    outs = []
+    for pdl in (0, -1):
+        m = mg.MGR(precision="mixed", pdl=pdl, apply_graph=-1)
+        m.setup(A, mk)
+        r = torch.as_tensor(ncpgen.normals(p.n, 3), device="cuda")
+        z = m.apply(r)
+        x, info = m.fgmres(A, torch.as_tensor(ncpgen.normals(p.n, 2), device="cuda"), rtol=1e-10)
+        outs.append((z, x, info["iterations"]))
+        m.close()
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
