@@ -604,7 +604,16 @@ struct ChunkSmem {
   double* gv;     // [32] the chunk's products
 };
 
-template <int SLOTS, int CAPA>
+// Table size: a power of two of at least 2 U (load at most one half).  CLEAN: the table is all
+// free at entry and is left all free (the compaction scan frees each slot it reads), so a warp
+// walking many rows initialises it once.
+__device__ __forceinline__ int chunk_table_size(int U) {
+  int H = 32;
+  while (H < 2 * U) H <<= 1;
+  return H;
+}
+
+template <int SLOTS, int CAPA, bool CLEAN>
 __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __restrict__ arp,
                                           const int32_t* __restrict__ aci, const double* __restrict__ av,
                                           const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
@@ -613,9 +622,9 @@ __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __res
   const int lane = threadIdx.x & 31;
   int32_t* K = sm.K;
   double* Vv = sm.V;
-  int H = 32;
-  while (H < 2 * U) H <<= 1;
-  for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
+  const int H = chunk_table_size(U);
+  if (!CLEAN)
+    for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
   const int64_t a0 = arp[i], a1 = arp[i + 1];
   for (int64_t pb = a0; pb < a1; pb += CAPA) {
     const int na = (int)((a1 - pb) < CAPA ? (a1 - pb) : CAPA);
@@ -695,6 +704,8 @@ __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __res
     double v = t < H ? Vv[t] : 0.0;
     unsigned msk = __ballot_sync(0xffffffffu, key >= 0);
     __syncwarp();
+    if (CLEAN && t < H) { K[t] = -1; Vv[t] = 0.0; }
+    __syncwarp();
     if (key >= 0) {
       int pos = base + __popc(msk & ((1u << lane) - 1));
       K[pos] = key;
@@ -708,6 +719,10 @@ __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __res
     warp_rank_store128(K, Vv, u, lane, scol + o, sval + o);
     if (lane == 0) cnt[i] = u;
     __syncwarp();
+    if (CLEAN) {
+      for (int t = lane; t < u; t += 32) { K[t] = -1; Vv[t] = 0.0; }
+      __syncwarp();
+    }
     return;
   }
   int n2 = 1;
@@ -732,6 +747,10 @@ __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __res
   for (int t = lane; t < u; t += 32) { scol[o + t] = K[t]; sval[o + t] = Vv[t]; }
   if (lane == 0) cnt[i] = u;
   __syncwarp();
+  if (CLEAN) {
+    for (int t = lane; t < n2; t += 32) { K[t] = -1; Vv[t] = 0.0; }
+    __syncwarp();
+  }
 }
 
 // The rows of a batch with TT_CAP < U <= FZ_SLOTS / 2 and at most FZ_CAPA A entries; the others with
@@ -767,7 +786,7 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
     return;
   }
   ChunkSmem sm{hk[w], hv[w], sst[w], sbg[w], sa[w], gv[w]};
-  chunk_row<FZ_SLOTS, FZ_CAPA>(i, U, arp, aci, av, brp, bci, bv, soff[i] - sbase, scol, sval, cnt, sm);
+  chunk_row<FZ_SLOTS, FZ_CAPA, false>(i, U, arp, aci, av, brp, bci, bv, soff[i] - sbase, scol, sval, cnt, sm);
 }
 
 // The listed rows, W warps per block with SLOTS hash slots each (dynamic shared memory), a fixed grid
@@ -795,9 +814,13 @@ __global__ void __launch_bounds__(32 * W, 2) k_spgemm_chunk_list(
   sm.K = reinterpret_cast<int32_t*>(base + (size_t)SLOTS * 8 + (size_t)CAPA * 16 + 32 * 8);
   sm.sst = reinterpret_cast<int32_t*>(base + (size_t)SLOTS * 12 + (size_t)CAPA * 16 + 32 * 8);
   const int64_t nr = *nrows;
+  if ((int64_t)blockIdx.x * W + w >= nr) return;
+  const int lane = threadIdx.x & 31;
+  for (int t = lane; t < SLOTS; t += 32) { sm.K[t] = -1; sm.V[t] = 0.0; }
+  __syncwarp();
   for (int64_t r = (int64_t)blockIdx.x * W + w; r < nr; r += (int64_t)gridDim.x * W) {
     const int64_t i = rows[r];
-    chunk_row<SLOTS, CAPA>(i, (int)ub[i], arp, aci, av, brp, bci, bv, soff[i] - sbase, scol, sval, cnt, sm);
+    chunk_row<SLOTS, CAPA, true>(i, (int)ub[i], arp, aci, av, brp, bci, bv, soff[i] - sbase, scol, sval, cnt, sm);
   }
 }
 
