@@ -613,8 +613,8 @@ __device__ __forceinline__ int chunk_table_size(int U) {
   return H;
 }
 
-template <int SLOTS, int CAPA, bool CLEAN>
-__device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __restrict__ arp,
+template <int SLOTS, int CAPA, bool CLEAN, int LIMIT>
+__device__ __forceinline__ bool chunk_row(int64_t i, int U, const int64_t* __restrict__ arp,
                                           const int32_t* __restrict__ aci, const double* __restrict__ av,
                                           const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
                                           const double* __restrict__ bv, int64_t o, int32_t* __restrict__ scol,
@@ -622,7 +622,8 @@ __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __res
   const int lane = threadIdx.x & 31;
   int32_t* K = sm.K;
   double* Vv = sm.V;
-  const int H = chunk_table_size(U);
+  const int H = chunk_table_size(U) < SLOTS ? chunk_table_size(U) : SLOTS;
+  int distinct = 0;  // keys in the table (a table of SLOTS slots stops the row at LIMIT keys)
   if (!CLEAN)
     for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
   const int64_t a0 = arp[i], a1 = arp[i + 1];
@@ -676,11 +677,12 @@ __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __res
       unsigned grp = __match_any_sync(0xffffffffu, col);
       sm.gv[lane] = val;
       __syncwarp();
+      bool fresh = false;
       if (col >= 0 && lane == __ffs(grp) - 1) {
         uint32_t h = hash32(col) & (H - 1);
         while (true) {
           int32_t prev = atomicCAS(&K[h], -1, col);
-          if (prev == -1 || prev == col) break;
+          if (prev == -1 || prev == col) { fresh = prev == -1; break; }
           h = (h + 1) & (H - 1);
         }
         double acc = Vv[h];
@@ -692,7 +694,15 @@ __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __res
         }
         Vv[h] = acc;
       }
+      distinct += __popc(__ballot_sync(0xffffffffu, fresh));
       __syncwarp();
+      if (distinct > LIMIT) {  // the row needs a larger table
+        if (CLEAN) {
+          for (int t = lane; t < H; t += 32) { K[t] = -1; Vv[t] = 0.0; }
+          __syncwarp();
+        }
+        return false;
+      }
     }
   }
   __syncwarp();
@@ -723,7 +733,7 @@ __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __res
       for (int t = lane; t < u; t += 32) { K[t] = -1; Vv[t] = 0.0; }
       __syncwarp();
     }
-    return;
+    return true;
   }
   int n2 = 1;
   while (n2 < u) n2 <<= 1;
@@ -751,21 +761,24 @@ __device__ __forceinline__ void chunk_row(int64_t i, int U, const int64_t* __res
     for (int t = lane; t < n2; t += 32) { K[t] = -1; Vv[t] = 0.0; }
     __syncwarp();
   }
+  return true;
 }
 
-// The rows of a batch with TT_CAP < U <= FZ_SLOTS / 2 and at most FZ_CAPA A entries; the others with
-// U <= FUSE_CAP are listed by product count for the list kernels below (lists 0, 1, 2: U up to 512,
-// 1024, 2048).
+// The rows of a batch with TT_CAP < U <= FUSE_CAP, four warps per block with 256-slot tables: the
+// table is sized by the row's distinct columns, not by its products (the coarse-operator rows keep a
+// small fraction of their products), so small tables keep many warps resident; a row whose distinct
+// columns pass FZ_LIMIT (a 70 % load) is stopped and listed for the 1024-slot list kernel, whose
+// overflow goes on to the 4096-slot one.
 constexpr int FZ_WARPS = 4;
 constexpr int FZ_CAPA = 128;
-constexpr int FZ_SLOTS = 512;
+constexpr int FZ_SLOTS = 256;
+constexpr int FZ_LIMIT = FZ_SLOTS * 7 / 10;
 
-__global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
+__global__ void __launch_bounds__(32 * FZ_WARPS, 8) k_spgemm_fused_chunk(
     int64_t r0, int64_t m, int64_t sbase, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
     const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
     const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
-    double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ lists, int64_t list_stride,
-    int* __restrict__ nlist) {
+    double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ list, int* __restrict__ nlist) {
   __shared__ int32_t hk[FZ_WARPS][FZ_SLOTS];
   __shared__ double hv[FZ_WARPS][FZ_SLOTS];
   __shared__ int32_t sst[FZ_WARPS][FZ_CAPA + 1];
@@ -776,17 +789,11 @@ __global__ void __launch_bounds__(32 * FZ_WARPS) k_spgemm_fused_chunk(
   int64_t i = r0 + (int64_t)blockIdx.x * FZ_WARPS + w;
   if (i >= m) return;
   int U = (int)ub[i];
-  if (U <= TT_CAP) return;  // k_spgemm_tiny
-  int na = (int)(arp[i + 1] - arp[i]);
-  if (U > FZ_SLOTS / 2 || na > FZ_CAPA) {  // the row goes to a list kernel
-    if (lane == 0 && U <= FUSE_CAP) {
-      const int l = U <= 512 ? 0 : (U <= 1024 ? 1 : 2);
-      lists[l * list_stride + atomicAdd(&nlist[l], 1)] = (int32_t)i;
-    }
-    return;
-  }
+  if (U <= TT_CAP || U > FUSE_CAP) return;  // k_spgemm_tiny; the symbolic path
   ChunkSmem sm{hk[w], hv[w], sst[w], sbg[w], sa[w], gv[w]};
-  chunk_row<FZ_SLOTS, FZ_CAPA, false>(i, U, arp, aci, av, brp, bci, bv, soff[i] - sbase, scol, sval, cnt, sm);
+  const bool done = chunk_row<FZ_SLOTS, FZ_CAPA, false, FZ_LIMIT>(i, U, arp, aci, av, brp, bci, bv, soff[i] - sbase,
+                                                                   scol, sval, cnt, sm);
+  if (!done && lane == 0) list[atomicAdd(nlist, 1)] = (int32_t)i;
 }
 
 // The listed rows, W warps per block with SLOTS hash slots each (dynamic shared memory), a fixed grid
@@ -796,13 +803,13 @@ constexpr size_t chunk_warp_bytes() {
   return ((size_t)SLOTS * 8 + (size_t)CAPA * 16 + 32 * 8 + (size_t)SLOTS * 4 + (size_t)(CAPA + 1) * 4 + 15) / 16 * 16;
 }
 
-template <int W, int SLOTS, int CAPA>
+template <int W, int SLOTS, int CAPA, int LIMIT>
 __global__ void __launch_bounds__(32 * W, 2) k_spgemm_chunk_list(
     const int32_t* __restrict__ rows, const int* __restrict__ nrows, int64_t sbase, const int64_t* __restrict__ arp,
     const int32_t* __restrict__ aci, const double* __restrict__ av, const int64_t* __restrict__ brp,
     const int32_t* __restrict__ bci, const double* __restrict__ bv, const int64_t* __restrict__ ub,
     const int64_t* __restrict__ soff, int32_t* __restrict__ scol, double* __restrict__ sval,
-    int64_t* __restrict__ cnt) {
+    int64_t* __restrict__ cnt, int32_t* __restrict__ over, int* __restrict__ nover) {
   extern __shared__ __align__(16) unsigned char dsm[];
   const int w = threadIdx.x >> 5;
   unsigned char* base = dsm + (size_t)w * chunk_warp_bytes<SLOTS, CAPA>();
@@ -820,27 +827,30 @@ __global__ void __launch_bounds__(32 * W, 2) k_spgemm_chunk_list(
   __syncwarp();
   for (int64_t r = (int64_t)blockIdx.x * W + w; r < nr; r += (int64_t)gridDim.x * W) {
     const int64_t i = rows[r];
-    chunk_row<SLOTS, CAPA, true>(i, (int)ub[i], arp, aci, av, brp, bci, bv, soff[i] - sbase, scol, sval, cnt, sm);
+    const bool done = chunk_row<SLOTS, CAPA, true, LIMIT>(i, (int)ub[i], arp, aci, av, brp, bci, bv, soff[i] - sbase,
+                                                          scol, sval, cnt, sm);
+    if (!done && lane == 0) over[atomicAdd(nover, 1)] = (int32_t)i;
   }
 }
 
-template <int W, int SLOTS, int CAPA>
+template <int W, int SLOTS, int CAPA, int LIMIT>
 static void launch_chunk_list(Ctx& c, const int32_t* rows, const int* nrows, int64_t sbase, const DCSR<double>& A,
                               const DCSR<double>& B, const int64_t* ub, const int64_t* soff, int32_t* scol,
-                              double* sval, int64_t* cnt, int64_t max_rows) {
+                              double* sval, int64_t* cnt, int64_t max_rows, int32_t* over, int* nover) {
   const size_t bytes = (size_t)W * chunk_warp_bytes<SLOTS, CAPA>();
   static int set_dev = -1;
   int dev = 0;
   CU(cudaGetDevice(&dev));
   if (set_dev != dev) {
-    CU(cudaFuncSetAttribute(k_spgemm_chunk_list<W, SLOTS, CAPA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CU(cudaFuncSetAttribute(k_spgemm_chunk_list<W, SLOTS, CAPA, LIMIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)bytes));
     set_dev = dev;
   }
   // a fixed grid: the list's length is known on the device only
   const unsigned grid = grid_for(max_rows, W, (int64_t)c.num_sms * 8);
-  k_spgemm_chunk_list<W, SLOTS, CAPA><<<grid, 32 * W, bytes, c.s>>>(rows, nrows, sbase, A.rp, A.ci, A.v, B.rp, B.ci,
-                                                                    B.v, ub, soff, scol, sval, cnt);
+  k_spgemm_chunk_list<W, SLOTS, CAPA, LIMIT><<<grid, 32 * W, bytes, c.s>>>(rows, nrows, sbase, A.rp, A.ci, A.v, B.rp,
+                                                                           B.ci, B.v, ub, soff, scol, sval, cnt, over,
+                                                                           nover);
   CU_LAUNCH();
 }
 
@@ -954,25 +964,24 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
   std::vector<DBuf<int64_t>> poff(nbatch > 1 ? nbatch : 0);
   std::vector<DBuf<int32_t>> pcol(poff.size());
   std::vector<DBuf<double>> pval(poff.size());
-  DBuf<int32_t> lists(c, 3 * m);
-  DBuf<int> nlist(c, 3);
+  DBuf<int32_t> lists(c, 2 * m);
+  DBuf<int> nlist(c, 2);
   for (int64_t b = 0; b < nbatch; ++b) {
     const int64_t i0 = bst[b], i1 = bst[b + 1], base = bbase[b];
     if (i1 <= i0) continue;
     {
       ProfScope ps2(c, "fused_small");
-      CU(cudaMemsetAsync(nlist.p, 0, 3 * sizeof(int), c.s));
+      CU(cudaMemsetAsync(nlist.p, 0, 2 * sizeof(int), c.s));
       k_spgemm_tiny<<<grid_for(i1 - i0, TT_THREADS), TT_THREADS, 0, c.s>>>(i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci,
                                                                            B.v, ub.p, soff.p, scol.p, sval.p, cnt.p);
       CU_LAUNCH();
       k_spgemm_fused_chunk<<<grid_for(i1 - i0, FZ_WARPS), 32 * FZ_WARPS, 0, c.s>>>(
-          i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, lists.p, m, nlist.p);
+          i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, lists.p, nlist.p);
       CU_LAUNCH();
-      launch_chunk_list<4, 1024, 256>(c, lists.p, nlist.p, base, A, B, ub.p, soff.p, scol.p, sval.p, cnt.p, i1 - i0);
-      launch_chunk_list<2, 2048, 256>(c, lists.p + m, nlist.p + 1, base, A, B, ub.p, soff.p, scol.p, sval.p, cnt.p,
-                                      i1 - i0);
-      launch_chunk_list<1, 4096, 512>(c, lists.p + 2 * m, nlist.p + 2, base, A, B, ub.p, soff.p, scol.p, sval.p,
-                                      cnt.p, i1 - i0);
+      launch_chunk_list<4, 1024, 256, 1024 * 7 / 10>(c, lists.p, nlist.p, base, A, B, ub.p, soff.p, scol.p, sval.p,
+                                                     cnt.p, i1 - i0, lists.p + m, nlist.p + 1);
+      launch_chunk_list<1, 4096, 512, 4096>(c, lists.p + m, nlist.p + 1, base, A, B, ub.p, soff.p, scol.p, sval.p,
+                                            cnt.p, i1 - i0, nullptr, nullptr);
     }
     if (nbatch > 1) {
       ProfScope ps3(c, "fused_copy");
