@@ -54,8 +54,13 @@ KERNEL_NAMES = SOLVE_KERNELS + SETUP_KERNELS
 # instance of the workload (dram__bytes_read.sum + dram__bytes_write.sum); the traffic of a full-size
 # launch is this ratio times its algorithmic bytes, which scale with the entries it streams.
 # k_bsr_sell<double> (FP64 SpMV): 295.12 MB of DRAM traffic for 298.14 MB algorithmic;
-# k_rows_sell<float, EpiResid, 4> on the AMG level-0 operator (20.37M entries): 183.74 MB for 173.17 MB.
-TRAFFIC = {"bsr3_spmv_f64": 295.1168e6 / 298137608.0, "amg0_rows": 183.735552e6 / 173174864.0}
+# (the AMG level-0 operator's capture, 1.06 x its bytes, was of its 32-bit-column layout: none now).
+TRAFFIC = {"bsr3_spmv_f64": 295.1168e6 / 298137608.0}
+# FP64 FMAs per algorithmic byte of the Krylov kernels bound by the FP64 rate: the multi-dot does one
+# FMA per 8-byte element it reads (V_k . w and w . w); the 3x3-block SpMV 9 per 76-byte block (the
+# row pointers and vectors, a few % of its bytes, are left out: a slight overestimate)
+FP64_FMA_PER_BYTE = {"mdot": 1.0 / 8.0, "bsr3_spmv_f64": 9.0 / 76.0}
+FP64_FMA_PEAK = 625.0  # G FP64 FMA/s, GB300 nominal (1.25 TFLOP/s dense FP64)
 
 
 def _args():
@@ -411,10 +416,20 @@ def main():
         per_launch = by_k / n_k
         achieved = per_launch / (t_k / n_k * 1e-3) / 1e9
         tr = TRAFFIC.get(k)
-        out["roofline"] = {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                           "frac": achieved / peak, "peak_source": peak_kind,
-                           "traffic": tr * per_launch if tr else None, "bytes_per_launch": per_launch,
-                           "avg_launch_us": t_k / n_k * 1e3, "launches": n_k}
+        if k in FP64_FMA_PER_BYTE:
+            # bound by GB300's FP64 rate (ncu: FP64 pipe ~87-91 % active), reported against it
+            fma = FP64_FMA_PER_BYTE[k] * per_launch / (t_k / n_k * 1e-3) / 1e9
+            out["roofline"] = {"kernel": k, "bound": "alu", "achieved": fma, "peak": FP64_FMA_PEAK, "unit": "GFMA/s",
+                               "frac": fma / FP64_FMA_PEAK,
+                               "peak_source": "nominal FP64 rate: 1.25 TFLOP/s dense = 625 G FP64 FMA/s",
+                               "traffic": tr * per_launch if tr else None, "bytes_per_launch": per_launch,
+                               "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak,
+                               "avg_launch_us": t_k / n_k * 1e3, "launches": n_k}
+        else:
+            out["roofline"] = {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                               "frac": achieved / peak, "peak_source": peak_kind,
+                               "traffic": tr * per_launch if tr else None, "bytes_per_launch": per_launch,
+                               "avg_launch_us": t_k / n_k * 1e3, "launches": n_k}
     out["kernel_ms_one_step"] = {k: v[1] for k, v in kt.items() if v[0]}
     if clocks:
         out["clocks"] = clocks

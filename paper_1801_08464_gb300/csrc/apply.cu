@@ -138,12 +138,54 @@ struct Quad<double> {
   }
 };
 
-template <class T, class Epi, int Q>
+// Column storage of the 4-slot groups: CM 0 = 32-bit indices; 1 = 16-bit offsets from the slice's
+// base; 2 = one-byte codes into the operator's table of offsets col - row (held in shared memory).
+struct QuadCols {
+  const int32_t* cp;
+  const uint16_t* cp16;
+  const uint8_t* cp8;
+  int32_t base;      // CM 1: the slice's base; CM 2: the row
+  const int32_t* tab;  // CM 2: the offsets (shared memory)
+};
+template <int CM>
+__device__ __forceinline__ int4 quad_cols(const QuadCols& qc, int64_t q) {
+  if constexpr (CM == 1) {
+    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(qc.cp16 + q * (4 * RS_C)));
+    return make_int4(qc.base + (int)(raw.x & 0xFFFFu), qc.base + (int)(raw.x >> 16), qc.base + (int)(raw.y & 0xFFFFu),
+                     qc.base + (int)(raw.y >> 16));
+  } else if constexpr (CM == 2) {
+    const uint32_t raw = __ldg(reinterpret_cast<const uint32_t*>(qc.cp8 + q * (4 * RS_C)));
+    return make_int4(qc.base + qc.tab[raw & 0xFFu], qc.base + qc.tab[(raw >> 8) & 0xFFu],
+                     qc.base + qc.tab[(raw >> 16) & 0xFFu], qc.base + qc.tab[raw >> 24]);
+  } else {
+    return __ldg(reinterpret_cast<const int4*>(qc.cp + q * (4 * RS_C)));
+  }
+}
+template <int CM>
+__device__ __forceinline__ QuadCols quad_setup(const int32_t* col, const uint16_t* col16, const int32_t* sbase,
+                                               const uint8_t* code, const int32_t* tab, int64_t s, int64_t j0, int t,
+                                               int64_t row) {
+  QuadCols qc{nullptr, nullptr, nullptr, 0, tab};
+  const int64_t o = j0 * RS_C + t * 4;
+  if constexpr (CM == 0) qc.cp = col + o;
+  if constexpr (CM == 1) { qc.cp16 = col16 + o; qc.base = sbase[s]; }
+  if constexpr (CM == 2) { qc.cp8 = code + o; qc.base = (int32_t)row; }
+  return qc;
+}
+
+template <class T, class Epi, int Q, int CM>
 __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __restrict__ soff,
-                                                   const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                   const int32_t* __restrict__ col, const uint16_t* __restrict__ col16,
+                                                   const int32_t* __restrict__ sbase, const uint8_t* __restrict__ code,
+                                                   const int32_t* __restrict__ otab, const T* __restrict__ val,
                                                    const int32_t* __restrict__ perm, const T* __restrict__ x,
                                                    Epi epi) {
+  __shared__ int32_t s_tab[CM == 2 ? 256 : 1];
   pdl_wait();
+  if constexpr (CM == 2) {
+    if (threadIdx.x < 256) s_tab[threadIdx.x] = otab[threadIdx.x];
+    __syncthreads();
+  }
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= nr) return;
   int64_t s = r / RS_C;
@@ -151,16 +193,14 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
   const int64_t row = perm ? (int64_t)perm[r] : r;
   const typename Epi::Pre pre = epi.pre(row);  // the epilogue's loads overlap the row's
   int64_t j0 = soff[s], nq = (soff[s + 1] - j0) / Q;
-  const int32_t* cp = col + j0 * RS_C + t * Q;
   const T* vp = val + j0 * RS_C + t * Q;
   T sum = 0;
   if constexpr (Q == 4) {
+    const QuadCols qc = quad_setup<CM>(col, col16, sbase, code, s_tab, s, j0, t, row);
 #pragma unroll 2
-    for (int64_t q = 0; q < nq; ++q) {
-      int4 c = __ldg(reinterpret_cast<const int4*>(cp + q * (4 * RS_C)));
-      sum += Quad<T>::dot(vp + q * (4 * RS_C), c, x);
-    }
+    for (int64_t q = 0; q < nq; ++q) sum += Quad<T>::dot(vp + q * (4 * RS_C), quad_cols<CM>(qc, q), x);
   } else {
+    const int32_t* cp = col + j0 * RS_C + t * Q;
 #pragma unroll 4
     for (int64_t j = 0; j < nq; ++j) sum += vp[j * RS_C] * ldg(x + cp[j * RS_C]);
   }
@@ -171,12 +211,21 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
 // the 8 rows of a slice and their H threads are 8H consecutive lanes, so one step of a slice reads
 // H consecutive 128-byte lines; partial sums meet by shuffles across lanes 8 and 16 apart.  Used
 // when one thread per row would leave the GPU with few waves of long rows (a tail).
-template <class T, class Epi, int H>
+template <class T, class Epi, int H, int CM>
 __global__ void __launch_bounds__(256) k_rows_sell_split(int64_t nr, const int64_t* __restrict__ soff,
-                                                         const int32_t* __restrict__ col, const T* __restrict__ val,
+                                                         const int32_t* __restrict__ col,
+                                                         const uint16_t* __restrict__ col16,
+                                                         const int32_t* __restrict__ sbase,
+                                                         const uint8_t* __restrict__ code,
+                                                         const int32_t* __restrict__ otab, const T* __restrict__ val,
                                                          const int32_t* __restrict__ perm, const T* __restrict__ x,
                                                          Epi epi) {
+  __shared__ int32_t s_tab[CM == 2 ? 256 : 1];
   pdl_wait();
+  if constexpr (CM == 2) {
+    if (threadIdx.x < 256) s_tab[threadIdx.x] = otab[threadIdx.x];
+    __syncthreads();
+  }
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t s = g / (RS_C * H);
   const int u = (int)(g - s * (RS_C * H));
@@ -189,13 +238,10 @@ __global__ void __launch_bounds__(256) k_rows_sell_split(int64_t nr, const int64
   T sum = 0;
   if (ok) {
     const int64_t j0 = soff[s], nq = (soff[s + 1] - j0) / 4;
-    const int32_t* cp = col + j0 * RS_C + t * 4;
+    const QuadCols qc = quad_setup<CM>(col, col16, sbase, code, s_tab, s, j0, t, row);
     const T* vp = val + j0 * RS_C + t * 4;
 #pragma unroll 2
-    for (int64_t q = h; q < nq; q += H) {
-      int4 c = __ldg(reinterpret_cast<const int4*>(cp + q * (4 * RS_C)));
-      sum += Quad<T>::dot(vp + q * (4 * RS_C), c, x);
-    }
+    for (int64_t q = h; q < nq; q += H) sum += Quad<T>::dot(vp + q * (4 * RS_C), quad_cols<CM>(qc, q), x);
   }
   if (H >= 2) sum += __shfl_xor_sync(0xffffffffu, sum, 8);
   if (H >= 4) sum += __shfl_xor_sync(0xffffffffu, sum, 16);
@@ -221,7 +267,10 @@ template <class T, class Epi>
 static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, const char* name = "csr_rows") {
   if (op.nr <= 0) return;
   // values and columns, row pointers, x once, the epilogue's row vectors
-  ProfScope ps(c, name, (double)op.nnz * (sizeof(T) + 4) + 8.0 * (op.nr + 1) + (double)op.nc * sizeof(T) +
+  // (the stored column form: 4 bytes per entry, or 2 plus a 4-byte base per slice of 8 rows, or a
+  // one-byte code plus the 1 KB offset table)
+  const double colb = op.c8 ? (double)op.nnz + 1024.0 : (op.c16 ? 2.0 * op.nnz + 0.5 * op.nr : 4.0 * op.nnz);
+  ProfScope ps(c, name, (double)op.nnz * sizeof(T) + colb + 8.0 * (op.nr + 1) + (double)op.nc * sizeof(T) +
                             (double)op.nr * epi.row_bytes());
   const int B = 256;
   if (op.sell) {
@@ -231,18 +280,31 @@ static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, co
     // (each thread keeps at least two 4-slot groups of an average row)
     if (op.q == 4)
       while (H < 4 && op.nr * H < 6 * device_threads() && (double)op.nnz >= 8.0 * 2 * H * (double)op.nr) H *= 2;
-    if (op.q == 4 && H == 1)
-      launch_pdl(c, k_rows_sell<T, Epi, 4>, grid_for(op.nr, B), B, 0, op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
-                                                                epi);
-    else if (op.q == 4 && H == 2)
-      launch_pdl(c, k_rows_sell_split<T, Epi, 2>, grid_for(slices * RS_C * 2, B), B, 0, op.nr, op.soff.p, op.scol.p,
-                                                                                    op.sval.p, op.perm.p, x, epi);
-    else if (op.q == 4)
-      launch_pdl(c, k_rows_sell_split<T, Epi, 4>, grid_for(slices * RS_C * 4, B), B, 0, op.nr, op.soff.p, op.scol.p,
-                                                                                    op.sval.p, op.perm.p, x, epi);
+    const int32_t* sc = op.scol.p;
+    const uint16_t* sc16 = op.scol16.p;
+    const int32_t* sb = op.sbase.p;
+    const uint8_t* cd = op.scode.p;
+    const int32_t* ot = op.otab.p;
+    const unsigned g1 = grid_for(op.nr, B), g2 = grid_for(slices * RS_C * 2, B), g4 = grid_for(slices * RS_C * 4, B);
+#define MGR_SELL_LAUNCH(CM)                                                                                       \
+  do {                                                                                                           \
+    if (H == 1)                                                                                                  \
+      launch_pdl(c, k_rows_sell<T, Epi, 4, CM>, g1, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, ot, op.sval.p,     \
+                 op.perm.p, x, epi);                                                                             \
+    else if (H == 2)                                                                                             \
+      launch_pdl(c, k_rows_sell_split<T, Epi, 2, CM>, g2, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, ot,          \
+                 op.sval.p, op.perm.p, x, epi);                                                                  \
+    else                                                                                                         \
+      launch_pdl(c, k_rows_sell_split<T, Epi, 4, CM>, g4, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, ot,          \
+                 op.sval.p, op.perm.p, x, epi);                                                                  \
+  } while (0)
+    if (op.q == 4 && op.c8) MGR_SELL_LAUNCH(2);
+    else if (op.q == 4 && op.c16) MGR_SELL_LAUNCH(1);
+    else if (op.q == 4) MGR_SELL_LAUNCH(0);
     else
-      launch_pdl(c, k_rows_sell<T, Epi, 1>, grid_for(op.nr, B), B, 0, op.nr, op.soff.p, op.scol.p, op.sval.p, op.perm.p, x,
-                                                                epi);
+      launch_pdl(c, k_rows_sell<T, Epi, 1, 0>, g1, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, ot, op.sval.p,
+                 op.perm.p, x, epi);
+#undef MGR_SELL_LAUNCH
     CU_LAUNCH();
     return;
   }

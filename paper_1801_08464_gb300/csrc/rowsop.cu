@@ -1,6 +1,8 @@
 // rowsop.cu -- construction of the apply operators in SELL-8 or CSR form (see rowsop.cuh).
 #include "rowsop.cuh"
 
+#include <climits>
+
 namespace mgr {
 
 // slice widths (longest row of each slice, rounded up to a multiple of q); rows in slice order are
@@ -62,6 +64,82 @@ __global__ void k_rs_fill(int64_t nr, int64_t npad, const int64_t* rp, const int
   }
 }
 
+// offsets col - row of the entries: the largest magnitude, then the used ones marked in a window of
+// 2 maxd + 1 flags
+__global__ void k_rs_offmax(int64_t nr, const int64_t* rp, const int32_t* ci, unsigned long long* maxd) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  unsigned long long m = 0;
+  if (r < nr)
+    for (int64_t k = rp[r]; k < rp[r + 1]; ++k) {
+      long long d = (long long)ci[k] - r;
+      m = max(m, (unsigned long long)(d < 0 ? -d : d));
+    }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));  // one atomic per warp
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(maxd, m);
+}
+__global__ void k_rs_offmark(int64_t nr, const int64_t* rp, const int32_t* ci, int64_t maxd, int32_t* flag) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  for (int64_t k = rp[r]; k < rp[r + 1]; ++k) {
+    int32_t* f = flag + ((int64_t)ci[k] - r + maxd);
+    if (*f == 0) *f = 1;  // most offsets repeat: read first, write once
+  }
+}
+__global__ void k_rs_offtab(int64_t nw, const int32_t* flag, const int32_t* code, int64_t maxd, int32_t* otab) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v < nw && flag[v]) otab[code[v]] = (int32_t)(v - maxd);
+}
+// the slots of row t of each slice as codes (padding: 255)
+__global__ void k_rs_pack8(int64_t nr, int64_t npad, const int64_t* rp, const int32_t* perm, const int64_t* soff,
+                           const int32_t* scol, const int32_t* code, int64_t maxd, uint8_t* scode) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= npad) return;
+  int64_t s = r / RS_C;
+  int t = (int)(r - s * RS_C);
+  int64_t b0 = soff[s], w = soff[s + 1] - b0;
+  int64_t row = r < nr ? (perm ? perm[r] : r) : 0;
+  int64_t len = r < nr ? rp[row + 1] - rp[row] : 0;
+  for (int64_t j = 0; j < w; ++j) {
+    int64_t o = b0 * RS_C + (j / RS_Q) * (RS_Q * RS_C) + t * RS_Q + (j % RS_Q);
+    scode[o] = j < len ? (uint8_t)code[(int64_t)scol[o] - row + maxd] : (uint8_t)255;
+  }
+}
+
+// per slice: the smallest column of its rows (base) and a flag when the slice spans more than 65,536
+__global__ void k_rs_base(int64_t nr, const int64_t* rp, const int32_t* ci, const int32_t* perm, int64_t nslices,
+                          int32_t* base, int* wide) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nslices) return;
+  int32_t lo = INT_MAX, hi = -1;
+  int64_t e = (s + 1) * RS_C < nr ? (s + 1) * RS_C : nr;
+  for (int64_t r = s * RS_C; r < e; ++r) {
+    int64_t o = perm ? perm[r] : r;
+    for (int64_t k = rp[o]; k < rp[o + 1]; ++k) {
+      lo = min(lo, ci[k]);
+      hi = max(hi, ci[k]);
+    }
+  }
+  if (hi < 0) lo = hi = 0;  // an empty slice
+  base[s] = lo;
+  if ((int64_t)hi - (int64_t)lo > 65535) atomicOr(wide, 1);
+}
+// the slots of row t of each slice as 16-bit offsets from the slice's base (padding slots, column 0
+// below a positive base, become offset 0)
+__global__ void k_rs_pack16(int64_t npad, const int64_t* soff, const int32_t* scol, const int32_t* base,
+                            uint16_t* scol16) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= npad) return;
+  int64_t s = r / RS_C;
+  int t = (int)(r - s * RS_C);
+  int64_t b0 = soff[s], w = soff[s + 1] - b0;
+  const int32_t bs = base[s];
+  for (int64_t j = 0; j < w; ++j) {
+    int64_t o = b0 * RS_C + (j / RS_Q) * (RS_Q * RS_C) + t * RS_Q + (j % RS_Q);
+    int32_t cc = scol[o];
+    scol16[o] = (uint16_t)(cc >= bs ? cc - bs : 0);
+  }
+}
+
 template <class T>
 __global__ void k_rs_cast(int64_t n, const double* a, T* b) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -99,6 +177,52 @@ void rowsop_build(Ctx& c, const DCSR<double>& A, RowsOp<T>& op) {
       k_rs_fill<T><<<grid_for(np, 256), 256, 0, c.s>>>(A.nr, np, A.rp, A.ci, A.v, op.perm.p, op.q, op.soff.p,
                                                       op.scol.p, op.sval.p);
       CU_LAUNCH();
+      if (op.q == RS_Q && A.nr == A.nc) {
+        // one-byte offset codes when at most 255 distinct offsets col - row occur
+        DBuf<unsigned long long> md(c, 1);
+        CU(cudaMemsetAsync(md.p, 0, sizeof(unsigned long long), c.s));
+        k_rs_offmax<<<grid_for(A.nr, 256), 256, 0, c.s>>>(A.nr, A.rp, A.ci, md.p);
+        CU_LAUNCH();
+        const int64_t maxd = (int64_t)read_scalar(c, md.p);
+        if (maxd <= (int64_t(1) << 22)) {
+          const int64_t nw = 2 * maxd + 1;
+          DBuf<int32_t> flag(c, nw), code(c, nw + 1);
+          CU(cudaMemsetAsync(flag.p, 0, sizeof(int32_t) * nw, c.s));
+          k_rs_offmark<<<grid_for(A.nr, 256), 256, 0, c.s>>>(A.nr, A.rp, A.ci, maxd, flag.p);
+          CU_LAUNCH();
+          scan_excl_i32(c, flag.p, code.p, nw);
+          const int32_t ncodes = read_scalar(c, code.p + nw);
+          if (ncodes <= 255) {
+            op.c8 = true;
+            op.otab.alloc(c, 256);
+            CU(cudaMemsetAsync(op.otab.p, 0, sizeof(int32_t) * 256, c.s));  // code 255 (padding): offset 0
+            k_rs_offtab<<<grid_for(nw, 256), 256, 0, c.s>>>(nw, flag.p, code.p, maxd, op.otab.p);
+            CU_LAUNCH();
+            op.scode.alloc(c, op.slots * RS_C);
+            k_rs_pack8<<<grid_for(np, 256), 256, 0, c.s>>>(A.nr, np, A.rp, op.perm.p, op.soff.p, op.scol.p, code.p,
+                                                           maxd, op.scode.p);
+            CU_LAUNCH();
+            op.scol.release();
+            return;
+          }
+        }
+      }
+      if (op.q == RS_Q) {
+        op.sbase.alloc(c, ns);
+        DBuf<int> wide(c, 1);
+        CU(cudaMemsetAsync(wide.p, 0, sizeof(int), c.s));
+        k_rs_base<<<grid_for(ns, 256), 256, 0, c.s>>>(A.nr, A.rp, A.ci, op.perm.p, ns, op.sbase.p, wide.p);
+        CU_LAUNCH();
+        if (read_scalar(c, wide.p) == 0) {
+          op.c16 = true;
+          op.scol16.alloc(c, op.slots * RS_C);
+          k_rs_pack16<<<grid_for(np, 256), 256, 0, c.s>>>(np, op.soff.p, op.scol.p, op.sbase.p, op.scol16.p);
+          CU_LAUNCH();
+          op.scol.release();
+        } else {
+          op.sbase.release();
+        }
+      }
       return;
     }
     op.soff.release();

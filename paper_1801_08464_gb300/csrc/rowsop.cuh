@@ -18,6 +18,12 @@
 // RS_SIGMA consecutive rows (stable), so a slice holds rows of similar length; perm[r] is then the
 // operator row stored at slice position r.  Windows keep the rows of a slice close together, so
 // their x gathers and outputs stay local.
+// Compressed columns: a square operator whose entries use at most 255 distinct offsets col - row is
+// stored with one-byte codes into a table of those offsets.  Otherwise, when every slice of an
+// operator with 4-slot groups spans fewer than 65,536
+// columns (the stencil-like operators of this path: a slice holds 8 consecutive rows, or rows of one
+// 256-row window), the columns are stored as 16-bit offsets from the slice's smallest column
+// (padding slots point at that column with value 0).
 // CSR: kept for operators with fewer than RS_MIN_ROWS rows, and when even the sorted slices would pad
 // more than 30 % above the nonzeros; the vector-CSR kernel (TPR lanes per row) runs those.
 #pragma once
@@ -46,6 +52,17 @@ struct RowsOp {
   DBuf<int32_t> perm;  // empty when rows keep their order
   DBuf<int32_t> scol;
   DBuf<T> sval;
+  // 4-slot groups whose slices span at most 65,536 columns keep 16-bit column offsets from a per-slice
+  // base instead of scol (6 bytes per FP32 entry instead of 8)
+  bool c16 = false;
+  DBuf<uint16_t> scol16;
+  DBuf<int32_t> sbase;
+  // square operators with 4-slot groups whose entries use at most 255 distinct offsets col - row (the
+  // stencil-like operators of the structured levels) keep one byte per entry: a code into the table
+  // of those offsets (code 255, offset 0, marks padding); 5 bytes per FP32 entry instead of 8
+  bool c8 = false;
+  DBuf<uint8_t> scode;
+  DBuf<int32_t> otab;  // 256 offsets
   // CSR
   DCSR<T> csr;
 };

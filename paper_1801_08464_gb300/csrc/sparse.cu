@@ -1031,13 +1031,16 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
     int64_t products = counts_to_rowptr(c, ub.p, pp.p, m);
     prof_add_bytes(c, name, 12.0 * (double)(A.nnz + products + C.nnz) + 16.0 * (double)(m + 1));
   }
-  ProfScope ps4(c, "spgemm_numeric");
-  k_spgemm_numeric_expand<<<grid_for(C.nr, NX_WARPS), 32 * NX_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci,
-                                                                                B.v, C.rp, C.ci, C.v, ub.p);
-  CU_LAUNCH();
-  k_spgemm_numeric<<<grid_for(C.nr, NUM_WARPS), 32 * NUM_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
-                                                                           C.rp, C.ci, C.v, ub.p);
-  CU_LAUNCH();
+  // the numeric pass of the rows over FUSE_CAP products (none in most products: no launch then)
+  if (hc[0] + hc[1] > 0) {
+    ProfScope ps4(c, "spgemm_numeric");
+    k_spgemm_numeric_expand<<<grid_for(C.nr, NX_WARPS), 32 * NX_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci,
+                                                                                  B.v, C.rp, C.ci, C.v, ub.p);
+    CU_LAUNCH();
+    k_spgemm_numeric<<<grid_for(C.nr, NUM_WARPS), 32 * NUM_WARPS, 0, c.s>>>(C.nr, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
+                                                                             C.rp, C.ci, C.v, ub.p);
+    CU_LAUNCH();
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
