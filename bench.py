@@ -53,8 +53,9 @@ KERNEL_NAMES = SOLVE_KERNELS + SETUP_KERNELS
 # DRAM bytes over algorithmic bytes of one launch, from one ncu capture of the kernel on an 80^3
 # instance of the workload (dram__bytes_read.sum + dram__bytes_write.sum); the traffic of a full-size
 # launch is this ratio times its algorithmic bytes, which scale with the entries it streams.
-# k_mdot (multi-dot, 16 vectors of 1,536,000): 200.73 MB of DRAM traffic for 196.61 MB algorithmic.
-TRAFFIC = {"mdot": 200.728320e6 / 196.608e6}
+# k_mdot (multi-dot, 16 vectors of 1,536,000): 200.73 MB of DRAM traffic for 196.61 MB algorithmic;
+# k_bsr_sell<double> (FP64 SpMV): 295.11 MB for 298.14 MB.
+TRAFFIC = {"mdot": 200.728320e6 / 196.608e6, "bsr3_spmv_f64": 295.114240e6 / 298137608.0}
 # FP64 FMAs per algorithmic byte of the Krylov kernels bound by the FP64 rate: the multi-dot does one
 # FMA per 8-byte element it reads (V_k . w and w . w); the 3x3-block SpMV 9 per 76-byte block (the
 # row pointers and vectors, a few % of its bytes, are left out: a slight overestimate)

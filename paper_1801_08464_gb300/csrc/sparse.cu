@@ -522,26 +522,45 @@ __global__ void __launch_bounds__(32 * NUM_WARPS) k_spgemm_numeric(int64_t m, co
 // Stores the u distinct (column, value) pairs K[0..u), V[0..u) (any order, u <= 128) at
 // ocol/oval in ascending column order: each lane holds up to 4 pairs and counts, in one pass over the
 // keys (broadcast shared-memory reads), how many are smaller; that count is the pair's position.
-__device__ __forceinline__ void warp_rank_store128(const int32_t* K, const double* V, int u, int lane,
-                                                   int32_t* ocol, double* oval) {
-  int32_t key[4];
-  int r[4];
+template <int NH>
+__device__ __forceinline__ void warp_rank_store(const int32_t* K, const double* V, int u, int lane, int32_t* ocol,
+                                                double* oval) {
+  int32_t key[NH];
+  int r[NH];
 #pragma unroll
-  for (int h = 0; h < 4; ++h) {
+  for (int h = 0; h < NH; ++h) {
     int t = lane + 32 * h;
     key[h] = t < u ? K[t] : INT_MAX;
     r[h] = 0;
   }
-  for (int j = 0; j < u; ++j) {
-    int32_t kj = K[j];
+  // the rank of a key is the number of smaller keys; four keys per (broadcast) 16-byte read
+  int j = 0;
+  for (; j + 4 <= u; j += 4) {
+    const int4 kk = *reinterpret_cast<const int4*>(K + j);
 #pragma unroll
-    for (int h = 0; h < 4; ++h) r[h] += (kj < key[h]);
+    for (int h = 0; h < NH; ++h)
+      r[h] += (kk.x < key[h]) + (kk.y < key[h]) + (kk.z < key[h]) + (kk.w < key[h]);
+  }
+  for (; j < u; ++j) {
+    const int32_t kj = K[j];
+#pragma unroll
+    for (int h = 0; h < NH; ++h) r[h] += (kj < key[h]);
   }
 #pragma unroll
-  for (int h = 0; h < 4; ++h) {
+  for (int h = 0; h < NH; ++h) {
     int t = lane + 32 * h;
     if (t < u) { ocol[r[h]] = key[h]; oval[r[h]] = V[t]; }
   }
+}
+
+// Places the u <= 128 distinct (column, value) pairs of K / V at their ranks in ocol / oval (sorted
+// by column): each lane ranks up to four keys against all u keys.
+__device__ __forceinline__ void warp_rank_store128(const int32_t* K, const double* V, int u, int lane,
+                                                   int32_t* ocol, double* oval) {
+  if (u <= 32) warp_rank_store<1>(K, V, u, lane, ocol, oval);
+  else if (u <= 64) warp_rank_store<2>(K, V, u, lane, ocol, oval);
+  else if (u <= 96) warp_rank_store<3>(K, V, u, lane, ocol, oval);
+  else warp_rank_store<4>(K, V, u, lane, ocol, oval);
 }
 
 // Fused product for rows with at most TT_CAP products, one thread per row: the products are taken
