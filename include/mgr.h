@@ -83,8 +83,8 @@ typedef struct {
                                             no longer needs them (the apply and the solve keep what
                                             they read); their introspection then returns
                                             MGR_ERR_STATE.  Default 0 */
-  int32_t spgemm_stage;                  /* SpGEMM products staged per batch of short rows (0: the
-                                            default 2^27; values <= 1024 also mean the default) */
+  int32_t spgemm_stage;                  /* SpGEMM products staged per batch of short rows (0 or any
+                                            value <= 1024: 2^29, or 2^27 with lean; 12 bytes each) */
   int32_t adjoint;                       /* 1: the setup also builds the transposed operators of the
                                             preconditioner, for mgr_apply_transpose and
                                             fgmres_solve_transpose (default 0) */

@@ -315,24 +315,47 @@ void launch_scal(Ctx& c, int64_t n, double alpha, const double* x, double* y) {
   CU_LAUNCH();
 }
 
-__global__ void k_xupdate(int64_t n, const double* __restrict__ Z, int64_t ldz, int nz, const double* __restrict__ y,
-                          double* __restrict__ x) {
+// x += Z y (one solution update per restart cycle): pairs of doubles per thread, one resident wave,
+// each entry's FMAs in ascending k as before; a misaligned x takes the scalar form
+__global__ void __launch_bounds__(KT) k_xupdate(int64_t n, const double* __restrict__ Z, int64_t ldz, int nz,
+                                                const double* __restrict__ y, double* __restrict__ x, int vec) {
   pdl_wait();
   __shared__ double sy[KRY_MAXV];
   if (threadIdx.x < nz) sy[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
+  if (vec) {
+    const int64_t n2 = n >> 1;
+    for (int64_t q = blockIdx.x * (int64_t)KT + threadIdx.x; q < n2; q += (int64_t)gridDim.x * KT) {
+      const int64_t i = 2 * q;
+      double2 s = *reinterpret_cast<const double2*>(x + i);
+#pragma unroll 8
+      for (int k = 0; k < nz; ++k) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(Z + k * ldz + i));
+        s.x = fma(sy[k], v.x, s.x);
+        s.y = fma(sy[k], v.y, s.y);
+      }
+      *reinterpret_cast<double2*>(x + i) = s;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+      const int64_t i = n - 1;
+      double s = x[i];
+      for (int k = 0; k < nz; ++k) s = fma(sy[k], Z[k * ldz + i], s);
+      x[i] = s;
+    }
+    return;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double s = x[i];
-#pragma unroll
-    for (int k = 0; k < KRY_MAXV; ++k)
-      if (k < nz) s += sy[k] * Z[k * ldz + i];
+    for (int k = 0; k < nz; ++k) s = fma(sy[k], Z[k * ldz + i], s);
     x[i] = s;
   }
 }
 void launch_xupdate(Ctx& c, int64_t n, const double* Z, int64_t ldz, int nz, const double* y, double* x) {
+  const int vec = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(Z)) & 15) == 0 && (ldz & 1) == 0;
+  const int grid = one_wave((const void*)k_xupdate);
   for (int k0 = 0; k0 < nz; k0 += KRY_MAXV) {
     int m = nz - k0 < KRY_MAXV ? nz - k0 : KRY_MAXV;
-    launch_pdl(c, k_xupdate, grid_for(n, 256, 4 * 1024), 256, 0, n, Z + k0 * ldz, ldz, m, y + k0, x);
+    launch_pdl(c, k_xupdate, grid, KT, 0, n, Z + k0 * ldz, ldz, m, y + k0, x, vec);
     CU_LAUNCH();
   }
 }

@@ -612,7 +612,8 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   h.valT32.release(); h.valT64.release(); h.binvT32.release(); h.binvT64.release(); h.cinvT.release();
   h.kry_valsT.release();
   ProfScope ps_all(c, "setup_total");
-  c.spgemm_stage = h.o.spgemm_stage;
+  // one batch for the products of a mid-size problem; the lean setup keeps the staging small
+  c.spgemm_stage = h.o.spgemm_stage > 1024 ? h.o.spgemm_stage : (h.o.lean ? (int64_t(1) << 27) : (int64_t(1) << 29));
   bsr3_validate(c, A, marker);
   h.nb = A.nb;
   h.nnzb = A.nnzb;
