@@ -487,13 +487,14 @@ constexpr int EXT_CAP = 256;
 __global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* srp,
                                 const int32_t* sci, const int8_t* cf, const int32_t* cidx, const int32_t* cfine,
                                 const int64_t* prp, const int32_t* pci, double* pv, double* den_g, double* q_g,
-                                int8_t* rowzero, const int8_t* only) {
+                                int8_t* rowzero, const int32_t* rows, int64_t nrows) {
   __shared__ double s_wt[EXT_WARPS][EXT_CAP], s_kt[EXT_WARPS][EXT_CAP];
   __shared__ int8_t s_wf[EXT_WARPS][EXT_CAP], s_kf[EXT_WARPS][EXT_CAP];
-  int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  // the rows listed by the shared-memory kernel (a warp per listed row)
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (i >= n) return;
-  if (only && !only[i]) return;
+  if (r >= nrows) return;
+  const int64_t i = rows[r];
   if (cf[i] == 1) {
     if (lane == 0) { pv[prp[i]] = 1.0; rowzero[i] = 0; }
     return;
@@ -651,7 +652,8 @@ __global__ void __launch_bounds__(EXT_TPB, 12) k_extpi_weights_row(
     int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
     const double* __restrict__ diag, const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
     const int8_t* __restrict__ cf, const int32_t* __restrict__ cfine, const int64_t* __restrict__ prp,
-    const int32_t* __restrict__ pci, double* __restrict__ pv, int8_t* __restrict__ rowzero, int8_t* __restrict__ rest) {
+    const int32_t* __restrict__ pci, double* __restrict__ pv, int8_t* __restrict__ rowzero, int8_t* __restrict__ rest,
+    int32_t* __restrict__ over, int* __restrict__ nover) {
   __shared__ int32_t s_pf[EXT_PCAP_T][EXT_TPB];
   __shared__ double s_num[EXT_PCAP_T][EXT_TPB];
   const int64_t i = blockIdx.x * (int64_t)EXT_TPB + threadIdx.x;
@@ -660,7 +662,7 @@ __global__ void __launch_bounds__(EXT_TPB, 12) k_extpi_weights_row(
   if (cf[i] == 1) { pv[prp[i]] = 1.0; rowzero[i] = 0; rest[i] = 0; return; }
   const int64_t p0 = prp[i];
   const int64_t np64 = prp[i + 1] - p0;
-  if (np64 > EXT_PCAP_T) { rest[i] = 1; return; }
+  if (np64 > EXT_PCAP_T) { rest[i] = 1; over[atomicAdd(nover, 1)] = (int32_t)i; return; }
   const int np = (int)np64;
   for (int t = 0; t < np; ++t) {
     s_pf[t][tx] = cfine[pci[p0 + t]];
@@ -732,24 +734,21 @@ __global__ void __launch_bounds__(32 * EXT_WARPS, MINB) k_extpi_weights_sh(
     const double* __restrict__ diag, const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
     const int8_t* __restrict__ cf, const int32_t* __restrict__ cfine, const int64_t* __restrict__ prp,
     const int32_t* __restrict__ pci, double* __restrict__ pv, int8_t* __restrict__ rowzero, int8_t* __restrict__ rest,
-    int pass) {
+    const int32_t* __restrict__ rows, int64_t nrows, int32_t* __restrict__ over, int* __restrict__ nover) {
   __shared__ int32_t s_pf[EXT_WARPS][PCAP];
   __shared__ double s_num[EXT_WARPS][PCAP];
   __shared__ int32_t s_s[EXT_WARPS][KCAP];
   __shared__ int32_t s_k[EXT_WARPS][KCAP];
   __shared__ double s_aik[EXT_WARPS][KCAP];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = (int64_t)blockIdx.x * EXT_WARPS + w;
-  if (i >= n) return;
-  if (pass == 1 && rest[i] != 1) return;
-  if (cf[i] == 1) {
-    if (lane == 0) { pv[prp[i]] = 1.0; rowzero[i] = 0; rest[i] = 0; }
-    return;
-  }
+  // the F rows listed by k_extpi_weights_row (a warp per listed row)
+  const int64_t r = (int64_t)blockIdx.x * EXT_WARPS + w;
+  if (r >= nrows) return;
+  const int64_t i = rows[r];
   const int64_t p0 = prp[i], np64 = prp[i + 1] - p0;
   const int64_t s0 = srp[i], ns64 = srp[i + 1] - s0;
   if (np64 > PCAP || ns64 > KCAP) {
-    if (lane == 0) rest[i] = (int8_t)(pass + 1);
+    if (lane == 0) { rest[i] = 2; over[atomicAdd(nover, 1)] = (int32_t)i; }
     return;
   }
   const int np = (int)np64, ns = (int)ns64;
@@ -1017,15 +1016,29 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
   DBuf<double> diag(c, n);
   k_diag<<<grid_for(n, B), B, 0, c.s>>>(n, A.rp, A.ci, A.v, diag.p);
   CU_LAUNCH();
+  DBuf<int32_t> list1(c, n), list2(c, n);
+  DBuf<int> nl(c, 2);
+  CU(cudaMemsetAsync(nl.p, 0, 2 * sizeof(int), c.s));
   k_extpi_weights_row<<<grid_for(n, EXT_TPB), EXT_TPB, 0, c.s>>>(n, A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p,
-                                                                 cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p);
+                                                                 cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p,
+                                                                 list1.p, nl.p);
   CU_LAUNCH();
-  k_extpi_weights_sh<EXT_PCAP_L, EXT_KCAP_L, 1><<<grid_for(n, EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(
-      n, A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p, cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p, 1);
-  CU_LAUNCH();
-  k_extpi_weights<<<grid_for(n * 32, 32 * EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp,
-                                                           Pf.ci, Pf.v, den.p, q.p, rowzero.p, rest.p);
-  CU_LAUNCH();
+  // the rows with more interpolation columns than the thread-per-row stage holds (a few %), then
+  // those beyond the warp kernel's caps (rare): launched over their lists only
+  const int n1 = read_scalar(c, nl.p);
+  if (n1 > 0) {
+    k_extpi_weights_sh<EXT_PCAP_L, EXT_KCAP_L, 1><<<grid_for(n1, EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(
+        n, A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p, cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p, list1.p, n1,
+        list2.p, nl.p + 1);
+    CU_LAUNCH();
+    const int n2 = read_scalar(c, nl.p + 1);
+    if (n2 > 0) {
+      k_extpi_weights<<<grid_for((int64_t)n2 * 32, 32 * EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(
+          n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp, Pf.ci, Pf.v, den.p, q.p, rowzero.p, list2.p,
+          n2);
+      CU_LAUNCH();
+    }
+  }
   DBuf<int64_t> cnt(c, n + 1);
   k_ptrunc<<<grid_for(n * 32, 128), 128, 0, c.s>>>(n, cf.p, Pf.rp, Pf.v, rowzero.p, pmax, keep.p, scale.p, cnt.p);
   CU_LAUNCH();

@@ -372,3 +372,51 @@ def test_programmatic_dependent_launch_matches_plain():
         m.close()
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
     assert outs[0][2] == outs[1][2]
+
+
+def test_amg_setup_with_wide_rows():
+    """AMG setup on a scalar M-matrix view with some rows of 180 entries (60 block neighbours): the
+    ext+i rows beyond the thread-per-row stage and beyond the warp kernel's caps take the listed
+    kernels; every AMG level matches the oracle bit for bit."""
+    import paper_1801_08464_gb300 as mg
+    rng = np.random.default_rng(17)
+    nb = 600
+    nbrs = [set() for _ in range(nb)]
+    for i in range(nb):
+        k = 60 if i % 50 == 0 else 4
+        for j in rng.choice(nb, k, replace=False):
+            if j != i:
+                nbrs[i].add(int(j))
+                nbrs[int(j)].add(i)
+    rowptr = [0]
+    colind, vals = [], []
+    for i in range(nb):
+        cols = sorted(nbrs[i] | {i})
+        for j in cols:
+            blk = -rng.uniform(0.5, 1.5, (3, 3)) if j != i else np.zeros((3, 3))
+            colind.append(j)
+            vals.append(blk)
+        rowptr.append(len(colind))
+    rowptr = np.array(rowptr, np.int64)
+    colind = np.array(colind, np.int32)
+    vals = np.array(vals)
+    rows = np.repeat(np.arange(nb), np.diff(rowptr))
+    # diagonally dominant diagonal blocks
+    for b in np.nonzero(rows == colind)[0]:
+        i = rows[b]
+        s = -vals[rowptr[i]:rowptr[i + 1]].sum(axis=(0, 2))
+        vals[b] = np.diag(s + 1.0) - 0.1
+    mk = np.zeros(3 * nb, np.int8)
+    p = ncpgen.Problem(ncpgen.GridConfig(nb, 1), nb, rowptr, colind, vals, np.ones(nb, np.int8), mk,
+                       np.zeros((nb, 3)), np.ones(nb))
+    opts = dict(amg_theta=0.25, amg_max_coarse=16)
+    A, mkd = to_gpu(p)
+    m = mg.MGR(**opts)
+    m.setup(A, mkd)
+    o = oracle.OracleMGR(rowptr, colind, vals, mk, **opts)
+    L, na = m.levels()
+    assert (L, na) == o.info() and L == 0 and na >= 2
+    for k in range(na - 1):
+        for kind_m, kind_o in ((mg.MAT_AMG_P, oracle.MAT_AMG_P), (mg.MAT_AMG_A, oracle.MAT_AMG_A)):
+            assert compare_csr(m.scipy(kind_m, k), o.scipy(kind_o, k), what=f"AMG kind {kind_m} level {k}") == 1.0
+    m.close()
