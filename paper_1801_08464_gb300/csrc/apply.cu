@@ -195,7 +195,20 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
   int64_t j0 = soff[s], nq = (soff[s + 1] - j0) / Q;
   const T* vp = val + j0 * RS_C + t * Q;
   T sum = 0;
-  if constexpr (Q == 4) {
+  if constexpr (Q == 4 && CM == 2) {
+    // one-byte codes: the codes of the next group are loaded before this group's table lookups and
+    // gathers (three dependent steps per group: codes, table, x)
+    const uint8_t* cp8 = code + j0 * RS_C + t * 4;
+    uint32_t nxt = nq > 0 ? __ldg(reinterpret_cast<const uint32_t*>(cp8)) : 0u;
+#pragma unroll 2
+    for (int64_t q = 0; q < nq; ++q) {
+      const uint32_t raw = nxt;
+      if (q + 1 < nq) nxt = __ldg(reinterpret_cast<const uint32_t*>(cp8 + (q + 1) * (4 * RS_C)));
+      const int4 c = make_int4((int32_t)row + s_tab[raw & 0xFFu], (int32_t)row + s_tab[(raw >> 8) & 0xFFu],
+                               (int32_t)row + s_tab[(raw >> 16) & 0xFFu], (int32_t)row + s_tab[raw >> 24]);
+      sum += Quad<T>::dot(vp + q * (4 * RS_C), c, x);
+    }
+  } else if constexpr (Q == 4) {
     const QuadCols qc = quad_setup<CM>(col, col16, sbase, code, s_tab, s, j0, t, row);
 #pragma unroll 2
     for (int64_t q = 0; q < nq; ++q) sum += Quad<T>::dot(vp + q * (4 * RS_C), quad_cols<CM>(qc, q), x);

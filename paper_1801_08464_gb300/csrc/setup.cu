@@ -1187,6 +1187,59 @@ __global__ void k_dense_right_half(int64_t n, const double* M, double* inv) {
   inv[t] = M[i * 2 * n + n + j];
 }
 
+// The same Gauss-Jordan elimination in one block for n <= GJ_ONE (the coarsest AMG grids): the
+// pivot search, the row swap, the scaling and the elimination of each column are separated by block
+// barriers instead of kernel boundaries, with the same operations in the same order (the multipliers
+// of column k are read before any row is updated), so the inverse is the one of the two-kernel form.
+constexpr int64_t GJ_ONE = 1024;
+__global__ void __launch_bounds__(1024) k_gj_one(int64_t n, double* M, int* err) {
+  __shared__ double bv[1024];
+  __shared__ int64_t bi[1024];
+  __shared__ double f[GJ_ONE];
+  const int64_t w = 2 * n;
+  for (int64_t k = 0; k < n; ++k) {
+    double best = -1.0;
+    int64_t arg = n;
+    for (int64_t i = k + threadIdx.x; i < n; i += blockDim.x) {
+      double a = fabs(M[i * w + k]);
+      if (a > best) { best = a; arg = i; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = arg;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) {
+        double a = bv[threadIdx.x + st];
+        int64_t ia = bi[threadIdx.x + st];
+        if (a > bv[threadIdx.x] || (a == bv[threadIdx.x] && ia < bi[threadIdx.x])) { bv[threadIdx.x] = a; bi[threadIdx.x] = ia; }
+      }
+      __syncthreads();
+    }
+    const int64_t p = bi[0];
+    if (bv[0] == 0.0 || !isfinite(bv[0]) || p >= n) {  // uniform over the block
+      if (threadIdx.x == 0) atomicOr(err, EBIT_SINGULAR);
+      return;
+    }
+    if (p != k)
+      for (int64_t j = threadIdx.x; j < w; j += blockDim.x) {
+        double t = M[k * w + j];
+        M[k * w + j] = M[p * w + j];
+        M[p * w + j] = t;
+      }
+    __syncthreads();
+    const double piv = M[k * w + k];
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < w; j += blockDim.x) M[k * w + j] = dv(M[k * w + j], piv);
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) f[i] = M[i * w + k];
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < n * w; e += blockDim.x) {
+      const int64_t i = e / w, j = e - i * w;
+      if (i != k && f[i] != 0.0) M[e] = __dsub_rn(M[e], dm(f[i], M[k * w + j]));
+    }
+    __syncthreads();
+  }
+}
+
 void dense_inverse(Ctx& c, const DCSR<double>& A, DBuf<double>& inv) {
   int64_t n = A.nr;
   inv.alloc(c, n * n);
@@ -1194,11 +1247,16 @@ void dense_inverse(Ctx& c, const DCSR<double>& A, DBuf<double>& inv) {
   DBuf<double> M(c, 2 * n * n);
   k_dense_from_csr<<<grid_for(n, 128), 128, 0, c.s>>>(n, A.rp, A.ci, A.v, M.p);
   CU_LAUNCH();
-  for (int64_t k = 0; k < n; ++k) {
-    k_gj_pivot<<<1, 1024, 0, c.s>>>(n, k, M.p, c.d_err);
+  if (n <= GJ_ONE) {
+    k_gj_one<<<1, 1024, 0, c.s>>>(n, M.p, c.d_err);
     CU_LAUNCH();
-    k_gj_eliminate<<<(unsigned)n, 128, 0, c.s>>>(n, k, M.p);
-    CU_LAUNCH();
+  } else {
+    for (int64_t k = 0; k < n; ++k) {
+      k_gj_pivot<<<1, 1024, 0, c.s>>>(n, k, M.p, c.d_err);
+      CU_LAUNCH();
+      k_gj_eliminate<<<(unsigned)n, 128, 0, c.s>>>(n, k, M.p);
+      CU_LAUNCH();
+    }
   }
   k_dense_right_half<<<grid_for(n * n, 256), 256, 0, c.s>>>(n, M.p, inv.p);
   CU_LAUNCH();
