@@ -80,6 +80,52 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NA], int na, do
   }
 }
 
+// The products of one block: KN vectors (KN <= MD_VEC, a compile-time count, so no FMA of a vector the
+// block does not hold is issued, not even predicated off) and, with DOW, w . w as well.
+template <int KN, bool DOW>
+__device__ __forceinline__ void mdot_rows(int64_t i0, int64_t i1, const double* __restrict__ V, int64_t ldv,
+                                          const double* __restrict__ w, double (&acc)[MD_VEC + 1]) {
+  // pairs of doubles: chunk is even and ldv is even, so every pair is 16-byte aligned
+  for (int64_t i = i0 + 2 * threadIdx.x; i < i1; i += 2 * KT) {
+    if (i + 1 < i1) {
+      double2 wi = *reinterpret_cast<const double2*>(w + i);
+      // one FMA per product: FP64 instructions, not bytes, bound this kernel on this GPU
+#pragma unroll
+      for (int k = 0; k < KN; ++k) {
+        double2 v = __ldg(reinterpret_cast<const double2*>(V + k * ldv + i));
+        acc[k] = fma(v.x, wi.x, acc[k]);
+        acc[k] = fma(v.y, wi.y, acc[k]);
+      }
+      if (DOW) {
+        acc[MD_VEC] = fma(wi.x, wi.x, acc[MD_VEC]);
+        acc[MD_VEC] = fma(wi.y, wi.y, acc[MD_VEC]);
+      }
+    } else {
+      double wi = w[i];
+#pragma unroll
+      for (int k = 0; k < KN; ++k) acc[k] = fma(V[k * ldv + i], wi, acc[k]);
+      if (DOW) acc[MD_VEC] = fma(wi, wi, acc[MD_VEC]);
+    }
+  }
+}
+
+template <bool DOW>
+__device__ __forceinline__ void mdot_rows_kn(int kn, int64_t i0, int64_t i1, const double* __restrict__ V,
+                                             int64_t ldv, const double* __restrict__ w, double (&acc)[MD_VEC + 1]) {
+  static_assert(MD_VEC == 8, "one case per vector count of a block");
+  switch (kn) {
+    case 0: mdot_rows<0, DOW>(i0, i1, V, ldv, w, acc); break;  // w . w alone
+    case 1: mdot_rows<1, DOW>(i0, i1, V, ldv, w, acc); break;
+    case 2: mdot_rows<2, DOW>(i0, i1, V, ldv, w, acc); break;
+    case 3: mdot_rows<3, DOW>(i0, i1, V, ldv, w, acc); break;
+    case 4: mdot_rows<4, DOW>(i0, i1, V, ldv, w, acc); break;
+    case 5: mdot_rows<5, DOW>(i0, i1, V, ldv, w, acc); break;
+    case 6: mdot_rows<6, DOW>(i0, i1, V, ldv, w, acc); break;
+    case 7: mdot_rows<7, DOW>(i0, i1, V, ldv, w, acc); break;
+    default: mdot_rows<8, DOW>(i0, i1, V, ldv, w, acc); break;
+  }
+}
+
 // 2-D multi-dot: block b handles vector group g = b % ng (vectors 8g .. 8g+7) on row chunk
 // x = b / ng, so the ng blocks sharing a chunk of w run together and re-read it from L2.  Group 0
 // also accumulates w . w.  Partial sums go to part[k * nx + x] (k = nv for w . w).
@@ -96,30 +142,9 @@ __global__ void __launch_bounds__(KT) k_mdot(int64_t n, const double* __restrict
   double acc[MD_VEC + 1];
 #pragma unroll
   for (int k = 0; k <= MD_VEC; ++k) acc[k] = 0.0;
-  // pairs of doubles: chunk is even and ldv is even, so every pair is 16-byte aligned
-  for (int64_t i = i0 + 2 * threadIdx.x; i < i1; i += 2 * KT) {
-    if (i + 1 < i1) {
-      double2 wi = *reinterpret_cast<const double2*>(w + i);
-      // one FMA per product: FP64 instructions, not bytes, bound this kernel on this GPU
-#pragma unroll
-      for (int k = 0; k < MD_VEC; ++k)
-        if (k < kn) {
-          double2 v = __ldg(reinterpret_cast<const double2*>(V + (k0 + k) * ldv + i));
-          acc[k] = fma(v.x, wi.x, acc[k]);
-          acc[k] = fma(v.y, wi.y, acc[k]);
-        }
-      if (dow) {
-        acc[MD_VEC] = fma(wi.x, wi.x, acc[MD_VEC]);
-        acc[MD_VEC] = fma(wi.y, wi.y, acc[MD_VEC]);
-      }
-    } else {
-      double wi = w[i];
-#pragma unroll
-      for (int k = 0; k < MD_VEC; ++k)
-        if (k < kn) acc[k] = fma(V[(k0 + k) * ldv + i], wi, acc[k]);
-      if (dow) acc[MD_VEC] = fma(wi, wi, acc[MD_VEC]);
-    }
-  }
+  // kn and dow are uniform over the block
+  if (dow) mdot_rows_kn<true>(kn, i0, i1, V + k0 * ldv, ldv, w, acc);
+  else mdot_rows_kn<false>(kn, i0, i1, V + k0 * ldv, ldv, w, acc);
   __shared__ double sh[KT / 32][MD_VEC + 1];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // reduce-scatter of the 8 vector sums across the warp (FP64 adds are the scarce instructions): at

@@ -16,7 +16,8 @@ from gpu_common import compare_csr, to_gpu
 
 pytestmark = pytest.mark.gpu
 
-BENCH_SOLVER = dict(amg_theta=0.5, amg_pmax=4, amg_smoother=0, amg_omega=0.8)
+BENCH_SOLVER = dict(amg_theta=0.58, amg_pmax=4, amg_smoother=0, amg_omega=0.8, amg_max_coarse=64,
+                    frelax_sweeps=[1, 1, 1])
 
 
 def test_64cube_full_parity_fp64():
