@@ -30,11 +30,10 @@ RTOL, RESTART, MAXIT = 1e-8, 30, 1000
 # Solver settings used for the 3-D workloads: strength threshold 0.58 (the middle of the range 0.55-0.6
 # where the iteration count is lowest: 41-42 at 128^3, against 50 at 0.5 and 48 at 0.62) and
 # interpolation truncation to 4 entries keep the AMG operator complexity low on the 25-63 point
-# pressure stencils; omega-Jacobi
-# (0.8) smoothing converges in fewer iterations than l1-Jacobi on these operators; one l1-Jacobi
-# sweep on the saturation and gas-absent constraint blocks (levels 2 and 3) converges in fewer
-# outer iterations than two; the AMG coarsens down to at most 64 rows, whose dense inverse is cheap
-# to build.
+# pressure stencils; omega-Jacobi (0.8) smoothing converges in fewer iterations than l1-Jacobi on
+# these operators; one l1-Jacobi sweep on the saturation and gas-absent constraint blocks (levels 2
+# and 3) converges in fewer outer iterations than two; the AMG coarsens down to at most 64 rows,
+# whose dense inverse is cheap to build.
 SOLVER = dict(amg_theta=0.58, amg_pmax=4, amg_smoother=0, amg_omega=0.8, amg_max_coarse=64, frelax_sweeps=[1, 1, 1])
 # The two-level unsaturated workloads (section 6.1): injective R at both reductions, three
 # l1-Jacobi sweeps on the saturation block, V(2,2) on the pressure system, default AMG settings.
@@ -58,9 +57,9 @@ KERNEL_NAMES = SOLVE_KERNELS + SETUP_KERNELS
 # DRAM bytes over algorithmic bytes of one launch, from one ncu capture of the kernel on an 80^3
 # instance of the workload (dram__bytes_read.sum + dram__bytes_write.sum); the traffic of a full-size
 # launch is this ratio times its algorithmic bytes, which scale with the entries it streams.
-# k_mdot (multi-dot, 16 vectors of 1,536,000): 200.73 MB of DRAM traffic for 196.61 MB algorithmic;
+# k_mdot (multi-dot, 16 vectors of 1,536,000): 200.42 MB of DRAM traffic for 196.61 MB algorithmic;
 # k_bsr_sell<double> (FP64 SpMV): 295.11 MB for 298.14 MB.
-TRAFFIC = {"mdot": 200.728320e6 / 196.608e6, "bsr3_spmv_f64": 295.114240e6 / 298137608.0}
+TRAFFIC = {"mdot": 200.42496e6 / 196.608e6, "bsr3_spmv_f64": 295.114240e6 / 298137608.0}
 # FP64 FMAs per algorithmic byte of the Krylov kernels bound by the FP64 rate: the multi-dot does one
 # FMA per 8-byte element it reads (V_k . w and w . w); the 3x3-block SpMV 9 per 76-byte block (the
 # row pointers and vectors, a few % of its bytes, are left out: a slight overestimate)
