@@ -253,13 +253,17 @@ void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const 
 }
 
 // v_out = s (w - sum_k h[k] V_k) (h and s read from device memory; s == nullptr means 1), and
-// ||v_out||^2 partials when part != nullptr.  v_out may alias w.
+// ||v_out||^2 partials when part != nullptr.  v_out may alias w.  NV > 0: the vector count nv is the
+// compile-time NV and the k loop is unrolled whole (no remainder loop that waits for one load at a
+// time); NV = 0 takes nv at run time.  Each entry subtracts its products in ascending k either way.
+template <int NV>
 __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
                                                 const double* __restrict__ h, const double* __restrict__ sp,
                                                 const double* w, double* vout, double* __restrict__ part) {
   pdl_wait();
+  const int cnt = NV > 0 ? NV : nv;
   __shared__ double sh_h[KRY_MAXV];
-  if (threadIdx.x < nv) sh_h[threadIdx.x] = h[threadIdx.x];
+  if (threadIdx.x < cnt) sh_h[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
   double sc = sp ? *sp : 1.0;
   double acc[1] = {0.0};
@@ -267,11 +271,20 @@ __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restr
   for (int64_t q = blockIdx.x * (int64_t)KT + threadIdx.x; q < n2; q += (int64_t)gridDim.x * KT) {
     int64_t i = 2 * q;
     double2 s = *reinterpret_cast<const double2*>(w + i);
+    if constexpr (NV > 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+        double2 v = __ldg(reinterpret_cast<const double2*>(V + k * ldv + i));
+        s.x -= sh_h[k] * v.x;
+        s.y -= sh_h[k] * v.y;
+      }
+    } else {
 #pragma unroll 8
-    for (int k = 0; k < nv; ++k) {
-      double2 v = __ldg(reinterpret_cast<const double2*>(V + k * ldv + i));
-      s.x -= sh_h[k] * v.x;
-      s.y -= sh_h[k] * v.y;
+      for (int k = 0; k < nv; ++k) {
+        double2 v = __ldg(reinterpret_cast<const double2*>(V + k * ldv + i));
+        s.x -= sh_h[k] * v.x;
+        s.y -= sh_h[k] * v.y;
+      }
     }
     s.x *= sc;
     s.y *= sc;
@@ -282,7 +295,7 @@ __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restr
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     int64_t i = n - 1;
     double s = w[i];
-    for (int k = 0; k < nv; ++k) s -= sh_h[k] * V[k * ldv + i];
+    for (int k = 0; k < cnt; ++k) s -= sh_h[k] * V[k * ldv + i];
     s *= sc;
     vout[i] = s;
     acc[0] += s * s;
@@ -290,12 +303,17 @@ __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restr
   if (part) block_reduce_store<1>(acc, 1, part);
 }
 
+using MupdateFn = void (*)(int64_t, const double*, int64_t, int, const double*, const double*, const double*, double*,
+                           double*);
+static const MupdateFn kMupdate[KRY_MAXV + 1] = {k_mupdate<0>, k_mupdate<1>, k_mupdate<2>, k_mupdate<3>, k_mupdate<4>, k_mupdate<5>, k_mupdate<6>, k_mupdate<7>, k_mupdate<8>, k_mupdate<9>, k_mupdate<10>, k_mupdate<11>, k_mupdate<12>, k_mupdate<13>, k_mupdate<14>, k_mupdate<15>, k_mupdate<16>, k_mupdate<17>, k_mupdate<18>, k_mupdate<19>, k_mupdate<20>, k_mupdate<21>, k_mupdate<22>, k_mupdate<23>, k_mupdate<24>, k_mupdate<25>, k_mupdate<26>, k_mupdate<27>, k_mupdate<28>, k_mupdate<29>, k_mupdate<30>, k_mupdate<31>, k_mupdate<32>};
+
 void launch_mupdate(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* h, const double* scale,
                     const double* w, double* vout, double* part, double* out) {
   if (nv > KRY_MAXV) throw Error(MGR_ERR_UNSUPPORTED, "update with more than 32 vectors");
   ProfScope ps(c, "mupdate", 8.0 * (nv + 2) * n);
-  const int grid = one_wave((const void*)k_mupdate);
-  launch_pdl(c, k_mupdate, grid, KT, 0, n, V, ldv, nv, h, scale, w, vout, out ? part : nullptr);
+  const MupdateFn fn = kMupdate[nv > 0 ? nv : 0];
+  const int grid = one_wave((const void*)fn);
+  launch_pdl(c, fn, grid, KT, 0, n, V, ldv, nv, h, scale, w, vout, out ? part : nullptr);
   CU_LAUNCH();
   if (out) {
     launch_pdl(c, k_reduce_parts, 1, 32, 0, grid, 1, part, out);
