@@ -252,8 +252,12 @@ mgr_status_t mgr_bsr3_outer_grad(const mgr_bsr3_t* A, const double* lambda, cons
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture.
  * All calls share the one array and it keeps the last call's contents (each call clears the counters
- * it needs): calls that overlap on the GPU -- on other streams or from other threads -- race.
- * Asynchronous on cuda_stream. */
+ * and the error word it needs): calls that overlap on the GPU -- on other streams or from other
+ * threads -- race.
+ * The input is checked on the device before anything is written through it: row pointers that do
+ * not run from 0 to nnzb without decreasing, or a column outside [0, nb), return MGR_ERR_INVALID_ARG
+ * (rowptr_t may then hold partial counts; colind_t and values_t are not written).
+ * Enqueued on cuda_stream; the call then synchronises that stream once to read the check. */
 mgr_status_t mgr_bsr3_transpose_noalloc(const mgr_bsr3_t* A, int64_t* rowptr_t, int32_t* colind_t, double* values_t,
                                         void* cuda_stream);
 

@@ -16,9 +16,11 @@ namespace {
 constexpr int64_t NA_MAX_NB = 1 << 16;    // block rows
 constexpr int64_t NA_MAX_NNZB = 1 << 19;  // stored blocks
 
-// counters [NA_MAX_NB + 1] followed by source indices [NA_MAX_NNZB]; every GPU that loads the
-// library holds this array (about 4.7 MB) until the process exits
-static __device__ __align__(256) unsigned long long g_transpose_scratch[NA_MAX_NB + 1 + NA_MAX_NNZB];
+// counters [NA_MAX_NB + 1], one error word, then source indices [NA_MAX_NNZB]; every GPU that
+// loads the library holds this array (about 4.7 MB) until the process exits
+constexpr int64_t NA_FLAG = NA_MAX_NB + 1;
+constexpr int64_t NA_SRC = NA_MAX_NB + 2;
+static __device__ __align__(256) unsigned long long g_transpose_scratch[NA_SRC + NA_MAX_NNZB];
 
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_scratch_mutex;
@@ -41,9 +43,27 @@ void* scratch_address() {
 __global__ void k_na_zero(int64_t n, unsigned long long* a) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) a[i] = 0;
 }
-__global__ void k_na_count(int64_t nnzb, const int32_t* ci, unsigned long long* cnt) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnzb; k += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&cnt[ci[k]], 1ull);
+// The input is checked before anything is written through it: the row pointers must run from 0 to
+// nnzb without decreasing, and every column must lie in [0, nb).  A violation sets the error word
+// and the later kernels write nothing, so a malformed matrix can never move a write outside the
+// fixed array or the caller's output buffers.
+__global__ void k_na_check_rows(int64_t nb, int64_t nnzb, const int64_t* rp, unsigned long long* flag) {
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nb; I += (int64_t)gridDim.x * blockDim.x) {
+    int64_t a = rp[I], b = rp[I + 1];
+    bool bad = a < 0 || b < a || b > nnzb || (I == 0 && a != 0) || (I == nb - 1 && b != nnzb);
+    if (bad) atomicOr(flag, 1ull);
+  }
+}
+__global__ void k_na_count(int64_t nb, int64_t nnzb, const int32_t* ci, unsigned long long* cnt,
+                           unsigned long long* flag) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnzb; k += (int64_t)gridDim.x * blockDim.x) {
+    int32_t J = ci[k];
+    if (J < 0 || J >= nb) {
+      atomicOr(flag, 2ull);
+      continue;
+    }
+    atomicAdd(&cnt[J], 1ull);
+  }
 }
 // single-block exclusive scan of n <= NA_MAX_NB counts into rpt[0..n]
 __global__ void __launch_bounds__(1024) k_na_scan(int64_t n, const unsigned long long* cnt, int64_t* rpt) {
@@ -77,9 +97,9 @@ __global__ void __launch_bounds__(1024) k_na_scan(int64_t n, const unsigned long
   if (threadIdx.x == blockDim.x - 1) rpt[n] = wsum[31];
 }
 __global__ void k_na_scatter(int64_t nb, const int64_t* rp, const int32_t* ci, const int64_t* rpt,
-                             unsigned long long* slot, int32_t* cit, int64_t* src) {
+                             unsigned long long* slot, int32_t* cit, int64_t* src, const unsigned long long* flag) {
   int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (I >= nb) return;
+  if (I >= nb || *flag) return;
   for (int64_t k = rp[I]; k < rp[I + 1]; ++k) {
     int32_t J = ci[k];
     int64_t d = rpt[J] + (int64_t)atomicAdd(&slot[J], 1ull);
@@ -89,9 +109,10 @@ __global__ void k_na_scatter(int64_t nb, const int64_t* rp, const int32_t* ci, c
 }
 // order each transposed block row by column (insertion sort of short rows) and copy the blocks
 // transposed
-__global__ void k_na_sort_fill(int64_t nb, const int64_t* rpt, int32_t* cit, int64_t* src, const double* v, double* vt) {
+__global__ void k_na_sort_fill(int64_t nb, const int64_t* rpt, int32_t* cit, int64_t* src, const double* v, double* vt,
+                               const unsigned long long* flag) {
   int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (J >= nb) return;
+  if (J >= nb || *flag) return;
   int64_t b = rpt[J], e = rpt[J + 1];
   for (int64_t a = b + 1; a < e; ++a) {
     int32_t key = cit[a];
@@ -118,7 +139,8 @@ using namespace mgr;
 
 extern "C" mgr_status_t mgr_bsr3_transpose_noalloc(const mgr_bsr3_t* A, int64_t* rowptr_t, int32_t* colind_t,
                                                    double* values_t, void* cuda_stream) {
-  if (!A || !rowptr_t || !colind_t || !values_t || A->nb <= 0 || !A->rowptr || !A->colind || !A->values)
+  if (!A || !rowptr_t || !colind_t || !values_t || A->nb <= 0 || A->nnzb < 0 || !A->rowptr || !A->colind ||
+      !A->values)
     return MGR_ERR_INVALID_ARG;
   if (A->nb > NA_MAX_NB || A->nnzb > NA_MAX_NNZB) {
     fprintf(stderr, "[mgr] mgr_bsr3_transpose_noalloc: nb %lld > %lld or nnzb %lld > %lld\n", (long long)A->nb,
@@ -128,20 +150,37 @@ extern "C" mgr_status_t mgr_bsr3_transpose_noalloc(const mgr_bsr3_t* A, int64_t*
   try {
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     unsigned long long* cnt = static_cast<unsigned long long*>(scratch_address());
-    int64_t* src = reinterpret_cast<int64_t*>(cnt + NA_MAX_NB + 1);
+    unsigned long long* flag = cnt + NA_FLAG;
+    int64_t* src = reinterpret_cast<int64_t*>(cnt + NA_SRC);
     int64_t nb = A->nb, nnzb = A->nnzb;
     k_na_zero<<<grid_for(nb + 1, 256, 1024), 256, 0, s>>>(nb + 1, cnt);
     CU_LAUNCH();
-    k_na_count<<<grid_for(nnzb, 256, 4096), 256, 0, s>>>(nnzb, A->colind, cnt);
+    k_na_zero<<<1, 32, 0, s>>>(1, flag);
     CU_LAUNCH();
+    k_na_check_rows<<<grid_for(nb, 256, 1024), 256, 0, s>>>(nb, nnzb, A->rowptr, flag);
+    CU_LAUNCH();
+    if (nnzb > 0) {
+      k_na_count<<<grid_for(nnzb, 256, 4096), 256, 0, s>>>(nb, nnzb, A->colind, cnt, flag);
+      CU_LAUNCH();
+    }
     k_na_scan<<<1, 1024, 0, s>>>(nb, cnt, rowptr_t);
     CU_LAUNCH();
     k_na_zero<<<grid_for(nb + 1, 256, 1024), 256, 0, s>>>(nb + 1, cnt);
     CU_LAUNCH();
-    k_na_scatter<<<grid_for(nb, 256), 256, 0, s>>>(nb, A->rowptr, A->colind, rowptr_t, cnt, colind_t, src);
+    k_na_scatter<<<grid_for(nb, 256), 256, 0, s>>>(nb, A->rowptr, A->colind, rowptr_t, cnt, colind_t, src, flag);
     CU_LAUNCH();
-    k_na_sort_fill<<<grid_for(nb, 256), 256, 0, s>>>(nb, rowptr_t, colind_t, src, A->values, values_t);
+    k_na_sort_fill<<<grid_for(nb, 256), 256, 0, s>>>(nb, rowptr_t, colind_t, src, A->values, values_t, flag);
     CU_LAUNCH();
+    // read the error word back (a device-to-host copy into a host variable; no allocation)
+    unsigned long long h_flag = 0;
+    CU(cudaMemcpyAsync(&h_flag, flag, sizeof(h_flag), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (h_flag) {
+      fprintf(stderr, "[mgr] mgr_bsr3_transpose_noalloc: malformed input (%s%s)\n",
+              (h_flag & 1ull) ? "row pointers not 0..nnzb non-decreasing" : "",
+              (h_flag & 2ull) ? ((h_flag & 1ull) ? ", column outside [0, nb)" : "column outside [0, nb)") : "");
+      return MGR_ERR_INVALID_ARG;
+    }
     return MGR_OK;
   } catch (const Error& e) {
     fprintf(stderr, "[mgr] %s\n", e.what());
