@@ -300,3 +300,25 @@ def extpi(rowptr, col, val, cf, theta=0.25, pmax=0):
     prp = np.empty(n + 1, np.int64); pci = np.empty(nnz.value, np.int32); pv = np.empty(nnz.value)
     lib.oracle_extpi_csr(*args, prp.ctypes.data, pci.ctypes.data, pv.ctypes.data)
     return sp.csr_matrix((pv, pci, prp), shape=(n, int((cf == 1).sum())))
+
+
+def pmis(rowptr, col, val, theta=0.25, seed=3, level=0):
+    """Strength graph (scipy CSR pattern, n x n) and PMIS splitting (1 = C, -1 = F) of a scalar matrix,
+    with the random numbers of AMG level `level` under `seed`."""
+    import scipy.sparse as sp
+    lib = _load()
+    lib.oracle_pmis_csr.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_double, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.c_void_p]
+    rp = np.ascontiguousarray(rowptr, np.int64); ci = np.ascontiguousarray(col, np.int32)
+    v = np.ascontiguousarray(val, np.float64)
+    n = rp.shape[0] - 1
+    nnz = ctypes.c_int64()
+    cf = np.zeros(n, np.int8)
+    lib.oracle_pmis_csr(n, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, theta, seed, level, None,
+                        ctypes.byref(nnz), None, None)
+    srp = np.empty(n + 1, np.int64); sci = np.empty(nnz.value, np.int32)
+    lib.oracle_pmis_csr(n, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, theta, seed, level, cf.ctypes.data,
+                        ctypes.byref(nnz), srp.ctypes.data, sci.ctypes.data)
+    S = sp.csr_matrix((np.ones(nnz.value), sci, srp), shape=(n, n))
+    return S, cf

@@ -1199,3 +1199,22 @@ int oracle_extpi_csr(int64_t n, const int64_t* rp, const int32_t* ci, const doub
   csr_free(&S); csr_free(&P);
   return O_OK;
 }
+
+/* Strength + PMIS on a caller-given scalar matrix (AMG level lev's random numbers), so the tests can
+ * check the splitting by brute force on small graphs.  cf receives 1 (C) / -1 (F); with srp != NULL
+ * the strength graph is returned too (two calls: first srp == NULL for its size). */
+int oracle_pmis_csr(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, double theta, uint64_t seed,
+                    int lev, int8_t* cf, int64_t* snnz_out, int64_t* srp, int32_t* sci) {
+  csr_t A = {n, n, rp[n], (int64_t*)rp, (int32_t*)ci, (double*)v};
+  csr_t S;
+  memset(&S, 0, sizeof S);
+  strength(&A, theta, &S);
+  *snnz_out = S.nnz;
+  if (cf) pmis(&S, seed, lev, cf);
+  if (srp) {
+    memcpy(srp, S.rp, sizeof(int64_t) * (size_t)(n + 1));
+    memcpy(sci, S.ci, sizeof(int32_t) * (size_t)S.nnz);
+  }
+  csr_free(&S);
+  return O_OK;
+}

@@ -406,3 +406,266 @@ def test_amg_frelaxation_exact_limit_is_two_level_formula(cfg, rtype):
     z[F] = eF + Wp @ ec
     zo = o.apply(r)
     assert np.linalg.norm(zo - z) <= 1e-10 * np.linalg.norm(z)
+
+
+# ---- Pins of the AMG components the paper leaves to BoomerAMG: interpolation truncation, PMIS on
+# ---- non-symmetric strength graphs, and the relaxation scalings (section 4 F-relaxation, section 6
+# ---- AMG coarse solve).  The expected values below are worked out by hand from the published
+# ---- definitions (extended+i: De Sterck, Falgout, Nolting & Yang 2008; PMIS: De Sterck, Yang &
+# ---- Heys 2006; l1-Jacobi: Baker, Falgout, Kolev & Yang 2011).
+
+def _csr(n, entries):
+    rows, cols, vals = zip(*entries)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    A.sort_indices()
+    return A.indptr.astype(np.int64), A.indices.astype(np.int32), A.data.astype(np.float64)
+
+
+# Two F points (0, 1) and four C points (2..5).  Row 0 is strongly connected to F point 1 and to C
+# points 2 and 3, and weakly (positive entry) to C point 4, which enters Chat_0 at distance two
+# through point 1; C point 5 enters the same way with no direct coupling.  theta = 0.25.
+EXTPI_ROWS = [(0, 0, 4.0), (0, 1, -2.0), (0, 2, -1.0), (0, 3, -1.5), (0, 4, 1.5),
+              (1, 0, -1.0), (1, 1, 5.0), (1, 4, -2.0), (1, 5, -1.0)] + [(i, i, 1.0) for i in range(2, 6)]
+EXTPI_CF = np.array([-1, -1, 1, 1, 1, 1], np.int8)
+# Hand computation, row 0: S_0 = {1, 2, 3} (threshold 0.25 * 2 = 0.5; the +1.5 entry is weak),
+# F_0^s = {1}, Chat_0 = {2, 3} + C_1^s = {2, 3, 4, 5}.  den_1 = abar_10 + abar_14 + abar_15 =
+# -1 - 2 - 1 = -4 (the negative entries of row 1 over Chat_0 + {0}), q_1 = a_01 / den_1 = 1/2.
+# Diagonal: a_00 + q_1 abar_10 = 4 - 1/2 = 7/2 (the weak neighbour 4 lies in Chat_0: not lumped).
+# Numerators a_0j + q_1 abar_1j: j = 2: -1; j = 3: -3/2; j = 4: 3/2 - 1 = 1/2; j = 5: -1/2.
+# Weights -(num / (7/2)): 2/7, 3/7, -1/7, 1/7 (row sum 5/7).
+# Row 1: S_1 = {0, 4, 5}, Chat_1 = {4, 5} + C_0^s = {2, 3, 4, 5}; den_0 over Chat_1 + {1} keeps the
+# negative entries of row 0: -2 - 1 - 3/2 = -9/2 (the +3/2 at column 4 has the diagonal's sign),
+# q_0 = -1 / (-9/2) = 2/9; diagonal 5 + (2/9)(-2) = 41/9; numerators: j = 2: (2/9)(-1) = -2/9;
+# j = 3: (2/9)(-3/2) = -1/3; j = 4: -2; j = 5: -1.  Weights 2/41, 3/41, 18/41, 9/41 (sum 32/41).
+EXTPI_FULL = {0: [2 / 7, 3 / 7, -1 / 7, 1 / 7], 1: [2 / 41, 3 / 41, 18 / 41, 9 / 41]}
+# Truncation to pmax entries keeps the largest |w| (equal |w|: the smaller column) and scales the
+# kept ones by (sum of all w) / (sum of kept w), so the row sum is unchanged.
+#   row 0, pmax 2: keeps 3/7, 2/7; factor (5/7)/(5/7) = 1.
+#   row 0, pmax 3: keeps 3/7, 2/7 and, of the tie |-1/7| = |1/7|, column 2 (w = -1/7); kept sum
+#     4/7, factor 5/4: 5/14, 15/28, -5/28.
+#   row 1, pmax 2: keeps 18/41, 9/41; factor (32/41)/(27/41) = 32/27: 64/123, 32/123.
+#   row 1, pmax 3: keeps 18/41, 9/41, 3/41; factor 32/30: 16/205, 96/205, 48/205.
+EXTPI_TRUNC = {2: {0: [2 / 7, 3 / 7, 0, 0], 1: [0, 0, 64 / 123, 32 / 123]},
+               3: {0: [5 / 14, 15 / 28, -5 / 28, 0], 1: [0, 16 / 205, 96 / 205, 48 / 205]}}
+
+
+def test_extpi_hand_computed_distance_two_row():
+    """Extended+i weights of two F rows with a distance-two C point, a weak positive coupling to a
+    point of Chat_i and a strong F-F coupling, against the hand computation above."""
+    rp, ci, v = _csr(6, EXTPI_ROWS)
+    P = oracle.extpi(rp, ci, v, EXTPI_CF, theta=0.25).toarray()
+    for i, w in EXTPI_FULL.items():
+        assert np.abs(P[i] - np.array(w)).max() <= 1e-15, (i, P[i], w)
+    assert np.array_equal(P[2:], np.eye(4))  # C points inject
+
+
+@pytest.mark.parametrize("pmax", [2, 3])
+def test_extpi_truncation_hand_computed(pmax):
+    """Interpolation truncation (amg_pmax): which entries survive (largest |w|, ties to the smaller
+    column), and the rescaling that keeps the row sum, against the hand computation above."""
+    rp, ci, v = _csr(6, EXTPI_ROWS)
+    P = oracle.extpi(rp, ci, v, EXTPI_CF, theta=0.25, pmax=pmax)
+    D = P.toarray()
+    for i, w in EXTPI_TRUNC[pmax].items():
+        assert np.abs(D[i] - np.array(w)).max() <= 1e-15, (i, D[i], w)
+        assert P.indptr[i + 1] - P.indptr[i] == pmax
+        assert abs(D[i].sum() - sum(EXTPI_FULL[i])) <= 1e-15
+    assert np.array_equal(D[2:], np.eye(4))
+
+
+def _random_graph_laplacian(nx, ny, seed):
+    """Periodic 5-point graph Laplacian with random positive conductances: a zero-row-sum M-matrix."""
+    rng = np.random.default_rng(seed)
+    n = nx * ny
+    ent = {}
+    for j in range(ny):
+        for i in range(nx):
+            a = j * nx + i
+            for b in (j * nx + (i + 1) % nx, ((j + 1) % ny) * nx + i):
+                g = float(rng.uniform(0.2, 2.0))
+                ent[(a, b)] = ent.get((a, b), 0.0) - g
+                ent[(b, a)] = ent.get((b, a), 0.0) - g
+                ent[(a, a)] = ent.get((a, a), 0.0) + g
+                ent[(b, b)] = ent.get((b, b), 0.0) + g
+    return _csr(n, [(r, c, x) for (r, c), x in ent.items()])
+
+
+@pytest.mark.parametrize("pmax", [1, 2, 3])
+def test_truncated_extpi_rows_sum_to_one_on_zero_row_sum_matrix(pmax):
+    """On a zero-row-sum M-matrix extended+i interpolates constants exactly (every row sums to 1);
+    truncation keeps that sum, keeps at most pmax entries, and leaves shorter rows unchanged."""
+    rp, ci, v = _random_graph_laplacian(10, 9, seed=pmax)
+    _, cf = oracle.pmis(rp, ci, v, theta=0.25, seed=11)
+    assert 0 < (cf == 1).sum() < len(cf)
+    full = oracle.extpi(rp, ci, v, cf, theta=0.25)
+    tr = oracle.extpi(rp, ci, v, cf, theta=0.25, pmax=pmax)
+    lf, lt = np.diff(full.indptr), np.diff(tr.indptr)
+    assert (lf > pmax).sum() > 10  # truncation is exercised
+    assert np.all(lt == np.minimum(lf, pmax))
+    s = np.asarray(tr.sum(axis=1)).ravel()
+    assert np.abs(s - 1.0).max() <= 1e-13
+    short = lf <= pmax
+    assert np.abs((full - tr).toarray()[short]).max() == 0.0
+    # the kept entries are the largest |w| of the full row
+    F = full.toarray()
+    T = tr.toarray()
+    for i in np.nonzero(~short)[0]:
+        kept = np.nonzero(T[i])[0]
+        dropped = np.setdiff1d(np.nonzero(F[i])[0], kept)
+        assert np.abs(F[i, kept]).min() >= np.abs(F[i, dropped]).max()
+
+
+def _directed(n, edges, weak=()):
+    """A scalar matrix whose strength graph (theta = 0.25) is exactly `edges` (i strongly depends
+    on j for (i, j) in edges): strong entries -1, weak entries -0.01, diagonal = row length + 1."""
+    ent = {(i, j): -1.0 for i, j in edges}
+    for i, j in weak:
+        ent.setdefault((i, j), -0.01)
+    for i in range(n):
+        ent[(i, i)] = 1.0 + sum(1 for (a, _b) in ent if a == i)
+    return _csr(n, [(r, c, x) for (r, c), x in ent.items()])
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_pmis_measure_counts_dependants(seed):
+    """PMIS's measure is lambda_i = |S^T_i|, the number of points that strongly depend on i.  Points
+    1..5 depend on 0 and 0 depends on 1: lambda = (5, 1, 0, 0, 0, 0) whatever the random part, so
+    2..5 (which influence nobody) start as F, 0 beats 1 and becomes C, and 1, depending on 0,
+    becomes F.  With the measure taken from S instead, every point has measure 1 and the random
+    part decides."""
+    rp, ci, v = _directed(6, [(0, 1)] + [(i, 0) for i in range(1, 6)])
+    S, cf = oracle.pmis(rp, ci, v, theta=0.25, seed=seed)
+    assert set(zip(*S.nonzero())) == {(0, 1)} | {(i, 0) for i in range(1, 6)}
+    assert cf.tolist() == [1, -1, -1, -1, -1, -1]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_pmis_f_rule_follows_dependence(seed):
+    """An undecided point becomes F when it strongly depends on a new C point, not when it
+    influences one.  0 depends on 1, and 1 (depended on by 0, 3, 4, 5: lambda 4) beats 0 (lambda 1,
+    from 2) and becomes C; 0 depends on it and becomes F.  Were the rule taken the other way round,
+    nothing would turn 0 into F (1 depends on nobody) and 0 would become C next to 1."""
+    rp, ci, v = _directed(6, [(0, 1), (2, 0), (3, 1), (4, 1), (5, 1)])
+    _, cf = oracle.pmis(rp, ci, v, theta=0.25, seed=seed)
+    assert cf.tolist() == [-1, 1, -1, -1, -1, -1]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_pmis_selection_looks_both_ways(seed):
+    """A point joins the independent set of a round only when it beats every undecided neighbour in
+    S + S^T, the points it depends on and the points that depend on it.  Here
+    lambda = (1, 1, 1, 0, 3, 2, 4), so the outcome does not depend on the random part: round 1
+    selects 6 (it beats 1, 2, 4); 1, 2, 4 depend on 6 and become F (3 influences nobody: F from the
+    start); round 2 selects 5 over 0; round 3 selects 0, whose only neighbour 5 is now C.  Were the
+    selection to look only at S_i, 0 (which depends on nobody) would be selected in round 1 and 5,
+    depending on it, would become F."""
+    edges = [(1, 5), (1, 6), (2, 5), (2, 6), (3, 1), (3, 2), (3, 4), (3, 6), (4, 6), (5, 0), (5, 4), (6, 4)]
+    rp, ci, v = _directed(7, edges)
+    _, cf = oracle.pmis(rp, ci, v, theta=0.25, seed=seed)
+    assert cf.tolist() == [1, -1, -1, -1, -1, 1, 1]
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_pmis_brute_force_on_random_nonsymmetric_graphs(seed):
+    """On random directed strength graphs of 12 points (S != S^T), checked point by point: every
+    point is decided; a C point is strongly depended on by someone; an F point either influences
+    nobody or strongly depends on a C point; and strong dependence among C points has no cycle.
+    (A C point i that depends on a C point j was selected in an earlier round than j: had j been
+    selected first, i would have become F in that round, and the two cannot be selected together,
+    being neighbours.  So, unlike on symmetric graphs, C points need not be independent in S + S^T,
+    but their dependences order them.)"""
+    rng = np.random.default_rng(1000 + seed)
+    n = 12
+    edges = {(i, j) for i in range(n) for j in range(n) if i != j and rng.random() < 0.18}
+    has_strong = {i for i, _ in edges}
+    # weak entries only in rows that also hold a strong one (a row's threshold is relative to its
+    # own largest entry)
+    weak = {(i, j) for i in range(n) for j in range(n) if i != j and i in has_strong and rng.random() < 0.1}
+    rp, ci, v = _directed(n, sorted(edges), sorted(weak))
+    S, cf = oracle.pmis(rp, ci, v, theta=0.25, seed=seed)
+    got = set(zip(*(x.tolist() for x in S.nonzero())))
+    assert got == edges
+    assert set(np.unique(cf).tolist()) <= {-1, 1}
+    dep = {i: {j for (a, j) in edges if a == i} for i in range(n)}      # S_i: what i depends on
+    infl = {i: {a for (a, j) in edges if j == i} for i in range(n)}     # S^T_i: who depends on i
+    C = {i for i in range(n) if cf[i] == 1}
+    for i in range(n):
+        if cf[i] == 1:
+            assert infl[i], i
+        else:
+            assert not infl[i] or dep[i] & C, (i, C)
+    # no cycle of strong dependence among C points (repeatedly remove C points that depend on no
+    # remaining C point)
+    left = set(C)
+    while left:
+        sinks = {i for i in left if not dep[i] & left}
+        assert sinks, ("dependence cycle among C points", left)
+        left -= sinks
+    if any(infl[i] for i in range(n)):
+        assert C
+
+
+# Two gas-present cells, markers (P, S, rho) = (2, 1, 0): the first reduction's F points are the two
+# rho dofs 2 and 5.  Their rows couple to each other (an F-F entry) and to P and S dofs (off-F
+# entries, which do not belong to A_ff).  Diagonal of dof 2 is negative to exercise the sign.
+MGR_BLOCKS = np.array([
+    # block (0, 0): rows dof 0..2, columns dof 0..2
+    [[6.0, 0.5, 0.25], [0.5, 5.0, 0.4], [0.7, -0.9, -3.0]],
+    # block (0, 1): rows dof 0..2, columns dof 3..5
+    [[-1.0, 0.1, 0.0], [0.2, -0.5, 0.0], [0.3, 0.0, 0.5]],
+    # block (1, 0)
+    [[-1.2, 0.0, 0.0], [0.0, -0.4, 0.0], [0.0, 0.6, -1.0]],
+    # block (1, 1)
+    [[7.0, 0.3, -0.2], [0.1, 4.0, 0.0], [0.2, -1.1, 4.0]],
+])
+MGR_RP = np.array([0, 2, 4], np.int64)
+MGR_CI = np.array([0, 1, 0, 1], np.int32)
+MGR_MARKER = np.array([2, 1, 0, 2, 1, 0], np.int8)
+
+
+@pytest.mark.parametrize("ftype,omega,expect", [
+    # l1-Jacobi over A_ff's row: dof 2: a_22 = -3, the F-F entry a_25 = 0.5 -> 1/(-3 - 0.5) = -2/7;
+    # dof 5: a_55 = 4, a_52 = -1 -> 1/(4 + 1) = 1/5.  The off-F entries (0.7, -0.9, 0.3 and 0.6,
+    # -1.1) are not part of A_ff and do not enter.
+    (1, 1.0, [-2 / 7, 1 / 5]),
+    # omega-Jacobi: omega / a_ii
+    (0, 0.7, [0.7 / -3.0, 0.7 / 4.0]),
+])
+def test_frelaxation_scaling_hand_computed(ftype, omega, expect):
+    """F-relaxation scaling of the Algorithm's step (2) on the first reduction: l1-Jacobi sums the
+    off-diagonal magnitudes of A_ff's row only, with the diagonal's sign; omega-Jacobi is
+    omega / a_ii."""
+    o = oracle.OracleMGR(MGR_RP, MGR_CI, MGR_BLOCKS.reshape(-1), MGR_MARKER, frelax_type=[ftype, 1, 1],
+                         frelax_omega=[omega, 1.0, 1.0], amg_max_coarse=4)
+    assert o.vec(oracle.VEC_F, 0).tolist() == [2, 5]
+    minv = o.vec(oracle.VEC_MINV, 0)
+    assert np.abs(minv - np.array(expect)).max() <= 1e-16, (minv, expect)
+
+
+@pytest.mark.parametrize("smoother,omega,expect", [
+    # l1-Jacobi over the whole row of the AMG level matrix, with the diagonal's sign:
+    # row 3: 2.5 + (1 + 0.5 + 0.25) = 4.25; row 4: -2 - (0.5 + 1) = -3.5
+    (1, 1.0, {3: 1 / 4.25, 4: 1 / -3.5}),
+    # omega-Jacobi: omega / a_ii
+    (0, 0.8, {3: 0.8 / 2.5, 4: 0.8 / -2.0}),
+])
+def test_amg_smoother_scaling_hand_computed(smoother, omega, expect):
+    """AMG smoother scaling (section 6's coarse solve): l1-Jacobi 1 / (a_ii + sign(a_ii) sum_{j != i}
+    |a_ij|) over the full row, omega-Jacobi omega / a_ii."""
+    n = 10
+    ent = []
+    for i in range(n):
+        ent.append((i, i, 3.0 + 0.1 * i))
+        if i > 0:
+            ent.append((i, i - 1, -1.0))
+        if i < n - 1:
+            ent.append((i, i + 1, -0.5))
+    ent = [e for e in ent if e[0] not in (3, 4)]
+    ent += [(3, 3, 2.5), (3, 2, -1.0), (3, 4, -0.5), (3, 7, 0.25),
+            (4, 4, -2.0), (4, 3, 0.5), (4, 5, 1.0)]
+    rp, ci, v = _csr(n, ent)
+    amg = oracle.OracleAMG(rp, ci, v, amg_max_coarse=2, amg_max_levels=2, amg_smoother=smoother,
+                           amg_omega=omega)
+    dinv = amg.vec(oracle.VEC_AMG_DINV, 0)
+    for i, x in expect.items():
+        assert abs(dinv[i] - x) <= 1e-16, (i, dinv[i], x)
