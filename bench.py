@@ -60,11 +60,14 @@ KERNEL_NAMES = SOLVE_KERNELS + SETUP_KERNELS
 # k_mdot (multi-dot, 16 vectors of 1,536,000): 200.42 MB of DRAM traffic for 196.61 MB algorithmic;
 # k_bsr_sell<double> (FP64 SpMV): 295.11 MB for 298.14 MB.
 TRAFFIC = {"mdot": 200.42496e6 / 196.608e6, "bsr3_spmv_f64": 295.114240e6 / 298137608.0}
-# FP64 FMAs per algorithmic byte of the Krylov kernels bound by the FP64 rate: the multi-dot does one
-# FMA per 8-byte element it reads (V_k . w and w . w); the 3x3-block SpMV 9 per 76-byte block (the
-# row pointers and vectors, a few % of its bytes, are left out: a slight overestimate)
-FP64_FMA_PER_BYTE = {"mdot": 1.0 / 8.0, "bsr3_spmv_f64": 9.0 / 76.0}
-FP64_FMA_PEAK = 625.0  # G FP64 FMA/s, GB300 nominal (1.25 TFLOP/s dense FP64)
+# Krylov kernels bound by GB300's FP64 FMA rate: their FMAs per launch.  The multi-dot does one FMA
+# per 8-byte element it reads (V_k . w and w . w), i.e. its algorithmic bytes / 8; the 3x3-block SpMV
+# 9 per stored block.
+FP64_BOUND = ("bsr3_spmv_f64", "mdot")
+# FGMRES(30) iterations of the oracle (FP64) on the full-size instances, measured once (the GPU's
+# FP64-hierarchy count agrees within one, checked by the full-size parity test): the CPU baseline's
+# sample solve is scaled per iteration to this count.
+FULL_SIZE_ITERATIONS = {"ncp3d_128_layered": 41}
 
 
 def _args():
@@ -76,6 +79,7 @@ def _args():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--grid", type=int, default=0, help="scaled instance: n^3 cells of the workload recipe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-full", action="store_true", help="time the oracle on the full-size instance (minutes)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--solver", default="", help="JSON dict of solver options overriding the defaults")
@@ -140,6 +144,22 @@ def run_oracle_sample(cfg, n_sample):
     t2 = time.perf_counter()
     return dict(cells=p.nb, setup_s=t1 - t0, solve_s=t2 - t1, iterations=info["iterations"],
                 converged=info["converged"])
+
+
+def oracle_estimate(cfg, workload, n_sample, full_iterations=None):
+    """The oracle's time for the full-size workload from a bounded n_sample^3 instance of its recipe:
+    setup scaled by cell count, solve scaled by cell count and per iteration to the full-size
+    iteration count (a sample converges in fewer iterations than the full grid).  Returns
+    (milliseconds, description)."""
+    r = run_oracle_sample(cfg, n_sample)
+    cells = cfg.nx * cfg.ny * cfg.nz
+    f = cells / r["cells"]
+    it = full_iterations or FULL_SIZE_ITERATIONS.get(workload) or r["iterations"]
+    ms = (r["setup_s"] * f + r["solve_s"] / r["iterations"] * it * f) * 1e3
+    desc = (f"{n_sample}^3 instance of the {workload} recipe, FP64 oracle on 1 core: setup {r['setup_s']:.2f} s "
+            f"x{f:.1f} (cells) + solve {r['solve_s']:.2f} s for {r['iterations']} iterations, scaled per "
+            f"iteration to the full grid's {it} and x{f:.1f} (cells)")
+    return ms, desc, r
 
 
 class ClockSampler:
@@ -264,20 +284,16 @@ def main():
     if a.impl == "reference":
         if rank != 0:
             return
-        n_s = 32
-        cells_full = cfg.nx * cfg.ny * cfg.nz
+        n_s = 48
         for _ in range(a.warmup):
             run_oracle_sample(cfg, n_s)
-        times = []
+        vals = []
         for _ in range(a.steps):
-            r = run_oracle_sample(cfg, n_s)
-            times.append((r["setup_s"] + r["solve_s"]) * 1e3)
-        scale = cells_full / r["cells"]
-        v = statistics.mean(times) * scale
-        sample = (f"{n_s}^3 instance of the {a.workload} recipe, FP64 oracle setup+solve to 1e-8, "
-                  f"time scaled by cell count x{scale:.1f}")
+            v, sample, r = oracle_estimate(cfg, a.workload, n_s)
+            vals.append(v)
+        v = statistics.mean(vals)
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": a.gpus,
-                          "steps": a.steps, "warmup": a.warmup, "ms_per_step": statistics.mean(times),
+                          "steps": a.steps, "warmup": a.warmup, "ms_per_step": v,
                           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                           "data": "synthetic", "config": config,
                           "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
@@ -329,7 +345,7 @@ def main():
             # (recording every kernel there would add event overhead to the measured steps)
             m.profile(True)
             step(m)
-            kt_full = {k: m.kernel_time(k) + (m.kernel_bytes(k),) for k in KERNEL_NAMES}
+            kt_full = {k: m.kernel_time(k) + (m.kernel_bytes(k), m.kernel_bytes_stored(k)) for k in KERNEL_NAMES}
             m.profile(False)
             solve = [k for k in SOLVE_KERNELS if kt_full[k][0] and kt_full[k][2]]
             dom = max(solve, key=lambda k: kt_full[k][1]) if solve else None
@@ -371,7 +387,7 @@ def main():
         if dom and flush_l2:
             kt_dom = (dom, kt_full[dom])
         else:
-            kt_dom = (dom, m.kernel_time(dom) + (m.kernel_bytes(dom),)) if dom else None
+            kt_dom = (dom, m.kernel_time(dom) + (m.kernel_bytes(dom), m.kernel_bytes_stored(dom))) if dom else None
         mem = m.memory_bytes()
         L, na = m.levels()
         hier = {"mgr": [list(_shape(m, mg.MAT_LEVEL, l)) for l in range(L + 1)],
@@ -379,6 +395,20 @@ def main():
         m.close()
         return ms, infos, setup_ms, launches, clocks, (kt_full, kt_dom), mem, hier
 
+    # GB300's FP64 FMA rate, measured (the roofline of the FP64-bound Krylov kernels), with the SM
+    # clock sampled while the probe runs
+    fp64_probe = None
+    if rank == 0:
+        sampler = ClockSampler(local)
+        mg.probe_fp64_fma(4096, 2)
+        g, ms_l = mg.probe_fp64_fma(4096, 40)
+        ck = sampler.stop()
+        fp64_probe = {"gfma_per_s": g, "ms_per_launch": ms_l, "launches": 40,
+                      "kernel": "8 independent FMA chains of 4096 per thread, full-occupancy grid",
+                      "clocks": ck}
+        if ck and ck.get("sm_mhz"):
+            fp64_probe["fma_per_clock_per_sm"] = g * 1e9 / (ck["sm_mhz"] * 1e6) / torch.cuda.get_device_properties(
+                local).multi_processor_count
     ms, infos, setup_ms, launches, clocks, (kt, kt_dom), mem, hier = timed("mixed", a.steps, profile=True)
     xr = x.cpu().numpy()
     relres = float(np.linalg.norm(b_h - p.to_scipy() @ xr) / np.linalg.norm(b_h))
@@ -390,19 +420,32 @@ def main():
            "solves_per_s_all_gpus": a.gpus * 1000.0 / ms, "gpu_launches": int(launches),
            "device_memory_gb": mem / 1e9, "hierarchy_rows_nnz": hier}
     # per-kernel achieved algorithmic bandwidth of the solve kernels, from the untimed profiled step
-    # (bytes declared by the library for each launch, divided by the CUDA-event time of the launches)
+    # (bytes declared by the library for each launch, divided by the CUDA-event time of the launches);
+    # frac counts a 4-byte column index per sparse entry, frac_stored the column form the sliced
+    # layouts hold (one-byte codes or 16-bit offsets where they apply)
     peak, peak_kind = _peaks()
     rk = {}
     for k in SOLVE_KERNELS:
-        n_k, t_k, by_k = kt.get(k, (0, 0.0, 0.0))
+        n_k, t_k, by_k, bs_k = kt.get(k, (0, 0.0, 0.0, 0.0))
         if n_k and by_k and t_k > 0:
             gbs = by_k / (t_k * 1e-3) / 1e9
             rk[k] = {"launches": n_k, "ms": t_k, "achieved_gbs": gbs, "frac": gbs / peak,
-                     "bytes_per_launch": by_k / n_k}
+                     "frac_stored": bs_k / (t_k * 1e-3) / 1e9 / peak, "bytes_per_launch": by_k / n_k}
     out["kernel_bandwidth"] = rk
+    # the whole preconditioner application (every apply kernel of the profiled step together)
+    app = [k for k in rk if k not in ("bsr3_spmv_f64", "mdot", "mupdate")]
+    if app:
+        t_a = sum(kt[k][1] for k in app)
+        by_a, bs_a = sum(kt[k][2] for k in app), sum(kt[k][3] for k in app)
+        out["roofline_apply"] = {"kernels": "mgr_apply (global relaxation, level residuals, F-relaxation, restriction, "
+                                            "interpolation, AMG V-cycle)", "bound": "hbm",
+                                 "ms_per_step": t_a, "applies": kt["global_relax"][0],
+                                 "achieved": by_a / (t_a * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                                 "frac": by_a / (t_a * 1e-3) / 1e9 / peak,
+                                 "frac_stored": bs_a / (t_a * 1e-3) / 1e9 / peak, "peak_source": peak_kind}
     sb = {}
     for k in SETUP_KERNELS:
-        n_k, t_k, by_k = kt.get(k, (0, 0.0, 0.0))
+        n_k, t_k, by_k, _ = kt.get(k, (0, 0.0, 0.0, 0.0))
         if n_k and by_k and t_k > 0:
             sb[k] = {"calls": n_k, "ms": t_k, "achieved_gbs": by_k / (t_k * 1e-3) / 1e9}
     out["setup_bandwidth"] = sb
@@ -416,24 +459,30 @@ def main():
                                  "bound": "issue", "ms": t_s, "achieved_gbs": by_s / (t_s * 1e-3) / 1e9,
                                  "frac_of_hbm": by_s / (t_s * 1e-3) / 1e9 / peak, "calls": sum(sb[k]["calls"] for k in rap)}
     if kt_dom:
-        k, (n_k, t_k, by_k) = kt_dom
+        k, (n_k, t_k, by_k, _) = kt_dom
         per_launch = by_k / n_k
-        achieved = per_launch / (t_k / n_k * 1e-3) / 1e9
+        us = t_k / n_k * 1e3
+        achieved = per_launch / (us * 1e-6) / 1e9
         tr = TRAFFIC.get(k)
-        if k in FP64_FMA_PER_BYTE:
-            # bound by GB300's FP64 rate (ncu: FP64 pipe ~87-91 % active), reported against it
-            fma = FP64_FMA_PER_BYTE[k] * per_launch / (t_k / n_k * 1e-3) / 1e9
-            out["roofline"] = {"kernel": k, "bound": "alu", "achieved": fma, "peak": FP64_FMA_PEAK, "unit": "GFMA/s",
-                               "frac": fma / FP64_FMA_PEAK,
-                               "peak_source": "nominal FP64 rate: 1.25 TFLOP/s dense = 625 G FP64 FMA/s",
-                               "traffic": tr * per_launch if tr else None, "bytes_per_launch": per_launch,
-                               "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak,
-                               "avg_launch_us": t_k / n_k * 1e3, "launches": n_k}
+        if k in FP64_BOUND and fp64_probe:
+            # bound by GB300's FP64 FMA rate (ncu: FP64 pipe ~87-91 % active), reported against the
+            # rate measured by the FMA-chain probe in this run, with the HBM fraction beside it
+            fma_launch = 9.0 * p.colind.shape[0] if k == "bsr3_spmv_f64" else per_launch / 8.0
+            fma = fma_launch / (us * 1e-6) / 1e9
+            out["roofline"] = {"kernel": k, "bound": "alu", "achieved": fma, "peak": fp64_probe["gfma_per_s"],
+                               "unit": "GFMA/s", "frac": fma / fp64_probe["gfma_per_s"],
+                               "peak_source": "measured in this run: FP64 FMA-chain probe (mgr_probe_fp64_fma)",
+                               "fma_per_launch": fma_launch, "traffic": tr * per_launch if tr else None,
+                               "bytes_per_launch": per_launch, "hbm_achieved_gbs": achieved,
+                               "hbm_frac": achieved / peak, "hbm_peak_source": peak_kind,
+                               "avg_launch_us": us, "launches": n_k}
         else:
             out["roofline"] = {"kernel": k, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                                "frac": achieved / peak, "peak_source": peak_kind,
                                "traffic": tr * per_launch if tr else None, "bytes_per_launch": per_launch,
-                               "avg_launch_us": t_k / n_k * 1e3, "launches": n_k}
+                               "avg_launch_us": us, "launches": n_k}
+    if fp64_probe:
+        out["fp64_probe"] = fp64_probe
     out["kernel_ms_one_step"] = {k: v[1] for k, v in kt.items() if v[0]}
     if clocks:
         out["clocks"] = clocks
@@ -474,14 +523,15 @@ def main():
         out["e2e"] = {"value": _max(e0.elapsed_time(e1)) / a.steps, "unit": "ms",
                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        n_s = 40
-        r = run_oracle_sample(cfg, n_s)
-        scale = (cfg.nx * cfg.ny * cfg.nz) / r["cells"]
-        out["cpu_baseline"] = {"value": (r["setup_s"] + r["solve_s"]) * 1e3 * scale, "unit": "ms", "cores": 1,
-                               "kind": "oracle",
-                               "sample": f"{n_s}^3 instance of the {a.workload} recipe, FP64 oracle setup "
-                                         f"{r['setup_s']:.2f} s + solve {r['solve_s']:.2f} s "
-                                         f"({r['iterations']} it), scaled by cell count x{scale:.1f}"}
+        it_full = (out.get("fp64") or {}).get("iterations") or out["iterations"]
+        if a.cpu_full:
+            r = run_oracle_sample(cfg, max(cfg.nx, cfg.ny, cfg.nz))
+            v = (r["setup_s"] + r["solve_s"]) * 1e3
+            sample = (f"the full {a.workload} instance, FP64 oracle on 1 core: setup {r['setup_s']:.1f} s + solve "
+                      f"{r['solve_s']:.1f} s ({r['iterations']} iterations)")
+        else:
+            v, sample, r = oracle_estimate(cfg, a.workload, 64, it_full)
+        out["cpu_baseline"] = {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:

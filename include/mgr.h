@@ -217,9 +217,13 @@ mgr_status_t mgr_profile_select(mgr_handle_t h, const char* names);
 mgr_status_t mgr_kernel_time(mgr_handle_t h, const char* name, int64_t* launches, double* total_ms);
 /* Algorithmic bytes of the launches recorded for `name` since profiling was enabled (host out): for
  * the solve kernels, every input element read once and every output element written once (values,
- * indices, row pointers, vectors), padding and cache re-reads not counted; 0 for the setup scopes.
- * Divided by mgr_kernel_time's milliseconds it gives the achieved algorithmic bandwidth. */
+ * a 4-byte column index per sparse entry, 8-byte row pointers, vectors), whatever form the layout
+ * stores; padding and cache re-reads not counted; 0 for the setup scopes.  Divided by
+ * mgr_kernel_time's milliseconds it gives the achieved algorithmic bandwidth.
+ * mgr_kernel_bytes_stored: the same count with the column indices in the form the sliced layouts
+ * store them (one-byte offset codes, 16-bit offsets, or 4-byte indices). */
 mgr_status_t mgr_kernel_bytes(mgr_handle_t h, const char* name, double* bytes);
+mgr_status_t mgr_kernel_bytes_stored(mgr_handle_t h, const char* name, double* bytes);
 
 /* ---- stand-alone kernels ----------------------------------------------------------------------- */
 /* y = A x (sub == NULL) or y = sub - A x, FP64, on `cuda_stream`.  The hot sparse product of the
@@ -236,6 +240,16 @@ mgr_status_t mgr_bsr3_transpose(const mgr_bsr3_t* A, int64_t* rowptr_t, int32_t*
  * stored block k = (I, J) (dL/dA = -lambda x^T restricted to the pattern). */
 mgr_status_t mgr_bsr3_outer_grad(const mgr_bsr3_t* A, const double* lambda, const double* x, double* grad,
                                  void* cuda_stream);
+
+/* ---- measurement ---------------------------------------------------------------------------- */
+/* FP64 FMA rate of this GPU, the roofline of the FP64-bound Krylov kernels (the 3x3-block SpMV and
+ * the Gram-Schmidt multi-dot and update issue FP64 FMAs faster than HBM feeds them on GB300).  Runs
+ * one warm-up and `launches` timed launches of a kernel of eight independent FMA chains of
+ * `chain_len` (a positive multiple of 4) FMAs per thread over a full-occupancy grid on `cuda_stream`,
+ * timed with CUDA events; writes the FMAs per second / 1e9 and the milliseconds per launch (host
+ * outs; the latter may be NULL).  Allocates one double of scratch; synchronises the stream. */
+mgr_status_t mgr_probe_fp64_fma(int64_t chain_len, int launches, void* cuda_stream, double* gfma_per_s,
+                                double* ms_per_launch);
 
 /* ---- allocation-free variant ------------------------------------------------------------------
  * The paper has no counterpart to this entry point.

@@ -66,7 +66,7 @@ EXPORTS = ["mgr_status_string", "mgr_options_default", "mgr_create", "mgr_setup"
            "mgr_destroy", "mgr_get_levels", "mgr_matrix_shape", "mgr_copy_matrix", "mgr_vector_len",
            "mgr_copy_vector", "mgr_memory_bytes", "mgr_memory_peak_bytes", "mgr_get_stats", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
            "mgr_bsr3_outer_grad", "mgr_profile", "mgr_profile_select", "mgr_kernel_time",
-           "mgr_kernel_bytes"]
+           "mgr_kernel_bytes", "mgr_kernel_bytes_stored", "mgr_probe_fp64_fma"]
 
 
 def lib():
@@ -103,7 +103,9 @@ def lib():
         L.mgr_profile.argtypes = [vp, i32]
         L.mgr_kernel_time.argtypes = [vp, ctypes.c_char_p, P(i64), P(ctypes.c_double)]
         L.mgr_kernel_bytes.argtypes = [vp, ctypes.c_char_p, P(ctypes.c_double)]
+        L.mgr_kernel_bytes_stored.argtypes = [vp, ctypes.c_char_p, P(ctypes.c_double)]
         L.mgr_profile_select.argtypes = [vp, ctypes.c_char_p]
+        L.mgr_probe_fp64_fma.argtypes = [i64, i32, vp, P(ctypes.c_double), P(ctypes.c_double)]
         for name in EXPORTS:
             getattr(L, name).restype = ctypes.c_int if name not in ("mgr_status_string", "mgr_options_default") \
                 else getattr(L, name).restype
@@ -304,6 +306,12 @@ class MGR:
         _check(lib().mgr_kernel_bytes(self._h, name.encode(), ctypes.byref(b)), "mgr_kernel_bytes")
         return b.value
 
+    def kernel_bytes_stored(self, name: str) -> float:
+        """The same bytes with the column indices in the form the sliced layouts store them."""
+        b = ctypes.c_double()
+        _check(lib().mgr_kernel_bytes_stored(self._h, name.encode(), ctypes.byref(b)), "mgr_kernel_bytes_stored")
+        return b.value
+
     def memory_bytes(self) -> int:
         b = ctypes.c_int64()
         _check(lib().mgr_memory_bytes(self._h, ctypes.byref(b)), "mgr_memory_bytes")
@@ -357,3 +365,11 @@ def bsr3_outer_grad(A: BSR3, lam, x):
 
 
 from .autograd import MgrSolve, mgr_solve  # noqa: E402
+
+
+def probe_fp64_fma(chain_len: int = 4096, launches: int = 20):
+    """Measured FP64 FMA rate of the current GPU (mgr_probe_fp64_fma): (G FMA/s, ms per launch)."""
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mgr_probe_fp64_fma(chain_len, launches, _stream(), ctypes.byref(g), ctypes.byref(ms)),
+           "mgr_probe_fp64_fma")
+    return g.value, ms.value

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIBPATH = os.path.join(LIBDIR, "libmgrgpu.so")
 OBJDIR = os.path.join(LIBDIR, "obj")
-UNITS = ["scan.cu", "sparse.cu", "setup.cu", "sell.cu", "rowsop.cu", "apply.cu", "krylov.cu", "mgr.cu", "noalloc.cu"]
+UNITS = ["scan.cu", "sparse.cu", "setup.cu", "sell.cu", "rowsop.cu", "apply.cu", "krylov.cu", "mgr.cu", "noalloc.cu", "probe.cu"]
 NOFMA = {"sparse.cu", "setup.cu"}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -279,12 +279,13 @@ static int64_t device_threads() {
 template <class T, class Epi>
 static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, const char* name = "csr_rows") {
   if (op.nr <= 0) return;
-  // values and columns, row pointers, x once, the epilogue's row vectors
-  // (the stored column form: 4 bytes per entry, or 2 plus a 4-byte base per slice of 8 rows, or a
-  // one-byte code plus the 1 KB offset table)
+  // values and 4-byte columns, row pointers, x once, the epilogue's row vectors; stored form: the
+  // columns as the layout holds them (4 bytes per entry, or 2 plus a 4-byte base per slice of 8
+  // rows, or a one-byte code plus the 1 KB offset table)
   const double colb = op.c8 ? (double)op.nnz + 1024.0 : (op.c16 ? 2.0 * op.nnz + 0.5 * op.nr : 4.0 * op.nnz);
-  ProfScope ps(c, name, (double)op.nnz * sizeof(T) + colb + 8.0 * (op.nr + 1) + (double)op.nc * sizeof(T) +
-                            (double)op.nr * epi.row_bytes());
+  const double rest = (double)op.nnz * sizeof(T) + 8.0 * (op.nr + 1) + (double)op.nc * sizeof(T) +
+                      (double)op.nr * epi.row_bytes();
+  ProfScope ps(c, name, rest + 4.0 * op.nnz, rest + colb);
   const int B = 256;
   if (op.sell) {
     // threads per row: enough for six waves of resident threads, at most 4

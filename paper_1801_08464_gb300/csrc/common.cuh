@@ -52,7 +52,8 @@ struct Prof {
     std::vector<cudaEvent_t> a, b;
     double ms = 0.0;
     int64_t n = 0;
-    double bytes = 0.0;  // algorithmic bytes declared by the timed launches
+    double bytes = 0.0;         // algorithmic bytes declared by the timed launches
+    double bytes_stored = 0.0;  // bytes of the stored (compressed) operator forms the launches read
   };
   std::map<std::string, Rec> recs;
   std::set<std::string> only;  // when not empty, only these names are recorded
@@ -104,9 +105,12 @@ struct ProfScope {
   const char* name;
   cudaEvent_t e1 = nullptr;
   // bytes: the algorithmic bytes of the work inside the scope (each input element read once, each
-  // output written once), summed per name for achieved-bandwidth figures
+  // output written once; a sparse entry counts its value and a 4-byte column index whatever form
+  // the layout stores), summed per name for achieved-bandwidth figures.  stored: the same count
+  // with the column indices as the layout stores them (one-byte codes, 16-bit offsets), when that
+  // differs (negative: equal to bytes).
   bool on = false;
-  ProfScope(Ctx& ctx, const char* n, double bytes = 0.0) : c(ctx), name(n) {
+  ProfScope(Ctx& ctx, const char* n, double bytes = 0.0, double stored = -1.0) : c(ctx), name(n) {
     if (!c.prof || !c.prof->wants(n)) return;
     on = true;
     cudaEvent_t e0 = c.prof->get();
@@ -115,6 +119,7 @@ struct ProfScope {
     Prof::Rec& r = c.prof->recs[name];
     r.a.push_back(e0);
     r.bytes += bytes;
+    r.bytes_stored += stored < 0.0 ? bytes : stored;
   }
   ~ProfScope() {
     if (!on) return;
@@ -126,7 +131,10 @@ struct ProfScope {
 // Adds algorithmic bytes to the record of `name` when the name is being profiled (for work whose
 // size is known only after its launches were issued).
 inline void prof_add_bytes(Ctx& c, const char* name, double bytes) {
-  if (c.prof && c.prof->wants(name)) c.prof->recs[name].bytes += bytes;
+  if (c.prof && c.prof->wants(name)) {
+    c.prof->recs[name].bytes += bytes;
+    c.prof->recs[name].bytes_stored += bytes;
+  }
 }
 
 void* dev_alloc(Ctx& c, size_t bytes);

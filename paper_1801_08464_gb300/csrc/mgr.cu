@@ -1208,6 +1208,17 @@ mgr_status_t mgr_kernel_bytes(mgr_handle_t h, const char* name, double* bytes) {
   });
 }
 
+mgr_status_t mgr_kernel_bytes_stored(mgr_handle_t h, const char* name, double* bytes) {
+  if (!h || !name || !bytes) return MGR_ERR_INVALID_ARG;
+  *bytes = 0.0;
+  if (!h->prof) return MGR_OK;
+  return guarded(h, [&] {
+    h->prof->settle();
+    auto it = h->prof->recs.find(name);
+    if (it != h->prof->recs.end()) *bytes = it->second.bytes_stored;
+  });
+}
+
 mgr_status_t mgr_memory_bytes(mgr_handle_t h, int64_t* bytes) {
   if (!h || !bytes) return MGR_ERR_INVALID_ARG;
   *bytes = h->c.bytes;

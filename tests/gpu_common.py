@@ -46,3 +46,37 @@ def compare_csr(g, o, rtol=1e-13, what=""):
 
 def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def compare_hierarchy(m, o, binv=True):
+    """Every setup object of a GPU hierarchy against the oracle's: level operators, W_p, W_r, P, R,
+    F/C splits and relaxation scalings of every MGR level; PMIS splits, strength graphs, P, R, A and
+    smoother scalings of every AMG level; the 3x3 block inverses.  Splittings and patterns bit for
+    bit; returns the smallest fraction of bit-identical values over the operators."""
+    import paper_1801_08464_gb300 as mg
+    import oracle
+    L, na = m.levels()
+    assert (L, na) == o.info()
+    same = []
+    for l in range(L + 1):
+        same.append(compare_csr(m.scipy(mg.MAT_LEVEL, l), o.scipy(oracle.MAT_LEVEL, l), what=f"A_{l}"))
+    for l in range(L):
+        for kind in (mg.MAT_WP, mg.MAT_WR, mg.MAT_P, mg.MAT_R):
+            same.append(compare_csr(m.scipy(kind, l), o.scipy(kind, l), what=f"kind{kind} level {l}"))
+        for kind in (mg.VEC_F, mg.VEC_C):
+            assert np.array_equal(m.vector(kind, l).cpu().numpy(), o.vec(kind, l)), f"F/C split of level {l}"
+        np.testing.assert_allclose(m.vector(mg.VEC_MINV, l).cpu().numpy(), o.vec(oracle.VEC_MINV, l), rtol=1e-14)
+    for k in range(na):
+        same.append(compare_csr(m.scipy(mg.MAT_AMG_A, k), o.scipy(oracle.MAT_AMG_A, k), what=f"AMG A_{k}"))
+        if k < na - 1:
+            assert np.array_equal(m.vector(mg.VEC_AMG_CF, k).cpu().numpy(), o.vec(oracle.VEC_AMG_CF, k)), \
+                f"PMIS split of AMG level {k}"
+            for kind in (mg.MAT_AMG_P, mg.MAT_AMG_R, mg.MAT_AMG_S):
+                same.append(compare_csr(m.scipy(kind, k), o.scipy(kind, k), what=f"AMG kind{kind} level {k}"))
+            np.testing.assert_allclose(m.vector(mg.VEC_AMG_DINV, k).cpu().numpy(), o.vec(oracle.VEC_AMG_DINV, k),
+                                       rtol=1e-14)
+    if binv:
+        ob = o.vec(oracle.VEC_BINV, 0)
+        np.testing.assert_allclose(m.vector(mg.VEC_BINV, 0).cpu().numpy(), ob, rtol=1e-13,
+                                   atol=1e-13 * np.abs(ob).max())
+    return min(same)

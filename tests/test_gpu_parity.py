@@ -125,8 +125,9 @@ def test_fgmres_parity_fp64(name, optname):
 
 
 def test_mixed_precision_iterations_and_error():
-    """FP32 hierarchy with FP64 Krylov: same 1e-8 residual at <= 1.2x the FP64 iterations; the error
-    against the FP64 oracle solution is reported.  Layered 1e4-contrast workload at 32^3."""
+    """FP32 hierarchy with FP64 Krylov: the same 1e-8 residual at <= 1.2x the FP64 oracle's
+    iterations (and the GPU's own FP64-hierarchy count); the errors of both GPU solutions against the
+    FP64 oracle's solution are stated and bounded.  Layered 1e4-contrast workload at 32^3."""
     import paper_1801_08464_gb300 as mg
     import torch
     cfg = ncpgen.GridConfig(32, 32, 32, sigma=1.0, layer_contrast=1e-4, absent_frac=0.4, absent_mode=1, seed=1)
@@ -148,9 +149,16 @@ def test_mixed_precision_iterations_and_error():
         assert info["converged"]
         assert np.linalg.norm(b - Asp @ x) <= 1e-8 * np.linalg.norm(b)
     it64, itmx = res["fp64"][1]["iterations"], res["mixed"][1]["iterations"]
-    assert itmx <= 1.2 * it64 + 1e-9, (itmx, it64)
+    err = {k: rel(x, xo) for k, (x, _) in res.items()}
     print(f"iterations fp64 {it64} mixed {itmx} oracle {io['iterations']}; "
-          f"rel. error vs FP64 oracle: fp64 {rel(res['fp64'][0], xo):.2e} mixed {rel(res['mixed'][0], xo):.2e}")
+          f"rel. error vs FP64 oracle: fp64 {err['fp64']:.2e} mixed {err['mixed']:.2e}")
+    assert itmx <= 1.2 * it64 + 1e-9, (itmx, it64)
+    assert itmx <= 1.2 * io["iterations"] + 1e-9, (itmx, io["iterations"])
+    assert abs(it64 - io["iterations"]) <= 1
+    # the FP32 hierarchy perturbs each preconditioned vector by about 1e-7 relative; the flexible
+    # iteration follows the FP64 one so closely that the two solutions differ far below the 1e-8
+    # tolerance (measured on a GB300: 2.8e-14 FP64, 5.4e-14 mixed)
+    assert err["fp64"] <= 1e-10 and err["mixed"] <= 1e-10, err
 
 
 def test_spmv_parity():
