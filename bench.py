@@ -41,7 +41,7 @@ UNSAT_SOLVER = dict(restrict_type=[0, 0], frelax_type=[1, 1], frelax_sweeps=[1, 
 L2_BYTES = 129 * 1024 * 1024
 
 
-SOLVE_KERNELS = ("bsr3_spmv_f64", "mdot", "mupdate", "global_relax", "bsr_resid_split",
+SOLVE_KERNELS = ("mgr_apply", "amg_tail", "bsr3_spmv_f64", "mdot", "mupdate", "global_relax", "bsr_resid_split",
                  "frelax0", "frelax1", "frelax2", "frelax3", "restrict0", "restrict1", "restrict2", "restrict3",
                  "interp0", "interp1", "interp2", "interp3", "amg0_rows", "amg1_rows", "amg2_rows", "amgc_rows",
                  "amg0_restrict", "amg1_restrict", "amgc_restrict", "amg0_prolong", "amg1_prolong", "amgc_prolong",
@@ -351,8 +351,9 @@ def main():
             dom = max(solve, key=lambda k: kt_full[k][1]) if solve else None
             # small systems replay the apply as a CUDA graph, which profiling turns off: their
             # dominant kernel is timed in the profiled step instead
+            # (with the whole applications and the coarse end of the V-cycle as two scopes of their own)
             if dom and not flush_l2:
-                m.profile(True, only=[dom])
+                m.profile(True, only=[dom, "mgr_apply", "amg_tail"])
         barrier()
         sampler = ClockSampler(local) if (profile and rank == 0) else None
         l0 = mg.launch_count()
@@ -388,12 +389,13 @@ def main():
             kt_dom = (dom, kt_full[dom])
         else:
             kt_dom = (dom, m.kernel_time(dom) + (m.kernel_bytes(dom), m.kernel_bytes_stored(dom))) if dom else None
+        live = {k: m.kernel_time(k) for k in ("mgr_apply", "amg_tail")} if (dom and not flush_l2) else {}
         mem = m.memory_bytes()
         L, na = m.levels()
         hier = {"mgr": [list(_shape(m, mg.MAT_LEVEL, l)) for l in range(L + 1)],
                 "amg": [list(_shape(m, mg.MAT_AMG_A, k)) for k in range(na)]}
         m.close()
-        return ms, infos, setup_ms, launches, clocks, (kt_full, kt_dom), mem, hier
+        return ms, infos, setup_ms, launches, clocks, (kt_full, kt_dom, live), mem, hier
 
     # GB300's FP64 FMA rate, measured (the roofline of the FP64-bound Krylov kernels), with the SM
     # clock sampled while the probe runs
@@ -409,7 +411,7 @@ def main():
         if ck and ck.get("sm_mhz"):
             fp64_probe["fma_per_clock_per_sm"] = g * 1e9 / (ck["sm_mhz"] * 1e6) / torch.cuda.get_device_properties(
                 local).multi_processor_count
-    ms, infos, setup_ms, launches, clocks, (kt, kt_dom), mem, hier = timed("mixed", a.steps, profile=True)
+    ms, infos, setup_ms, launches, clocks, (kt, kt_dom, live), mem, hier = timed("mixed", a.steps, profile=True)
     xr = x.cpu().numpy()
     relres = float(np.linalg.norm(b_h - p.to_scipy() @ xr) / np.linalg.norm(b_h))
     out = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
@@ -432,17 +434,26 @@ def main():
             rk[k] = {"launches": n_k, "ms": t_k, "achieved_gbs": gbs, "frac": gbs / peak,
                      "frac_stored": bs_k / (t_k * 1e-3) / 1e9 / peak, "bytes_per_launch": by_k / n_k}
     out["kernel_bandwidth"] = rk
-    # the whole preconditioner application (every apply kernel of the profiled step together)
+    # the whole preconditioner application: the algorithmic bytes of every apply kernel of the
+    # profiled step, per application, over the time of whole applications inside the timed region
+    # (one event pair per application: no per-kernel events between the launches)
     app = [k for k in rk if k not in ("bsr3_spmv_f64", "mdot", "mupdate")]
-    if app:
-        t_a = sum(kt[k][1] for k in app)
-        by_a, bs_a = sum(kt[k][2] for k in app), sum(kt[k][3] for k in app)
-        out["roofline_apply"] = {"kernels": "mgr_apply (global relaxation, level residuals, F-relaxation, restriction, "
-                                            "interpolation, AMG V-cycle)", "bound": "hbm",
-                                 "ms_per_step": t_a, "applies": kt["global_relax"][0],
-                                 "achieved": by_a / (t_a * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                                 "frac": by_a / (t_a * 1e-3) / 1e9 / peak,
-                                 "frac_stored": bs_a / (t_a * 1e-3) / 1e9 / peak, "peak_source": peak_kind}
+    n_app = kt.get("mgr_apply", (0,))[0]
+    if app and n_app:
+        t_prof = sum(kt[k][1] for k in app)
+        by_a, bs_a = sum(kt[k][2] for k in app) / n_app, sum(kt[k][3] for k in app) / n_app
+        n_live, t_live = live.get("mgr_apply", (0, 0.0))
+        ra = {"kernels": "mgr_apply (global relaxation, level residuals, F-relaxation, restriction, interpolation, "
+                         "AMG V-cycle)", "bound": "hbm", "bytes_per_apply": by_a, "bytes_stored_per_apply": bs_a,
+              "ms_per_apply_kernels_profiled": t_prof / n_app, "peak": peak, "unit": "GB/s", "peak_source": peak_kind}
+        if n_live:
+            us = t_live / n_live * 1e3
+            ra.update({"us_per_apply": us, "applies_timed": n_live, "achieved": by_a / (us * 1e-6) / 1e9,
+                       "frac": by_a / (us * 1e-6) / 1e9 / peak, "frac_stored": bs_a / (us * 1e-6) / 1e9 / peak})
+            n_t, t_t = live.get("amg_tail", (0, 0.0))
+            if n_t:
+                ra["us_per_apply_amg_tail"] = t_t / n_t * 1e3
+        out["roofline_apply"] = ra
     sb = {}
     for k in SETUP_KERNELS:
         n_k, t_k, by_k, _ = kt.get(k, (0, 0.0, 0.0, 0.0))

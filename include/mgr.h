@@ -201,6 +201,8 @@ mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_laun
  *           level: "amg0_rows", "amg1_rows", "amg2_rows", "amgc_rows" (smoothing and residual passes,
  *           levels 3 and coarser together), "amg0_restrict", "amg1_restrict", "amgc_restrict",
  *           "amg0_prolong", "amg1_prolong", "amgc_prolong" (transfers, levels 2 and coarser together);
+ *           "mgr_apply" (each whole forward application), "amg_tail" (the coarse solver's cycle from
+ *           AMG level 3 down, as one scope);
  *   setup:  "setup_total", "setup_mgr_level", "setup_mgr_rap", "setup_amg", "setup_amg_strength",
  *           "setup_amg_pmis", "setup_amg_extpi", "extpi_pattern", "extpi_weights",
  *           "setup_amg_transpose", "setup_amg_rap", "setup_dense_inverse", "setup_cast_alloc",

@@ -113,13 +113,64 @@ __global__ void __launch_bounds__(256) k_rows(int64_t nr, const int64_t* __restr
   if (ok && sub == 0) epi.post(r, s, pre);
 }
 
+// Streaming loads of operator values and column codes: read once per pass, so they skip L1 and
+// leave it to the x gathers, which the rows of a block share.
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2* p) {
+  double2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
+  uint32_t v;
+  asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream(const uint2* p) {
+  uint2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int4 ld_stream(const int4* p) {
+  int4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.s32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_stream(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p) {
+  double v;
+  asm("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) {
+  int32_t v;
+  asm("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p));
+  return v;
+}
+
 // SELL form: one thread per row, slots walked four at a time (padding slots add 0 * x[0])
 template <class T>
 struct Quad;
 template <>
 struct Quad<float> {
   __device__ static __forceinline__ float dot(const float* vp, int4 c, const float* x) {
-    float4 v = __ldg(reinterpret_cast<const float4*>(vp));
+    float4 v = ld_stream(reinterpret_cast<const float4*>(vp));
     float s = v.x * __ldg(x + c.x);
     s = fmaf(v.y, __ldg(x + c.y), s);
     s = fmaf(v.z, __ldg(x + c.z), s);
@@ -129,8 +180,8 @@ struct Quad<float> {
 template <>
 struct Quad<double> {
   __device__ static __forceinline__ double dot(const double* vp, int4 c, const double* x) {
-    double2 a = __ldg(reinterpret_cast<const double2*>(vp));
-    double2 b = __ldg(reinterpret_cast<const double2*>(vp) + 1);
+    double2 a = ld_stream(reinterpret_cast<const double2*>(vp));
+    double2 b = ld_stream(reinterpret_cast<const double2*>(vp) + 1);
     double s = a.x * __ldg(x + c.x);
     s = fma(a.y, __ldg(x + c.y), s);
     s = fma(b.x, __ldg(x + c.z), s);
@@ -138,38 +189,72 @@ struct Quad<double> {
   }
 };
 
+// A 4-slot group of values (streamed) and its product with the four columns given by a word of
+// one-byte codes into the table of offsets col - row: the same products in the same order as
+// Quad<T>::dot.
+template <class T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+  __device__ static __forceinline__ float4 load(const float* p) { return ld_stream(reinterpret_cast<const float4*>(p)); }
+  __device__ static __forceinline__ float code_dot(const float4& v, uint32_t raw, int32_t row, const int32_t* tab,
+                                                   const float* x) {
+    float s = v.x * __ldg(x + row + tab[raw & 0xFFu]);
+    s = fmaf(v.y, __ldg(x + row + tab[(raw >> 8) & 0xFFu]), s);
+    s = fmaf(v.z, __ldg(x + row + tab[(raw >> 16) & 0xFFu]), s);
+    return fmaf(v.w, __ldg(x + row + tab[raw >> 24]), s);
+  }
+};
+template <>
+struct Vec4<double> {
+  struct type { double2 a, b; };
+  __device__ static __forceinline__ type load(const double* p) {
+    return {ld_stream(reinterpret_cast<const double2*>(p)), ld_stream(reinterpret_cast<const double2*>(p) + 1)};
+  }
+  __device__ static __forceinline__ double code_dot(const type& v, uint32_t raw, int32_t row, const int32_t* tab,
+                                                    const double* x) {
+    double s = v.a.x * __ldg(x + row + tab[raw & 0xFFu]);
+    s = fma(v.a.y, __ldg(x + row + tab[(raw >> 8) & 0xFFu]), s);
+    s = fma(v.b.x, __ldg(x + row + tab[(raw >> 16) & 0xFFu]), s);
+    return fma(v.b.y, __ldg(x + row + tab[raw >> 24]), s);
+  }
+};
+
 // Column storage of the 4-slot groups: CM 0 = 32-bit indices; 1 = 16-bit offsets from the slice's
-// base; 2 = one-byte codes into the operator's table of offsets col - row (held in shared memory).
+// base; 2 = one-byte codes into the operator's table of offsets col - row (held in shared memory),
+// laid out in 16-slot groups (rs_code_pos).
 struct QuadCols {
   const int32_t* cp;
   const uint16_t* cp16;
   const uint8_t* cp8;
   int32_t base;      // CM 1: the slice's base; CM 2: the row
   const int32_t* tab;  // CM 2: the offsets (shared memory)
+  int t;               // CM 2: the row within its slice
 };
 template <int CM>
 __device__ __forceinline__ int4 quad_cols(const QuadCols& qc, int64_t q) {
   if constexpr (CM == 1) {
-    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(qc.cp16 + q * (4 * RS_C)));
+    const uint2 raw = ld_stream(reinterpret_cast<const uint2*>(qc.cp16 + q * (4 * RS_C)));
     return make_int4(qc.base + (int)(raw.x & 0xFFFFu), qc.base + (int)(raw.x >> 16), qc.base + (int)(raw.y & 0xFFFFu),
                      qc.base + (int)(raw.y >> 16));
   } else if constexpr (CM == 2) {
-    const uint32_t raw = __ldg(reinterpret_cast<const uint32_t*>(qc.cp8 + q * (4 * RS_C)));
+    const uint32_t raw = ld_stream(reinterpret_cast<const uint32_t*>(qc.cp8 + rs_code_pos(4 * q, qc.t)));
     return make_int4(qc.base + qc.tab[raw & 0xFFu], qc.base + qc.tab[(raw >> 8) & 0xFFu],
                      qc.base + qc.tab[(raw >> 16) & 0xFFu], qc.base + qc.tab[raw >> 24]);
   } else {
-    return __ldg(reinterpret_cast<const int4*>(qc.cp + q * (4 * RS_C)));
+    return ld_stream(reinterpret_cast<const int4*>(qc.cp + q * (4 * RS_C)));
   }
 }
 template <int CM>
 __device__ __forceinline__ QuadCols quad_setup(const int32_t* col, const uint16_t* col16, const int32_t* sbase,
-                                               const uint8_t* code, const int32_t* tab, int64_t s, int64_t j0, int t,
-                                               int64_t row) {
-  QuadCols qc{nullptr, nullptr, nullptr, 0, tab};
+                                               const uint8_t* code, const int64_t* coff, const int32_t* tab, int64_t s,
+                                               int64_t j0, int t, int64_t row) {
+  QuadCols qc{nullptr, nullptr, nullptr, 0, tab, t};
   const int64_t o = j0 * RS_C + t * 4;
   if constexpr (CM == 0) qc.cp = col + o;
   if constexpr (CM == 1) { qc.cp16 = col16 + o; qc.base = sbase[s]; }
-  if constexpr (CM == 2) { qc.cp8 = code + o; qc.base = (int32_t)row; }
+  if constexpr (CM == 2) { qc.cp8 = code + coff[s] * RS_C; qc.base = (int32_t)row; }
   return qc;
 }
 
@@ -177,6 +262,7 @@ template <class T, class Epi, int Q, int CM>
 __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __restrict__ soff,
                                                    const int32_t* __restrict__ col, const uint16_t* __restrict__ col16,
                                                    const int32_t* __restrict__ sbase, const uint8_t* __restrict__ code,
+                                                   const int64_t* __restrict__ coff,
                                                    const int32_t* __restrict__ otab, const T* __restrict__ val,
                                                    const int32_t* __restrict__ perm, const T* __restrict__ x,
                                                    Epi epi) {
@@ -196,20 +282,24 @@ __global__ void __launch_bounds__(256) k_rows_sell(int64_t nr, const int64_t* __
   const T* vp = val + j0 * RS_C + t * Q;
   T sum = 0;
   if constexpr (Q == 4 && CM == 2) {
-    // one-byte codes: the codes of the next group are loaded before this group's table lookups and
-    // gathers (three dependent steps per group: codes, table, x)
-    const uint8_t* cp8 = code + j0 * RS_C + t * 4;
-    uint32_t nxt = nq > 0 ? __ldg(reinterpret_cast<const uint32_t*>(cp8)) : 0u;
-#pragma unroll 2
-    for (int64_t q = 0; q < nq; ++q) {
-      const uint32_t raw = nxt;
-      if (q + 1 < nq) nxt = __ldg(reinterpret_cast<const uint32_t*>(cp8 + (q + 1) * (4 * RS_C)));
-      const int4 c = make_int4((int32_t)row + s_tab[raw & 0xFFu], (int32_t)row + s_tab[(raw >> 8) & 0xFFu],
-                               (int32_t)row + s_tab[(raw >> 16) & 0xFFu], (int32_t)row + s_tab[raw >> 24]);
-      sum += Quad<T>::dot(vp + q * (4 * RS_C), c, x);
+    // one-byte codes: the codes of four groups come in one 16-byte load, then the four groups'
+    // values, then their gathers and products (in group order)
+    const uint8_t* cb = code + coff[s] * RS_C + t * 16;
+    const int32_t r32 = (int32_t)row;
+#pragma unroll 1
+    for (int64_t q0 = 0; q0 < nq; q0 += 4) {
+      const uint4 cw = ld_stream(reinterpret_cast<const uint4*>(cb + q0 * (4 * RS_C)));
+      typename Vec4<T>::type vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u < nq) vv[u] = Vec4<T>::load(vp + (q0 + u) * (4 * RS_C));
+      const uint32_t w4[4] = {cw.x, cw.y, cw.z, cw.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u < nq) sum += Vec4<T>::code_dot(vv[u], w4[u], r32, s_tab, x);
     }
   } else if constexpr (Q == 4) {
-    const QuadCols qc = quad_setup<CM>(col, col16, sbase, code, s_tab, s, j0, t, row);
+    const QuadCols qc = quad_setup<CM>(col, col16, sbase, code, coff, s_tab, s, j0, t, row);
 #pragma unroll 2
     for (int64_t q = 0; q < nq; ++q) sum += Quad<T>::dot(vp + q * (4 * RS_C), quad_cols<CM>(qc, q), x);
   } else {
@@ -230,6 +320,7 @@ __global__ void __launch_bounds__(256) k_rows_sell_split(int64_t nr, const int64
                                                          const uint16_t* __restrict__ col16,
                                                          const int32_t* __restrict__ sbase,
                                                          const uint8_t* __restrict__ code,
+                                                         const int64_t* __restrict__ coff,
                                                          const int32_t* __restrict__ otab, const T* __restrict__ val,
                                                          const int32_t* __restrict__ perm, const T* __restrict__ x,
                                                          Epi epi) {
@@ -251,7 +342,7 @@ __global__ void __launch_bounds__(256) k_rows_sell_split(int64_t nr, const int64
   T sum = 0;
   if (ok) {
     const int64_t j0 = soff[s], nq = (soff[s + 1] - j0) / 4;
-    const QuadCols qc = quad_setup<CM>(col, col16, sbase, code, s_tab, s, j0, t, row);
+    const QuadCols qc = quad_setup<CM>(col, col16, sbase, code, coff, s_tab, s, j0, t, row);
     const T* vp = val + j0 * RS_C + t * 4;
 #pragma unroll 2
     for (int64_t q = h; q < nq; q += H) sum += Quad<T>::dot(vp + q * (4 * RS_C), quad_cols<CM>(qc, q), x);
@@ -299,24 +390,25 @@ static void run_rows(Ctx& c, const RowsOp<T>& op, const T* x, const Epi& epi, co
     const int32_t* sb = op.sbase.p;
     const uint8_t* cd = op.scode.p;
     const int32_t* ot = op.otab.p;
+    const int64_t* cf = op.coff.p;
     const unsigned g1 = grid_for(op.nr, B), g2 = grid_for(slices * RS_C * 2, B), g4 = grid_for(slices * RS_C * 4, B);
 #define MGR_SELL_LAUNCH(CM)                                                                                       \
   do {                                                                                                           \
     if (H == 1)                                                                                                  \
-      launch_pdl(c, k_rows_sell<T, Epi, 4, CM>, g1, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, ot, op.sval.p,     \
+      launch_pdl(c, k_rows_sell<T, Epi, 4, CM>, g1, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, cf, ot, op.sval.p,     \
                  op.perm.p, x, epi);                                                                             \
     else if (H == 2)                                                                                             \
-      launch_pdl(c, k_rows_sell_split<T, Epi, 2, CM>, g2, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, ot,          \
+      launch_pdl(c, k_rows_sell_split<T, Epi, 2, CM>, g2, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, cf, ot,          \
                  op.sval.p, op.perm.p, x, epi);                                                                  \
     else                                                                                                         \
-      launch_pdl(c, k_rows_sell_split<T, Epi, 4, CM>, g4, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, ot,          \
+      launch_pdl(c, k_rows_sell_split<T, Epi, 4, CM>, g4, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, cf, ot,          \
                  op.sval.p, op.perm.p, x, epi);                                                                  \
   } while (0)
     if (op.q == 4 && op.c8) MGR_SELL_LAUNCH(2);
     else if (op.q == 4 && op.c16) MGR_SELL_LAUNCH(1);
     else if (op.q == 4) MGR_SELL_LAUNCH(0);
     else
-      launch_pdl(c, k_rows_sell<T, Epi, 1, 0>, g1, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, ot, op.sval.p,
+      launch_pdl(c, k_rows_sell<T, Epi, 1, 0>, g1, B, 0, op.nr, op.soff.p, sc, sc16, sb, cd, cf, ot, op.sval.p,
                  op.perm.p, x, epi);
 #undef MGR_SELL_LAUNCH
     CU_LAUNCH();

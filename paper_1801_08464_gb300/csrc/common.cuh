@@ -111,7 +111,7 @@ struct ProfScope {
   // differs (negative: equal to bytes).
   bool on = false;
   ProfScope(Ctx& ctx, const char* n, double bytes = 0.0, double stored = -1.0) : c(ctx), name(n) {
-    if (!c.prof || !c.prof->wants(n)) return;
+    if (!n || !c.prof || !c.prof->wants(n)) return;
     on = true;
     cudaEvent_t e0 = c.prof->get();
     e1 = c.prof->get();

@@ -191,6 +191,8 @@ const T* vcycle(mgr_handle_s& h, const AmgRef& g, int k, const T* b, bool transp
     launch_dense_gemv<T>(c, g.nco, transposed ? g.cinvT : g.cinv, b, x);
     return x;
   }
+  // the coarse end of the coarse solver's cycle (levels 3 and below) as one timed scope
+  ProfScope tail(c, (g.coarse && k == 3 && !transposed) ? "amg_tail" : nullptr);
   AmgLevel& A = (*g.lv)[k];
   const RowsOp<T>& Av = transposed ? tv<T>(A.AT64, A.AT32) : tv<T>(A.A64, A.A32);
   const int npre = transposed ? g.post : g.pre;
@@ -369,6 +371,7 @@ void capture_apply(mgr_handle_s& h) {
 
 void do_apply(mgr_handle_s& h, const double* r, double* z) {
   const bool mixed = h.o.precision == MGR_PREC_MIXED;
+  ProfScope whole(h.c, "mgr_apply");  // the whole preconditioner application
   // the first apply after a setup runs directly (it also settles the launch-shape caches); the
   // second captures the graph, and later ones replay it
   if (graph_wanted(h) && h.applies++ >= 1) {

@@ -90,8 +90,13 @@ __global__ void k_rs_offtab(int64_t nw, const int32_t* flag, const int32_t* code
   if (v < nw && flag[v]) otab[code[v]] = (int32_t)(v - maxd);
 }
 // the slots of row t of each slice as codes (padding: 255)
+__global__ void k_rs_cwidth(int64_t ns, const int64_t* soff, int64_t* cw) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s < ns) cw[s] = (soff[s + 1] - soff[s] + 15) / 16 * 16;
+}
 __global__ void k_rs_pack8(int64_t nr, int64_t npad, const int64_t* rp, const int32_t* perm, const int64_t* soff,
-                           const int32_t* scol, const int32_t* code, int64_t maxd, uint8_t* scode) {
+                           const int64_t* coff, const int32_t* scol, const int32_t* code, int64_t maxd,
+                           uint8_t* scode) {
   int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (r >= npad) return;
   int64_t s = r / RS_C;
@@ -99,9 +104,10 @@ __global__ void k_rs_pack8(int64_t nr, int64_t npad, const int64_t* rp, const in
   int64_t b0 = soff[s], w = soff[s + 1] - b0;
   int64_t row = r < nr ? (perm ? perm[r] : r) : 0;
   int64_t len = r < nr ? rp[row + 1] - rp[row] : 0;
-  for (int64_t j = 0; j < w; ++j) {
+  const int64_t cb = coff[s] * RS_C, cw = coff[s + 1] - coff[s];
+  for (int64_t j = 0; j < cw; ++j) {
     int64_t o = b0 * RS_C + (j / RS_Q) * (RS_Q * RS_C) + t * RS_Q + (j % RS_Q);
-    scode[o] = j < len ? (uint8_t)code[(int64_t)scol[o] - row + maxd] : (uint8_t)255;
+    scode[cb + rs_code_pos(j, t)] = (j < w && j < len) ? (uint8_t)code[(int64_t)scol[o] - row + maxd] : (uint8_t)255;
   }
 }
 
@@ -198,9 +204,13 @@ void rowsop_build(Ctx& c, const DCSR<double>& A, RowsOp<T>& op) {
             CU(cudaMemsetAsync(op.otab.p, 0, sizeof(int32_t) * 256, c.s));  // code 255 (padding): offset 0
             k_rs_offtab<<<grid_for(nw, 256), 256, 0, c.s>>>(nw, flag.p, code.p, maxd, op.otab.p);
             CU_LAUNCH();
-            op.scode.alloc(c, op.slots * RS_C);
-            k_rs_pack8<<<grid_for(np, 256), 256, 0, c.s>>>(A.nr, np, A.rp, op.perm.p, op.soff.p, op.scol.p, code.p,
-                                                           maxd, op.scode.p);
+            op.coff.alloc(c, ns + 1);
+            k_rs_cwidth<<<grid_for(ns, 256), 256, 0, c.s>>>(ns, op.soff.p, width.p);
+            CU_LAUNCH();
+            const int64_t cslots = counts_to_rowptr(c, width.p, op.coff.p, ns);
+            op.scode.alloc(c, cslots * RS_C);
+            k_rs_pack8<<<grid_for(np, 256), 256, 0, c.s>>>(A.nr, np, A.rp, op.perm.p, op.soff.p, op.coff.p,
+                                                           op.scol.p, code.p, maxd, op.scode.p);
             CU_LAUNCH();
             op.scol.release();
             return;

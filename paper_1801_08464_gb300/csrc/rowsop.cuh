@@ -19,7 +19,10 @@
 // operator row stored at slice position r.  Windows keep the rows of a slice close together, so
 // their x gathers and outputs stay local.
 // Compressed columns: a square operator whose entries use at most 255 distinct offsets col - row is
-// stored with one-byte codes into a table of those offsets.  Otherwise, when every slice of an
+// stored with one-byte codes into a table of those offsets.  The codes are laid out in groups of 16
+// slots (slice widths rounded up to 16, padding code 255): slot j of row t of slice s at
+// CB_s * 8 + (j / 16) * 128 + t * 16 + j % 16, so one thread reads the codes of four 4-slot groups as
+// one 16-byte load (CB_s: the rounded widths of the slices before s).  Otherwise, when every slice of an
 // operator with 4-slot groups spans fewer than 65,536
 // columns (the stencil-like operators of this path: a slice holds 8 consecutive rows, or rows of one
 // 256-row window), the columns are stored as 16-bit offsets from the slice's smallest column
@@ -62,10 +65,16 @@ struct RowsOp {
   // of those offsets (code 255, offset 0, marks padding); 5 bytes per FP32 entry instead of 8
   bool c8 = false;
   DBuf<uint8_t> scode;
+  DBuf<int64_t> coff;  // code slice offsets CB_s (slots)
   DBuf<int32_t> otab;  // 256 offsets
   // CSR
   DCSR<T> csr;
 };
+
+// Position of slot j of row t within a slice in the one-byte code layout.
+__host__ __device__ __forceinline__ int64_t rs_code_pos(int64_t j, int t) {
+  return (j / 16) * 128 + (int64_t)t * 16 + (j % 16);
+}
 
 // Build from an FP64 CSR matrix, casting the values to T.
 template <class T>
