@@ -249,7 +249,7 @@ mgr_status_t mgr_bsr3_outer_grad(const mgr_bsr3_t* A, const double* lambda, cons
  * one warm-up and `launches` timed launches of a kernel of eight independent FMA chains of
  * `chain_len` (a positive multiple of 4) FMAs per thread over a full-occupancy grid on `cuda_stream`,
  * timed with CUDA events; writes the FMAs per second / 1e9 and the milliseconds per launch (host
- * outs; the latter may be NULL).  Allocates one double of scratch; synchronises the stream. */
+ * outs; the latter may be NULL).  Allocates three doubles of scratch; synchronises the stream. */
 mgr_status_t mgr_probe_fp64_fma(int64_t chain_len, int launches, void* cuda_stream, double* gfma_per_s,
                                 double* ms_per_launch);
 
