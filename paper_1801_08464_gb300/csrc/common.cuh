@@ -273,7 +273,12 @@ void bsr3_to_csr(Ctx& c, const mgr_bsr3_t& A, DCSR<double>& out);        // exac
 void bsr3_block_inverse(Ctx& c, const mgr_bsr3_t& A, double* binv);      // sets EBIT_SINGULAR
 // C = A * B: structural pattern, each entry summed in ascending intermediate index.
 // C = A B (Gustavson order); `name` labels the call in the per-kernel timing
-void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C, const char* name = "spgemm");
+// C = A B in Gustavson's order (every entry summed from 0.0 in ascending intermediate index).
+// sort_rows: rows of 33..256 products are formed by a warp sort of their products rather than a
+// hash table (measured faster for the injective-R coarse operators A_C P of the second and third
+// reductions, slower for the first reduction's and the AMG products).
+void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C, const char* name = "spgemm",
+            bool sort_rows = false);
 // Pattern of C = A * B only (values left unallocated), same pattern rules.
 void transpose(Ctx& c, const DCSR<double>& A, DCSR<double>& T);          // rows sorted by column
 // Sort each row segment [rp[i], rp[i+1]) of (ci, v) by ci (keys unique within a row).

@@ -126,69 +126,72 @@ __device__ __forceinline__ void mdot_rows_kn(int kn, int64_t i0, int64_t i1, con
   }
 }
 
-// 2-D multi-dot: block b handles vector group g = b % ng (vectors 8g .. 8g+7) on row chunk
-// x = b / ng, so the ng blocks sharing a chunk of w run together and re-read it from L2.  Group 0
-// also accumulates w . w.  Partial sums go to part[k * nx + x] (k = nv for w . w).
+// Multi-dot: block x handles row chunk x for every vector group g (vectors 8g .. 8g+7) in turn, so
+// every block streams the same number of vectors (a 2-D grid of group blocks left the blocks of a
+// short last group idle for most of the launch).  Group 0 also accumulates w . w.  Partial sums go
+// to part[k * nx + x] (k = nv for w . w).
 __global__ void __launch_bounds__(KT) k_mdot(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
                                              const double* __restrict__ w, int ww, int ng, int nx, int64_t chunk,
                                              double* __restrict__ part) {
   pdl_wait();
-  int g = blockIdx.x % ng;
-  int x = blockIdx.x / ng;
-  int k0 = g * MD_VEC;
-  int kn = nv - k0 < MD_VEC ? nv - k0 : MD_VEC;
-  bool dow = ww && g == 0;
-  int64_t i0 = (int64_t)x * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
-  double acc[MD_VEC + 1];
-#pragma unroll
-  for (int k = 0; k <= MD_VEC; ++k) acc[k] = 0.0;
-  // kn and dow are uniform over the block
-  if (dow) mdot_rows_kn<true>(kn, i0, i1, V + k0 * ldv, ldv, w, acc);
-  else mdot_rows_kn<false>(kn, i0, i1, V + k0 * ldv, ldv, w, acc);
+  const int x = blockIdx.x;
+  const int64_t i0 = (int64_t)x * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
   __shared__ double sh[KT / 32][MD_VEC + 1];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // reduce-scatter of the 8 vector sums across the warp (FP64 adds are the scarce instructions): at
-  // offsets 16, 8, 4 each lane keeps half of its values and adds its partner's copy of that half
-  // (4 + 2 + 1 adds), then a butterfly over offsets 2 and 1; lane L ends with the warp's sum of
-  // vector ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).  9 adds instead of 40.
-  {
-    static_assert(MD_VEC == 8, "the reduce-scatter is written for 8 vectors per block");
-    double h4[4], h2[2], h1;
-    const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int g = 0; g < ng; ++g) {
+    const int k0 = g * MD_VEC;
+    const int kn = nv - k0 < MD_VEC ? nv - k0 : MD_VEC;
+    const bool dow = ww && g == 0;
+    double acc[MD_VEC + 1];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      double send = b16 ? acc[j] : acc[j + 4];
-      double keep = b16 ? acc[j + 4] : acc[j];
-      h4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      double send = b8 ? h4[j] : h4[j + 2];
-      double keep = b8 ? h4[j + 2] : h4[j];
-      h2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
+    for (int k = 0; k <= MD_VEC; ++k) acc[k] = 0.0;
+    // kn and dow are uniform over the block
+    if (dow) mdot_rows_kn<true>(kn, i0, i1, V + k0 * ldv, ldv, w, acc);
+    else mdot_rows_kn<false>(kn, i0, i1, V + k0 * ldv, ldv, w, acc);
+    // reduce-scatter of the 8 vector sums across the warp (FP64 adds are the scarce instructions): at
+    // offsets 16, 8, 4 each lane keeps half of its values and adds its partner's copy of that half
+    // (4 + 2 + 1 adds), then a butterfly over offsets 2 and 1; lane L ends with the warp's sum of
+    // vector ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).  9 adds instead of 40.
     {
-      double send = b4 ? h2[0] : h2[1];
-      double keep = b4 ? h2[1] : h2[0];
-      h1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      static_assert(MD_VEC == 8, "the reduce-scatter is written for 8 vectors per block");
+      double h4[4], h2[2], h1;
+      const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        double send = b16 ? acc[j] : acc[j + 4];
+        double keep = b16 ? acc[j + 4] : acc[j];
+        h4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        double send = b8 ? h4[j] : h4[j + 2];
+        double keep = b8 ? h4[j + 2] : h4[j];
+        h2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      {
+        double send = b4 ? h2[0] : h2[1];
+        double keep = b4 ? h2[1] : h2[0];
+        h1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      h1 += __shfl_xor_sync(0xffffffffu, h1, 2);
+      h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
+      if ((lane & 3) == 0) sh[wid][(b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0)] = h1;
+      if (dow) {  // uniform over the block
+        double v = warp_sum(acc[MD_VEC]);
+        if (lane == 0) sh[wid][MD_VEC] = v;
+      }
     }
-    h1 += __shfl_xor_sync(0xffffffffu, h1, 2);
-    h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
-    if ((lane & 3) == 0) sh[wid][(b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0)] = h1;
-    if (dow) {  // uniform over the block
-      double v = warp_sum(acc[MD_VEC]);
-      if (lane == 0) sh[wid][MD_VEC] = v;
+    __syncthreads();
+    if (threadIdx.x <= MD_VEC) {
+      int k = threadIdx.x;
+      if (k < kn || (k == MD_VEC && dow)) {
+        double s = 0.0;
+        for (int w2 = 0; w2 < KT / 32; ++w2) s += sh[w2][k];
+        int out = (k == MD_VEC) ? nv : k0 + k;
+        part[(int64_t)out * nx + x] = s;
+      }
     }
-  }
-  __syncthreads();
-  if (threadIdx.x <= MD_VEC) {
-    int k = threadIdx.x;
-    if (k < kn || (k == MD_VEC && dow)) {
-      double s = 0.0;
-      for (int w2 = 0; w2 < KT / 32; ++w2) s += sh[w2][k];
-      int out = (k == MD_VEC) ? nv : k0 + k;
-      part[(int64_t)out * nx + x] = s;
-    }
+    __syncthreads();  // sh is reused by the next group
   }
 }
 
@@ -226,8 +229,8 @@ static int one_wave(const void* fn) {
   return nb;
 }
 
-static int md_nx(int64_t n, int ng, int64_t* chunk) {
-  int nx = one_wave((const void*)k_mdot) / ng;
+static int md_nx(int64_t n, int64_t* chunk) {
+  int nx = one_wave((const void*)k_mdot);
   if (nx < 1) nx = 1;
   int64_t c = (n + nx - 1) / nx;
   c = (c + 1) & ~int64_t(1);
@@ -243,9 +246,9 @@ void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const 
   int ng = (nv + MD_VEC - 1) / MD_VEC;
   if (ng < 1) ng = 1;
   int64_t chunk;
-  int nx = md_nx(n, ng, &chunk);
+  int nx = md_nx(n, &chunk);
   ProfScope ps(c, "mdot", 8.0 * (nv + 1) * n);
-  launch_pdl(c, k_mdot, ng * nx, KT, 0, n, V, ldv, nv, w, ww, ng, nx, chunk, part);
+  launch_pdl(c, k_mdot, nx, KT, 0, n, V, ldv, nv, w, ww, ng, nx, chunk, part);
   CU_LAUNCH();
   int na = nv + ww;
   launch_pdl(c, k_reduce_parts, (na + 7) / 8, 256, 0, nx, na, part, out);

@@ -242,7 +242,7 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
     } else {
       DCSR<double> AC;
       csr_gather_rows(c, A, L.C.p, nC, AC);
-      spgemm(c, AC, L.P, Anext, kRAP[li]);
+      spgemm(c, AC, L.P, Anext, kRAP[li], true);
     }
   }
   mk_next.alloc(c, nC);

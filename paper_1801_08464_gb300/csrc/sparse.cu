@@ -783,11 +783,168 @@ __device__ __forceinline__ bool chunk_row(int64_t i, int U, const int64_t* __res
   return true;
 }
 
-// The rows of a batch with TT_CAP < U <= FUSE_CAP, four warps per block with 256-slot tables: the
+// Rows of TT_CAP < U <= WS_CAP products, one warp per row, by a sort instead of a hash table: the row's
+// products are formed once into shared memory (A entries 32 at a time, each lane writing the products
+// of its entry in B-row order, so product t follows the (k, q) order), their keys
+// ((column - the row's smallest column) << 8 | t) are bitonic-sorted across the warp, 32E keys held
+// E per lane, and every run of equal columns is summed by the lane holding its first key: from 0.0,
+// in ascending t, i.e. ascending intermediate index k (Gustavson's order, bit for bit the sums of
+// the hash kernels and of the oracle).  Rows whose columns span 2^24 or more are listed for the hash
+// kernels.  The sorted runs come out in column order, so no sort of the output follows.
+constexpr int WS_CAP = 256;  // a sort of 32E keys, E <= 8 per lane (longer rows: the hash kernels)
+constexpr int WS_WARPS = 4;
+
+template <int E>
+__device__ __forceinline__ void ws_sort(uint32_t (&key)[8], int lane) {
+  constexpr int N = 32 * E;
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j < E) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int pe = e ^ j;
+          if (pe > e) {
+            const int g = lane * E + e;
+            const bool up = (g & k) == 0;
+            const uint32_t a = key[e], b = key[pe];
+            if ((a > b) == up) { key[e] = b; key[pe] = a; }
+          }
+        }
+      } else {
+        const int lm = j / E;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int g = lane * E + e;
+          const uint32_t other = __shfl_xor_sync(0xffffffffu, key[e], lm);
+          const bool up = (g & k) == 0;
+          const bool lower = (g & j) == 0;
+          // the lower position keeps the smaller key in an ascending run, the larger otherwise
+          key[e] = (lower == up) ? min(key[e], other) : max(key[e], other);
+        }
+      }
+    }
+  }
+}
+
+template <int E>
+__device__ __forceinline__ int ws_row(int lane, int U, int32_t cbase, const int32_t* sc, const double* sv,
+                                      uint32_t* sk, int32_t* __restrict__ ocol, double* __restrict__ oval) {
+  uint32_t key[8];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int t = lane * E + e;
+    key[e] = t < U ? ((uint32_t)(sc[t] - cbase) << 8) | (uint32_t)t : 0xFFFFFFFFu;
+  }
+  ws_sort<E>(key, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e) sk[lane * E + e] = key[e];
+  __syncwarp();
+  // run heads among this lane's keys, their output positions by a warp scan of the head counts
+  int nh = 0;
+  unsigned heads = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int g = lane * E + e;
+    if (g < U && (g == 0 || (key[e] >> 8) != (sk[g - 1] >> 8))) { heads |= 1u << e; ++nh; }
+  }
+  int x = nh;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  int pos = x - nh;
+  const int total = __shfl_sync(0xffffffffu, x, 31);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (heads & (1u << e)) {
+      int g = lane * E + e;
+      const uint32_t c = key[e] >> 8;
+      double acc = 0.0;
+      do {
+        acc = __dadd_rn(acc, sv[sk[g] & 0xFFu]);
+        ++g;
+      } while (g < U && (sk[g] >> 8) == c);
+      ocol[pos] = cbase + (int32_t)c;
+      oval[pos] = acc;
+      ++pos;
+    }
+  }
+  return total;
+}
+
+__global__ void __launch_bounds__(32 * WS_WARPS) k_spgemm_wsort(
+    int64_t r0, int64_t m, int64_t sbase, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+    const double* __restrict__ av, const int64_t* __restrict__ brp, const int32_t* __restrict__ bci,
+    const double* __restrict__ bv, const int64_t* __restrict__ ub, const int64_t* __restrict__ soff,
+    int32_t* __restrict__ scol, double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ list,
+    int* __restrict__ nlist, int cap) {
+  __shared__ int32_t s_col[WS_WARPS][WS_CAP];
+  __shared__ double s_val[WS_WARPS][WS_CAP];
+  __shared__ uint32_t s_key[WS_WARPS][WS_CAP];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = r0 + (int64_t)blockIdx.x * WS_WARPS + w;
+  if (i >= m) return;
+  const int U = (int)ub[i];
+  if (U <= TT_CAP || U > cap) return;  // k_spgemm_tiny; the hash kernels
+  int32_t* sc = s_col[w];
+  double* sv = s_val[w];
+  // products in (k, q) order: product t at sc[t], sv[t]
+  int32_t cmin = INT_MAX, cmax = INT_MIN;
+  int base = 0;
+  const int64_t a0 = arp[i], a1 = arp[i + 1];
+  for (int64_t p0 = a0; p0 < a1; p0 += 32) {
+    const int64_t p = p0 + lane;
+    int len = 0;
+    int64_t b0 = 0;
+    double a = 0.0;
+    if (p < a1) {
+      const int32_t k = aci[p];
+      b0 = brp[k];
+      len = (int)(brp[k + 1] - b0);
+      a = av[p];
+    }
+    int x = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    int t = base + x - len;
+    for (int q = 0; q < len; ++q, ++t) {
+      const int32_t j = bci[b0 + q];
+      sc[t] = j;
+      sv[t] = __dmul_rn(a, bv[b0 + q]);
+      cmin = min(cmin, j);
+      cmax = max(cmax, j);
+    }
+    base += __shfl_sync(0xffffffffu, x, 31);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cmin = min(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
+    cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+  }
+  if ((int64_t)cmax - (int64_t)cmin >= (int64_t(1) << 24)) {  // keys would not fit: the hash kernels
+    if (lane == 0) list[atomicAdd(nlist, 1)] = (int32_t)i;
+    return;
+  }
+  __syncwarp();
+  const int64_t o = soff[i] - sbase;
+  int total;
+  if (U <= 64) total = ws_row<2>(lane, U, cmin, sc, sv, s_key[w], scol + o, sval + o);
+  else if (U <= 128) total = ws_row<4>(lane, U, cmin, sc, sv, s_key[w], scol + o, sval + o);
+  else total = ws_row<8>(lane, U, cmin, sc, sv, s_key[w], scol + o, sval + o);
+  if (lane == 0) cnt[i] = total;
+}
+
+// The rows of a batch with WS_CAP < U <= FUSE_CAP, four warps per block with 256-slot tables: the
 // table is sized by the row's distinct columns, not by its products (the coarse-operator rows keep a
 // small fraction of their products), so small tables keep many warps resident; a row whose distinct
-// columns pass FZ_LIMIT (a 70 % load) is stopped and listed for the 1024-slot list kernel, whose
-// overflow goes on to the 4096-slot one.
+// columns pass FZ_LIMIT (a 70 % load) is stopped and listed, like the rows k_spgemm_wsort cannot key,
+// for the 1024-slot list kernel, whose overflow goes on to the 4096-slot one.
 constexpr int FZ_WARPS = 4;
 constexpr int FZ_CAPA = 128;
 constexpr int FZ_SLOTS = 256;
@@ -797,7 +954,8 @@ __global__ void __launch_bounds__(32 * FZ_WARPS, 8) k_spgemm_fused_chunk(
     int64_t r0, int64_t m, int64_t sbase, const int64_t* __restrict__ arp, const int32_t* __restrict__ aci, const double* __restrict__ av,
     const int64_t* __restrict__ brp, const int32_t* __restrict__ bci, const double* __restrict__ bv,
     const int64_t* __restrict__ ub, const int64_t* __restrict__ soff, int32_t* __restrict__ scol,
-    double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ list, int* __restrict__ nlist) {
+    double* __restrict__ sval, int64_t* __restrict__ cnt, int32_t* __restrict__ list, int* __restrict__ nlist,
+    int lo) {
   __shared__ int32_t hk[FZ_WARPS][FZ_SLOTS];
   __shared__ double hv[FZ_WARPS][FZ_SLOTS];
   __shared__ int32_t sst[FZ_WARPS][FZ_CAPA + 1];
@@ -808,7 +966,7 @@ __global__ void __launch_bounds__(32 * FZ_WARPS, 8) k_spgemm_fused_chunk(
   int64_t i = r0 + (int64_t)blockIdx.x * FZ_WARPS + w;
   if (i >= m) return;
   int U = (int)ub[i];
-  if (U <= TT_CAP || U > FUSE_CAP) return;  // k_spgemm_tiny; the symbolic path
+  if (U <= lo || U > FUSE_CAP) return;  // k_spgemm_tiny or k_spgemm_wsort; the symbolic path
   ChunkSmem sm{hk[w], hv[w], sst[w], sbg[w], sa[w], gv[w]};
   const bool done = chunk_row<FZ_SLOTS, FZ_CAPA, false, FZ_LIMIT>(i, U, arp, aci, av, brp, bci, bv, soff[i] - sbase,
                                                                    scol, sval, cnt, sm);
@@ -922,7 +1080,9 @@ __global__ void k_small_ub(int64_t m, const int64_t* ub, int64_t* us) {
   if (i < m) us[i] = ub[i] <= FUSE_CAP ? ub[i] : 0;
 }
 
-void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C, const char* name) {
+void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& C, const char* name, bool sort_rows) {
+  // rows of TT_CAP < U <= cap products take the sort kernel, longer ones the hash kernels
+  const int sort_cap = sort_rows ? WS_CAP : TT_CAP;
   if (A.nc != B.nr) throw Error(MGR_ERR_INVALID_ARG, "spgemm: inner dimensions differ");
   int64_t m = A.nr;
   C.nr = m;
@@ -994,8 +1154,13 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
       k_spgemm_tiny<<<grid_for(i1 - i0, TT_THREADS), TT_THREADS, 0, c.s>>>(i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci,
                                                                            B.v, ub.p, soff.p, scol.p, sval.p, cnt.p);
       CU_LAUNCH();
+      if (sort_cap > TT_CAP) {
+        k_spgemm_wsort<<<grid_for(i1 - i0, WS_WARPS), 32 * WS_WARPS, 0, c.s>>>(
+            i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, lists.p, nlist.p, sort_cap);
+        CU_LAUNCH();
+      }
       k_spgemm_fused_chunk<<<grid_for(i1 - i0, FZ_WARPS), 32 * FZ_WARPS, 0, c.s>>>(
-          i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, lists.p, nlist.p);
+          i0, i1, base, A.rp, A.ci, A.v, B.rp, B.ci, B.v, ub.p, soff.p, scol.p, sval.p, cnt.p, lists.p, nlist.p, sort_cap);
       CU_LAUNCH();
       launch_chunk_list<4, 1024, 256, 1024 * 7 / 10>(c, lists.p, nlist.p, base, A, B, ub.p, soff.p, scol.p, sval.p,
                                                      cnt.p, i1 - i0, lists.p + m, nlist.p + 1);
