@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <map>
 #include <set>
 #include <stdexcept>
@@ -92,7 +93,7 @@ struct Ctx {
   Prof* prof = nullptr;
   cudaStream_t s = nullptr;
   int* d_err = nullptr;        // device int, error bits
-  int* h_pinned = nullptr;     // pinned host scratch (small readbacks)
+  void* h_pinned = nullptr;    // pinned host scratch of 8 bytes for scalar read-backs (may be null)
   int64_t spgemm_stage = 0;    // staged products per SpGEMM batch (0: the library default)
   int64_t bytes = 0;           // bytes currently allocated through this context
   int64_t peak = 0;
@@ -183,9 +184,16 @@ struct DCSR {
 // Read back a device scalar (synchronises the stream).
 template <class T>
 T read_scalar(Ctx& c, const T* dptr) {
+  static_assert(sizeof(T) <= 8, "scalar read-backs of at most 8 bytes");
   T h;
-  CU(cudaMemcpyAsync(&h, dptr, sizeof(T), cudaMemcpyDeviceToHost, c.s));
-  CU(cudaStreamSynchronize(c.s));
+  if (c.h_pinned) {  // a copy into pinned memory is a plain DMA: no staging by the driver
+    CU(cudaMemcpyAsync(c.h_pinned, dptr, sizeof(T), cudaMemcpyDeviceToHost, c.s));
+    CU(cudaStreamSynchronize(c.s));
+    memcpy(&h, c.h_pinned, sizeof(T));
+  } else {
+    CU(cudaMemcpyAsync(&h, dptr, sizeof(T), cudaMemcpyDeviceToHost, c.s));
+    CU(cudaStreamSynchronize(c.s));
+  }
   return h;
 }
 void check_errors(Ctx& c, const char* phase);  // reads d_err, throws on set bits, clears it

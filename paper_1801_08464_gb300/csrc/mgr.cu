@@ -1008,6 +1008,7 @@ mgr_status_t mgr_create(mgr_handle_t* out, const mgr_options_t* opt, void* strea
     CU(cudaMalloc(&h->c.d_err, sizeof(int)));
     CU(cudaMemset(h->c.d_err, 0, sizeof(int)));
     CU(cudaMallocHost(&h->hpin, 512 * sizeof(double)));
+    h->c.h_pinned = h->hpin + 511;  // the last slot: scalar read-backs of the setup
   });
   if (st != MGR_OK) {
     if (h->c.d_err) cudaFree(h->c.d_err);

@@ -958,15 +958,19 @@ static void pmis(Ctx& c, const DCSR<double>& S, uint64_t seed, int lev, DBuf<int
   CU_LAUNCH();
   int left = read_scalar(c, und.p);
   int rounds = 0;
+  // the undecided count is read back after every second round: a round after the last decision
+  // selects nothing and marks nothing, so the splitting is the same, with half the host round trips
   while (left > 0) {
-    if (++rounds > 10000) throw Error(MGR_ERR_CUDA, "PMIS did not terminate");
-    k_pmis_select<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, St.rp, St.ci, w.p, cf.p, nc.p);
-    CU_LAUNCH();
-    k_pmis_mark_c<<<grid_for(n, B), B, 0, c.s>>>(n, nc.p, cf.p);
-    CU_LAUNCH();
-    CU(cudaMemsetAsync(und.p, 0, sizeof(int), c.s));
-    k_pmis_mark_f<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, cf.p, und.p);
-    CU_LAUNCH();
+    for (int r = 0; r < 2; ++r) {
+      if (++rounds > 10000) throw Error(MGR_ERR_CUDA, "PMIS did not terminate");
+      k_pmis_select<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, St.rp, St.ci, w.p, cf.p, nc.p);
+      CU_LAUNCH();
+      k_pmis_mark_c<<<grid_for(n, B), B, 0, c.s>>>(n, nc.p, cf.p);
+      CU_LAUNCH();
+      CU(cudaMemsetAsync(und.p, 0, sizeof(int), c.s));
+      k_pmis_mark_f<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, cf.p, und.p);
+      CU_LAUNCH();
+    }
     left = read_scalar(c, und.p);
   }
 }
