@@ -5,7 +5,9 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <set>
 #include <stdexcept>
 #include <vector>
@@ -30,7 +32,7 @@ inline void cuda_check(cudaError_t e, const char* what, const char* file, int li
 }
 #define CU(x) ::mgr::cuda_check((x), #x, __FILE__, __LINE__)
 // Every kernel launch of the library is followed by CU_LAUNCH(), which checks it and counts it.
-extern unsigned long long g_launch_count;
+extern std::atomic<unsigned long long> g_launch_count;
 #define CU_LAUNCH()                                                                  \
   do {                                                                               \
     ::mgr::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__);      \
@@ -99,6 +101,10 @@ struct Ctx {
   int64_t peak = 0;
   int num_sms = 152;
   bool pdl = true;             // programmatic dependent launch for the kernels launched with launch_pdl
+  // a context on a second stream and host thread books its device bytes on `acct` (the handle's
+  // main context), under `mu` while the two run at once
+  Ctx* acct = nullptr;
+  std::mutex* mu = nullptr;
 };
 
 struct ProfScope {

@@ -16,6 +16,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <thread>
+
 #include "apply.cuh"
 #include "hier.cuh"
 
@@ -23,6 +25,10 @@ using namespace mgr;
 
 struct mgr_handle_s {
   Ctx c;
+  // second context (own stream and error word): the apply copies of the MGR levels are built on it
+  // by a second host thread while the AMG hierarchy is set up on the main stream
+  Ctx cw;
+  std::mutex acct_mu;
   mgr_options_t o;
   int device = 0;
   bool ready = false;
@@ -458,9 +464,8 @@ void release_csr(DCSR<double>& M) {
 }
 
 // The apply operators of MGR level l in the working precision (SELL or CSR copies of A_ff, A_cf, W_p).
-void cast_mgr_level(mgr_handle_s& h, MgrLevel& L) {
+void cast_mgr_level(mgr_handle_s& h, MgrLevel& L, Ctx& c) {
   if (L.cast) return;
-  Ctx& c = h.c;
   if (h.o.precision == MGR_PREC_MIXED) {
     rowsop_build<float>(c, L.Aff, L.Aff32);
     rowsop_build<float>(c, L.Acf, L.Acf32);
@@ -494,9 +499,8 @@ void cast_mgr_level(mgr_handle_s& h, MgrLevel& L) {
   L.cast = true;
 }
 
-void cast_amg_level(mgr_handle_s& h, AmgLevel& G) {
+void cast_amg_level(mgr_handle_s& h, AmgLevel& G, Ctx& c) {
   if (G.cast) return;
-  Ctx& c = h.c;
   if (h.o.precision == MGR_PREC_MIXED) {
     rowsop_build<float>(c, G.A, G.A32);
     rowsop_build<float>(c, G.P, G.P32);
@@ -517,8 +521,16 @@ void cast_amg_level(mgr_handle_s& h, AmgLevel& G) {
   G.cast = true;
 }
 
-void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
-  Ctx& c = h.c;
+void rehome_amg_level(AmgLevel& G, Ctx& c) {
+  rowsop_rehome(G.A32, c); rowsop_rehome(G.P32, c); rowsop_rehome(G.R32, c);
+  rowsop_rehome(G.A64, c); rowsop_rehome(G.P64, c); rowsop_rehome(G.R64, c);
+  rowsop_rehome(G.AT32, c); rowsop_rehome(G.AT64, c);
+  G.dinv32.c = &c;
+}
+
+// The apply copies that depend on the MGR levels only: A's values in the sliced layout (and the
+// block inverses in FP32) and every MGR level's operators (with the F-relaxation AMG levels).
+void cast_mgr_part(mgr_handle_s& h, const mgr_bsr3_t& A, Ctx& c) {
   int64_t nv = 9 * SELL_C * h.sell.slots;
   bool mixed = h.o.precision == MGR_PREC_MIXED;
   if (mixed) {
@@ -531,10 +543,31 @@ void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A) {
     sell_fill_values<double, double>(c, h.sell, A.values, h.val64.p);
   }
   for (int l = 0; l < h.L; ++l) {
-    cast_mgr_level(h, h.lev[l]);
-    for (size_t k = 0; k + 1 < h.lev[l].famg.size(); ++k) cast_amg_level(h, h.lev[l].famg[k]);
+    cast_mgr_level(h, h.lev[l], c);
+    for (size_t k = 0; k + 1 < h.lev[l].famg.size(); ++k) cast_amg_level(h, h.lev[l].famg[k], c);
   }
-  for (size_t k = 0; k + 1 < h.amg.size(); ++k) cast_amg_level(h, h.amg[k]);
+}
+
+// Hands the buffers built by cast_mgr_part on context `from` over to the handle's main context.
+void rehome_mgr_part(mgr_handle_s& h) {
+  Ctx& c = h.c;
+  h.val32.c = &c; h.binv32.c = &c; h.val64.c = &c;
+  for (int l = 0; l < h.L; ++l) {
+    MgrLevel& L = h.lev[l];
+    rowsop_rehome(L.Aff32, c); rowsop_rehome(L.Acf32, c); rowsop_rehome(L.Wp32, c);
+    rowsop_rehome(L.Aff64, c); rowsop_rehome(L.Acf64, c); rowsop_rehome(L.Wp64, c);
+    rowsop_rehome(L.WpT32, c); rowsop_rehome(L.AcfT32, c); rowsop_rehome(L.AffT32, c);
+    rowsop_rehome(L.WpT64, c); rowsop_rehome(L.AcfT64, c); rowsop_rehome(L.AffT64, c);
+    L.minv32.c = &c;
+    for (size_t k = 0; k + 1 < L.famg.size(); ++k) rehome_amg_level(L.famg[k], c);
+  }
+}
+
+void cast_hierarchy(mgr_handle_s& h, const mgr_bsr3_t& A, bool mgr_part) {
+  Ctx& c = h.c;
+  bool mixed = h.o.precision == MGR_PREC_MIXED;
+  if (mgr_part) cast_mgr_part(h, A, c);
+  for (size_t k = 0; k + 1 < h.amg.size(); ++k) cast_amg_level(h, h.amg[k], c);
   if (h.o.adjoint) {
     // A^T in the sliced layout (its src renumbered to A's blocks, values transposed block by block),
     // the transposed diagonal-block inverses and the transposed coarsest inverse
@@ -587,7 +620,7 @@ void build_famg(mgr_handle_s& h, int l) {
   ProfScope ps(c, "setup_famg");
   if (h.o.lean) {
     amg_build(c, L.Aff, false, af, L.famg, L.fcinv, L.fnco, [&](AmgLevel& G) {
-      cast_amg_level(h, G);
+      cast_amg_level(h, G, c);
       release_csr(G.A);
       release_csr(G.P);
       release_csr(G.R);
@@ -659,7 +692,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     if (h.o.frelax_type[l] == 2) build_famg(h, l);
     if (h.o.lean) {  // the level's FP64 operators are not read again
       MgrLevel& Lv = h.lev[l];
-      cast_mgr_level(h, Lv);
+      cast_mgr_level(h, Lv, c);
       release_csr(Lv.A);
       release_csr(Lv.Wp);
       release_csr(Lv.Wr);
@@ -668,6 +701,50 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
       release_csr(Lv.Aff);
       release_csr(Lv.Acf);
     }
+  }
+  // Without the lean setup the apply copies of the MGR levels (and A's sliced values) depend on
+  // nothing the coarse solver builds: a second host thread builds them on the second context's
+  // stream while this thread sets the coarse solver up (both threads mostly issue launches and
+  // wait for read-backs, which leaves the GPU room for both).  Their buffers are handed over to the
+  // main context once the thread has joined.
+  std::thread caster;
+  std::exception_ptr caster_err;
+  struct Joiner {
+    std::thread& t;
+    ~Joiner() { if (t.joinable()) t.join(); }
+  } joiner{caster};
+  const bool overlap = !h.o.lean;
+  if (overlap) {
+    Ctx& w = h.cw;
+    if (!w.s) CU(cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
+    if (!w.d_err) {
+      CU(cudaMalloc(&w.d_err, sizeof(int)));
+      CU(cudaMemsetAsync(w.d_err, 0, sizeof(int), c.s));
+    }
+    w.h_pinned = h.hpin + 510;
+    w.prof = nullptr;
+    w.spgemm_stage = c.spgemm_stage;
+    w.num_sms = c.num_sms;
+    w.pdl = c.pdl;
+    w.acct = &c;
+    w.mu = &h.acct_mu;
+    c.mu = &h.acct_mu;
+    cudaEvent_t built = nullptr;
+    CU(cudaEventCreateWithFlags(&built, cudaEventDisableTiming));
+    CU(cudaEventRecord(built, c.s));
+    CU(cudaStreamWaitEvent(w.s, built, 0));
+    CU(cudaEventDestroy(built));
+    caster = std::thread([&h, &A, &caster_err, dev = h.device] {
+      try {
+        CU(cudaSetDevice(dev));
+        cast_mgr_part(h, A, h.cw);
+        CU(cudaStreamSynchronize(h.cw.s));
+        check_errors(h.cw, "apply copies of the MGR levels");
+      } catch (...) {
+        caster_err = std::current_exception();
+        cudaStreamSynchronize(h.cw.s);
+      }
+    });
   }
   // coarse solve on the last level
   DCSR<double>& Ac = h.lev[L].A;
@@ -685,7 +762,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
       // the AMG takes the pressure operator over, and each level's FP64 matrices are freed once the
       // next level is built
       amg_build(c, h.lev[L].A, true, ao, h.amg, h.cinv, h.nco, [&](AmgLevel& G) {
-        cast_amg_level(h, G);
+        cast_amg_level(h, G, c);
         release_csr(G.A);
         release_csr(G.P);
         release_csr(G.R);
@@ -695,9 +772,15 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
       amg_build(c, h.lev[L].A, false, ao, h.amg, h.cinv, h.nco, nullptr);
     }
   }
+  if (overlap) {
+    caster.join();
+    c.mu = nullptr;
+    rehome_mgr_part(h);
+    if (caster_err) std::rethrow_exception(caster_err);
+  }
   {
     ProfScope ps(c, "setup_cast_alloc");
-    cast_hierarchy(h, A);
+    cast_hierarchy(h, A, !overlap);
     alloc_work(h);
   }
   CU(cudaStreamSynchronize(c.s));
@@ -1068,6 +1151,14 @@ mgr_status_t mgr_destroy(mgr_handle_t h) {
     h->gstream = nullptr;
     h->lev.clear();
     h->amg.clear();
+    rehome_mgr_part(*h);  // buffers a failed setup left on the second context
+    if (h->cw.s) {
+      CU(cudaStreamSynchronize(h->cw.s));
+      cudaStreamDestroy(h->cw.s);
+      h->cw.s = nullptr;
+    }
+    if (h->cw.d_err) cudaFree(h->cw.d_err);
+    h->cw.d_err = nullptr;
   });
   {
     // remaining buffers are released by the destructor (stream-ordered frees)

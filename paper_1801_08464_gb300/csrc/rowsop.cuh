@@ -76,6 +76,14 @@ __host__ __device__ __forceinline__ int64_t rs_code_pos(int64_t j, int t) {
   return (j / 16) * 128 + (int64_t)t * 16 + (j % 16);
 }
 
+// Hands every buffer of op over to the context c: later releases are ordered on c's stream.
+template <class T>
+void rowsop_rehome(RowsOp<T>& op, Ctx& c) {
+  op.soff.c = &c; op.perm.c = &c; op.scol.c = &c; op.sval.c = &c; op.scol16.c = &c; op.sbase.c = &c;
+  op.scode.c = &c; op.coff.c = &c; op.otab.c = &c;
+  op.csr.rp.c = &c; op.csr.ci.c = &c; op.csr.v.c = &c;
+}
+
 // Build from an FP64 CSR matrix, casting the values to T.
 template <class T>
 void rowsop_build(Ctx& c, const DCSR<double>& A, RowsOp<T>& op);

@@ -3,7 +3,7 @@
 
 namespace mgr {
 
-unsigned long long g_launch_count = 0;
+std::atomic<unsigned long long> g_launch_count{0};
 
 void* dev_alloc(Ctx& c, size_t bytes) {
   void* p = nullptr;
@@ -12,15 +12,21 @@ void* dev_alloc(Ctx& c, size_t bytes) {
     cudaGetLastError();
     throw Error(MGR_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
   }
-  c.bytes += (int64_t)bytes;
-  if (c.bytes > c.peak) c.peak = c.bytes;
+  Ctx& a = c.acct ? *c.acct : c;
+  std::unique_lock<std::mutex> lock;
+  if (c.mu) lock = std::unique_lock<std::mutex>(*c.mu);
+  a.bytes += (int64_t)bytes;
+  if (a.bytes > a.peak) a.peak = a.bytes;
   return p;
 }
 
 void dev_free(Ctx& c, void* p, size_t bytes) {
   if (!p) return;
   cudaFreeAsync(p, c.s);
-  c.bytes -= (int64_t)bytes;
+  Ctx& a = c.acct ? *c.acct : c;
+  std::unique_lock<std::mutex> lock;
+  if (c.mu) lock = std::unique_lock<std::mutex>(*c.mu);
+  a.bytes -= (int64_t)bytes;
 }
 
 void check_errors(Ctx& c, const char* phase) {
