@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
 #include <cstring>
 #include <functional>
 #include <type_traits>
@@ -702,18 +704,48 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
       release_csr(Lv.Acf);
     }
   }
-  // Without the lean setup the apply copies of the MGR levels (and A's sliced values) depend on
-  // nothing the coarse solver builds: a second host thread builds them on the second context's
-  // stream while this thread sets the coarse solver up (both threads mostly issue launches and
-  // wait for read-backs, which leaves the GPU room for both).  Their buffers are handed over to the
-  // main context once the thread has joined.
+  // Without the lean setup the apply copies are built by a second host thread on the second
+  // context's stream while this thread carries on with the hierarchy: first those of the MGR levels
+  // (and A's sliced values), which depend on nothing the coarse solver builds, then those of each
+  // AMG level as soon as the next level has been built from it.  Both threads mostly issue launches
+  // and wait for read-backs, which leaves the GPU room for both.  The buffers are handed over to
+  // the main context once the thread has joined.
+  struct Tasks {
+    std::mutex m;
+    std::condition_variable cv;
+    std::deque<std::function<void()>> q;
+    bool closed = false;
+  } tasks;
   std::thread caster;
   std::exception_ptr caster_err;
   struct Joiner {
+    Tasks& tk;
     std::thread& t;
-    ~Joiner() { if (t.joinable()) t.join(); }
-  } joiner{caster};
+    ~Joiner() {
+      {
+        std::lock_guard<std::mutex> g(tk.m);
+        tk.closed = true;
+      }
+      tk.cv.notify_all();
+      if (t.joinable()) t.join();
+    }
+  } joiner{tasks, caster};
   const bool overlap = !h.o.lean;
+  // a task for the caster, ordered after everything issued so far on the main stream
+  auto post = [&](std::function<void()> fn) {
+    cudaEvent_t ev = nullptr;
+    CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CU(cudaEventRecord(ev, c.s));
+    {
+      std::lock_guard<std::mutex> g(tasks.m);
+      tasks.q.push_back([&h, ev, fn] {
+        CU(cudaStreamWaitEvent(h.cw.s, ev, 0));
+        CU(cudaEventDestroy(ev));
+        fn();
+      });
+    }
+    tasks.cv.notify_one();
+  };
   if (overlap) {
     Ctx& w = h.cw;
     if (!w.s) CU(cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
@@ -729,22 +761,28 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     w.acct = &c;
     w.mu = &h.acct_mu;
     c.mu = &h.acct_mu;
-    cudaEvent_t built = nullptr;
-    CU(cudaEventCreateWithFlags(&built, cudaEventDisableTiming));
-    CU(cudaEventRecord(built, c.s));
-    CU(cudaStreamWaitEvent(w.s, built, 0));
-    CU(cudaEventDestroy(built));
-    caster = std::thread([&h, &A, &caster_err, dev = h.device] {
+    caster = std::thread([&h, &tasks, &caster_err, dev = h.device] {
       try {
         CU(cudaSetDevice(dev));
-        cast_mgr_part(h, A, h.cw);
+        for (;;) {
+          std::function<void()> fn;
+          {
+            std::unique_lock<std::mutex> g(tasks.m);
+            tasks.cv.wait(g, [&] { return tasks.closed || !tasks.q.empty(); });
+            if (tasks.q.empty()) break;
+            fn = std::move(tasks.q.front());
+            tasks.q.pop_front();
+          }
+          if (!caster_err) fn();
+        }
         CU(cudaStreamSynchronize(h.cw.s));
-        check_errors(h.cw, "apply copies of the MGR levels");
+        check_errors(h.cw, "apply copies");
       } catch (...) {
         caster_err = std::current_exception();
         cudaStreamSynchronize(h.cw.s);
       }
     });
+    post([&h, &A] { cast_mgr_part(h, A, h.cw); });
   }
   // coarse solve on the last level
   DCSR<double>& Ac = h.lev[L].A;
@@ -769,13 +807,23 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
         release_csr(G.S);
       });
     } else {
-      amg_build(c, h.lev[L].A, false, ao, h.amg, h.cinv, h.nco, nullptr);
+      h.amg.reserve(64 + (size_t)std::max(0, h.o.amg_max_levels));  // the caster holds references to levels
+      amg_build(c, h.lev[L].A, false, ao, h.amg, h.cinv, h.nco, [&](AmgLevel& G) {
+        AmgLevel* g = &G;
+        post([&h, g] { cast_amg_level(h, *g, h.cw); });
+      });
     }
   }
   if (overlap) {
+    {
+      std::lock_guard<std::mutex> g(tasks.m);
+      tasks.closed = true;
+    }
+    tasks.cv.notify_all();
     caster.join();
     c.mu = nullptr;
     rehome_mgr_part(h);
+    for (AmgLevel& G : h.amg) rehome_amg_level(G, c);
     if (caster_err) std::rethrow_exception(caster_err);
   }
   {
