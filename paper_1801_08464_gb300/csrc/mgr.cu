@@ -553,7 +553,8 @@ void cast_mgr_part(mgr_handle_s& h, const mgr_bsr3_t& A, Ctx& c) {
 // Hands the buffers built by cast_mgr_part on context `from` over to the handle's main context.
 void rehome_mgr_part(mgr_handle_s& h) {
   Ctx& c = h.c;
-  h.val32.c = &c; h.binv32.c = &c; h.val64.c = &c;
+  h.val32.c = &c; h.binv32.c = &c; h.val64.c = &c; h.binv.c = &c;
+  h.sell.soff.c = &c; h.sell.col.c = &c; h.sell.src.c = &c;
   for (int l = 0; l < h.L; ++l) {
     MgrLevel& L = h.lev[l];
     rowsop_rehome(L.Aff32, c); rowsop_rehome(L.Acf32, c); rowsop_rehome(L.Wp32, c);
@@ -661,49 +662,6 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   h.ci0.alloc(c, A.nnzb);
   CU(cudaMemcpyAsync(h.rp0.p, A.rowptr, sizeof(int64_t) * (A.nb + 1), cudaMemcpyDeviceToDevice, c.s));
   CU(cudaMemcpyAsync(h.ci0.p, A.colind, sizeof(int32_t) * A.nnzb, cudaMemcpyDeviceToDevice, c.s));
-  sell_build_pattern(c, A.nb, A.nnzb, A.rowptr, A.colind, h.sell);
-  int L;
-  {
-    DBuf<int> mx(c, 1);
-    CU(cudaMemsetAsync(mx.p, 0, sizeof(int), c.s));
-    k_max_marker<<<grid_for(n, 256), 256, 0, c.s>>>(n, marker, mx.p);
-    CU_LAUNCH();
-    L = read_scalar(c, mx.p);
-  }
-  h.L = L;
-  // global relaxation blocks
-  h.binv.alloc(c, 9 * A.nb);
-  bsr3_block_inverse(c, A, h.binv.p);
-  check_errors(c, "3x3 diagonal blocks");
-  h.lev.resize(L + 1);
-  h.lev[0].n = n;
-  bsr3_to_csr(c, A, h.lev[0].A);
-  h.lev[0].mk.alloc(c, n);
-  CU(cudaMemcpyAsync(h.lev[0].mk.p, marker, n, cudaMemcpyDeviceToDevice, c.s));
-  for (int l = 0; l < L; ++l) {
-    LevelOpts lo;
-    lo.frelax_type = h.o.frelax_type[l];
-    lo.sweeps = h.o.frelax_sweeps[l];
-    lo.omega = h.o.frelax_omega[l];
-    lo.restrict_type = h.o.restrict_type[l];
-    DBuf<int8_t> mk_next;
-    ProfScope ps(c, "setup_mgr_level");
-    mgr_reduce_level(c, h.lev[l], l, lo, h.lev[l + 1].A, mk_next);
-    h.lev[l + 1].n = h.lev[l].nC;
-    h.lev[l + 1].mk = std::move(mk_next);
-    if (h.o.frelax_type[l] == 2) build_famg(h, l);
-    if (h.o.lean) {  // the level's FP64 operators are not read again
-      MgrLevel& Lv = h.lev[l];
-      cast_mgr_level(h, Lv, c);
-      release_csr(Lv.A);
-      release_csr(Lv.Wp);
-      release_csr(Lv.Wr);
-      release_csr(Lv.P);
-      release_csr(Lv.R);
-      release_csr(Lv.Aff);
-      release_csr(Lv.Acf);
-    }
-  }
   // Without the lean setup the apply copies are built by a second host thread on the second
   // context's stream while this thread carries on with the hierarchy: first those of the MGR levels
   // (and A's sliced values), which depend on nothing the coarse solver builds, then those of each
@@ -782,8 +740,56 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
         cudaStreamSynchronize(h.cw.s);
       }
     });
-    post([&h, &A] { cast_mgr_part(h, A, h.cw); });
   }
+  // the sliced layout of A's pattern and the 3x3 block inverses are read by the apply and the Krylov
+  // products only: with the caster they are built on its stream while the MGR levels are set up
+  auto build_sell_binv = [&h, &A](Ctx& x) {
+    sell_build_pattern(x, A.nb, A.nnzb, A.rowptr, A.colind, h.sell);
+    h.binv.alloc(x, 9 * A.nb);
+    bsr3_block_inverse(x, A, h.binv.p);
+    check_errors(x, "3x3 diagonal blocks");
+  };
+  if (overlap) post([&h, build_sell_binv] { build_sell_binv(h.cw); });
+  else build_sell_binv(c);
+  int L;
+  {
+    DBuf<int> mx(c, 1);
+    CU(cudaMemsetAsync(mx.p, 0, sizeof(int), c.s));
+    k_max_marker<<<grid_for(n, 256), 256, 0, c.s>>>(n, marker, mx.p);
+    CU_LAUNCH();
+    L = read_scalar(c, mx.p);
+  }
+  h.L = L;
+  h.lev.resize(L + 1);
+  h.lev[0].n = n;
+  bsr3_to_csr(c, A, h.lev[0].A);
+  h.lev[0].mk.alloc(c, n);
+  CU(cudaMemcpyAsync(h.lev[0].mk.p, marker, n, cudaMemcpyDeviceToDevice, c.s));
+  for (int l = 0; l < L; ++l) {
+    LevelOpts lo;
+    lo.frelax_type = h.o.frelax_type[l];
+    lo.sweeps = h.o.frelax_sweeps[l];
+    lo.omega = h.o.frelax_omega[l];
+    lo.restrict_type = h.o.restrict_type[l];
+    DBuf<int8_t> mk_next;
+    ProfScope ps(c, "setup_mgr_level");
+    mgr_reduce_level(c, h.lev[l], l, lo, h.lev[l + 1].A, mk_next);
+    h.lev[l + 1].n = h.lev[l].nC;
+    h.lev[l + 1].mk = std::move(mk_next);
+    if (h.o.frelax_type[l] == 2) build_famg(h, l);
+    if (h.o.lean) {  // the level's FP64 operators are not read again
+      MgrLevel& Lv = h.lev[l];
+      cast_mgr_level(h, Lv, c);
+      release_csr(Lv.A);
+      release_csr(Lv.Wp);
+      release_csr(Lv.Wr);
+      release_csr(Lv.P);
+      release_csr(Lv.R);
+      release_csr(Lv.Aff);
+      release_csr(Lv.Acf);
+    }
+  }
+  if (overlap) post([&h, &A] { cast_mgr_part(h, A, h.cw); });
   // coarse solve on the last level
   DCSR<double>& Ac = h.lev[L].A;
   if (h.o.coarse_solver == 1) {
