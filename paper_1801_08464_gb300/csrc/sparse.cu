@@ -829,8 +829,8 @@ __device__ __forceinline__ void ws_sort(uint32_t (&key)[8], int lane) {
 }
 
 template <int E>
-__device__ __forceinline__ int ws_row(int lane, int U, int32_t cbase, const int32_t* sc, const double* sv,
-                                      uint32_t* sk, int32_t* __restrict__ ocol, double* __restrict__ oval) {
+__device__ __forceinline__ int ws_row(int lane, int U, int32_t cbase, int32_t* sc, const double* sv, uint32_t* sk,
+                                      int32_t* __restrict__ ocol, double* __restrict__ oval) {
   uint32_t key[8];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
@@ -841,7 +841,8 @@ __device__ __forceinline__ int ws_row(int lane, int U, int32_t cbase, const int3
 #pragma unroll
   for (int e = 0; e < E; ++e) sk[lane * E + e] = key[e];
   __syncwarp();
-  // run heads among this lane's keys, their output positions by a warp scan of the head counts
+  // run heads among this lane's keys; their positions, in order, go to sc (the products' columns
+  // are no longer needed: a key holds its column)
   int nh = 0;
   unsigned heads = 0;
 #pragma unroll
@@ -858,18 +859,21 @@ __device__ __forceinline__ int ws_row(int lane, int U, int32_t cbase, const int3
   int pos = x - nh;
   const int total = __shfl_sync(0xffffffffu, x, 31);
 #pragma unroll
-  for (int e = 0; e < E; ++e) {
-    if (heads & (1u << e)) {
-      int g = lane * E + e;
-      const uint32_t c = key[e] >> 8;
+  for (int e = 0; e < E; ++e)
+    if (heads & (1u << e)) sc[pos++] = lane * E + e;
+  __syncwarp();
+  // one run per lane: the FP64 additions of 32 runs go in one instruction stream (a lane holding
+  // several heads would walk its runs one after another while the other lanes idle)
+  for (int h0 = 0; h0 < total; h0 += 32) {
+    const int hh = h0 + lane;
+    if (hh < total) {
+      int g = sc[hh];
+      const int end = hh + 1 < total ? sc[hh + 1] : U;
+      const uint32_t k0 = sk[g];
       double acc = 0.0;
-      do {
-        acc = __dadd_rn(acc, sv[sk[g] & 0xFFu]);
-        ++g;
-      } while (g < U && (sk[g] >> 8) == c);
-      ocol[pos] = cbase + (int32_t)c;
-      oval[pos] = acc;
-      ++pos;
+      for (; g < end; ++g) acc = __dadd_rn(acc, sv[sk[g] & 0xFFu]);
+      ocol[hh] = cbase + (int32_t)(k0 >> 8);
+      oval[hh] = acc;
     }
   }
   return total;
