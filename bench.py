@@ -336,8 +336,18 @@ def main():
     def timed(prec, steps, profile=False):
         m = mg.MGR(precision=prec, **SOLVER)
         infos = []
-        for _ in range(a.warmup):
-            step(m)
+        waits = {}
+        for wi in range(a.warmup):
+            if wi == a.warmup - 1:
+                # host waits on the GPU (read-backs, synchronisations) of one setup and one solve
+                w0 = mg.host_wait_count()
+                m.setup(A, mk)
+                w1 = mg.host_wait_count()
+                x.zero_()
+                m.fgmres(A, b, x, rtol=RTOL, restart=RESTART, maxit=MAXIT)
+                waits = {"setup": w1 - w0, "solve": mg.host_wait_count() - w1}
+            else:
+                step(m)
         kt_full, dom = {}, None
         if profile:
             # one more untimed step with every kernel timed: the per-kernel table, and the choice of
@@ -395,7 +405,7 @@ def main():
         hier = {"mgr": [list(_shape(m, mg.MAT_LEVEL, l)) for l in range(L + 1)],
                 "amg": [list(_shape(m, mg.MAT_AMG_A, k)) for k in range(na)]}
         m.close()
-        return ms, infos, setup_ms, launches, clocks, (kt_full, kt_dom, live), mem, hier
+        return ms, infos, setup_ms, launches, clocks, (kt_full, kt_dom, live), mem, hier, waits
 
     # GB300's FP64 FMA rate, measured (the roofline of the FP64-bound Krylov kernels), with the SM
     # clock sampled while the probe runs
@@ -411,7 +421,7 @@ def main():
         if ck and ck.get("sm_mhz"):
             fp64_probe["fma_per_clock_per_sm"] = g * 1e9 / (ck["sm_mhz"] * 1e6) / torch.cuda.get_device_properties(
                 local).multi_processor_count
-    ms, infos, setup_ms, launches, clocks, (kt, kt_dom, live), mem, hier = timed("mixed", a.steps, profile=True)
+    ms, infos, setup_ms, launches, clocks, (kt, kt_dom, live), mem, hier, waits = timed("mixed", a.steps, profile=True)
     xr = x.cpu().numpy()
     relres = float(np.linalg.norm(b_h - p.to_scipy() @ xr) / np.linalg.norm(b_h))
     out = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
@@ -420,6 +430,7 @@ def main():
            "iterations": infos[-1]["iterations"], "setup_ms": statistics.mean(setup_ms),
            "solve_ms": statistics.mean(i["solve_ms"] for i in infos), "relres_true": relres,
            "solves_per_s_all_gpus": a.gpus * 1000.0 / ms, "gpu_launches": int(launches),
+           "host_waits_per_step": waits,
            "device_memory_gb": mem / 1e9, "hierarchy_rows_nnz": hier}
     # per-kernel achieved algorithmic bandwidth of the solve kernels, from the untimed profiled step
     # (bytes declared by the library for each launch, divided by the CUDA-event time of the launches);
@@ -498,7 +509,7 @@ def main():
     if clocks:
         out["clocks"] = clocks
     if not a.no_fp64:
-        ms64, infos64, setup64, _, _, _, _, _ = timed("fp64", max(1, a.steps))
+        ms64, infos64, setup64, _, _, _, _, _, _ = timed("fp64", max(1, a.steps))
         out["fp64"] = {"ms_per_step": ms64, "iterations": infos64[-1]["iterations"],
                        "setup_ms": statistics.mean(setup64), "solve_ms": statistics.mean(i["solve_ms"] for i in infos64),
                        "speedup_mixed_vs_fp64": ms64 / ms}

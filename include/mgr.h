@@ -191,6 +191,11 @@ mgr_status_t mgr_memory_peak_bytes(mgr_handle_t h, int64_t* bytes);
  * count of kernel launches issued by this library since load. */
 mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_launches, int64_t* graph_nodes,
                            int64_t* total_launches);
+/* Process-wide count of host waits on the GPU issued by this library since load (host out): scalar
+ * read-backs (sizes of products and coarse grids, PMIS progress, Krylov scalars) and stream
+ * synchronisations.  A measurement aid: in the setup each wait leaves the GPU idle until the host
+ * has issued the next launch.  NULL: MGR_ERR_INVALID_ARG. */
+mgr_status_t mgr_get_host_waits(int64_t* waits);
 
 /* Per-kernel timing on the handle's stream: enable = 1 starts recording CUDA events around every
  * launch of the named kernels and clears earlier totals, enable = 0 stops.  mgr_kernel_time returns

@@ -64,7 +64,7 @@ class SolveInfo(ctypes.Structure):
 EXPORTS = ["mgr_status_string", "mgr_options_default", "mgr_create", "mgr_setup", "mgr_apply", "fgmres_solve",
            "mgr_apply_transpose", "fgmres_solve_transpose",
            "mgr_destroy", "mgr_get_levels", "mgr_matrix_shape", "mgr_copy_matrix", "mgr_vector_len",
-           "mgr_copy_vector", "mgr_memory_bytes", "mgr_memory_peak_bytes", "mgr_get_stats", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
+           "mgr_copy_vector", "mgr_memory_bytes", "mgr_memory_peak_bytes", "mgr_get_stats", "mgr_get_host_waits", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
            "mgr_bsr3_outer_grad", "mgr_profile", "mgr_profile_select", "mgr_kernel_time",
            "mgr_kernel_bytes", "mgr_kernel_bytes_stored", "mgr_probe_fp64_fma"]
 
@@ -97,6 +97,7 @@ def lib():
         L.mgr_memory_bytes.argtypes = [vp, P(i64)]
         L.mgr_memory_peak_bytes.argtypes = [vp, P(i64)]
         L.mgr_get_stats.argtypes = [vp, P(ctypes.c_double), P(i64), P(i64), P(i64)]
+        L.mgr_get_host_waits.argtypes = [P(i64)]
         L.mgr_bsr3_spmv.argtypes = [P(Bsr3), vp, vp, vp, vp]
         L.mgr_bsr3_transpose.argtypes = [P(Bsr3), vp, vp, vp, vp]
         L.mgr_bsr3_outer_grad.argtypes = [P(Bsr3), vp, vp, vp, vp]
@@ -328,6 +329,13 @@ class MGR:
         _check(lib().mgr_get_stats(self._h, ctypes.byref(s), ctypes.byref(a), ctypes.byref(g), ctypes.byref(t)),
                "mgr_get_stats")
         return dict(setup_ms=s.value, apply_launches=a.value, graph_nodes=g.value, total_launches=t.value)
+
+
+def host_wait_count() -> int:
+    """Process-wide number of host waits on the GPU (read-backs, synchronisations) issued by the library."""
+    t = ctypes.c_int64()
+    _check(lib().mgr_get_host_waits(ctypes.byref(t)), "mgr_get_host_waits")
+    return t.value
 
 
 def launch_count() -> int:

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <set>
@@ -33,6 +34,9 @@ inline void cuda_check(cudaError_t e, const char* what, const char* file, int li
 #define CU(x) ::mgr::cuda_check((x), #x, __FILE__, __LINE__)
 // Every kernel launch of the library is followed by CU_LAUNCH(), which checks it and counts it.
 extern std::atomic<unsigned long long> g_launch_count;
+// Every host wait on a stream (a scalar read-back, a synchronisation) is counted too: in the setup
+// each one leaves the GPU idle while the host reads the value and issues the next launches.
+extern std::atomic<unsigned long long> g_wait_count;
 #define CU_LAUNCH()                                                                  \
   do {                                                                               \
     ::mgr::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__);      \
@@ -90,12 +94,14 @@ struct Prof {
   }
 };
 
+constexpr int PIN_SLOTS = 16;
+
 // Execution context: stream, device error word, allocation accounting.
 struct Ctx {
   Prof* prof = nullptr;
   cudaStream_t s = nullptr;
   int* d_err = nullptr;        // device int, error bits
-  void* h_pinned = nullptr;    // pinned host scratch of 8 bytes for scalar read-backs (may be null)
+  void* h_pinned = nullptr;    // pinned host scratch of PIN_SLOTS 8-byte slots for read-backs (may be null)
   int64_t spgemm_stage = 0;    // staged products per SpGEMM batch (0: the library default)
   int64_t bytes = 0;           // bytes currently allocated through this context
   int64_t peak = 0;
@@ -200,7 +206,36 @@ T read_scalar(Ctx& c, const T* dptr) {
     CU(cudaMemcpyAsync(&h, dptr, sizeof(T), cudaMemcpyDeviceToHost, c.s));
     CU(cudaStreamSynchronize(c.s));
   }
+  ++g_wait_count;
   return h;
+}
+// Waits for the context's stream (counted in g_wait_count).
+inline void host_wait(Ctx& c) {
+  CU(cudaStreamSynchronize(c.s));
+  ++g_wait_count;
+}
+// Several device scalars (at most PIN_SLOTS, 8 bytes each at most) read back with one wait.
+struct ReadItem {
+  const void* src;
+  void* dst;
+  size_t bytes;
+};
+inline void read_back(Ctx& c, std::initializer_list<ReadItem> items) {
+  if (items.size() > (size_t)PIN_SLOTS) throw Error(MGR_ERR_CUDA, "read_back: too many items");
+  char* hp = static_cast<char*>(c.h_pinned);
+  size_t k = 0;
+  for (const ReadItem& it : items) {
+    CU(cudaMemcpyAsync(hp ? hp + 8 * k : it.dst, it.src, it.bytes, cudaMemcpyDeviceToHost, c.s));
+    ++k;
+  }
+  host_wait(c);
+  if (hp) {
+    k = 0;
+    for (const ReadItem& it : items) {
+      memcpy(it.dst, hp + 8 * k, it.bytes);
+      ++k;
+    }
+  }
 }
 void check_errors(Ctx& c, const char* phase);  // reads d_err, throws on set bits, clears it
 
@@ -283,6 +318,9 @@ void fill_f64(Ctx& c, double* p, double v, int64_t n);
 // ---------------------------------------------------------------------------------------------
 // Sparse setup primitives (sparse.cu).  All FP64, deterministic, no fused multiply-add.
 void bsr3_validate(Ctx& c, const mgr_bsr3_t& A, const int8_t* marker);  // throws INVALID_ARG
+// the host checks and the device check, whose error bits the caller reads (check_errors) before any
+// kernel indexes with the pattern
+void bsr3_validate_launch(Ctx& c, const mgr_bsr3_t& A, const int8_t* marker);
 void bsr3_to_csr(Ctx& c, const mgr_bsr3_t& A, DCSR<double>& out);        // exact zeros dropped
 void bsr3_block_inverse(Ctx& c, const mgr_bsr3_t& A, double* binv);      // sets EBIT_SINGULAR
 // C = A * B: structural pattern, each entry summed in ascending intermediate index.
@@ -301,6 +339,8 @@ void sort_rows(Ctx& c, int64_t nr, const int64_t* rp, int32_t* ci, double* v);
 // CSR float copy
 void csr_to_f32(Ctx& c, const DCSR<double>& A, DCSR<float>& B);
 void copy_csr(Ctx& c, const DCSR<double>& A, DCSR<double>& B);
-void csr_gather_rows(Ctx& c, const DCSR<double>& A, const int32_t* rows, int64_t nr, DCSR<double>& B);
+// B = the rows `rows` of A; nnz >= 0: B's entry count, known to the caller (no read-back)
+void csr_gather_rows(Ctx& c, const DCSR<double>& A, const int32_t* rows, int64_t nr, DCSR<double>& B,
+                     int64_t nnz = -1);
 
 }  // namespace mgr

@@ -2,6 +2,7 @@
 // MGR preconditioner) and of the adjoint helpers: BSR SpMV, deterministic multi-dot products with
 // warp-shuffle reductions, Gram-Schmidt updates, solution update, block transpose, outer-product
 // gradient.  Reductions are two-stage with a fixed grid, so results do not depend on timing.
+#include <array>
 #include <map>
 #include <mutex>
 
@@ -58,8 +59,7 @@ void launch_sell_spmv_f64(Ctx& c, const SellPattern& S, const double* vals, cons
 
 // ---- multi-dot ---------------------------------------------------------------------------------
 constexpr int KT = 256;
-constexpr int MD_VEC = 8;        // vectors per block column of the 2-D multi-dot grid
-constexpr int MD_BLOCKS = 1216;  // upper bound of the grids below (8 blocks per SM on 152 SMs)
+constexpr int MD_BLOCKS = 1216;  // upper bound of the one-wave grids below (8 blocks per SM on 152 SMs)
 
 template <int NA>
 __device__ __forceinline__ void block_reduce_store(double (&acc)[NA], int na, double* part) {
@@ -80,120 +80,100 @@ __device__ __forceinline__ void block_reduce_store(double (&acc)[NA], int na, do
   }
 }
 
-// The products of one block: KN vectors (KN <= MD_VEC, a compile-time count, so no FMA of a vector the
-// block does not hold is issued, not even predicated off) and, with DOW, w . w as well.
-template <int KN, bool DOW>
-__device__ __forceinline__ void mdot_rows(int64_t i0, int64_t i1, const double* __restrict__ V, int64_t ldv,
-                                          const double* __restrict__ w, double (&acc)[MD_VEC + 1]) {
-  // pairs of doubles: chunk is even and ldv is even, so every pair is 16-byte aligned
-  for (int64_t i = i0 + 2 * threadIdx.x; i < i1; i += 2 * KT) {
-    if (i + 1 < i1) {
-      double2 wi = *reinterpret_cast<const double2*>(w + i);
-      // one FMA per product: FP64 instructions, not bytes, bound this kernel on this GPU
-#pragma unroll
-      for (int k = 0; k < KN; ++k) {
-        double2 v = __ldg(reinterpret_cast<const double2*>(V + k * ldv + i));
-        acc[k] = fma(v.x, wi.x, acc[k]);
-        acc[k] = fma(v.y, wi.y, acc[k]);
-      }
-      if (DOW) {
-        acc[MD_VEC] = fma(wi.x, wi.x, acc[MD_VEC]);
-        acc[MD_VEC] = fma(wi.y, wi.y, acc[MD_VEC]);
-      }
-    } else {
-      double wi = w[i];
-#pragma unroll
-      for (int k = 0; k < KN; ++k) acc[k] = fma(V[k * ldv + i], wi, acc[k]);
-      if (DOW) acc[MD_VEC] = fma(wi, wi, acc[MD_VEC]);
-    }
-  }
-}
-
-template <bool DOW>
-__device__ __forceinline__ void mdot_rows_kn(int kn, int64_t i0, int64_t i1, const double* __restrict__ V,
-                                             int64_t ldv, const double* __restrict__ w, double (&acc)[MD_VEC + 1]) {
-  static_assert(MD_VEC == 8, "one case per vector count of a block");
-  switch (kn) {
-    case 0: mdot_rows<0, DOW>(i0, i1, V, ldv, w, acc); break;  // w . w alone
-    case 1: mdot_rows<1, DOW>(i0, i1, V, ldv, w, acc); break;
-    case 2: mdot_rows<2, DOW>(i0, i1, V, ldv, w, acc); break;
-    case 3: mdot_rows<3, DOW>(i0, i1, V, ldv, w, acc); break;
-    case 4: mdot_rows<4, DOW>(i0, i1, V, ldv, w, acc); break;
-    case 5: mdot_rows<5, DOW>(i0, i1, V, ldv, w, acc); break;
-    case 6: mdot_rows<6, DOW>(i0, i1, V, ldv, w, acc); break;
-    case 7: mdot_rows<7, DOW>(i0, i1, V, ldv, w, acc); break;
-    default: mdot_rows<8, DOW>(i0, i1, V, ldv, w, acc); break;
-  }
-}
-
-// Multi-dot: block x handles row chunk x for every vector group g (vectors 8g .. 8g+7) in turn, so
-// every block streams the same number of vectors (a 2-D grid of group blocks left the blocks of a
-// short last group idle for most of the launch).  Group 0 also accumulates w . w.  Partial sums go
-// to part[k * nx + x] (k = nv for w . w).
-__global__ void __launch_bounds__(KT) k_mdot(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
-                                             const double* __restrict__ w, int ww, int ng, int nx, int64_t chunk,
-                                             double* __restrict__ part) {
-  pdl_wait();
-  const int x = blockIdx.x;
-  const int64_t i0 = (int64_t)x * chunk, i1 = i0 + chunk < n ? i0 + chunk : n;
-  __shared__ double sh[KT / 32][MD_VEC + 1];
+// Sums of NA per-thread values over the block (KT threads), thread t < NA ending with sum t.  Within a
+// warp a reduce-scatter: each step keeps half of the values and adds the partner lane's copy of that
+// half (P = 32 values cost 31 FP64 additions per lane, a shuffle tree per value 160); a shuffle tree
+// per value when NA is small.
+template <int NA>
+__device__ __forceinline__ double block_reduce_many(const double (&acc)[NA]) {
+  __shared__ double red[KT / 32][NA];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int g = 0; g < ng; ++g) {
-    const int k0 = g * MD_VEC;
-    const int kn = nv - k0 < MD_VEC ? nv - k0 : MD_VEC;
-    const bool dow = ww && g == 0;
-    double acc[MD_VEC + 1];
+  if constexpr (NA * 5 <= 31) {
 #pragma unroll
-    for (int k = 0; k <= MD_VEC; ++k) acc[k] = 0.0;
-    // kn and dow are uniform over the block
-    if (dow) mdot_rows_kn<true>(kn, i0, i1, V + k0 * ldv, ldv, w, acc);
-    else mdot_rows_kn<false>(kn, i0, i1, V + k0 * ldv, ldv, w, acc);
-    // reduce-scatter of the 8 vector sums across the warp (FP64 adds are the scarce instructions): at
-    // offsets 16, 8, 4 each lane keeps half of its values and adds its partner's copy of that half
-    // (4 + 2 + 1 adds), then a butterfly over offsets 2 and 1; lane L ends with the warp's sum of
-    // vector ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).  9 adds instead of 40.
-    {
-      static_assert(MD_VEC == 8, "the reduce-scatter is written for 8 vectors per block");
-      double h4[4], h2[2], h1;
-      const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+    for (int k = 0; k < NA; ++k) {
+      const double v = warp_sum(acc[k]);
+      if (lane == 0) red[wid][k] = v;
+    }
+  } else {
+    constexpr int P = NA <= 32 ? 32 : 64;
+    double v[P];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        double send = b16 ? acc[j] : acc[j + 4];
-        double keep = b16 ? acc[j + 4] : acc[j];
-        h4[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-      }
+    for (int k = 0; k < P; ++k) v[k] = k < NA ? acc[k] : 0.0;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        double send = b8 ? h4[j] : h4[j + 2];
-        double keep = b8 ? h4[j + 2] : h4[j];
-        h2[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-      }
-      {
-        double send = b4 ? h2[0] : h2[1];
-        double keep = b4 ? h2[1] : h2[0];
-        h1 = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-      }
-      h1 += __shfl_xor_sync(0xffffffffu, h1, 2);
-      h1 += __shfl_xor_sync(0xffffffffu, h1, 1);
-      if ((lane & 3) == 0) sh[wid][(b16 ? 4 : 0) + (b8 ? 2 : 0) + (b4 ? 1 : 0)] = h1;
-      if (dow) {  // uniform over the block
-        double v = warp_sum(acc[MD_VEC]);
-        if (lane == 0) sh[wid][MD_VEC] = v;
+    for (int o = 16, c = P; o >= 1; o >>= 1, c >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int j = 0; j < c / 2; ++j) {
+        const double lo = v[j], hi = v[j + c / 2];
+        const double send = up ? lo : hi;
+        const double keep = up ? hi : lo;
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
       }
     }
-    __syncthreads();
-    if (threadIdx.x <= MD_VEC) {
-      int k = threadIdx.x;
-      if (k < kn || (k == MD_VEC && dow)) {
-        double s = 0.0;
-        for (int w2 = 0; w2 < KT / 32; ++w2) s += sh[w2][k];
-        int out = (k == MD_VEC) ? nv : k0 + k;
-        part[(int64_t)out * nx + x] = s;
-      }
+    // lane L now holds the warp sums of values (P/32) L + j, j < P/32
+#pragma unroll
+    for (int j = 0; j < P / 32; ++j) {
+      const int k = (P / 32) * lane + j;
+      if (k < NA) red[wid][k] = v[j];
     }
-    __syncthreads();  // sh is reused by the next group
   }
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < NA) {
+#pragma unroll
+    for (int q = 0; q < KT / 32; ++q) s += red[q][threadIdx.x];
+  }
+  return s;
 }
+
+// Multi-dot in one pass over the rows: every thread takes pairs of rows and all NV vectors at once
+// (w read once, one FMA per product, one instantiation per vector count so the k loop is unrolled
+// whole), grid-stride over one resident wave.  Staging the tiles through shared memory with bulk
+// copies, or prefetching the next pair into registers, measured slower: the FP64 pipe, not the
+// loads, sets the pace.  With ww, acc[NV] takes w . w.  Partials: part[k * gridDim.x + x] (a second
+// launch adds them up; the last block doing it in place measured slower, since its serial sum over
+// the blocks' partials is on the critical path).
+template <int NV>
+__global__ void __launch_bounds__(KT) k_mdot(int64_t n, const double* __restrict__ V, int64_t ldv,
+                                             const double* __restrict__ w, int ww, double* __restrict__ part) {
+  pdl_wait();
+  double acc[NV + 1];
+#pragma unroll
+  for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
+  const int64_t n2 = n >> 1;
+  // pairs of doubles: V, w 16-byte aligned and ldv even, so every pair is aligned
+  for (int64_t q = blockIdx.x * (int64_t)KT + threadIdx.x; q < n2; q += (int64_t)gridDim.x * KT) {
+    const int64_t i = 2 * q;
+    const double2 wi = *reinterpret_cast<const double2*>(w + i);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const double2 v = __ldg(reinterpret_cast<const double2*>(V + k * ldv + i));
+      acc[k] = fma(v.x, wi.x, acc[k]);
+      acc[k] = fma(v.y, wi.y, acc[k]);
+    }
+    if (ww) {
+      acc[NV] = fma(wi.x, wi.x, acc[NV]);
+      acc[NV] = fma(wi.y, wi.y, acc[NV]);
+    }
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t i = n - 1;
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = fma(V[k * ldv + i], wi, acc[k]);
+    if (ww) acc[NV] = fma(wi, wi, acc[NV]);
+  }
+  const double s = block_reduce_many<NV + 1>(acc);
+  const int t = threadIdx.x;
+  if (t < NV || (t == NV && ww)) part[(int64_t)t * gridDim.x + blockIdx.x] = s;
+}
+
+using MdotFn = void (*)(int64_t, const double*, int64_t, const double*, int, double*);
+template <int... I>
+constexpr std::array<MdotFn, sizeof...(I)> mdot_table(std::integer_sequence<int, I...>) {
+  return {k_mdot<I + 1>...};
+}
+static const std::array<MdotFn, KRY_MAXV> kMdot = mdot_table(std::make_integer_sequence<int, KRY_MAXV>{});
 
 // out[k] = sum over the nx partials of k, in a fixed order (a warp per k, strided lanes, then a
 // fixed shuffle tree)
@@ -229,28 +209,20 @@ static int one_wave(const void* fn) {
   return nb;
 }
 
-static int md_nx(int64_t n, int64_t* chunk) {
-  int nx = one_wave((const void*)k_mdot);
-  if (nx < 1) nx = 1;
-  int64_t c = (n + nx - 1) / nx;
-  c = (c + 1) & ~int64_t(1);
-  if (c < 2 * KT) c = 2 * KT;
-  *chunk = c;
-  return (int)((n + c - 1) / c);
-}
-
 void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* w, bool want_ww, double* part,
                  double* out) {
   if (nv > KRY_MAXV) throw Error(MGR_ERR_UNSUPPORTED, "multi-dot with more than 32 vectors");
-  int ww = want_ww ? 1 : 0;
-  int ng = (nv + MD_VEC - 1) / MD_VEC;
-  if (ng < 1) ng = 1;
-  int64_t chunk;
-  int nx = md_nx(n, &chunk);
+  const int ww = want_ww ? 1 : 0;
   ProfScope ps(c, "mdot", 8.0 * (nv + 1) * n);
-  launch_pdl(c, k_mdot, nx, KT, 0, n, V, ldv, nv, w, ww, ng, nx, chunk, part);
+  if (nv < 1) {  // w . w alone
+    launch_nrm2sq(c, n, w, part, out);
+    return;
+  }
+  const MdotFn fn = kMdot[nv - 1];
+  const int nx = one_wave((const void*)fn);
+  launch_pdl(c, fn, nx, KT, 0, n, V, ldv, w, ww, part);
   CU_LAUNCH();
-  int na = nv + ww;
+  const int na = nv + ww;
   launch_pdl(c, k_reduce_parts, (na + 7) / 8, 256, 0, nx, na, part, out);
   CU_LAUNCH();
 }
@@ -259,7 +231,9 @@ void launch_mdot(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const 
 // ||v_out||^2 partials when part != nullptr.  v_out may alias w.  NV > 0: the vector count nv is the
 // compile-time NV and the k loop is unrolled whole (no remainder loop that waits for one load at a
 // time); NV = 0 takes nv at run time.  Each entry subtracts its products in ascending k either way.
-template <int NV>
+// NORM: the squared norm is accumulated (an FMA per entry, which the FP64 pipe pays for) only when
+// it is wanted.
+template <int NV, bool NORM>
 __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
                                                 const double* __restrict__ h, const double* __restrict__ sp,
                                                 const double* w, double* vout, double* __restrict__ part) {
@@ -292,8 +266,10 @@ __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restr
     s.x *= sc;
     s.y *= sc;
     *reinterpret_cast<double2*>(vout + i) = s;
-    acc[0] = fma(s.x, s.x, acc[0]);
-    acc[0] = fma(s.y, s.y, acc[0]);
+    if (NORM) {
+      acc[0] = fma(s.x, s.x, acc[0]);
+      acc[0] = fma(s.y, s.y, acc[0]);
+    }
   }
   if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
     int64_t i = n - 1;
@@ -303,18 +279,24 @@ __global__ void __launch_bounds__(KT) k_mupdate(int64_t n, const double* __restr
     vout[i] = s;
     acc[0] += s * s;
   }
-  if (part) block_reduce_store<1>(acc, 1, part);
+  if (NORM) block_reduce_store<1>(acc, 1, part);
 }
 
 using MupdateFn = void (*)(int64_t, const double*, int64_t, int, const double*, const double*, const double*, double*,
                            double*);
-static const MupdateFn kMupdate[KRY_MAXV + 1] = {k_mupdate<0>, k_mupdate<1>, k_mupdate<2>, k_mupdate<3>, k_mupdate<4>, k_mupdate<5>, k_mupdate<6>, k_mupdate<7>, k_mupdate<8>, k_mupdate<9>, k_mupdate<10>, k_mupdate<11>, k_mupdate<12>, k_mupdate<13>, k_mupdate<14>, k_mupdate<15>, k_mupdate<16>, k_mupdate<17>, k_mupdate<18>, k_mupdate<19>, k_mupdate<20>, k_mupdate<21>, k_mupdate<22>, k_mupdate<23>, k_mupdate<24>, k_mupdate<25>, k_mupdate<26>, k_mupdate<27>, k_mupdate<28>, k_mupdate<29>, k_mupdate<30>, k_mupdate<31>, k_mupdate<32>};
+template <bool NORM, int... I>
+constexpr std::array<MupdateFn, sizeof...(I)> mupdate_table(std::integer_sequence<int, I...>) {
+  return {k_mupdate<I, NORM>...};
+}
+static const std::array<MupdateFn, KRY_MAXV + 1> kMupdate[2] = {
+    mupdate_table<false>(std::make_integer_sequence<int, KRY_MAXV + 1>{}),
+    mupdate_table<true>(std::make_integer_sequence<int, KRY_MAXV + 1>{})};
 
 void launch_mupdate(Ctx& c, int64_t n, const double* V, int64_t ldv, int nv, const double* h, const double* scale,
                     const double* w, double* vout, double* part, double* out) {
   if (nv > KRY_MAXV) throw Error(MGR_ERR_UNSUPPORTED, "update with more than 32 vectors");
   ProfScope ps(c, "mupdate", 8.0 * (nv + 2) * n);
-  const MupdateFn fn = kMupdate[nv > 0 ? nv : 0];
+  const MupdateFn fn = kMupdate[out ? 1 : 0][nv > 0 ? nv : 0];
   const int grid = one_wave((const void*)fn);
   launch_pdl(c, fn, grid, KT, 0, n, V, ldv, nv, h, scale, w, vout, out ? part : nullptr);
   CU_LAUNCH();

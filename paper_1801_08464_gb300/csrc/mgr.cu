@@ -653,7 +653,18 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   ProfScope ps_all(c, "setup_total");
   // one batch for the products of a mid-size problem; the lean setup keeps the staging small
   c.spgemm_stage = h.o.spgemm_stage > 1024 ? h.o.spgemm_stage : (h.o.lean ? (int64_t(1) << 27) : (int64_t(1) << 29));
-  bsr3_validate(c, A, marker);
+  // the pattern and marker checks and the number of reductions (the largest marker) with one wait
+  bsr3_validate_launch(c, A, marker);
+  int L;
+  {
+    DBuf<int> mx(c, 1);
+    CU(cudaMemsetAsync(mx.p, 0, sizeof(int), c.s));
+    k_max_marker<<<grid_for(3 * A.nb, 256), 256, 0, c.s>>>(3 * A.nb, marker, mx.p);
+    CU_LAUNCH();
+    int err = 0;
+    read_back(c, {{c.d_err, &err, sizeof(int)}, {mx.p, &L, sizeof(int)}});
+    if (err) check_errors(c, "bsr3_validate");
+  }
   h.nb = A.nb;
   h.nnzb = A.nnzb;
   int64_t n = 3 * A.nb;
@@ -711,7 +722,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
       CU(cudaMalloc(&w.d_err, sizeof(int)));
       CU(cudaMemsetAsync(w.d_err, 0, sizeof(int), c.s));
     }
-    w.h_pinned = h.hpin + 510;
+    w.h_pinned = h.hpin + 512 - PIN_SLOTS;
     w.prof = nullptr;
     w.spgemm_stage = c.spgemm_stage;
     w.num_sms = c.num_sms;
@@ -751,14 +762,6 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
   };
   if (overlap) post([&h, build_sell_binv] { build_sell_binv(h.cw); });
   else build_sell_binv(c);
-  int L;
-  {
-    DBuf<int> mx(c, 1);
-    CU(cudaMemsetAsync(mx.p, 0, sizeof(int), c.s));
-    k_max_marker<<<grid_for(n, 256), 256, 0, c.s>>>(n, marker, mx.p);
-    CU_LAUNCH();
-    L = read_scalar(c, mx.p);
-  }
   h.L = L;
   h.lev.resize(L + 1);
   h.lev[0].n = n;
@@ -837,7 +840,7 @@ void do_setup(mgr_handle_s& h, const mgr_bsr3_t& A, const int8_t* marker) {
     cast_hierarchy(h, A, !overlap);
     alloc_work(h);
   }
-  CU(cudaStreamSynchronize(c.s));
+  host_wait(c);
   h.ready = true;
   h.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -877,7 +880,7 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
   memset(&loc, 0, sizeof loc);
   auto rd = [&](const double* d, int cnt) {
     CU(cudaMemcpyAsync(hp, d, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c.s));
-    CU(cudaStreamSynchronize(c.s));
+    host_wait(c);
   };
   double* V = h.V.p;
   double* Z = h.Z.p;
@@ -962,7 +965,7 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
           launch_mdot(c, n, V, ld, j + 1, w, true, h.part.p, dsc + 96);
           launch_pyth_scale(c, j + 1, dsc + 96, dsc + 96 + j + 1, dsc + 160);
           CU(cudaMemcpyAsync(hp + 96, dsc + 96, sizeof(double) * 66, cudaMemcpyDeviceToHost, c.s));
-          CU(cudaStreamSynchronize(c.s));
+          host_wait(c);
           for (int i = 0; i <= j; ++i) hcol[i] += hp[96 + i];
           double n2 = hp[96 + 64];
           nw = n2 > 0.0 ? std::sqrt(n2) : 0.0;
@@ -1013,7 +1016,7 @@ mgr_status_t do_fgmres(mgr_handle_s& h, const mgr_bsr3_t& A, const double* b, do
       loc.restarts++;
     }
   }
-  CU(cudaStreamSynchronize(c.s));
+  host_wait(c);
   loc.iterations = it;
   loc.status = st;
   loc.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -1145,7 +1148,9 @@ mgr_status_t mgr_create(mgr_handle_t* out, const mgr_options_t* opt, void* strea
     CU(cudaMalloc(&h->c.d_err, sizeof(int)));
     CU(cudaMemset(h->c.d_err, 0, sizeof(int)));
     CU(cudaMallocHost(&h->hpin, 512 * sizeof(double)));
-    h->c.h_pinned = h->hpin + 511;  // the last slot: scalar read-backs of the setup
+    // the last 2 PIN_SLOTS slots: read-backs of the setup (main context, then the second one);
+    // the Krylov read-backs use the first 256
+    h->c.h_pinned = h->hpin + 512 - 2 * PIN_SLOTS;
   });
   if (st != MGR_OK) {
     if (h->c.d_err) cudaFree(h->c.d_err);
@@ -1377,6 +1382,12 @@ mgr_status_t mgr_memory_bytes(mgr_handle_t h, int64_t* bytes) {
 mgr_status_t mgr_memory_peak_bytes(mgr_handle_t h, int64_t* bytes) {
   if (!h || !bytes) return MGR_ERR_INVALID_ARG;
   *bytes = h->c.peak;
+  return MGR_OK;
+}
+
+mgr_status_t mgr_get_host_waits(int64_t* waits) {
+  if (!waits) return MGR_ERR_INVALID_ARG;
+  *waits = (int64_t)g_wait_count;
   return MGR_OK;
 }
 

@@ -4,6 +4,7 @@
 namespace mgr {
 
 std::atomic<unsigned long long> g_launch_count{0};
+std::atomic<unsigned long long> g_wait_count{0};
 
 void* dev_alloc(Ctx& c, size_t bytes) {
   void* p = nullptr;

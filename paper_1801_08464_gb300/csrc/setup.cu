@@ -138,6 +138,18 @@ __global__ void k_i64_add_one(int64_t n, int64_t* a) {
   if (i < n) a[i] += 1;
 }
 
+// Row pointers from per-row counts, without reading the total (the caller sets M.nnz, from a
+// read-back of M.rp[nr] batched with others or from the sizes of other operators), then csr_alloc.
+static void csr_rows(Ctx& c, DCSR<double>& M, int64_t nr, int64_t nc, const int64_t* cnt) {
+  M.nr = nr;
+  M.nc = nc;
+  M.rp.alloc(c, nr + 1);
+  scan_excl_i64(c, cnt, M.rp.p, nr);
+}
+static void csr_alloc(Ctx& c, DCSR<double>& M) {
+  M.ci.alloc(c, M.nnz);
+  M.v.alloc(c, M.nnz);
+}
 static void alloc_csr(Ctx& c, DCSR<double>& M, int64_t nr, int64_t nc, const int64_t* cnt) {
   M.nr = nr;
   M.nc = nc;
@@ -157,8 +169,10 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
     CU_LAUNCH();
     scan_excl_i32(c, ff.p, fpre.p, n);
     scan_excl_i32(c, cf.p, cpre.p, n);
-    L.nF = read_scalar(c, fpre.p + n);
-    L.nC = read_scalar(c, cpre.p + n);
+    int32_t nf = 0, nc = 0;
+    read_back(c, {{fpre.p + n, &nf, sizeof(int32_t)}, {cpre.p + n, &nc, sizeof(int32_t)}});
+    L.nF = nf;
+    L.nC = nc;
     L.F.alloc(c, L.nF);
     L.C.alloc(c, L.nC);
     L.map.alloc(c, n);
@@ -175,35 +189,47 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
                                                 L.dff.p, L.minv.p, c.d_err);
     CU_LAUNCH();
   }
-  check_errors(c, "MGR D_ff");
-  // W_p and A_ff
-  {
-    DBuf<int64_t> cw(c, nF + 1), cfcnt(c, nF + 1);
-    if (nF) {
-      k_count_sel<true><<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, L.map.p, cw.p);
-      CU_LAUNCH();
-      k_count_sel<false><<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, L.map.p, cfcnt.p);
-      CU_LAUNCH();
-    }
-    alloc_csr(c, L.Wp, nF, nC, cw.p);
-    alloc_csr(c, L.Aff, nF, nF, cfcnt.p);
-    if (nF) {
-      k_fill_wp_aff<<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, L.Wp.rp.p,
-                                                    L.Wp.ci.p, L.Wp.v.p, L.Aff.rp.p, L.Aff.ci.p, L.Aff.v.p);
-      CU_LAUNCH();
-    }
-  }
-  // A_cf, W_r, R
-  {
-    DBuf<int64_t> ca(c, nC + 1);
-    k_count_sel<false><<<grid_for(nC, B), B, 0, c.s>>>(nC, L.C.p, A.rp.p, A.ci.p, L.map.p, ca.p);
+  // the sizes of W_p, A_ff and A_cf (and the D_ff check) with one wait; those of W_r, R and P follow
+  // from them
+  DBuf<int64_t> cw(c, nF + 1), cfcnt(c, nF + 1), ca(c, nC + 1);
+  if (nF) {
+    k_count_sel<true><<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, L.map.p, cw.p);
     CU_LAUNCH();
-    alloc_csr(c, L.Acf, nC, nF, ca.p);
+    k_count_sel<false><<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, L.map.p, cfcnt.p);
+    CU_LAUNCH();
+  }
+  k_count_sel<false><<<grid_for(nC, B), B, 0, c.s>>>(nC, L.C.p, A.rp.p, A.ci.p, L.map.p, ca.p);
+  CU_LAUNCH();
+  csr_rows(c, L.Wp, nF, nC, cw.p);
+  csr_rows(c, L.Aff, nF, nF, cfcnt.p);
+  csr_rows(c, L.Acf, nC, nF, ca.p);
+  {
+    int err = 0;
+    read_back(c, {{L.Wp.rp.p + nF, &L.Wp.nnz, sizeof(int64_t)}, {L.Aff.rp.p + nF, &L.Aff.nnz, sizeof(int64_t)},
+                  {L.Acf.rp.p + nC, &L.Acf.nnz, sizeof(int64_t)}, {c.d_err, &err, sizeof(int)}});
+    if (err) check_errors(c, "MGR D_ff");
+  }
+  csr_alloc(c, L.Wp);
+  csr_alloc(c, L.Aff);
+  csr_alloc(c, L.Acf);
+  // W_p and A_ff
+  if (nF) {
+    k_fill_wp_aff<<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, L.Wp.rp.p,
+                                                  L.Wp.ci.p, L.Wp.v.p, L.Aff.rp.p, L.Aff.ci.p, L.Aff.v.p);
+    CU_LAUNCH();
+  }
+  // A_cf, W_r, R: W_r has A_cf's pattern; R's rows hold one more entry than A_cf's (non-injective)
+  // or exactly one (injective)
+  {
     bool noninj = o.restrict_type == 1;
     if (noninj) {
-      alloc_csr(c, L.Wr, nC, nF, ca.p);
+      csr_rows(c, L.Wr, nC, nF, ca.p);
+      L.Wr.nnz = L.Acf.nnz;
+      csr_alloc(c, L.Wr);
       k_i64_add_one<<<grid_for(nC, B), B, 0, c.s>>>(nC, ca.p);
       CU_LAUNCH();
+      csr_rows(c, L.R, nC, n, ca.p);
+      L.R.nnz = L.Acf.nnz + nC;
     } else {
       L.Wr.nr = nC; L.Wr.nc = nF; L.Wr.nnz = 0;
       L.Wr.rp.alloc(c, nC + 1);
@@ -211,8 +237,10 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
       L.Wr.ci.alloc(c, 0);
       L.Wr.v.alloc(c, 0);
       fill_i64(c, ca.p, 1, nC);
+      csr_rows(c, L.R, nC, n, ca.p);
+      L.R.nnz = nC;
     }
-    alloc_csr(c, L.R, nC, n, ca.p);
+    csr_alloc(c, L.R);
     k_fill_acf_wr<<<grid_for(nC, B), B, 0, c.s>>>(nC, L.C.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, noninj ? 1 : 0,
                                                    L.Acf.rp.p, L.Acf.ci.p, L.Acf.v.p, L.Wr.rp.p, L.Wr.ci.p, L.Wr.v.p,
                                                    L.R.rp.p, L.R.ci.p, L.R.v.p);
@@ -223,7 +251,10 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
     DBuf<int64_t> cp(c, n + 1);
     k_p_count<<<grid_for(n, B), B, 0, c.s>>>(n, L.map.p, L.Wp.rp.p, cp.p);
     CU_LAUNCH();
-    alloc_csr(c, L.P, n, nC, cp.p);
+    // W_p's entries and one per C point
+    csr_rows(c, L.P, n, nC, cp.p);
+    L.P.nnz = L.Wp.nnz + nC;
+    csr_alloc(c, L.P);
     k_p_fill<<<grid_for(n, B), B, 0, c.s>>>(n, L.map.p, L.Wp.rp.p, L.Wp.ci.p, L.Wp.v.p, L.P.rp.p, L.P.ci.p, L.P.v.p);
     CU_LAUNCH();
   }
@@ -241,7 +272,8 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
       spgemm(c, L.R, AP, Anext, kRAP[li]);
     } else {
       DCSR<double> AC;
-      csr_gather_rows(c, A, L.C.p, nC, AC);
+      // the C rows of A hold every entry the F rows (split into W_p and A_ff) do not
+      csr_gather_rows(c, A, L.C.p, nC, AC, A.nnz - L.Wp.nnz - L.Aff.nnz);
       spgemm(c, AC, L.P, Anext, kRAP[li], true);
     }
   }
@@ -401,9 +433,13 @@ __global__ void k_pmis_select(int64_t n, const int64_t* srp, const int32_t* sci,
   }
   nc[i] = 1;
 }
-__global__ void k_pmis_mark_c(int64_t n, const int8_t* nc, int8_t* st) {
+// the selected points become C; *ncnt counts the C points (one atomic per warp)
+__global__ void k_pmis_mark_c(int64_t n, const int8_t* nc, int8_t* st, int* ncnt) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n && nc[i]) st[i] = 1;
+  const bool sel = i < n && nc[i];
+  if (sel) st[i] = 1;
+  const unsigned m = __ballot_sync(0xffffffffu, sel);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(ncnt, __popc(m));
 }
 // undecided points that strongly depend on a C point become F; count what stays undecided
 __global__ void k_pmis_mark_f(int64_t n, const int64_t* srp, const int32_t* sci, int8_t* st, int* und) {
@@ -484,17 +520,13 @@ __device__ __forceinline__ bool opposite_bits(double a, double d) {
 constexpr int EXT_WARPS = 4;
 constexpr int EXT_CAP = 256;
 
-__global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* srp,
-                                const int32_t* sci, const int8_t* cf, const int32_t* cidx, const int32_t* cfine,
-                                const int64_t* prp, const int32_t* pci, double* pv, double* den_g, double* q_g,
-                                int8_t* rowzero, const int32_t* rows, int64_t nrows) {
-  __shared__ double s_wt[EXT_WARPS][EXT_CAP], s_kt[EXT_WARPS][EXT_CAP];
-  __shared__ int8_t s_wf[EXT_WARPS][EXT_CAP], s_kf[EXT_WARPS][EXT_CAP];
-  // the rows listed by the shared-memory kernel (a warp per listed row)
-  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (r >= nrows) return;
-  const int64_t i = rows[r];
+__device__ __forceinline__ void extpi_full_row(int64_t i, const int64_t* rp, const int32_t* ci, const double* v,
+                                               const int64_t* srp, const int32_t* sci, const int8_t* cf,
+                                               const int32_t* cidx, const int32_t* cfine, const int64_t* prp,
+                                               const int32_t* pci, double* pv, double* den_g, double* q_g,
+                                               int8_t* rowzero, double* s_wt_w, double* s_kt_w, int8_t* s_wf_w,
+                                               int8_t* s_kf_w) {
+  const int lane = threadIdx.x & 31;
   if (cf[i] == 1) {
     if (lane == 0) { pv[prp[i]] = 1.0; rowzero[i] = 0; }
     return;
@@ -515,7 +547,6 @@ __global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, con
   }
   __syncwarp();
   double at = 0.0;
-  int w = (threadIdx.x >> 5) & (EXT_WARPS - 1);
   int64_t r0 = rp[i], len = rp[i + 1] - r0, ns = s1 - s0;
   if (len <= EXT_CAP && ns <= EXT_CAP) {
     // the terms of the diagonal are formed by the lanes in parallel, then added by lane 0 in order
@@ -523,8 +554,8 @@ __global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, con
       int32_t nn = ci[r0 + t];
       bool lump = nn != i && find_i32(sci, s0, s1, nn) < 0 &&
                   !(cf[nn] == 1 && find_i32(pci, p0, p1, cidx[nn]) >= 0);
-      s_wt[w][t] = lump ? v[r0 + t] : 0.0;
-      s_wf[w][t] = lump;
+      s_wt_w[t] = lump ? v[r0 + t] : 0.0;
+      s_wf_w[t] = lump;
     }
     for (int64_t p = s0 + lane; p < s1; p += 32) {
       int32_t k = sci[p];
@@ -543,16 +574,16 @@ __global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, con
           f = 1;
         }
       }
-      s_kt[w][p - s0] = term;
-      s_kf[w][p - s0] = f;
+      s_kt_w[p - s0] = term;
+      s_kf_w[p - s0] = f;
     }
     __syncwarp();
     if (lane == 0) {
       at = csr_get(rp, ci, v, i, (int32_t)i);
       for (int64_t t = 0; t < len; ++t)
-        if (s_wf[w][t]) at = dd(at, s_wt[w][t]);
+        if (s_wf_w[t]) at = dd(at, s_wt_w[t]);
       for (int64_t t = 0; t < ns; ++t)
-        if (s_kf[w][t]) at = dd(at, s_kt[w][t]);
+        if (s_kf_w[t]) at = dd(at, s_kt_w[t]);
       rowzero[i] = (at == 0.0);
     }
   } else if (lane == 0) {
@@ -592,6 +623,25 @@ __global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(int64_t n, con
       if (opposite(akj, csr_get(rp, ci, v, k, k))) num = dd(num, dm(q_g[p], akj));
     }
     pv[t] = (at != 0.0) ? -dv(num, at) : 0.0;
+  }
+}
+
+// The rows listed by the shared-memory kernel, *nrows of them (a count on the device, so the host
+// does not wait for it): a warp per listed row, warps striding over the list.
+__global__ void __launch_bounds__(32 * EXT_WARPS) k_extpi_weights(const int64_t* rp, const int32_t* ci, const double* v,
+                                                                  const int64_t* srp, const int32_t* sci, const int8_t* cf,
+                                                                  const int32_t* cidx, const int32_t* cfine,
+                                                                  const int64_t* prp, const int32_t* pci, double* pv,
+                                                                  double* den_g, double* q_g, int8_t* rowzero,
+                                                                  const int32_t* rows, const int* nrows) {
+  __shared__ double s_wt[EXT_WARPS][EXT_CAP], s_kt[EXT_WARPS][EXT_CAP];
+  __shared__ int8_t s_wf[EXT_WARPS][EXT_CAP], s_kf[EXT_WARPS][EXT_CAP];
+  const int w = threadIdx.x >> 5;
+  const int nr = *nrows;
+  for (int64_t r = (int64_t)blockIdx.x * EXT_WARPS + w; r < nr; r += (int64_t)gridDim.x * EXT_WARPS) {
+    extpi_full_row(rows[r], rp, ci, v, srp, sci, cf, cidx, cfine, prp, pci, pv, den_g, q_g, rowzero, s_wt[w], s_kt[w],
+                   s_wf[w], s_kf[w]);
+    __syncwarp();
   }
 }
 
@@ -728,23 +778,15 @@ __global__ void __launch_bounds__(EXT_TPB, 12) k_extpi_weights_row(
 }
 
 // pass 1: the rows with rest == 1 (within the caps; others get rest = 2).
-template <int PCAP, int KCAP, int MINB>
-__global__ void __launch_bounds__(32 * EXT_WARPS, MINB) k_extpi_weights_sh(
-    int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
+template <int PCAP, int KCAP>
+__device__ __forceinline__ void extpi_sh_row(
+    int64_t i, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
     const double* __restrict__ diag, const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
     const int8_t* __restrict__ cf, const int32_t* __restrict__ cfine, const int64_t* __restrict__ prp,
     const int32_t* __restrict__ pci, double* __restrict__ pv, int8_t* __restrict__ rowzero, int8_t* __restrict__ rest,
-    const int32_t* __restrict__ rows, int64_t nrows, int32_t* __restrict__ over, int* __restrict__ nover) {
-  __shared__ int32_t s_pf[EXT_WARPS][PCAP];
-  __shared__ double s_num[EXT_WARPS][PCAP];
-  __shared__ int32_t s_s[EXT_WARPS][KCAP];
-  __shared__ int32_t s_k[EXT_WARPS][KCAP];
-  __shared__ double s_aik[EXT_WARPS][KCAP];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the F rows listed by k_extpi_weights_row (a warp per listed row)
-  const int64_t r = (int64_t)blockIdx.x * EXT_WARPS + w;
-  if (r >= nrows) return;
-  const int64_t i = rows[r];
+    int32_t* __restrict__ over, int* __restrict__ nover, int32_t* pf, double* num, int32_t* sr, int32_t* s_k_w,
+    double* s_aik_w) {
+  const int lane = threadIdx.x & 31;
   const int64_t p0 = prp[i], np64 = prp[i + 1] - p0;
   const int64_t s0 = srp[i], ns64 = srp[i + 1] - s0;
   if (np64 > PCAP || ns64 > KCAP) {
@@ -752,9 +794,6 @@ __global__ void __launch_bounds__(32 * EXT_WARPS, MINB) k_extpi_weights_sh(
     return;
   }
   const int np = (int)np64, ns = (int)ns64;
-  int32_t* pf = s_pf[w];
-  double* num = s_num[w];
-  int32_t* sr = s_s[w];
   for (int t = lane; t < np; t += 32) {
     pf[t] = cfine[pci[p0 + t]];
     num[t] = 0.0;
@@ -783,15 +822,15 @@ __global__ void __launch_bounds__(32 * EXT_WARPS, MINB) k_extpi_weights_sh(
     unsigned ms = __ballot_sync(0xffffffffu, sf);
     if (sf) {
       int pos = nk + __popc(ms & ((1u << lane) - 1u));
-      s_k[w][pos] = nn;
-      s_aik[w][pos] = val;
+      s_k_w[pos] = nn;
+      s_aik_w[pos] = val;
     }
     nk += __popc(ms);
   }
   __syncwarp();
   for (int p = 0; p < nk; ++p) {
-    const int32_t k = s_k[w][p];
-    const double aik = s_aik[w][p];
+    const int32_t k = s_k_w[p];
+    const double aik = s_aik_w[p];
     const double akk = diag[k];
     const int64_t k0 = rp[k], k1 = rp[k + 1];
     double den = 0.0, aki = 0.0;
@@ -856,6 +895,30 @@ __global__ void __launch_bounds__(32 * EXT_WARPS, MINB) k_extpi_weights_sh(
   if (lane == 0) { rowzero[i] = (at == 0.0); rest[i] = 0; }
   __syncwarp();
   for (int t = lane; t < np; t += 32) pv[p0 + t] = (at != 0.0) ? -dv(num[t], at) : 0.0;
+}
+
+// The F rows listed by k_extpi_weights_row, *nrows of them (a count on the device, so the host does
+// not wait for it): a warp per listed row, warps striding over the list.
+template <int PCAP, int KCAP, int MINB>
+__global__ void __launch_bounds__(32 * EXT_WARPS, MINB) k_extpi_weights_sh(
+    const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ v,
+    const double* __restrict__ diag, const int64_t* __restrict__ srp, const int32_t* __restrict__ sci,
+    const int8_t* __restrict__ cf, const int32_t* __restrict__ cfine, const int64_t* __restrict__ prp,
+    const int32_t* __restrict__ pci, double* __restrict__ pv, int8_t* __restrict__ rowzero, int8_t* __restrict__ rest,
+    const int32_t* __restrict__ rows, const int* __restrict__ nrows, int32_t* __restrict__ over,
+    int* __restrict__ nover) {
+  __shared__ int32_t s_pf[EXT_WARPS][PCAP];
+  __shared__ double s_num[EXT_WARPS][PCAP];
+  __shared__ int32_t s_s[EXT_WARPS][KCAP];
+  __shared__ int32_t s_k[EXT_WARPS][KCAP];
+  __shared__ double s_aik[EXT_WARPS][KCAP];
+  const int w = threadIdx.x >> 5;
+  const int nr = *nrows;
+  for (int64_t r = (int64_t)blockIdx.x * EXT_WARPS + w; r < nr; r += (int64_t)gridDim.x * EXT_WARPS) {
+    extpi_sh_row<PCAP, KCAP>(rows[r], rp, ci, v, diag, srp, sci, cf, cfine, prp, pci, pv, rowzero, rest, over, nover,
+                             s_pf[w], s_num[w], s_s[w], s_k[w], s_aik[w]);
+    __syncwarp();
+  }
 }
 
 // Keep / truncation: an empty-flagged row keeps nothing; with pmax > 0 a longer F row keeps its pmax
@@ -943,36 +1006,39 @@ static void strength(Ctx& c, const DCSR<double>& A, double theta, DCSR<double>& 
   CU_LAUNCH();
 }
 
-static void pmis(Ctx& c, const DCSR<double>& S, uint64_t seed, int lev, DBuf<int8_t>& cf) {
+// returns the number of C points
+static int64_t pmis(Ctx& c, const DCSR<double>& S, uint64_t seed, int lev, DBuf<int8_t>& cf) {
   int64_t n = S.nr;
   DCSR<double> St;
   transpose(c, S, St);
   DBuf<double> w(c, n);
   DBuf<int8_t> nc(c, n);
-  DBuf<int> und(c, 1);
+  DBuf<int> und(c, 2);  // undecided points, C points
   cf.alloc(c, n);
   const int B = 256;
   uint64_t key = host_splitmix64(seed ^ ((uint64_t)(lev + 1) << 48));
-  CU(cudaMemsetAsync(und.p, 0, sizeof(int), c.s));
+  CU(cudaMemsetAsync(und.p, 0, 2 * sizeof(int), c.s));
   k_pmis_init<<<grid_for(n, B), B, 0, c.s>>>(n, St.rp, key, w.p, cf.p, und.p);
   CU_LAUNCH();
-  int left = read_scalar(c, und.p);
   int rounds = 0;
-  // the undecided count is read back after every second round: a round after the last decision
-  // selects nothing and marks nothing, so the splitting is the same, with half the host round trips
+  // the undecided count is read back after every second round, and not before the first: a round
+  // after the last decision selects nothing and marks nothing, so the splitting is the same, with
+  // fewer host round trips; the C points are counted on the device and read with it
+  int left = 1, ncount = 0;
   while (left > 0) {
     for (int r = 0; r < 2; ++r) {
       if (++rounds > 10000) throw Error(MGR_ERR_CUDA, "PMIS did not terminate");
       k_pmis_select<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, St.rp, St.ci, w.p, cf.p, nc.p);
       CU_LAUNCH();
-      k_pmis_mark_c<<<grid_for(n, B), B, 0, c.s>>>(n, nc.p, cf.p);
+      k_pmis_mark_c<<<grid_for(n, B), B, 0, c.s>>>(n, nc.p, cf.p, und.p + 1);
       CU_LAUNCH();
       CU(cudaMemsetAsync(und.p, 0, sizeof(int), c.s));
       k_pmis_mark_f<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, cf.p, und.p);
       CU_LAUNCH();
     }
-    left = read_scalar(c, und.p);
+    read_back(c, {{und.p, &left, sizeof(int)}, {und.p + 1, &ncount, sizeof(int)}});
   }
+  return ncount;
 }
 
 static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DBuf<int8_t>& cf, int64_t nC, int pmax,
@@ -991,8 +1057,13 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
     DBuf<int64_t> cm(c, n + 1), ct(c, n + 1);
     k_extpi_sel_count<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, cf.p, cm.p, ct.p);
     CU_LAUNCH();
-    M.nr = n; M.nc = n; M.rp.alloc(c, n + 1); M.nnz = counts_to_rowptr(c, cm.p, M.rp.p, n); M.ci.alloc(c, M.nnz);
-    T.nr = n; T.nc = nC; T.rp.alloc(c, n + 1); T.nnz = counts_to_rowptr(c, ct.p, T.rp.p, n); T.ci.alloc(c, T.nnz);
+    M.nr = n; M.nc = n; M.rp.alloc(c, n + 1);
+    T.nr = n; T.nc = nC; T.rp.alloc(c, n + 1);
+    scan_excl_i64(c, cm.p, M.rp.p, n);
+    scan_excl_i64(c, ct.p, T.rp.p, n);
+    read_back(c, {{M.rp.p + n, &M.nnz, sizeof(int64_t)}, {T.rp.p + n, &T.nnz, sizeof(int64_t)}});
+    M.ci.alloc(c, M.nnz);
+    T.ci.alloc(c, T.nnz);
     k_extpi_sel_fill<<<grid_for(n, B), B, 0, c.s>>>(n, S.rp, S.ci, cf.p, cidx.p, M.rp, M.ci, T.rp, T.ci);
     CU_LAUNCH();
   }
@@ -1010,7 +1081,10 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
     DBuf<int64_t> cnt(c, n + 1);
     k_pfull_count<<<grid_for(n, B), B, 0, c.s>>>(n, cf.p, Q.rp, cnt.p);
     CU_LAUNCH();
-    alloc_csr(c, Pf, n, nC, cnt.p);
+    // M has no rows at C points, so Q's F rows hold all its entries: P_full has those and one per C point
+    csr_rows(c, Pf, n, nC, cnt.p);
+    Pf.nnz = Q.nnz + nC;
+    csr_alloc(c, Pf);
     k_pfull_fill<<<grid_for(n, B), B, 0, c.s>>>(n, cf.p, cidx.p, Q.rp, Q.ci, Pf.rp, Pf.ci);
     CU_LAUNCH();
   }
@@ -1028,21 +1102,15 @@ static void extpi(Ctx& c, const DCSR<double>& A, const DCSR<double>& S, const DB
                                                                  list1.p, nl.p);
   CU_LAUNCH();
   // the rows with more interpolation columns than the thread-per-row stage holds (a few %), then
-  // those beyond the warp kernel's caps (rare): launched over their lists only
-  const int n1 = read_scalar(c, nl.p);
-  if (n1 > 0) {
-    k_extpi_weights_sh<EXT_PCAP_L, EXT_KCAP_L, 1><<<grid_for(n1, EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(
-        n, A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p, cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p, list1.p, n1,
-        list2.p, nl.p + 1);
-    CU_LAUNCH();
-    const int n2 = read_scalar(c, nl.p + 1);
-    if (n2 > 0) {
-      k_extpi_weights<<<grid_for((int64_t)n2 * 32, 32 * EXT_WARPS), 32 * EXT_WARPS, 0, c.s>>>(
-          n, A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp, Pf.ci, Pf.v, den.p, q.p, rowzero.p, list2.p,
-          n2);
-      CU_LAUNCH();
-    }
-  }
+  // those beyond the warp kernel's caps (rare): warps stride over their lists, whose lengths stay on
+  // the device
+  k_extpi_weights_sh<EXT_PCAP_L, EXT_KCAP_L, 1><<<8 * c.num_sms, 32 * EXT_WARPS, 0, c.s>>>(
+      A.rp, A.ci, A.v, diag.p, S.rp, S.ci, cf.p, cfine.p, Pf.rp, Pf.ci, Pf.v, rowzero.p, rest.p, list1.p, nl.p, list2.p,
+      nl.p + 1);
+  CU_LAUNCH();
+  k_extpi_weights<<<2 * c.num_sms, 32 * EXT_WARPS, 0, c.s>>>(A.rp, A.ci, A.v, S.rp, S.ci, cf.p, cidx.p, cfine.p, Pf.rp,
+                                                              Pf.ci, Pf.v, den.p, q.p, rowzero.p, list2.p, nl.p + 1);
+  CU_LAUNCH();
   DBuf<int64_t> cnt(c, n + 1);
   k_ptrunc<<<grid_for(n * 32, 128), 128, 0, c.s>>>(n, cf.p, Pf.rp, Pf.v, rowzero.p, pmax, keep.p, scale.p, cnt.p);
   CU_LAUNCH();
@@ -1075,17 +1143,10 @@ void amg_build(Ctx& c, DCSR<double>& A0, bool take, const AmgOpts& o, std::vecto
       ProfScope ps(c, "setup_amg_strength");
       strength(c, L.A, o.theta, L.S);
     }
-    {
-      ProfScope ps(c, "setup_amg_pmis");
-      pmis(c, L.S, o.seed, k, L.cf);
-    }
     int64_t nC;
     {
-      DBuf<int32_t> flag(c, n), pre(c, n + 1);
-      k_flag_c<<<grid_for(n, B), B, 0, c.s>>>(n, L.cf.p, flag.p);
-      CU_LAUNCH();
-      scan_excl_i32(c, flag.p, pre.p, n);
-      nC = read_scalar(c, pre.p + n);
+      ProfScope ps(c, "setup_amg_pmis");
+      nC = pmis(c, L.S, o.seed, k, L.cf);
     }
     if (nC == 0 || nC == n) {
       L.cf.release();
@@ -1101,9 +1162,10 @@ void amg_build(Ctx& c, DCSR<double>& A0, bool take, const AmgOpts& o, std::vecto
       transpose(c, L.P, L.R);
     }
     L.dinv.alloc(c, n);
+    // a zero or non-finite diagonal sets the error word, checked once with the coarsest inverse (the
+    // scalings are first read by the apply)
     k_smoother_diag<<<grid_for(n, B), B, 0, c.s>>>(n, L.A.rp, L.A.ci, L.A.v, o.smoother, o.omega, L.dinv.p, c.d_err);
     CU_LAUNCH();
-    check_errors(c, "AMG smoother diagonal");
     AmgLevel next;
     {
       ProfScope ps(c, "setup_amg_rap");
@@ -1123,7 +1185,7 @@ void amg_build(Ctx& c, DCSR<double>& A0, bool take, const AmgOpts& o, std::vecto
   if (nco > 4096) throw Error(MGR_ERR_UNSUPPORTED, "AMG coarsest grid larger than 4096 rows");
   ProfScope ps(c, "setup_dense_inverse");
   dense_inverse(c, lv.back().A, cinv);
-  check_errors(c, "AMG coarsest inverse");
+  check_errors(c, "AMG smoother diagonal or coarsest inverse");
 }
 
 // ===================================== dense inverse ==========================================

@@ -38,12 +38,15 @@ __global__ void k_bsr_validate(int64_t nb, int64_t nnzb, const int64_t* rp, cons
   if (!ok || !diag) atomicOr(err, EBIT_PATTERN);
 }
 
-void bsr3_validate(Ctx& c, const mgr_bsr3_t& A, const int8_t* marker) {
+void bsr3_validate_launch(Ctx& c, const mgr_bsr3_t& A, const int8_t* marker) {
   if (A.nb <= 0 || A.nnzb < A.nb || !A.rowptr || !A.colind || !A.values)
     throw Error(MGR_ERR_INVALID_ARG, "bsr3: bad sizes or null pointers");
   if (A.nb >= (1ll << 31) / 3) throw Error(MGR_ERR_UNSUPPORTED, "bsr3: 3*nb must fit in int32");
   k_bsr_validate<<<grid_for(A.nb, 256), 256, 0, c.s>>>(A.nb, A.nnzb, A.rowptr, A.colind, marker, c.d_err);
   CU_LAUNCH();
+}
+void bsr3_validate(Ctx& c, const mgr_bsr3_t& A, const int8_t* marker) {
+  bsr3_validate_launch(c, A, marker);
   check_errors(c, "bsr3_validate");
 }
 
@@ -1113,10 +1116,12 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
     CU_LAUNCH();
   }
   DBuf<int64_t> soff(c, m + 1);
-  int64_t nstage = counts_to_rowptr(c, us.p, soff.p, m);
-  int hc[2];
-  CU(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, c.s));
-  CU(cudaStreamSynchronize(c.s));
+  scan_excl_i64(c, us.p, soff.p, m);
+  // one wait for the staged total and the two row classes of the symbolic pass
+  int64_t nstage = 0;
+  int hc[2] = {0, 0};
+  read_back(c, {{soff.p + m, &nstage, sizeof(int64_t)}, {counters.p, &hc[0], sizeof(int)},
+                {counters.p + 1, &hc[1], sizeof(int)}});
   // the fused rows are staged (up to their product count each) in batches of at most
   // stage + FUSE_CAP entries; with several batches, each is packed to its exact size before
   // the next one is staged, so the transient memory follows the output, not the product count
@@ -1131,7 +1136,7 @@ void spgemm(Ctx& c, const DCSR<double>& A, const DCSR<double>& B, DCSR<double>& 
     CU_LAUNCH();
     CU(cudaMemcpyAsync(bst.data(), dbs.p, sizeof(int64_t) * nbatch, cudaMemcpyDeviceToHost, c.s));
     CU(cudaMemcpyAsync(bbase.data(), dbb.p, sizeof(int64_t) * nbatch, cudaMemcpyDeviceToHost, c.s));
-    CU(cudaStreamSynchronize(c.s));
+    host_wait(c);
     for (int64_t b = nbatch - 1; b >= 0; --b) {
       bst[b] = std::min(bst[b], bst[b + 1]);
       bbase[b] = std::min(bbase[b], bbase[b + 1]);
@@ -1283,11 +1288,7 @@ __global__ void __launch_bounds__(32 * SORT_WARPS) k_sort_rows_warp(int64_t nr, 
 }
 
 template <bool HASV>
-__global__ void k_sort_rows_block(const int32_t* rows, const int64_t* rp, int32_t* ci, double* v) {
-  extern __shared__ unsigned char sm_raw[];
-  int32_t* sk = reinterpret_cast<int32_t*>(sm_raw);
-  double* sv = reinterpret_cast<double*>(sm_raw + sizeof(int32_t) * SORT_BCAP);
-  int64_t i = rows[blockIdx.x];
+__device__ void sort_row_block(int64_t i, const int64_t* rp, int32_t* ci, double* v, int32_t* sk, double* sv) {
   int64_t b = rp[i];
   int L = (int)(rp[i + 1] - b);
   if (L > SORT_BCAP) {
@@ -1327,6 +1328,20 @@ __global__ void k_sort_rows_block(const int32_t* rows, const int64_t* rp, int32_
   }
 }
 
+// The rows listed by the warp kernel, *nrows of them (a count on the device, so the host does not
+// wait for it): blocks stride over the list.
+template <bool HASV>
+__global__ void k_sort_rows_block(const int32_t* rows, const int* nrows, const int64_t* rp, int32_t* ci, double* v) {
+  extern __shared__ unsigned char sm_raw[];
+  int32_t* sk = reinterpret_cast<int32_t*>(sm_raw);
+  double* sv = reinterpret_cast<double*>(sm_raw + sizeof(int32_t) * SORT_BCAP);
+  const int nr = *nrows;
+  for (int r = blockIdx.x; r < nr; r += gridDim.x) {
+    sort_row_block<HASV>(rows[r], rp, ci, v, sk, sv);
+    __syncthreads();  // the next row reuses the shared arrays
+  }
+}
+
 void sort_rows(Ctx& c, int64_t nr, const int64_t* rp, int32_t* ci, double* v) {
   if (nr <= 0) return;
   DBuf<int> nbig(c, 1);
@@ -1337,19 +1352,17 @@ void sort_rows(Ctx& c, int64_t nr, const int64_t* rp, int32_t* ci, double* v) {
   else
     k_sort_rows_warp<false><<<grid_for(nr, SORT_WARPS), 32 * SORT_WARPS, 0, c.s>>>(nr, rp, ci, v, nbig.p, big.p);
   CU_LAUNCH();
-  int hb = read_scalar(c, nbig.p);
-  if (hb > 0) {
-    size_t sh = (sizeof(int32_t) + sizeof(double)) * SORT_BCAP;
-    if (v) {
-      CU(cudaFuncSetAttribute(k_sort_rows_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-      k_sort_rows_block<true><<<hb, 512, sh, c.s>>>(big.p, rp, ci, v);
-      CU_LAUNCH();
-    } else {
-      CU(cudaFuncSetAttribute(k_sort_rows_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
-      k_sort_rows_block<false><<<hb, 512, sh, c.s>>>(big.p, rp, ci, v);
-      CU_LAUNCH();
-    }
+  // rows over the warp kernel's cap (rare): a block each, launched without reading their count
+  const size_t sh = (sizeof(int32_t) + sizeof(double)) * SORT_BCAP;
+  const unsigned g = (unsigned)(nr < c.num_sms ? nr : c.num_sms);
+  if (v) {
+    CU(cudaFuncSetAttribute(k_sort_rows_block<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    k_sort_rows_block<true><<<g, 512, sh, c.s>>>(big.p, nbig.p, rp, ci, v);
+  } else {
+    CU(cudaFuncSetAttribute(k_sort_rows_block<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    k_sort_rows_block<false><<<g, 512, sh, c.s>>>(big.p, nbig.p, rp, ci, v);
   }
+  CU_LAUNCH();
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1430,7 +1443,7 @@ __global__ void k_gather_rows_fill(int64_t nr, const int32_t* rows, const int64_
     ov[o + (k - b)] = v[k];
   }
 }
-void csr_gather_rows(Ctx& c, const DCSR<double>& A, const int32_t* rows, int64_t nr, DCSR<double>& B) {
+void csr_gather_rows(Ctx& c, const DCSR<double>& A, const int32_t* rows, int64_t nr, DCSR<double>& B, int64_t nnz) {
   DBuf<int64_t> cnt(c, nr + 1);
   B.nr = nr;
   B.nc = A.nc;
@@ -1439,7 +1452,12 @@ void csr_gather_rows(Ctx& c, const DCSR<double>& A, const int32_t* rows, int64_t
     k_gather_rows_count<<<grid_for(nr, 256), 256, 0, c.s>>>(nr, rows, A.rp, cnt.p);
     CU_LAUNCH();
   }
-  B.nnz = counts_to_rowptr(c, cnt.p, B.rp.p, nr);
+  if (nnz >= 0) {
+    scan_excl_i64(c, cnt.p, B.rp.p, nr);
+    B.nnz = nnz;
+  } else {
+    B.nnz = counts_to_rowptr(c, cnt.p, B.rp.p, nr);
+  }
   B.ci.alloc(c, B.nnz);
   B.v.alloc(c, B.nnz);
   if (nr > 0) {
