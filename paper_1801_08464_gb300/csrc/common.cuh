@@ -298,6 +298,33 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Row copies by groups of RG lanes (a warp takes 32 / RG rows): lane g of a group takes entries g,
+// g + RG, ... of its row, and the output position of an entry is its row's running offset plus the
+// number of lower lanes of its group that write in the same round (a ballot masked to the group), so
+// a round writes RG consecutive entries of a row instead of one entry of each of 32 rows.
+constexpr int RG = 8;
+struct RowGroup {
+  int g;           // lane within the group
+  unsigned gmask;  // the group's lanes
+  unsigned below;  // the group's lanes below this one
+};
+__device__ __forceinline__ RowGroup row_group() {
+  const int lane = threadIdx.x & 31;
+  RowGroup r;
+  r.g = lane & (RG - 1);
+  r.gmask = ((1u << RG) - 1u) << (lane & ~(RG - 1));
+  r.below = r.gmask & ((1u << lane) - 1u);
+  return r;
+}
+__device__ __forceinline__ int warp_max_int(int x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -70,46 +70,117 @@ __global__ void k_count_sel(int64_t nr, const int32_t* rows, const int64_t* rp, 
   cnt[r] = s;
 }
 
-// W_p = -D_ff^-1 A_fc (rows F, coarse columns) and A_ff (rows F, F-local columns)
-__global__ void k_fill_wp_aff(int64_t nF, const int32_t* F, const int64_t* rp, const int32_t* ci, const double* v,
-                              const int32_t* map, const double* dff, const int64_t* wrp, int32_t* wci, double* wv,
-                              const int64_t* frp, int32_t* fci, double* fv) {
-  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (f >= nF) return;
-  int32_t i = F[f];
-  int64_t ow = wrp[f], of = frp[f];
-  double d = dff[f];
-  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-    int32_t m = map[ci[k]];
-    if (m >= 0) { wci[ow] = m; wv[ow] = -dv(v[k], d); ++ow; }
-    else { fci[of] = -m - 1; fv[of] = v[k]; ++of; }
+// W_p = -D_ff^-1 A_fc (rows F, coarse columns) and A_ff (rows F, F-local columns); a group of RG
+// lanes per F row, entries in row order
+__global__ void __launch_bounds__(256) k_fill_wp_aff(int64_t nF, const int32_t* F, const int64_t* rp,
+                                                     const int32_t* ci, const double* v, const int32_t* map,
+                                                     const double* dff, const int64_t* wrp, int32_t* wci, double* wv,
+                                                     const int64_t* frp, int32_t* fci, double* fv) {
+  const RowGroup G = row_group();
+  const int64_t f = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / RG;
+  const bool act = f < nF;
+  int64_t k0 = 0, ow = 0, of = 0;
+  int len = 0;
+  double d = 1.0;
+  if (act) {
+    const int32_t i = F[f];
+    k0 = rp[i];
+    len = (int)(rp[i + 1] - k0);
+    ow = wrp[f];
+    of = frp[f];
+    d = dff[f];
+  }
+  const int rounds = warp_max_int((len + RG - 1) / RG);
+  for (int r = 0; r < rounds; ++r) {
+    const int t = r * RG + G.g;
+    const bool in = act && t < len;
+    int32_t m = 0;
+    double x = 0.0;
+    if (in) {
+      m = map[ci[k0 + t]];
+      x = v[k0 + t];
+    }
+    const unsigned bc = __ballot_sync(0xffffffffu, in && m >= 0) & G.gmask;
+    const unsigned bf = __ballot_sync(0xffffffffu, in && m < 0) & G.gmask;
+    if (in) {
+      if (m >= 0) {
+        const int64_t o = ow + __popc(bc & G.below);
+        wci[o] = m;
+        wv[o] = -dv(x, d);
+      } else {
+        const int64_t o = of + __popc(bf & G.below);
+        fci[o] = -m - 1;
+        fv[o] = x;
+      }
+    }
+    ow += __popc(bc);
+    of += __popc(bf);
   }
 }
 
 // A_cf (rows C, F-local columns), and for a non-injective restriction W_r = -A_cf D_ff^-1 and the
-// rows of R = [W_r, I] in fine column order (the 1 placed at the C point's own column).
-__global__ void k_fill_acf_wr(int64_t nC, const int32_t* C, const int64_t* rp, const int32_t* ci, const double* v,
-                              const int32_t* map, const double* dff, int noninj, const int64_t* arp, int32_t* aci,
-                              double* av, const int64_t* wrp, int32_t* wci, double* wv, const int64_t* rrp, int32_t* rci,
-                              double* rv) {
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= nC) return;
-  int32_t i = C[c];
-  int64_t oa = arp[c], ow = noninj ? wrp[c] : 0, orr = rrp[c];
-  bool placed = false;
-  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-    int32_t j = ci[k], m = map[j];
-    if (m >= 0) continue;
-    int32_t f = -m - 1;
-    aci[oa] = f; av[oa] = v[k]; ++oa;
-    if (noninj) {
-      double w = -dv(v[k], dff[f]);
-      wci[ow] = f; wv[ow] = w; ++ow;
-      if (!placed && j > i) { rci[orr] = i; rv[orr] = 1.0; ++orr; placed = true; }
-      rci[orr] = j; rv[orr] = w; ++orr;
-    }
+// rows of R = [W_r, I] in fine column order: the 1 at the C point's own column i follows the F
+// entries with columns below i.  A group of RG lanes per C row.
+__global__ void __launch_bounds__(256) k_fill_acf_wr(int64_t nC, const int32_t* C, const int64_t* rp,
+                                                     const int32_t* ci, const double* v, const int32_t* map,
+                                                     const double* dff, int noninj, const int64_t* arp, int32_t* aci,
+                                                     double* av, const int64_t* wrp, int32_t* wci, double* wv,
+                                                     const int64_t* rrp, int32_t* rci, double* rv) {
+  const RowGroup G = row_group();
+  const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / RG;
+  const bool act = c < nC;
+  int32_t i = 0;
+  int64_t k0 = 0, oa = 0, ow = 0, orr = 0;
+  int len = 0, nless = 0;
+  if (act) {
+    i = C[c];
+    k0 = rp[i];
+    len = (int)(rp[i + 1] - k0);
+    oa = arp[c];
+    ow = noninj ? wrp[c] : 0;
+    orr = rrp[c];
   }
-  if (!placed) { rci[orr] = i; rv[orr] = 1.0; }
+  const int64_t r0 = orr;
+  const int rounds = warp_max_int((len + RG - 1) / RG);
+  for (int r = 0; r < rounds; ++r) {
+    const int t = r * RG + G.g;
+    const bool in = act && t < len;
+    int32_t j = 0, m = 0;
+    double x = 0.0;
+    if (in) {
+      j = ci[k0 + t];
+      m = map[j];
+      x = v[k0 + t];
+    }
+    const bool isf = in && m < 0;
+    const unsigned bf = __ballot_sync(0xffffffffu, isf) & G.gmask;
+    const unsigned bl = __ballot_sync(0xffffffffu, isf && j < i) & G.gmask;
+    if (isf) {
+      const int rank = __popc(bf & G.below);
+      const int32_t f = -m - 1;
+      aci[oa + rank] = f;
+      av[oa + rank] = x;
+      if (noninj) {
+        const double w = -dv(x, dff[f]);
+        wci[ow + rank] = f;
+        wv[ow + rank] = w;
+        const int64_t o = orr + rank + (j > i ? 1 : 0);
+        rci[o] = j;
+        rv[o] = w;
+      }
+    }
+    oa += __popc(bf);
+    if (noninj) {
+      ow += __popc(bf);
+      orr += __popc(bf);
+    }
+    nless += __popc(bl);
+  }
+  if (act && G.g == 0) {
+    const int64_t o = r0 + (noninj ? nless : 0);
+    rci[o] = i;
+    rv[o] = 1.0;
+  }
 }
 
 // P = [W_p; I] in fine row order
@@ -214,7 +285,7 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
   csr_alloc(c, L.Acf);
   // W_p and A_ff
   if (nF) {
-    k_fill_wp_aff<<<grid_for(nF, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, L.Wp.rp.p,
+    k_fill_wp_aff<<<grid_for(nF * RG, B), B, 0, c.s>>>(nF, L.F.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, L.Wp.rp.p,
                                                   L.Wp.ci.p, L.Wp.v.p, L.Aff.rp.p, L.Aff.ci.p, L.Aff.v.p);
     CU_LAUNCH();
   }
@@ -241,7 +312,7 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
       L.R.nnz = nC;
     }
     csr_alloc(c, L.R);
-    k_fill_acf_wr<<<grid_for(nC, B), B, 0, c.s>>>(nC, L.C.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, noninj ? 1 : 0,
+    k_fill_acf_wr<<<grid_for(nC * RG, B), B, 0, c.s>>>(nC, L.C.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, noninj ? 1 : 0,
                                                    L.Acf.rp.p, L.Acf.ci.p, L.Acf.v.p, L.Wr.rp.p, L.Wr.ci.p, L.Wr.v.p,
                                                    L.R.rp.p, L.R.ci.p, L.R.v.p);
     CU_LAUNCH();

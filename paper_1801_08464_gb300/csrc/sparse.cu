@@ -63,18 +63,42 @@ __global__ void k_bsr_csr_count(int64_t nb, const int64_t* rp, const double* v, 
     for (int q = 0; q < 3; ++q) s += (v[9 * k + 3 * p + q] != 0.0);
   cnt[r] = s;
 }
-__global__ void k_bsr_csr_fill(int64_t nb, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* orp,
-                               int32_t* oci, double* ov) {
-  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (r >= 3 * nb) return;
-  int64_t I = r / 3;
-  int p = (int)(r - 3 * I);
-  int64_t o = orp[r];
-  for (int64_t k = rp[I]; k < rp[I + 1]; ++k)
-    for (int q = 0; q < 3; ++q) {
-      double x = v[9 * k + 3 * p + q];
-      if (x != 0.0) { oci[o] = 3 * ci[k] + q; ov[o] = x; ++o; }
+// a group of RG lanes per scalar row: entry t of row 3I+p is value q = t % 3 of block b0 + t / 3
+__global__ void __launch_bounds__(256) k_bsr_csr_fill(int64_t nb, const int64_t* rp, const int32_t* ci,
+                                                      const double* v, const int64_t* orp, int32_t* oci, double* ov) {
+  const RowGroup G = row_group();
+  const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / RG;
+  const bool act = r < 3 * nb;
+  int64_t b0 = 0, o = 0;
+  int p = 0, len = 0;
+  if (act) {
+    const int64_t I = r / 3;
+    p = (int)(r - 3 * I);
+    b0 = rp[I];
+    len = 3 * (int)(rp[I + 1] - b0);
+    o = orp[r];
+  }
+  const int rounds = warp_max_int((len + RG - 1) / RG);
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int t = rd * RG + G.g;
+    const bool in = act && t < len;
+    double x = 0.0;
+    int64_t k = 0;
+    int q = 0;
+    if (in) {
+      k = b0 + t / 3;
+      q = t - 3 * (t / 3);
+      x = v[9 * k + 3 * p + q];
     }
+    const bool nz = in && x != 0.0;
+    const unsigned bn = __ballot_sync(0xffffffffu, nz) & G.gmask;
+    if (nz) {
+      const int64_t d = o + __popc(bn & G.below);
+      oci[d] = 3 * ci[k] + q;
+      ov[d] = x;
+    }
+    o += __popc(bn);
+  }
 }
 
 void bsr3_to_csr(Ctx& c, const mgr_bsr3_t& A, DCSR<double>& out) {
@@ -87,7 +111,8 @@ void bsr3_to_csr(Ctx& c, const mgr_bsr3_t& A, DCSR<double>& out) {
   out.nnz = counts_to_rowptr(c, cnt.p, out.rp.p, n);
   out.ci.alloc(c, out.nnz);
   out.v.alloc(c, out.nnz);
-  k_bsr_csr_fill<<<grid_for(n, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.colind, A.values, out.rp.p, out.ci.p, out.v.p);
+  k_bsr_csr_fill<<<grid_for(n * RG, 256), 256, 0, c.s>>>(A.nb, A.rowptr, A.colind, A.values, out.rp.p, out.ci.p,
+                                                         out.v.p);
   CU_LAUNCH();
 }
 
