@@ -119,68 +119,32 @@ __global__ void __launch_bounds__(256) k_fill_wp_aff(int64_t nF, const int32_t* 
 }
 
 // A_cf (rows C, F-local columns), and for a non-injective restriction W_r = -A_cf D_ff^-1 and the
-// rows of R = [W_r, I] in fine column order: the 1 at the C point's own column i follows the F
-// entries with columns below i.  A group of RG lanes per C row.
-__global__ void __launch_bounds__(256) k_fill_acf_wr(int64_t nC, const int32_t* C, const int64_t* rp,
-                                                     const int32_t* ci, const double* v, const int32_t* map,
-                                                     const double* dff, int noninj, const int64_t* arp, int32_t* aci,
-                                                     double* av, const int64_t* wrp, int32_t* wci, double* wv,
-                                                     const int64_t* rrp, int32_t* rci, double* rv) {
-  const RowGroup G = row_group();
-  const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / RG;
-  const bool act = c < nC;
-  int32_t i = 0;
-  int64_t k0 = 0, oa = 0, ow = 0, orr = 0;
-  int len = 0, nless = 0;
-  if (act) {
-    i = C[c];
-    k0 = rp[i];
-    len = (int)(rp[i + 1] - k0);
-    oa = arp[c];
-    ow = noninj ? wrp[c] : 0;
-    orr = rrp[c];
-  }
-  const int64_t r0 = orr;
-  const int rounds = warp_max_int((len + RG - 1) / RG);
-  for (int r = 0; r < rounds; ++r) {
-    const int t = r * RG + G.g;
-    const bool in = act && t < len;
-    int32_t j = 0, m = 0;
-    double x = 0.0;
-    if (in) {
-      j = ci[k0 + t];
-      m = map[j];
-      x = v[k0 + t];
-    }
-    const bool isf = in && m < 0;
-    const unsigned bf = __ballot_sync(0xffffffffu, isf) & G.gmask;
-    const unsigned bl = __ballot_sync(0xffffffffu, isf && j < i) & G.gmask;
-    if (isf) {
-      const int rank = __popc(bf & G.below);
-      const int32_t f = -m - 1;
-      aci[oa + rank] = f;
-      av[oa + rank] = x;
-      if (noninj) {
-        const double w = -dv(x, dff[f]);
-        wci[ow + rank] = f;
-        wv[ow + rank] = w;
-        const int64_t o = orr + rank + (j > i ? 1 : 0);
-        rci[o] = j;
-        rv[o] = w;
-      }
-    }
-    oa += __popc(bf);
+// rows of R = [W_r, I] in fine column order (the 1 placed at the C point's own column).  A thread per
+// C row: the group-of-lanes form of the other row copies measured slower here (0.72 against 0.48 ms
+// per launch at 128^3), its extra ballots and dependent gathers (column, map, D_ff) per round
+// outweighing the coalesced writes.
+__global__ void k_fill_acf_wr(int64_t nC, const int32_t* C, const int64_t* rp, const int32_t* ci, const double* v,
+                              const int32_t* map, const double* dff, int noninj, const int64_t* arp, int32_t* aci,
+                              double* av, const int64_t* wrp, int32_t* wci, double* wv, const int64_t* rrp, int32_t* rci,
+                              double* rv) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= nC) return;
+  int32_t i = C[c];
+  int64_t oa = arp[c], ow = noninj ? wrp[c] : 0, orr = rrp[c];
+  bool placed = false;
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+    int32_t j = ci[k], m = map[j];
+    if (m >= 0) continue;
+    int32_t f = -m - 1;
+    aci[oa] = f; av[oa] = v[k]; ++oa;
     if (noninj) {
-      ow += __popc(bf);
-      orr += __popc(bf);
+      double w = -dv(v[k], dff[f]);
+      wci[ow] = f; wv[ow] = w; ++ow;
+      if (!placed && j > i) { rci[orr] = i; rv[orr] = 1.0; ++orr; placed = true; }
+      rci[orr] = j; rv[orr] = w; ++orr;
     }
-    nless += __popc(bl);
   }
-  if (act && G.g == 0) {
-    const int64_t o = r0 + (noninj ? nless : 0);
-    rci[o] = i;
-    rv[o] = 1.0;
-  }
+  if (!placed) { rci[orr] = i; rv[orr] = 1.0; }
 }
 
 // P = [W_p; I] in fine row order
@@ -312,7 +276,7 @@ void mgr_reduce_level(Ctx& c, MgrLevel& L, int l, const LevelOpts& o, DCSR<doubl
       L.R.nnz = nC;
     }
     csr_alloc(c, L.R);
-    k_fill_acf_wr<<<grid_for(nC * RG, B), B, 0, c.s>>>(nC, L.C.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, noninj ? 1 : 0,
+    k_fill_acf_wr<<<grid_for(nC, B), B, 0, c.s>>>(nC, L.C.p, A.rp.p, A.ci.p, A.v.p, L.map.p, L.dff.p, noninj ? 1 : 0,
                                                    L.Acf.rp.p, L.Acf.ci.p, L.Acf.v.p, L.Wr.rp.p, L.Wr.ci.p, L.Wr.v.p,
                                                    L.R.rp.p, L.R.ci.p, L.R.v.p);
     CU_LAUNCH();
