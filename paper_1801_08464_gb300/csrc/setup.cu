@@ -1011,9 +1011,15 @@ __global__ void k_smoother_diag(int64_t n, const int64_t* rp, const int32_t* ci,
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double d = 0.0, l1 = 0.0;
-  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-    if (ci[k] == i) d = v[k];
-    else l1 = dd(l1, fabs(v[k]));
+  // the l1 sum (FP64 additions in row order) only for the l1-Jacobi scaling that uses it
+  if (type == 1) {
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      if (ci[k] == i) d = v[k];
+      else l1 = dd(l1, fabs(v[k]));
+    }
+  } else {
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      if (ci[k] == i) d = v[k];
   }
   double den = (type == 1) ? dd(d, (d >= 0.0) ? l1 : -l1) : d;
   if (den == 0.0 || !isfinite(den)) { atomicOr(err, EBIT_SINGULAR); dinv[i] = 0.0; return; }
