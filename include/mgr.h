@@ -196,6 +196,14 @@ mgr_status_t mgr_get_stats(mgr_handle_t h, double* setup_ms, int64_t* apply_laun
  * synchronisations.  A measurement aid: in the setup each wait leaves the GPU idle until the host
  * has issued the next launch.  NULL: MGR_ERR_INVALID_ARG. */
 mgr_status_t mgr_get_host_waits(int64_t* waits);
+/* Index audit of a set-up handle (host out, synchronises): on the device, every column index the
+ * apply and the Krylov products gather with is recomputed from its stored form (CSR columns, sliced
+ * 32-bit columns, slice base + 16-bit offset, row + offset-table code) and checked against the
+ * operator's column count, with the slice offsets, row pointers, row permutations and the F/C/map
+ * lists of every level; *bad = the number of violations (0 for a sound hierarchy).  A debugging aid
+ * that stands in for a memory checker: an index out of range here is an out-of-bounds gather in
+ * the apply.  Before mgr_setup: MGR_ERR_STATE. */
+mgr_status_t mgr_audit(mgr_handle_t h, int64_t* bad);
 
 /* Per-kernel timing on the handle's stream: enable = 1 starts recording CUDA events around every
  * launch of the named kernels and clears earlier totals, enable = 0 stops.  mgr_kernel_time returns

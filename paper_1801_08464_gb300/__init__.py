@@ -64,7 +64,7 @@ class SolveInfo(ctypes.Structure):
 EXPORTS = ["mgr_status_string", "mgr_options_default", "mgr_create", "mgr_setup", "mgr_apply", "fgmres_solve",
            "mgr_apply_transpose", "fgmres_solve_transpose",
            "mgr_destroy", "mgr_get_levels", "mgr_matrix_shape", "mgr_copy_matrix", "mgr_vector_len",
-           "mgr_copy_vector", "mgr_memory_bytes", "mgr_memory_peak_bytes", "mgr_get_stats", "mgr_get_host_waits", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
+           "mgr_copy_vector", "mgr_memory_bytes", "mgr_memory_peak_bytes", "mgr_get_stats", "mgr_get_host_waits", "mgr_audit", "mgr_bsr3_spmv", "mgr_bsr3_transpose",
            "mgr_bsr3_outer_grad", "mgr_profile", "mgr_profile_select", "mgr_kernel_time",
            "mgr_kernel_bytes", "mgr_kernel_bytes_stored", "mgr_probe_fp64_fma"]
 
@@ -98,6 +98,7 @@ def lib():
         L.mgr_memory_peak_bytes.argtypes = [vp, P(i64)]
         L.mgr_get_stats.argtypes = [vp, P(ctypes.c_double), P(i64), P(i64), P(i64)]
         L.mgr_get_host_waits.argtypes = [P(i64)]
+        L.mgr_audit.argtypes = [vp, P(i64)]
         L.mgr_bsr3_spmv.argtypes = [P(Bsr3), vp, vp, vp, vp]
         L.mgr_bsr3_transpose.argtypes = [P(Bsr3), vp, vp, vp, vp]
         L.mgr_bsr3_outer_grad.argtypes = [P(Bsr3), vp, vp, vp, vp]
@@ -256,6 +257,13 @@ class MGR:
         if raise_on_fail and rc not in (0,):
             raise MgrError(rc, "fgmres_solve_transpose" if transpose else "fgmres_solve")
         return x, out
+
+    def audit(self) -> int:
+        """Number of out-of-range indices and out-of-order offsets in the hierarchy's apply operators
+        (0 for a sound setup); see mgr_audit."""
+        t = ctypes.c_int64()
+        _check(lib().mgr_audit(self._h, ctypes.byref(t)), "mgr_audit")
+        return t.value
 
     def levels(self):
         a, b = ctypes.c_int(), ctypes.c_int()

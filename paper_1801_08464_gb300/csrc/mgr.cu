@@ -1167,6 +1167,80 @@ mgr_status_t mgr_setup(mgr_handle_t h, const mgr_bsr3_t* A, const int8_t* cf_mar
   return guarded(h, [&] { do_setup(*h, *A, cf_marker); });
 }
 
+// ---- index audit -------------------------------------------------------------------------------
+__global__ void k_audit_sell32(int64_t nb, const int64_t* soff, const int32_t* col, unsigned long long* bad) {
+  const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (I >= nb) return;
+  const int64_t s = I / SELL_C;
+  const int t = (int)(I - s * SELL_C);
+  const int64_t b0 = soff[s], b1 = soff[s + 1];
+  unsigned long long nbad = b1 < b0;
+  for (int64_t j = b0; j < b1; ++j) {
+    const int32_t J = col[j * SELL_C + t];
+    nbad += (J < 0 || J >= nb);
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+__global__ void k_audit_list(int64_t n, const int32_t* a, int64_t hi, unsigned long long* bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n && (a[i] < 0 || a[i] >= hi)) atomicAdd(bad, 1ull);
+}
+// map[d] = c (a C point, c < nC) or -(f + 1) (an F point, f < nF)
+__global__ void k_audit_map(int64_t n, const int32_t* map, int64_t nF, int64_t nC, unsigned long long* bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t m = map[i];
+  if (m >= 0 ? m >= nC : (-m - 1) >= nF) atomicAdd(bad, 1ull);
+}
+
+static void audit_amg(Ctx& c, const std::vector<AmgLevel>& lv, unsigned long long* bad) {
+  for (const AmgLevel& G : lv) {
+    rowsop_audit(c, G.A32, bad); rowsop_audit(c, G.P32, bad); rowsop_audit(c, G.R32, bad);
+    rowsop_audit(c, G.A64, bad); rowsop_audit(c, G.P64, bad); rowsop_audit(c, G.R64, bad);
+    rowsop_audit(c, G.AT32, bad); rowsop_audit(c, G.AT64, bad);
+  }
+}
+
+static void audit_sell(Ctx& c, const SellPattern& S, unsigned long long* bad) {
+  if (S.nb <= 0 || !S.col.p) return;
+  k_audit_sell32<<<grid_for(S.nb, 256), 256, 0, c.s>>>(S.nb, S.soff.p, S.col.p, bad);
+  CU_LAUNCH();
+}
+
+mgr_status_t mgr_audit(mgr_handle_t h, int64_t* bad) {
+  if (!h || !bad) return MGR_ERR_INVALID_ARG;
+  if (!h->ready) return MGR_ERR_STATE;
+  return guarded(h, [&] {
+    Ctx& c = h->c;
+    DBuf<unsigned long long> cnt(c, 1);
+    CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), c.s));
+    audit_sell(c, h->sell, cnt.p);
+    if (h->has_t) audit_sell(c, h->sellT, cnt.p);
+    for (int l = 0; l < h->L; ++l) {
+      const MgrLevel& L = h->lev[l];
+      rowsop_audit(c, L.Aff32, cnt.p); rowsop_audit(c, L.Acf32, cnt.p); rowsop_audit(c, L.Wp32, cnt.p);
+      rowsop_audit(c, L.Aff64, cnt.p); rowsop_audit(c, L.Acf64, cnt.p); rowsop_audit(c, L.Wp64, cnt.p);
+      rowsop_audit(c, L.WpT32, cnt.p); rowsop_audit(c, L.AcfT32, cnt.p); rowsop_audit(c, L.AffT32, cnt.p);
+      rowsop_audit(c, L.WpT64, cnt.p); rowsop_audit(c, L.AcfT64, cnt.p); rowsop_audit(c, L.AffT64, cnt.p);
+      if (L.nF > 0 && L.F.p) {
+        k_audit_list<<<grid_for(L.nF, 256), 256, 0, c.s>>>(L.nF, L.F.p, L.n, cnt.p);
+        CU_LAUNCH();
+      }
+      if (L.nC > 0 && L.C.p) {
+        k_audit_list<<<grid_for(L.nC, 256), 256, 0, c.s>>>(L.nC, L.C.p, L.n, cnt.p);
+        CU_LAUNCH();
+      }
+      if (L.n > 0 && L.map.p) {
+        k_audit_map<<<grid_for(L.n, 256), 256, 0, c.s>>>(L.n, L.map.p, L.nF, L.nC, cnt.p);
+        CU_LAUNCH();
+      }
+      audit_amg(c, L.famg, cnt.p);
+    }
+    audit_amg(c, h->amg, cnt.p);
+    *bad = (int64_t)read_scalar(c, cnt.p);
+  });
+}
+
 mgr_status_t mgr_apply(mgr_handle_t h, const double* r, double* z) {
   if (!h || !r || !z) return MGR_ERR_INVALID_ARG;
   if (!h->ready) return MGR_ERR_STATE;

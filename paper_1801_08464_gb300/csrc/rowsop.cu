@@ -251,6 +251,77 @@ void rowsop_build(Ctx& c, const DCSR<double>& A, RowsOp<T>& op) {
   }
 }
 
+// ---- index audit ---------------------------------------------------------------------------------
+// Every column an apply kernel gathers with, recomputed from the stored form the way those kernels
+// compute it (32-bit column, slice base + 16-bit offset, row + table[code]), must lie in [0, nc); the
+// slice offsets and row pointers must not decrease and the row permutation must stay in [0, nr).
+// Each violation adds one to *bad.
+__global__ void k_audit_rows_sell(int64_t nr, int64_t nc, int q, const int64_t* soff, const int32_t* perm,
+                                  const int32_t* scol, const uint16_t* scol16, const int32_t* sbase,
+                                  const uint8_t* scode, const int64_t* coff, const int32_t* otab,
+                                  unsigned long long* bad) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  const int64_t s = r / RS_C;
+  const int t = (int)(r - s * RS_C);
+  const int64_t b0 = soff[s], w = soff[s + 1] - b0;
+  unsigned long long nbad = 0;
+  const int64_t row = perm ? (int64_t)perm[r] : r;
+  if (w < 0 || row < 0 || row >= nr) {
+    atomicAdd(bad, 1ull);
+    return;
+  }
+  if (scode) {
+    const int64_t cb = coff[s] * RS_C, cw = coff[s + 1] - coff[s];
+    if (cw < w) ++nbad;
+    for (int64_t j = 0; j < cw; ++j) {
+      const int64_t col = row + otab[scode[cb + rs_code_pos(j, t)]];
+      nbad += (col < 0 || col >= nc);
+    }
+  } else {
+    for (int64_t j = 0; j < w; ++j) {
+      const int64_t o = b0 * RS_C + (j / q) * (q * RS_C) + t * q + (j % q);
+      const int64_t col = scol16 ? (int64_t)sbase[s] + scol16[o] : (int64_t)scol[o];
+      nbad += (col < 0 || col >= nc);
+    }
+  }
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+template <class TI>
+__global__ void k_audit_csr(int64_t nr, int64_t nc, int64_t nnz, const int64_t* rp, const TI* ci,
+                            unsigned long long* bad) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  const int64_t a = rp[r], b = rp[r + 1];
+  if (a < 0 || a > b || b > nnz || (r == 0 && a != 0) || (r == nr - 1 && b != nnz)) {
+    atomicAdd(bad, 1ull);
+    return;
+  }
+  unsigned long long nbad = 0;
+  for (int64_t k = a; k < b; ++k) nbad += (ci[k] < 0 || (int64_t)ci[k] >= nc);
+  if (nbad) atomicAdd(bad, nbad);
+}
+
+template <class T>
+void rowsop_audit(Ctx& c, const RowsOp<T>& op, unsigned long long* bad) {
+  if (op.nr <= 0) return;
+  if (op.sell) {
+    k_audit_rows_sell<<<grid_for(op.nr, 256), 256, 0, c.s>>>(
+        op.nr, op.nc, op.q, op.soff.p, op.perm.p, (op.c8 || op.c16) ? nullptr : op.scol.p,
+        op.c16 ? op.scol16.p : nullptr, op.c16 ? op.sbase.p : nullptr, op.c8 ? op.scode.p : nullptr, op.coff.p,
+        op.otab.p, bad);
+    CU_LAUNCH();
+  } else if (op.csr.rp.p) {
+    k_audit_csr<int32_t><<<grid_for(op.nr, 256), 256, 0, c.s>>>(op.nr, op.nc, op.csr.nnz, op.csr.rp.p, op.csr.ci.p,
+                                                                bad);
+    CU_LAUNCH();
+  }
+}
+
+template void rowsop_audit<float>(Ctx&, const RowsOp<float>&, unsigned long long*);
+template void rowsop_audit<double>(Ctx&, const RowsOp<double>&, unsigned long long*);
+
 template void rowsop_build<float>(Ctx&, const DCSR<double>&, RowsOp<float>&);
 template void rowsop_build<double>(Ctx&, const DCSR<double>&, RowsOp<double>&);
 

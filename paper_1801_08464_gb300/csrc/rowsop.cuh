@@ -88,4 +88,9 @@ void rowsop_rehome(RowsOp<T>& op, Ctx& c) {
 template <class T>
 void rowsop_build(Ctx& c, const DCSR<double>& A, RowsOp<T>& op);
 
+// Adds to *bad (device) the number of stored column indices, recomputed as the apply kernels do,
+// that fall outside [0, nc), and of offsets, pointers or row permutations out of order or range.
+template <class T>
+void rowsop_audit(Ctx& c, const RowsOp<T>& op, unsigned long long* bad);
+
 }  // namespace mgr

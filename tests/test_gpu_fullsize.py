@@ -61,6 +61,8 @@ def test_128cube_mixed_properties():
     A, mk = to_gpu(p)
     m = mg.MGR(precision="mixed", **BENCH_SOLVER)
     m.setup(A, mk)
+    # every index the apply gathers with is in range, in the sliced layouts of the benchmark's hierarchy
+    assert m.audit() == 0
     N, M = p.nb, int(p.gas_present.sum())
     sizes = [m.matrix(mg.MAT_LEVEL, l)[3][0] for l in range(4)]
     assert sizes == [3 * N, 3 * N - M, 2 * N - M, N]

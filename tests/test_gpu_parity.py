@@ -124,6 +124,29 @@ def test_fgmres_parity_fp64(name, optname):
     m.close()
 
 
+def test_fgmres_longest_restart():
+    """FGMRES(32), the longest restart the library takes: the multi-dot and the Gram-Schmidt update
+    then run with every vector count from 1 to 32 (one kernel instantiation each).  Without the
+    global relaxation the 16^3 case needs more than one full cycle (the oracle: 59 iterations to
+    1e-8), so the last instantiations run too.  Iterations within 2 of the oracle's (two restart
+    cycles), residual <= 1e-8, tight FP64 solutions within 1e-10 of the oracle's."""
+    import torch
+    p = ncpgen.make_problem(PARITY["ncp3d_16"])
+    A, mk, m, o = _pair(p, global_relax=0)
+    b = ncpgen.normals(p.n, 2)
+    bt = torch.as_tensor(b, device="cuda")
+    x, info = m.fgmres(A, bt, rtol=1e-8, restart=32)
+    xo, io = o.fgmres(b, rtol=1e-8, restart=32)
+    assert io["iterations"] > 32
+    assert info["converged"]
+    assert np.linalg.norm(b - p.to_scipy() @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
+    assert abs(info["iterations"] - io["iterations"]) <= 2, (info["iterations"], io["iterations"])
+    x2, _ = m.fgmres(A, bt, rtol=1e-12, restart=32, maxit=3000)
+    xo2, _ = o.fgmres(b, rtol=1e-12, restart=32, maxit=3000)
+    assert rel(x2.cpu().numpy(), xo2) <= 1e-10
+    m.close()
+
+
 def test_mixed_precision_iterations_and_error():
     """FP32 hierarchy with FP64 Krylov: the same 1e-8 residual at <= 1.2x the FP64 oracle's
     iterations (and the GPU's own FP64-hierarchy count); the errors of both GPU solutions against the
