@@ -695,65 +695,6 @@ void launch_scale(Ctx& c, int64_t n, const T* d, const T* b, T* x) {
   launch_pdl(c, k_scale_vec<T>, grid_for(n, 256), 256, 0, n, d, b, x);
   CU_LAUNCH();
 }
-// The first smoothing sweep of a V-cycle from a zero guess (x = d b) folded into its residual
-// res = b - A x, for the small CSR levels where each launch costs more than its data: every gathered
-// x_j is formed as d_j * b_j, rounded exactly as the scaling pass rounds it, so x and res are those
-// of the two passes bit for bit.
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-template <class T, int TPR>
-__global__ void __launch_bounds__(256) k_rows_scaled_resid(int64_t nr, const int64_t* __restrict__ rp,
-                                                           const int32_t* __restrict__ ci, const T* __restrict__ v,
-                                                           const T* __restrict__ d, const T* __restrict__ b,
-                                                           T* __restrict__ x, T* __restrict__ res) {
-  pdl_wait();
-  int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t r = gt / TPR;
-  int sub = (int)(gt % TPR);
-  bool ok = r < nr;
-  T s = 0, bi = 0, di = 0;
-  if (ok && sub == 0) {
-    bi = b[r];
-    di = d[r];
-  }
-  if (ok) {
-    int64_t k1 = rp[r + 1];
-    for (int64_t k = rp[r] + sub; k < k1; k += TPR) {
-      const int32_t j = ci[k];
-      const T xj = mul_rn(ldg(d + j), ldg(b + j));
-      s += v[k] * xj;
-    }
-  }
-#pragma unroll
-  for (int o = TPR / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, TPR);
-  if (ok && sub == 0) {
-    x[r] = mul_rn(di, bi);
-    res[r] = bi - s;
-  }
-}
-
-template <class T>
-bool launch_scaled_resid(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, T* x, T* res, const char* name) {
-  if (A.sell || A.nr <= 0 || A.nr > SCALED_RESID_MAX_ROWS) return false;
-  const DCSR<T>& M = A.csr;
-  ProfScope ps(c, name, (double)M.nnz * (sizeof(T) + 4) + 8.0 * (M.nr + 1) + 2.0 * M.nc * sizeof(T) +
-                            3.0 * M.nr * sizeof(T));
-  const double avg = M.nr ? (double)M.nnz / (double)M.nr : 0.0;
-  const int B = 256;
-  if (avg <= 5.0)
-    launch_pdl(c, k_rows_scaled_resid<T, 2>, grid_for(M.nr * 2, B), B, 0, M.nr, M.rp, M.ci, M.v, d, b, x, res);
-  else if (avg <= 12.0)
-    launch_pdl(c, k_rows_scaled_resid<T, 4>, grid_for(M.nr * 4, B), B, 0, M.nr, M.rp, M.ci, M.v, d, b, x, res);
-  else if (avg <= 24.0)
-    launch_pdl(c, k_rows_scaled_resid<T, 8>, grid_for(M.nr * 8, B), B, 0, M.nr, M.rp, M.ci, M.v, d, b, x, res);
-  else if (avg <= 128.0)
-    launch_pdl(c, k_rows_scaled_resid<T, 16>, grid_for(M.nr * 16, B), B, 0, M.nr, M.rp, M.ci, M.v, d, b, x, res);
-  else
-    launch_pdl(c, k_rows_scaled_resid<T, 32>, grid_for(M.nr * 32, B), B, 0, M.nr, M.rp, M.ci, M.v, d, b, x, res);
-  CU_LAUNCH();
-  return true;
-}
-
 template <class T>
 void launch_resid(Ctx& c, const RowsOp<T>& A, const T* x, const T* b, T* res, const char* name) {
   run_rows(c, A, x, EpiResid<T>{b, res}, name);
@@ -815,7 +756,6 @@ void launch_cast_f32(Ctx& c, int64_t n, const double* a, float* b) {
   template void launch_to_f64<T>(Ctx&, int64_t, const T*, double*);                                                \
   template void launch_scale<T>(Ctx&, int64_t, const T*, const T*, T*);                                            \
   template void launch_resid<T>(Ctx&, const RowsOp<T>&, const T*, const T*, T*, const char*);                     \
-  template bool launch_scaled_resid<T>(Ctx&, const RowsOp<T>&, const T*, const T*, T*, T*, const char*);          \
   template void launch_jacobi<T>(Ctx&, const RowsOp<T>&, const T*, const T*, const T*, T*, const char*);          \
   template void launch_spmv<T>(Ctx&, const RowsOp<T>&, const T*, T*, const char*);                                \
   template void launch_prolong_add<T>(Ctx&, const RowsOp<T>&, const T*, T*, const char*);                         \

@@ -72,12 +72,6 @@ void launch_scale(Ctx& c, int64_t n, const T* d, const T* b, T* x);             
 template <class T>
 void launch_resid(Ctx& c, const RowsOp<T>& A, const T* x, const T* b, T* res,
                   const char* name = "csr_rows");                                           // res = b - A x
-// x = d b and res = b - A x in one launch, for CSR operators of at most SCALED_RESID_MAX_ROWS rows;
-// returns false (nothing launched) for the others
-constexpr int64_t SCALED_RESID_MAX_ROWS = 65536;
-template <class T>
-bool launch_scaled_resid(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, T* x, T* res,
-                         const char* name = "csr_rows");
 template <class T>
 void launch_jacobi(Ctx& c, const RowsOp<T>& A, const T* d, const T* b, const T* xi, T* xo,
                    const char* name = "csr_rows");                                          // xo = xi + d (b - A xi)

@@ -210,15 +210,12 @@ const T* vcycle(mgr_handle_s& h, const AmgRef& g, int k, const T* b, bool transp
   T* xb = P<T>((*g.xb)[k]);
   T* res = P<T>((*g.res)[k]);
   const char* nm = g.coarse ? lvl_name(kAmgRows, 4, k) : "famg_rows";
-  // one pre-smoothing sweep on a small CSR level: the sweep from zero and the residual in one launch
-  if (!(npre == 1 && launch_scaled_resid<T>(c, Av, d, b, xa, res, nm))) {
-    launch_scale<T>(c, A.n, d, b, xa);
-    for (int s = 1; s < npre; ++s) {
-      launch_jacobi<T>(c, Av, d, b, xa, xb, nm);
-      std::swap(xa, xb);
-    }
-    launch_resid<T>(c, Av, xa, b, res, nm);
+  launch_scale<T>(c, A.n, d, b, xa);
+  for (int s = 1; s < npre; ++s) {
+    launch_jacobi<T>(c, Av, d, b, xa, xb, nm);
+    std::swap(xa, xb);
   }
+  launch_resid<T>(c, Av, xa, b, res, nm);
   T* bc = P<T>((*g.b)[k + 1]);
   launch_spmv<T>(c, tv<T>(A.R64, A.R32), res, bc, g.coarse ? lvl_name(kAmgRestrict, 3, k) : "famg_transfer");
   const T* xc = vcycle<T>(h, g, k + 1, bc, transposed);
