@@ -23,6 +23,9 @@
  * (De Sterck, Yang & Heys 2006), extended+i interpolation (De Sterck, Falgout, Nolting & Yang 2008),
  * l1-Jacobi smoothing (Baker, Falgout, Kolev & Yang 2011), flexible GMRES (Saad 1993).
  * Readings where the paper is silent are stated at each function.
+ * Parity unpinned: the PMIS tie rule between exactly equal weights (the larger index wins).  The
+ * weights carry 53 random bits, so ties do not occur in any output a test can observe; every other
+ * part is pinned by the CPU tests against closed forms, dense solves and brute force.
  *
  * Sparse matrices are CSR with int64 row pointers, int32 columns sorted ascending, FP64 values.
  */
